@@ -1,0 +1,191 @@
+/*
+ * fft3.h -- C ABI of libfft3: batched forward and inverse 3D complex DFTs on
+ * one GB300 (sm_103a), computed as passes of batched 1D DFTs along each
+ * dimension with the data redistributions between passes fused into the
+ * passes' loads and stores.
+ *
+ * The operations follow Popovici, Schatz, Franchetti, Low, "A Flexible
+ * Framework for Parallel Multi-Dimensional DFTs":
+ *   - Section 2.1: y = DFT_n x with DFT_n = [w_n^{lk}], w_n = exp(-2 pi i / n)
+ *     for the forward transform (the printed exponent is garbled and is read
+ *     with the imaginary unit); the inverse uses exp(+2 pi i / n) and is
+ *     unnormalised, so inverse(forward(x)) = n0*n1*n2 * x.
+ *   - Section 2.3: an n0 x n1 x n2 array is stored column major with n0
+ *     fastest; element (j0, j1, j2) of batch entry b is at complex offset
+ *     j0 + n0*(j1 + n1*(j2 + n2*b)).  In PyTorch terms a contiguous complex64
+ *     tensor of shape (batch, n2, n1, n0).
+ *   - Sections 2.3 and 2.4: the slab-pencil and pencil-pencil-pencil
+ *     decompositions; Section 3.2 and Fig. cuboid: the volumetric
+ *     decomposition, where each 1D DFT is itself split Cooley-Tukey style
+ *     (n = a*b, Eq. ct) over a group of p cooperating thread blocks holding the
+ *     line in elemental-cyclic order.
+ *
+ * Data: complex64, interleaved (re, im) float32, 8 bytes per element.
+ * Device pointers must be 16-byte aligned (cudaMalloc / torch allocations are).
+ *
+ * Errors: every entry point returns FFT3_OK (0) or a negative FFT3_ERR_*
+ * code; fft3_last_error() then holds a message for the calling thread.  The
+ * library never aborts or exits the process.
+ *
+ * Threading: plans are independent objects; one plan must not execute on two
+ * streams at once (its workspace and counters are shared).
+ */
+#ifndef FFT3_H
+#define FFT3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft3_plan_s *fft3_plan; /* opaque; owned by the library */
+
+/* arithmetic of the line transforms; storage is always complex64 */
+enum fft3_dtype {
+    FFT3_C64_FP32 = 0,         /* FP32 CUDA-core butterflies */
+    FFT3_C64_SPLITBF16_TC = 1  /* radix-16 sub-DFTs as split-BF16 tensor-core GEMMs, FP32 accumulate */
+};
+
+enum fft3_decomp {
+    FFT3_SLAB_PENCIL = 0, /* 2D DFT on n0 x n1 slabs, then DFT_{n2} (Section 2.3, Fig. 3ddftopt a) */
+    FFT3_PENCIL3 = 1,     /* DFT_{n0}, DFT_{n1}, DFT_{n2} (Section 2.3, Fig. 3ddftopt b) */
+    FFT3_VOLUMETRIC = 2,  /* every 1D DFT split over p cooperating blocks (Section 3.2) */
+    FFT3_AUTO = 3         /* the planner's choice (cost model, else a fixed default) */
+};
+
+enum fft3_direction { FFT3_FORWARD = -1, FFT3_INVERSE = +1 }; /* sign of the exponent */
+
+enum fft3_status {
+    FFT3_OK = 0,
+    FFT3_ERR_INVALID_ARG = -1,         /* null pointer, non-positive size, bad enum */
+    FFT3_ERR_UNSUPPORTED_SIZE = -2,    /* prime factor > 5, line too long, infeasible split */
+    FFT3_ERR_OOM = -3,                 /* device or host allocation failed */
+    FFT3_ERR_CUDA = -4,                /* CUDA runtime error; message in fft3_last_error() */
+    FFT3_ERR_TIMEOUT = -5,             /* a bounded device-side wait expired */
+    FFT3_ERR_INPLACE_UNSUPPORTED = -6, /* in == out */
+    FFT3_ERR_NO_DEVICE = -7            /* no CUDA device visible */
+};
+
+/* Pencil-pencil-pencil variants (options.variant). */
+enum fft3_ppp_variant {
+    FFT3_PPP_NATURAL = 0, /* x pass out-of-place, y and z passes in place on strided lines */
+    FFT3_PPP_ROTATE = 1   /* each pass stores its result rotated xyz -> yzx -> zxy -> xyz (Section 2.4) */
+};
+
+/* Optional planner controls.  Zero-initialise and set what you need. */
+typedef struct fft3_options {
+    int variant;      /* fft3_ppp_variant for FFT3_PENCIL3 */
+    int radix_order;  /* index into the candidate radix orders of each line length (0 = default) */
+    int tile_lines;   /* lines per tile of a strided pass, 8 or 16 (0 = default 16) */
+    int mesh[3];      /* volumetric: blocks cooperating on one line of dim d, 1/2/4/8 (0 = auto) */
+    int slab_mode;    /* slab-pencil: 0 = auto, 1 = one block per slab in shared memory,
+                         2 = L2-resident x/y stages in one persistent launch,
+                         3 = x and y passes as two launches */
+    int reserved[8];  /* test hooks of the failure-detection tests, 0 in normal use:
+                         [0] = s + 1 makes the x tiles of slab s never signal their
+                         completion, so the waits of its y tiles expire;
+                         [1] = bound of each device-side wait, in thousands of clock
+                         cycles (0 = about two seconds) */
+} fft3_options;
+
+/* Create a plan for `batch` transforms of n0 x n1 x n2 (n0 fastest).
+ * dtype: fft3_dtype; decomposition: fft3_decomp; direction: fft3_direction.
+ * Allocates the plan's device twiddle tables (computed in FP64 on the GPU,
+ * rounded to float32) and any workspace on the current device.
+ * Returns FFT3_ERR_UNSUPPORTED_SIZE for sizes with a prime factor > 5 or
+ * line lengths above 4096, and for volumetric meshes that do not divide the
+ * Cooley-Tukey split (p | a and p | b, Section 3.2). */
+int fft3_plan_create(fft3_plan *out, int n0, int n1, int n2, int batch, int dtype,
+                     int decomposition, int direction);
+
+/* As fft3_plan_create, with planner controls (opts may be NULL). */
+int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int dtype,
+                        int decomposition, int direction, const fft3_options *opts);
+
+/* Batched uneven transforms: `count` independent 3D DFTs, problem i of size
+ * dims[3i] x dims[3i+1] x dims[3i+2] (first fastest) starting at complex
+ * offset offsets[i] of both the input and output buffers, executed by one
+ * persistent launch (captured once in a CUDA graph).  Line lengths <= 128.
+ * decomposition: FFT3_SLAB_PENCIL, FFT3_PENCIL3 or FFT3_AUTO (per size class).
+ * `tuning` may be NULL or point to `count` ints of per-problem tile hints
+ * (0 = default). */
+int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets,
+                          int dtype, int decomposition, int direction, const int *tuning);
+
+/* Execute on `stream` (a cudaStream_t, NULL = legacy default stream).
+ * in, out: device pointers to batch*n0*n1*n2 complex64 values (or the
+ * extent covered by the offsets of a batched plan).  `in` is not modified.
+ * Asynchronous and stream ordered.  in == out returns
+ * FFT3_ERR_INPLACE_UNSUPPORTED. */
+int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream);
+
+/* Execute from and to HOST memory: copies `h_in` to plan-owned device
+ * buffers, transforms, copies the result to `h_out`, then synchronises
+ * `stream`.  Pinned host memory gives full copy bandwidth.  The device
+ * staging buffers are allocated on the first call and kept by the plan. */
+int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *stream);
+
+/* Reads and clears the plan's device error flag (set when a bounded wait in a
+ * persistent kernel expired).  Synchronises the plan's last stream. */
+int fft3_plan_check(fft3_plan p);
+
+int fft3_plan_destroy(fft3_plan p);
+
+/* Device bytes the plan owns besides its twiddle tables (workspace). */
+size_t fft3_plan_workspace_bytes(fft3_plan p);
+
+/* Number of kernel launches one fft3_plan_execute issues. */
+int fft3_plan_launches(fft3_plan p);
+
+/* JSON description of the pass schedule (decomposition, passes, kernels,
+ * line lengths, radix lists, layouts, bytes moved).  Returns the length
+ * needed (excluding the terminator), or a negative error. */
+int fft3_plan_describe(fft3_plan p, char *buf, size_t len);
+
+/* Host-only planning, no device needed: the JSON schedule that
+ * fft3_plan_create_ex would build.  Same return convention as describe. */
+int fft3_plan_schedule(int n0, int n1, int n2, int batch, int dtype, int decomposition,
+                       int direction, const fft3_options *opts, char *buf, size_t len);
+
+/* Host-only: the radix list the planner uses for a line of length n under
+ * radix_order `order`; returns the number of stages (<= cap) or a negative
+ * error (FFT3_ERR_UNSUPPORTED_SIZE for a prime factor > 5). */
+int fft3_factorize(int n, int order, int *radices, int cap);
+
+/* FP64 GPU twiddle generator (Section 2.1, twiddle matrix w_n^{kl}): for each
+ * of `count` integer exponents m[i] (device int64 array) writes
+ * w_n^{m[i]} = exp(sign*2 pi i m[i]/n), with m reduced mod n in integers, as
+ * doubles to d_out64 (2*count, may be NULL) and rounded to float32 to
+ * d_out32 (2*count, may be NULL).  Device pointers; asynchronous on stream. */
+int fft3_twiddles(int n, int sign, const int64_t *d_m, int64_t count, double *d_out64,
+                  float *d_out32, void *stream);
+
+/* Layout probe: runs the first `npasses` passes of the plan's schedule (all of
+ * them when npasses < 0) with every line transform replaced by the identity,
+ * so the composed load/store maps (the redistributions) can be compared
+ * bit-exactly with their definitions.  Carry integer source indices in the
+ * float32 pairs.  The result always lands in `out` (a pass that ends in the
+ * plan's workspace is followed by a copy to `out`). */
+int fft3_plan_probe_layout(fft3_plan p, const void *in, void *out, int npasses, void *stream);
+
+/* Executes pass `k` (0-based) of the schedule alone, on the same buffers as
+ * fft3_plan_execute: used to time passes one by one with events.  The
+ * transform is only complete after passes 0 .. launches-1 ran in order. */
+int fft3_plan_execute_pass(fft3_plan p, int k, const void *in, void *out, void *stream);
+
+/* Split-BF16 helper used by the tensor-core path, exposed for tests:
+ * hi[i] = bf16(x[i]), lo[i] = bf16(x[i] - hi[i]) (round to nearest even),
+ * written as raw uint16 bit patterns.  Device pointers. */
+int fft3_split_bf16(const float *d_x, int64_t count, uint16_t *d_hi, uint16_t *d_lo,
+                    void *stream);
+
+const char *fft3_last_error(void);
+int fft3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFT3_H */

@@ -419,3 +419,25 @@ def adam_step(params, grads, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=
         new_m.append(mi)
         new_v.append(vi)
     return new_p, new_m, new_v
+
+
+def dft3_sampled(x, n0: int, n1: int, n2: int, k0s, k1s, k2s, sign: int = FORWARD,
+                 chunk_rows: int = 1 << 16) -> np.ndarray:
+    """Selected outputs X[k0, k1, k2] (for k0 in k0s, k1 in k1s, k2 in k2s) of
+    the 3D DFT of one (n2, n1, n0) array, by the separable definition of
+    Section 2.3 restricted to those frequencies: a product with the selected
+    columns of DFT_{n0}, then of DFT_{n1}, then of DFT_{n2}.  Cost is one
+    sweep over x, so it serves arrays far too large for ``fft3``.
+    Returns an array of shape (len(k0s), len(k1s), len(k2s))."""
+    k0s, k1s, k2s = (np.asarray(k, dtype=np.int64) for k in (k0s, k1s, k2s))
+    F0 = roots(n0, np.outer(np.arange(n0), k0s) % n0, sign).reshape(n0, k0s.size)
+    F1 = roots(n1, np.outer(np.arange(n1), k1s) % n1, sign).reshape(n1, k1s.size)
+    F2 = roots(n2, np.outer(np.arange(n2), k2s) % n2, sign).reshape(n2, k2s.size)
+    rows = np.asarray(x).reshape(n2 * n1, n0)
+    A = np.empty((n2 * n1, k0s.size), dtype=np.complex128)
+    for s in range(0, n2 * n1, chunk_rows):
+        e = min(n2 * n1, s + chunk_rows)
+        A[s:e] = rows[s:e].astype(np.complex128) @ F0
+    A = A.reshape(n2, n1, k0s.size)
+    B = np.einsum("zyk,yl->zkl", A, F1)
+    return np.einsum("zkl,zm->klm", B, F2)

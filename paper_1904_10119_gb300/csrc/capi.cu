@@ -1,0 +1,638 @@
+// capi.cu -- the C ABI of libfft3 (include/fft3.h): plan objects, twiddle
+// generation at plan time, and the launch of each pass of a schedule.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fft3.h"
+#include "geom.h"
+#include "planner.h"
+#include "plans.h"
+
+namespace fft3 {
+__global__ void k_pass_g(PassArgs a);
+__global__ void k_slab(PassArgs a);
+__global__ void k_vol(PassArgs a);
+__global__ void k_probe_pass(PassArgs a);
+__global__ void k_copy(const float2 *in, float2 *out, int64_t total);
+__global__ void k_roots(int n, int sign, const int64_t *m, int64_t count, double *o64, float2 *o32);
+__global__ void k_split_bf16(const float *x, int64_t count, uint16_t *hi, uint16_t *lo);
+extern const FixedKernels g_fixed_kernels_a[];
+extern const int g_fixed_kernels_a_count;
+extern const FixedKernels g_fixed_kernels_b[];
+extern const int g_fixed_kernels_b_count;
+
+const FixedKernels *fixed_kernels(int id)
+{
+    for (int i = 0; i < g_fixed_kernels_a_count; ++i)
+        if (g_fixed_kernels_a[i].id == id)
+            return &g_fixed_kernels_a[i];
+    for (int i = 0; i < g_fixed_kernels_b_count; ++i)
+        if (g_fixed_kernels_b[i].id == id)
+            return &g_fixed_kernels_b[i];
+    return nullptr;
+}
+} // namespace fft3
+
+using namespace fft3;
+
+// ------------------------------------------------------------- errors ---- //
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(x)                                                                                \
+    do {                                                                                           \
+        cudaError_t e_ = (x);                                                                      \
+        if (e_ != cudaSuccess) {                                                                   \
+            cudaGetLastError();                                                                    \
+            return fail(e_ == cudaErrorMemoryAllocation ? FFT3_ERR_OOM : FFT3_ERR_CUDA,            \
+                        std::string(#x) + ": " + cudaGetErrorString(e_));                          \
+        }                                                                                          \
+    } while (0)
+
+// ------------------------------------------------------------- plans ----- //
+struct Launch {
+    const void *func = nullptr;
+    dim3 grid, block;
+    int smem = 0;
+    int cluster = 1;
+    int kind = 0;
+    PassArgs args{};
+    int src = BUF_IN, dst = BUF_OUT;
+    bool reset_counters = false;
+    // identity probe of the same pass geometry
+    PassGeom probe_g{};
+    int probe_n = 1;
+};
+
+struct fft3_plan_s {
+    Schedule sched;
+    int device = 0;
+    int64_t elems = 0; // complex elements per array
+    float2 *d_tw = nullptr;
+    float2 *d_ws = nullptr;
+    size_t ws_bytes = 0;
+    int *d_counters = nullptr;
+    size_t counters_bytes = 0;
+    unsigned *d_err = nullptr;
+    std::vector<Launch> launches;
+    float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
+    cudaStream_t last_stream = nullptr;
+};
+
+static int device_sms(int dev)
+{
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+static int prepare_func(const void *func, int smem)
+{
+    if (smem > 48 * 1024)
+        CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return FFT3_OK;
+}
+
+static int occupancy_grid(const void *func, int threads, int smem, int64_t ntiles, int dev, dim3 *grid)
+{
+    int nb = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, smem));
+    if (nb < 1)
+        return fail(FFT3_ERR_UNSUPPORTED_SIZE, "kernel does not fit on an SM with this launch shape");
+    int64_t g = (int64_t)nb * device_sms(dev);
+    if (ntiles > 0)
+        g = std::min<int64_t>(g, ntiles);
+    grid->x = (unsigned)std::max<int64_t>(1, g);
+    grid->y = grid->z = 1;
+    return FFT3_OK;
+}
+
+static LineRt to_rt(const LineChoice &l, int tw_off)
+{
+    LineRt r{};
+    r.n = l.n;
+    r.T = l.T;
+    r.nst = l.nst;
+    r.tw_off = tw_off;
+    for (int i = 0; i < kMaxStages; ++i)
+        r.rad[i] = l.rad[i];
+    return r;
+}
+
+static PassGeom natural_x(const Schedule &s)
+{
+    PassGeom g{};
+    int64_t N = (int64_t)s.n0 * s.n1 * s.n2;
+    g.C = s.n1; g.A = s.n2; g.B = s.batch;
+    g.ij = 1; g.ic = s.n0; g.ia = (int64_t)s.n0 * s.n1; g.ib = N;
+    g.ok = g.ij; g.oc = g.ic; g.oa = g.ia; g.ob = g.ib;
+    return g;
+}
+
+static int build_launches(fft3_plan_s *P)
+{
+    const Schedule &s = P->sched;
+    const int conj = s.direction == FFT3_INVERSE ? 1 : 0;
+    for (const PassPlan &p : s.passes) {
+        Launch L;
+        L.kind = p.kind;
+        L.src = p.src;
+        L.dst = p.dst;
+        PassArgs &a = L.args;
+        a.g = p.g;
+        a.conj = conj;
+        a.ntiles = p.ntiles;
+        a.tiles_c = p.tiles_c;
+        a.lpt = p.lpt;
+        a.err = P->d_err;
+        // test hooks (options.reserved[0] = slab whose x tiles never signal, plus one;
+        // options.reserved[1] = wait budget in thousands of cycles)
+        a.nosignal_slab = s.opts.reserved[0] > 0 ? (int64_t)s.opts.reserved[0] - 1 : -1;
+        a.wait_budget = s.opts.reserved[1] > 0 ? (long long)s.opts.reserved[1] * 1000LL : 4000000000LL;
+        int64_t base = -1, end = 0;
+        for (int k = 0; k < 3; ++k) {
+            if (p.tw_seg[k] < 0)
+                continue;
+            const TwSeg &sg = s.tw[p.tw_seg[k]];
+            if (base < 0)
+                base = sg.off;
+            end = sg.off + ((int64_t)sg.m.size() + 15) / 16 * 16;
+        }
+        if (base < 0)
+            base = 0;
+        a.tw = P->d_tw + base;
+        a.tw_len = (int)(end - base);
+        if (p.tw_seg[0] >= 0)
+            a.L[0] = to_rt(p.line, (int)(s.tw[p.tw_seg[0]].off - base));
+        if (p.tw_seg[1] >= 0)
+            a.L[1] = to_rt(p.line2, (int)(s.tw[p.tw_seg[1]].off - base));
+        if (p.tw_seg[2] >= 0)
+            a.tw_split_off = (int)(s.tw[p.tw_seg[2]].off - base);
+        a.p = p.p;
+        a.split_a = p.split_a;
+        a.split_b = p.split_b;
+        L.probe_g = p.g;
+        L.probe_n = p.line.n;
+        L.smem = p.smem_bytes;
+        L.block = dim3(std::max(1, p.threads));
+        const FixedKernels *fk = p.line.fixed >= 0 ? fixed_kernels(p.line.fixed) : nullptr;
+        switch (p.kind) {
+        case PK_J: L.func = fk ? fk->j : nullptr; break;
+        case PK_JROT: L.func = fk ? fk->jrot : nullptr; break;
+        case PK_C: L.func = fk ? (p.lpt == 16 ? fk->c16 : fk->c8) : nullptr; break;
+        case PK_G: L.func = (const void *)&k_pass_g; break;
+        case PK_SLAB:
+            L.func = (const void *)&k_slab;
+            L.probe_g = natural_x(s);
+            L.probe_n = s.n0;
+            break;
+        case PK_SLABL2:
+            L.func = fk ? fk->l2 : nullptr;
+            L.reset_counters = true;
+            L.probe_g = natural_x(s);
+            L.probe_n = s.n0;
+            break;
+        case PK_VOL:
+            L.func = (const void *)&k_vol;
+            L.cluster = p.p;
+            L.probe_n = p.split_a * p.split_b;
+            break;
+        case PK_COPY:
+            L.func = (const void *)&k_copy;
+            L.probe_n = 1;
+            break;
+        default: break;
+        }
+        if (!L.func)
+            return fail(FFT3_ERR_UNSUPPORTED_SIZE, "no compiled kernel for this pass");
+        int rc = prepare_func(L.func, L.smem);
+        if (rc)
+            return rc;
+        if (p.kind == PK_VOL) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = p.p;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(p.p * 4);
+            cfg.blockDim = L.block;
+            cfg.dynamicSmemBytes = L.smem;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int ncl = 0;
+            CUDA_TRY(cudaOccupancyMaxActiveClusters(&ncl, (const void *)&k_vol, &cfg));
+            if (ncl < 1)
+                return fail(FFT3_ERR_UNSUPPORTED_SIZE, "volumetric cluster does not fit on the GPU");
+            int64_t g = std::min<int64_t>(ncl, p.ntiles);
+            L.grid = dim3((unsigned)(std::max<int64_t>(1, g) * p.p));
+        } else if (p.kind == PK_COPY) {
+            L.grid = dim3((unsigned)std::min<int64_t>(4096, (P->elems + 255) / 256 + 1));
+            L.block = dim3(256);
+        } else if (p.kind == PK_SLABL2) {
+            rc = occupancy_grid(L.func, L.block.x, L.smem, 0, P->device, &L.grid);
+            if (rc)
+                return rc;
+            P->counters_bytes = std::max(P->counters_bytes,
+                                         (size_t)(1 + p.g.A * p.g.B) * sizeof(int));
+        } else {
+            rc = occupancy_grid(L.func, L.block.x, L.smem, p.ntiles, P->device, &L.grid);
+            if (rc)
+                return rc;
+        }
+        P->launches.push_back(L);
+    }
+    return FFT3_OK;
+}
+
+static void free_plan(fft3_plan_s *P)
+{
+    if (!P)
+        return;
+    cudaFree(P->d_tw);
+    cudaFree(P->d_ws);
+    cudaFree(P->d_counters);
+    cudaFree(P->d_err);
+    cudaFree(P->d_stage_in);
+    cudaFree(P->d_stage_out);
+    delete P;
+}
+
+static int generate_twiddles(fft3_plan_s *P)
+{
+    const Schedule &s = P->sched;
+    int64_t total = std::max<int64_t>(16, s.tw_total);
+    CUDA_TRY(cudaMalloc(&P->d_tw, total * sizeof(float2)));
+    CUDA_TRY(cudaMemset(P->d_tw, 0, total * sizeof(float2)));
+    size_t maxm = 1;
+    for (const TwSeg &sg : s.tw)
+        maxm = std::max(maxm, sg.m.size());
+    int64_t *d_m = nullptr;
+    CUDA_TRY(cudaMalloc(&d_m, maxm * sizeof(int64_t)));
+    for (const TwSeg &sg : s.tw) {
+        cudaError_t e = cudaMemcpy(d_m, sg.m.data(), sg.m.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            int blocks = (int)std::min<int64_t>(1024, ((int64_t)sg.m.size() + 255) / 256);
+            k_roots<<<std::max(1, blocks), 256>>>(sg.n, FFT3_FORWARD, d_m, (int64_t)sg.m.size(), nullptr,
+                                                  P->d_tw + sg.off);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaFree(d_m);
+            return fail(FFT3_ERR_CUDA, std::string("twiddle generation: ") + cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(d_m);
+    if (e != cudaSuccess)
+        return fail(FFT3_ERR_CUDA, std::string("twiddle generation: ") + cudaGetErrorString(e));
+    return FFT3_OK;
+}
+
+static int check_device(int *dev)
+{
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return fail(FFT3_ERR_NO_DEVICE, "no CUDA device visible");
+    }
+    CUDA_TRY(cudaGetDevice(dev));
+    return FFT3_OK;
+}
+
+extern "C" {
+
+const char *fft3_last_error(void) { return g_err.c_str(); }
+
+int fft3_version(void) { return 1; }
+
+int fft3_factorize(int n, int order, int *radices, int cap)
+{
+    if (!radices || cap < 1 || n < 1 || order < 0)
+        return fail(FFT3_ERR_INVALID_ARG, "bad argument to fft3_factorize");
+    int r = factorize(n, order, radices, cap);
+    if (r < 0)
+        return fail(r, "length has a prime factor other than 2, 3, 5 or too many stages");
+    return r;
+}
+
+int fft3_plan_schedule(int n0, int n1, int n2, int batch, int dtype, int decomposition, int direction,
+                       const fft3_options *opts, char *buf, size_t len)
+{
+    Schedule s;
+    std::string err;
+    int rc = build_schedule(n0, n1, n2, batch, dtype, decomposition, direction, opts, &s, &err);
+    if (rc)
+        return fail(rc, err);
+    std::string j = s.json();
+    if (buf && len > 0) {
+        size_t c = std::min(len - 1, j.size());
+        memcpy(buf, j.data(), c);
+        buf[c] = 0;
+    }
+    return (int)j.size();
+}
+
+int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int dtype,
+                        int decomposition, int direction, const fft3_options *opts)
+{
+    if (!out)
+        return fail(FFT3_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    auto *P = new (std::nothrow) fft3_plan_s();
+    if (!P)
+        return fail(FFT3_ERR_OOM, "host allocation failed");
+    std::string err;
+    int rc = build_schedule(n0, n1, n2, batch, dtype, decomposition, direction, opts, &P->sched, &err);
+    if (rc) {
+        delete P;
+        return fail(rc, err);
+    }
+    if (dtype == FFT3_C64_SPLITBF16_TC) {
+        delete P;
+        return fail(FFT3_ERR_UNSUPPORTED_SIZE, "split-BF16 tensor-core path is not built in this library");
+    }
+    rc = check_device(&P->device);
+    if (rc) {
+        delete P;
+        return rc;
+    }
+    P->elems = (int64_t)n0 * n1 * n2 * batch;
+    cudaError_t e = cudaMalloc(&P->d_err, sizeof(unsigned));
+    if (e == cudaSuccess)
+        e = cudaMemset(P->d_err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        free_plan(P);
+        return fail(FFT3_ERR_CUDA, std::string("plan allocation: ") + cudaGetErrorString(e));
+    }
+    rc = generate_twiddles(P);
+    if (!rc)
+        rc = build_launches(P);
+    if (!rc && P->sched.need_ws) {
+        P->ws_bytes = (size_t)P->elems * sizeof(float2);
+        e = cudaMalloc(&P->d_ws, P->ws_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(FFT3_ERR_OOM, "workspace allocation failed");
+        }
+    }
+    if (!rc && P->counters_bytes) {
+        e = cudaMalloc(&P->d_counters, P->counters_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(FFT3_ERR_OOM, "counter allocation failed");
+        }
+        for (Launch &L : P->launches)
+            L.args.counters = P->d_counters;
+    }
+    if (rc) {
+        free_plan(P);
+        return rc;
+    }
+    *out = P;
+    return FFT3_OK;
+}
+
+int fft3_plan_create(fft3_plan *out, int n0, int n1, int n2, int batch, int dtype, int decomposition,
+                     int direction)
+{
+    return fft3_plan_create_ex(out, n0, n1, n2, batch, dtype, decomposition, direction, nullptr);
+}
+
+static int launch_one(fft3_plan_s *P, const Launch &L, const void *func, PassArgs a, cudaStream_t st)
+{
+    if (L.reset_counters)
+        CUDA_TRY(cudaMemsetAsync(P->d_counters, 0, P->counters_bytes, st));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = L.grid;
+    cfg.blockDim = L.block;
+    cfg.dynamicSmemBytes = L.smem;
+    cfg.stream = st;
+    if (L.cluster > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = L.cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    void *params[1] = {&a};
+    CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params));
+    return FFT3_OK;
+}
+
+static float2 *buf_ptr(fft3_plan_s *P, int id, const void *in, void *out)
+{
+    return id == BUF_IN ? (float2 *)in : (id == BUF_OUT ? (float2 *)out : P->d_ws);
+}
+
+int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream)
+{
+    if (!p || !in || !out)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan or buffer");
+    if (in == out)
+        return fail(FFT3_ERR_INPLACE_UNSUPPORTED, "in-place execution is not supported (in == out)");
+    if (((uintptr_t)in | (uintptr_t)out) & 7)
+        return fail(FFT3_ERR_INVALID_ARG, "buffers must be 8-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    p->last_stream = st;
+    for (const Launch &L : p->launches) {
+        PassArgs a = L.args;
+        a.in = buf_ptr(p, L.src, in, out);
+        a.out = buf_ptr(p, L.dst, in, out);
+        if (L.kind == PK_COPY) {
+            k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems);
+            CUDA_TRY(cudaGetLastError());
+            continue;
+        }
+        int rc = launch_one(p, L, L.func, a, st);
+        if (rc)
+            return rc;
+    }
+    return FFT3_OK;
+}
+
+int fft3_plan_probe_layout(fft3_plan p, const void *in, void *out, int npasses, void *stream)
+{
+    if (!p || !in || !out || in == out)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan or buffer, or in == out");
+    cudaStream_t st = (cudaStream_t)stream;
+    int count = (int)p->launches.size();
+    if (npasses >= 0 && npasses < count)
+        count = npasses;
+    int last_dst = BUF_IN;
+    for (int i = 0; i < count; ++i) {
+        const Launch &L = p->launches[i];
+        PassArgs a = L.args;
+        a.in = buf_ptr(p, L.src, in, out);
+        a.out = buf_ptr(p, L.dst, in, out);
+        last_dst = L.dst;
+        if (L.kind == PK_COPY || a.in == a.out) {
+            if (a.in != a.out) {
+                k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems);
+                CUDA_TRY(cudaGetLastError());
+            }
+            continue; // an in-place pass moves nothing
+        }
+        a.g = L.probe_g;
+        a.L[0].n = L.probe_n;
+        int64_t total = (int64_t)L.probe_n * a.g.C * a.g.A * a.g.B;
+        int blocks = (int)std::min<int64_t>(8192, (total + 255) / 256);
+        k_probe_pass<<<std::max(1, blocks), 256, 0, st>>>(a);
+        CUDA_TRY(cudaGetLastError());
+    }
+    if (last_dst == BUF_WS) {
+        k_copy<<<4096, 256, 0, st>>>(p->d_ws, (float2 *)out, p->elems);
+        CUDA_TRY(cudaGetLastError());
+    } else if (last_dst == BUF_IN) {
+        k_copy<<<4096, 256, 0, st>>>((const float2 *)in, (float2 *)out, p->elems);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return FFT3_OK;
+}
+
+int fft3_plan_execute_pass(fft3_plan p, int k, const void *in, void *out, void *stream)
+{
+    if (!p || !in || !out)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan or buffer");
+    if (in == out)
+        return fail(FFT3_ERR_INPLACE_UNSUPPORTED, "in-place execution is not supported (in == out)");
+    if (k < 0 || k >= (int)p->launches.size())
+        return fail(FFT3_ERR_INVALID_ARG, "pass index out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    p->last_stream = st;
+    const Launch &L = p->launches[k];
+    PassArgs a = L.args;
+    a.in = buf_ptr(p, L.src, in, out);
+    a.out = buf_ptr(p, L.dst, in, out);
+    if (L.kind == PK_COPY) {
+        k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems);
+        CUDA_TRY(cudaGetLastError());
+        return FFT3_OK;
+    }
+    return launch_one(p, L, L.func, a, st);
+}
+
+int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *stream)
+{
+    if (!p || !h_in || !h_out)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan or buffer");
+    size_t bytes = (size_t)p->elems * sizeof(float2);
+    if (!p->d_stage_in) {
+        CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
+        CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(p->d_stage_in, h_in, bytes, cudaMemcpyHostToDevice, st));
+    int rc = fft3_plan_execute(p, p->d_stage_in, p->d_stage_out, stream);
+    if (rc)
+        return rc;
+    CUDA_TRY(cudaMemcpyAsync(h_out, p->d_stage_out, bytes, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return FFT3_OK;
+}
+
+int fft3_plan_check(fft3_plan p)
+{
+    if (!p)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan");
+    CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+    unsigned flags = 0;
+    CUDA_TRY(cudaMemcpy(&flags, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (flags) {
+        CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(unsigned)));
+        if (flags & kErrWaitTimeout)
+            return fail(FFT3_ERR_TIMEOUT, "a bounded device-side wait expired");
+        return fail(FFT3_ERR_CUDA, "device error flags set: " + std::to_string(flags));
+    }
+    return FFT3_OK;
+}
+
+int fft3_plan_destroy(fft3_plan p)
+{
+    if (!p)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan");
+    free_plan(p);
+    return FFT3_OK;
+}
+
+size_t fft3_plan_workspace_bytes(fft3_plan p) { return p ? p->ws_bytes : 0; }
+
+int fft3_plan_launches(fft3_plan p)
+{
+    if (!p)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan");
+    return (int)p->launches.size();
+}
+
+int fft3_plan_describe(fft3_plan p, char *buf, size_t len)
+{
+    if (!p)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan");
+    std::string j = p->sched.json();
+    // append the launch shapes
+    std::string l = ",\"launches\":[";
+    for (size_t i = 0; i < p->launches.size(); ++i) {
+        const Launch &L = p->launches[i];
+        l += (i ? "," : "") + std::string("{\"grid\":") + std::to_string(L.grid.x) +
+             ",\"block\":" + std::to_string(L.block.x) + ",\"smem\":" + std::to_string(L.smem) +
+             ",\"cluster\":" + std::to_string(L.cluster) + "}";
+    }
+    l += "]}";
+    j = j.substr(0, j.size() - 1) + l;
+    if (buf && len > 0) {
+        size_t c = std::min(len - 1, j.size());
+        memcpy(buf, j.data(), c);
+        buf[c] = 0;
+    }
+    return (int)j.size();
+}
+
+int fft3_twiddles(int n, int sign, const int64_t *d_m, int64_t count, double *d_out64, float *d_out32,
+                  void *stream)
+{
+    if (n < 1 || count < 0 || !d_m || (sign != -1 && sign != 1))
+        return fail(FFT3_ERR_INVALID_ARG, "bad argument to fft3_twiddles");
+    if (count == 0)
+        return FFT3_OK;
+    int blocks = (int)std::min<int64_t>(4096, (count + 255) / 256);
+    k_roots<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, sign, d_m, count, d_out64, (float2 *)d_out32);
+    CUDA_TRY(cudaGetLastError());
+    return FFT3_OK;
+}
+
+int fft3_split_bf16(const float *d_x, int64_t count, uint16_t *d_hi, uint16_t *d_lo, void *stream)
+{
+    if (!d_x || !d_hi || !d_lo || count < 0)
+        return fail(FFT3_ERR_INVALID_ARG, "bad argument to fft3_split_bf16");
+    if (count == 0)
+        return FFT3_OK;
+    int blocks = (int)std::min<int64_t>(4096, (count + 255) / 256);
+    k_split_bf16<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_x, count, d_hi, d_lo);
+    CUDA_TRY(cudaGetLastError());
+    return FFT3_OK;
+}
+
+int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets, int dtype,
+                          int decomposition, int direction, const int *tuning)
+{
+    (void)count; (void)dims; (void)offsets; (void)dtype; (void)decomposition; (void)direction; (void)tuning;
+    if (out)
+        *out = nullptr;
+    return fail(FFT3_ERR_UNSUPPORTED_SIZE, "batched uneven plans are not built in this library");
+}
+
+} // extern "C"

@@ -1,0 +1,331 @@
+// fft_engine.cuh -- device-side building blocks of the line transforms.
+//
+// A line of n complex values is transformed by a sequence of Stockham
+// radix-R stages (the Cooley-Tukey split n = n0*n1 of Section 2.1, Eq. ct,
+// applied repeatedly with the transposition (III) folded into the index
+// map of every stage so the result comes out in natural order):
+//
+//   stage with radix R, NS = product of the radices of the earlier stages,
+//   butterfly q in [0, n/R):
+//     v[r]  = src[q + r*n/R]                                   r < R
+//     v[r] *= w_{NS*R}^{r*(q mod NS)}                           twiddle (II)
+//     v     = DFT_R v                                           butterfly (I/IV)
+//     dst[(q div NS)*NS*R + (q mod NS) + r*NS] = v[r]
+//
+// The twiddles of all stages sit in one stage-major table:
+//   table[off_s + (r-1)*NS_s + k] = w_n^{r*k*n/(NS_s*R_s)},  r in [1,R), k < NS_s,
+// off_s = sum over earlier stages of (R-1)*NS, which is at most n-1 entries.
+// The table is produced in FP64 on the GPU and rounded to float32
+// (twiddle.cu).  The butterflies below are the forward transform; the
+// inverse is computed as conj(DFT(conj(x))) by conjugating on load and store.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "geom.h"
+
+namespace fft3 {
+
+// ------------------------------------------------------------ complex ---- //
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); } // a * (-i)
+__device__ __forceinline__ float2 mul_pi(float2 a) { return make_float2(-a.y, a.x); } // a * (+i)
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// cos(2 pi m / 16) and sin(2 pi m / 16) from the first-octant values.
+constexpr double kC16 = 0.923879532511286756128183189396788933; // cos(pi/8)
+constexpr double kS16 = 0.382683432365089771728459984030398866; // sin(pi/8)
+constexpr double kH = 0.707106781186547524400844362104849039;   // sqrt(1/2)
+
+__host__ __device__ constexpr double cos16(int m)
+{
+    m &= 15;
+    return m == 0 ? 1.0 : m == 1 ? kC16 : m == 2 ? kH : m == 3 ? kS16 : m == 4 ? 0.0
+         : m == 5 ? -kS16 : m == 6 ? -kH : m == 7 ? -kC16 : m == 8 ? -1.0 : m == 9 ? -kC16
+         : m == 10 ? -kH : m == 11 ? -kS16 : m == 12 ? 0.0 : m == 13 ? kS16 : m == 14 ? kH : kC16;
+}
+__host__ __device__ constexpr double sin16(int m) { return cos16(m - 4); }
+
+// a * w_R^M with w_R = exp(-2 pi i / R), R in {2, 4, 8, 16}, M known at compile time.
+template <int R, int M>
+__device__ __forceinline__ float2 mul_w(float2 a)
+{
+    constexpr int m16 = ((M % R) + R) % R * (16 / R);
+    if constexpr (m16 == 0) {
+        return a;
+    } else if constexpr (m16 == 4) {
+        return mul_mi(a);
+    } else if constexpr (m16 == 8) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (m16 == 12) {
+        return mul_pi(a);
+    } else if constexpr (m16 == 2 || m16 == 6 || m16 == 10 || m16 == 14) {
+        // (c - i s) with |c| = |s| = sqrt(1/2)
+        constexpr float c = (float)cos16(m16), s = (float)sin16(m16);
+        return make_float2((a.x * c + a.y * s), (a.y * c - a.x * s));
+    } else {
+        constexpr float c = (float)cos16(m16), s = (float)sin16(m16);
+        return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+    }
+}
+
+// ---------------------------------------------------------- butterflies -- //
+// In-register forward DFT_R of v[0..R) in natural order (Section 2.1 definition).
+template <int R>
+struct Bfly;
+
+template <>
+struct Bfly<2> {
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <>
+struct Bfly<4> {
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        float2 t2 = cadd(v[1], v[3]), t3 = mul_mi(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+
+// 8 = 2 * 4 (Eq. ct with n0 = 2, n1 = 4): DFT_4 on x[i0 + 2 i1], twiddle
+// w_8^{i0 k1}, DFT_2 across i0, output y[k1 + 4 k0].
+template <>
+struct Bfly<8> {
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        Bfly<4>::run(e);
+        Bfly<4>::run(o);
+        o[1] = mul_w<8, 1>(o[1]);
+        o[2] = mul_w<8, 2>(o[2]);
+        o[3] = mul_w<8, 3>(o[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + 4] = csub(e[k], o[k]);
+        }
+    }
+};
+
+// 16 = 4 * 4 (Eq. ct with n0 = n1 = 4).
+template <>
+struct Bfly<16> {
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        float2 t[4][4];
+#pragma unroll
+        for (int i0 = 0; i0 < 4; ++i0) {
+#pragma unroll
+            for (int i1 = 0; i1 < 4; ++i1)
+                t[i0][i1] = v[i0 + 4 * i1];
+            Bfly<4>::run(t[i0]);
+        }
+        t[1][1] = mul_w<16, 1>(t[1][1]);
+        t[1][2] = mul_w<16, 2>(t[1][2]);
+        t[1][3] = mul_w<16, 3>(t[1][3]);
+        t[2][1] = mul_w<16, 2>(t[2][1]);
+        t[2][2] = mul_w<16, 4>(t[2][2]);
+        t[2][3] = mul_w<16, 6>(t[2][3]);
+        t[3][1] = mul_w<16, 3>(t[3][1]);
+        t[3][2] = mul_w<16, 6>(t[3][2]);
+        t[3][3] = mul_w<16, 9>(t[3][3]);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 c[4] = {t[0][k1], t[1][k1], t[2][k1], t[3][k1]};
+            Bfly<4>::run(c);
+#pragma unroll
+            for (int k0 = 0; k0 < 4; ++k0)
+                v[k1 + 4 * k0] = c[k0];
+        }
+    }
+};
+
+// DFT_3: w_3 = -1/2 - i sqrt(3)/2.
+template <>
+struct Bfly<3> {
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        constexpr float s3 = 0.866025403784438646763723170752936183f; // sin(2 pi / 3)
+        float2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        float2 a = make_float2(fmaf(-0.5f, s.x, v[0].x), fmaf(-0.5f, s.y, v[0].y));
+        float2 b = cscale(d, s3);
+        v[0] = cadd(v[0], s);
+        v[1] = make_float2(a.x + b.y, a.y - b.x); // a - i b
+        v[2] = make_float2(a.x - b.y, a.y + b.x); // a + i b
+    }
+};
+
+// DFT_5 with the conjugate-pair form: y_1,4 = a1 -/+ i b1, y_2,3 = a2 -/+ i b2.
+template <>
+struct Bfly<5> {
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        constexpr float c1 = 0.309016994374947424102293417182819059f;  // cos(2 pi/5)
+        constexpr float c2 = -0.809016994374947424102293417182819059f; // cos(4 pi/5)
+        constexpr float s1 = 0.951056516295153572116439333379382143f;  // sin(2 pi/5)
+        constexpr float s2 = 0.587785252292473129168705954639072769f;  // sin(4 pi/5)
+        float2 x0 = v[0];
+        float2 sa = cadd(v[1], v[4]), da = csub(v[1], v[4]);
+        float2 sb = cadd(v[2], v[3]), db = csub(v[2], v[3]);
+        float2 a1 = make_float2(x0.x + c1 * sa.x + c2 * sb.x, x0.y + c1 * sa.y + c2 * sb.y);
+        float2 a2 = make_float2(x0.x + c2 * sa.x + c1 * sb.x, x0.y + c2 * sa.y + c1 * sb.y);
+        float2 b1 = make_float2(s1 * da.x + s2 * db.x, s1 * da.y + s2 * db.y);
+        float2 b2 = make_float2(s2 * da.x - s1 * db.x, s2 * da.y - s1 * db.y);
+        v[0] = make_float2(x0.x + sa.x + sb.x, x0.y + sa.y + sb.y);
+        v[1] = make_float2(a1.x + b1.y, a1.y - b1.x);
+        v[4] = make_float2(a1.x - b1.y, a1.y + b1.x);
+        v[2] = make_float2(a2.x + b2.y, a2.y - b2.x);
+        v[3] = make_float2(a2.x - b2.y, a2.y + b2.x);
+    }
+};
+
+// ------------------------------------------------------ stage indexing -- //
+// Shared-memory position of intra-line index `pos` for the line-major layout:
+// one padding slot per 16 keeps the first stages' strided writes free of
+// bank conflicts.
+__host__ __device__ __forceinline__ constexpr int padpos(int pos) { return pos + (pos >> 4); }
+
+// Line pitch (complex elements) of the padded line-major layout; odd so that
+// reading one position of 16 consecutive lines is conflict free too.
+__host__ __device__ constexpr int line_pitch(int n) { return (padpos(n - 1) + 1) | 1; }
+
+// One compile-time Stockham stage (see the file header).  `src(j)` returns
+// element j of this thread's line, `dst(k, v)` stores element k.  When the
+// source and destination alias, SYNC_MID places a block barrier between
+// reading every input and writing any output.
+template <int N, int T, int R, int NS, bool SYNC_MID, class Src, class Dst>
+__device__ __forceinline__ void stage_fixed(int t, const Src &src, const Dst &dst, const float2 *tw)
+{
+    constexpr int NB = N / R;
+    constexpr int BPT = (NB + T - 1) / T;
+    constexpr bool FULL = (NB % T) == 0;
+    float2 v[BPT][R];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int q = t + b * T;
+        if (FULL || q < NB) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                v[b][r] = src(q + r * NB);
+        }
+    }
+    if constexpr (SYNC_MID)
+        __syncthreads();
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int q = t + b * T;
+        if (FULL || q < NB) {
+            const int k = (NS == 1) ? 0 : q % NS;
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r)
+                    v[b][r] = cmul(v[b][r], tw[(r - 1) * NS + k]);
+            }
+            Bfly<R>::run(v[b]);
+            const int base = (NS == 1) ? q * R : (q / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                dst(base + r * NS, v[b][r]);
+        }
+    }
+}
+
+// Compile-time radix list.
+template <int... Rs>
+struct Radices {
+    static constexpr int count = sizeof...(Rs);
+};
+
+template <int N, int T, int NS, class Rad>
+struct EngineFixed;
+
+// Last stage: source is shared memory (or global for a single-stage line),
+// destination is the caller's sink.
+template <int N, int T, int NS, int R>
+struct EngineFixed<N, T, NS, Radices<R>> {
+    template <bool FIRST, bool SINK_ALIASES, class Src, class Smem, class Dst>
+    __device__ __forceinline__ static void run(int t, const Src &src, const Smem &, const Dst &dst,
+                                               const float2 *tw)
+    {
+        stage_fixed<N, T, R, NS, SINK_ALIASES>(t, src, dst, tw);
+    }
+};
+
+template <int N, int T, int NS, int R, int R2, int... Rest>
+struct EngineFixed<N, T, NS, Radices<R, R2, Rest...>> {
+    template <bool FIRST, bool SINK_ALIASES, class Src, class Smem, class Dst>
+    __device__ __forceinline__ static void run(int t, const Src &src, const Smem &sm, const Dst &dst,
+                                               const float2 *tw)
+    {
+        // The first stage reads its own source; later stages read the shared
+        // buffer they also write, so they need the mid-stage barrier.
+        stage_fixed<N, T, R, NS, !FIRST>(t, src, sm, tw);
+        __syncthreads();
+        EngineFixed<N, T, NS * R, Radices<R2, Rest...>>::template run<false, SINK_ALIASES>(
+            t, sm, sm, dst, tw + (R - 1) * NS);
+    }
+};
+
+// --------------------------------------------------- runtime stage path -- //
+// Same stage with R known at compile time but n, T, NS at run time; used by
+// the generic kernels whose radix list is data (any 2*3*5-smooth length).
+template <int R, class Src, class Dst>
+__device__ __forceinline__ void stage_rt(int n, int T, int NS, int t, const Src &src, const Dst &dst,
+                                         const float2 *tw, bool active)
+{
+    const int NB = n / R;
+    if (!active)
+        return;
+    for (int q = t; q < NB; q += T) {
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            v[r] = src(q + r * NB);
+        const int k = q % NS;
+        if (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r)
+                v[r] = cmul(v[r], tw[(r - 1) * NS + k]);
+        }
+        Bfly<R>::run(v);
+        const int base = (q / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            dst(base + r * NS, v[r]);
+    }
+}
+
+template <class Src, class Dst>
+__device__ __forceinline__ void stage_rt_dispatch(int R, int n, int T, int NS, int t, const Src &src,
+                                                  const Dst &dst, const float2 *tw, bool active)
+{
+    switch (R) {
+    case 2: stage_rt<2>(n, T, NS, t, src, dst, tw, active); break;
+    case 3: stage_rt<3>(n, T, NS, t, src, dst, tw, active); break;
+    case 4: stage_rt<4>(n, T, NS, t, src, dst, tw, active); break;
+    case 5: stage_rt<5>(n, T, NS, t, src, dst, tw, active); break;
+    case 8: stage_rt<8>(n, T, NS, t, src, dst, tw, active); break;
+    case 16: stage_rt<16>(n, T, NS, t, src, dst, tw, active); break;
+    default: break;
+    }
+}
+
+} // namespace fft3

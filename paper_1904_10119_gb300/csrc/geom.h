@@ -1,0 +1,49 @@
+// geom.h -- plain (host and device) description of one pass of batched 1D
+// DFTs; see pass_kernels.cuh for the meaning of every field.
+#pragma once
+
+#include <stdint.h>
+#include <vector_types.h>
+
+namespace fft3 {
+
+struct PassGeom {
+    int64_t C, A, B;
+    int64_t ij, ic, ia, ib;
+    int64_t ok, oc, oa, ob;
+};
+
+// Error flag bits written by device code (read back by fft3_plan_check).
+enum : unsigned {
+    kErrWaitTimeout = 1u,
+    kErrBadTile = 2u,
+};
+
+constexpr int kMaxStages = 12;
+
+// A line transform with its radix list known only at run time.
+struct LineRt {
+    int n, T, nst, tw_off; // tw_off: offset of its stage-major table inside the pass table
+    int rad[kMaxStages];
+};
+
+struct PassArgs {
+    const float2 *in;
+    float2 *out;
+    PassGeom g;
+    const float2 *tw; // the pass's twiddle tables (global memory), tw_len entries
+    int tw_len;
+    int conj;         // 1: inverse via conj(DFT(conj x))
+    int64_t ntiles;
+    int64_t tiles_c;
+    int lpt;          // lines (or slabs) per tile
+    LineRt L[2];      // runtime line plans: generic L[0]; slab x = L[0], y = L[1];
+                      // volumetric rows (DFT_b) = L[0], columns (DFT_a) = L[1]
+    int p, split_a, split_b, tw_split_off; // volumetric split n = a*b over p blocks
+    unsigned *err;    // device error flags (persistent kernels)
+    int *counters;    // per-slab completion counters + ticket (persistent kernels)
+    long long wait_budget; // clock cycles a bounded wait may spin before giving up
+    int64_t nosignal_slab; // test hook: x tiles of this slab never signal (-1 = off)
+};
+
+} // namespace fft3

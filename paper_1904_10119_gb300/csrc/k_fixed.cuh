@@ -1,0 +1,41 @@
+// k_fixed.cuh -- instantiation of the compile-time pass kernels for one half of
+// the fixed-plan list (plans.h); each half is its own translation unit so the
+// two compile in parallel.
+#pragma once
+
+#include "pass_kernels.cuh"
+#include "plans.h"
+#include "slab_l2.cuh"
+
+namespace fft3 {
+
+template <int N, int T>
+constexpr bool has_slab_l2() { return (N == 1024 || N == 512 || N == 256) && T * 16 <= 1024; }
+
+template <int N, int T, class Rad>
+constexpr const void *slab_l2_ptr()
+{
+    if constexpr (has_slab_l2<N, T>())
+        return (const void *)&k_slab_l2<N, T, Rad>;
+    else
+        return nullptr;
+}
+
+template <int N, int T, class Rad, int LPT>
+constexpr const void *pass_c_ptr()
+{
+    if constexpr (LPT > 0)
+        return (const void *)&k_pass_c<N, T, Rad, LPT>;
+    else
+        return nullptr;
+}
+
+} // namespace fft3
+
+#define FFT3_KERNEL_ROW(ID, N, T, ...)                                                          \
+    {ID,                                                                                        \
+     (const void *)&fft3::k_pass_j<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_j(T), false>,    \
+     (const void *)&fft3::k_pass_j<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_rot(T), true>,   \
+     fft3::pass_c_ptr<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_c(T, 16)>(),                  \
+     fft3::pass_c_ptr<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_c(T, 8)>(),                   \
+     fft3::slab_l2_ptr<N, T, fft3::Radices<__VA_ARGS__>>()},

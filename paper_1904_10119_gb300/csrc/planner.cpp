@@ -1,0 +1,662 @@
+// planner.cpp -- lowers a decomposition of the 3D DFT to a schedule of passes.
+//
+// Decompositions (paper Sections 2.3, 2.4 and 3.2):
+//   pencil-pencil-pencil  DFT_{n0}, then DFT_{n1}, then DFT_{n2}.  Two variants:
+//     natural: the x pass writes `out`, the y and z passes run in place on
+//              strided lines of `out` (tiles of adjacent columns);
+//     rotate:  each pass reads contiguous lines and stores its result rotated,
+//              xyz -> yzx -> zxy -> xyz (Section 2.4), so the next pass's lines
+//              are contiguous again; the rotation is the store epilogue.
+//   slab-pencil           2D DFT of every n0 x n1 slab (x lines then y lines
+//                         on data kept on chip or in L2), then DFT_{n2}.
+//   volumetric            every dimension's 1D DFT split n = a*b (Eq. ct) over
+//                         a cluster of p blocks that hold the line in
+//                         elemental-cyclic order; one exchange per dimension
+//                         when p | a and p | b (Section 3.2).
+// Parallelism limits of Section 2.5 become the tile counts of each pass; the
+// divisibility condition of Section 3.2 is checked for every volumetric split.
+#include "planner.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <sstream>
+
+#include "plans.h"
+
+namespace fft3 {
+
+// ------------------------------------------------------ fixed-plan table -- //
+#define FFT3_META_ROW(ID, N, T, ...) {ID, N, T, 0, {__VA_ARGS__}},
+static FixedPlanMeta g_meta[] = {FFT3_FIXED_PLANS(FFT3_META_ROW)};
+#undef FFT3_META_ROW
+static const int g_nmeta = (int)(sizeof(g_meta) / sizeof(g_meta[0]));
+
+static void init_meta()
+{
+    static bool done = false;
+    if (done)
+        return;
+    for (int i = 0; i < g_nmeta; ++i) {
+        int c = 0;
+        while (c < 8 && g_meta[i].rad[c] > 0)
+            ++c;
+        g_meta[i].nrad = c;
+    }
+    done = true;
+}
+
+int fixed_plan_count() { return g_nmeta; }
+const FixedPlanMeta &fixed_plan_meta(int id)
+{
+    init_meta();
+    return g_meta[id];
+}
+
+static inline int tw_slots_h(int len) { return ((len > 0 ? len : 1) + 15) / 16 * 16; }
+static inline int padpos_h(int p) { return p + (p >> 4); }
+static inline int pitch_h(int n) { return (padpos_h(n - 1) + 1) | 1; }
+
+// ----------------------------------------------------------- factorise --- //
+static bool smooth235(int n, int *e2, int *e3, int *e5)
+{
+    *e2 = *e3 = *e5 = 0;
+    if (n < 1)
+        return false;
+    while (n % 2 == 0) { n /= 2; ++*e2; }
+    while (n % 3 == 0) { n /= 3; ++*e3; }
+    while (n % 5 == 0) { n /= 5; ++*e5; }
+    return n == 1;
+}
+
+int factorize(int n, int order, int *rad, int cap)
+{
+    int e2, e3, e5;
+    if (!smooth235(n, &e2, &e3, &e5))
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    std::vector<int> r;
+    int mode = order % 4;
+    if (mode == 0 || mode == 1) { // radix 16 first, then 8/4/2, then 5s and 3s
+        for (int i = 0; i < e2 / 4; ++i) r.push_back(16);
+        if (e2 % 4) r.push_back(1 << (e2 % 4));
+        for (int i = 0; i < e5; ++i) r.push_back(5);
+        for (int i = 0; i < e3; ++i) r.push_back(3);
+        if (mode == 1) std::reverse(r.begin(), r.end());
+    } else if (mode == 2) { // radix 4 first
+        for (int i = 0; i < e2 / 2; ++i) r.push_back(4);
+        if (e2 % 2) r.push_back(2);
+        for (int i = 0; i < e3; ++i) r.push_back(3);
+        for (int i = 0; i < e5; ++i) r.push_back(5);
+    } else { // radix 8 first
+        for (int i = 0; i < e2 / 3; ++i) r.push_back(8);
+        if (e2 % 3) r.push_back(1 << (e2 % 3));
+        for (int i = 0; i < e3; ++i) r.push_back(3);
+        for (int i = 0; i < e5; ++i) r.push_back(5);
+    }
+    if ((int)r.size() > cap)
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    for (size_t i = 0; i < r.size(); ++i)
+        rad[i] = r[i];
+    return (int)r.size();
+}
+
+// Candidates for a line: fixed plans of that length (in table order).
+static std::vector<int> fixed_candidates(int n)
+{
+    init_meta();
+    std::vector<int> c;
+    for (int i = 0; i < g_nmeta; ++i)
+        if (g_meta[i].n == n)
+            c.push_back(i);
+    return c;
+}
+
+static int choose_line(int n, int order, bool allow_fixed, LineChoice *lc, std::string *err)
+{
+    lc->n = n;
+    std::vector<int> fc = allow_fixed ? fixed_candidates(n) : std::vector<int>();
+    if (!fc.empty()) {
+        const FixedPlanMeta &m = g_meta[fc[order % fc.size()]];
+        lc->fixed = m.id;
+        lc->T = m.T;
+        lc->nst = m.nrad;
+        for (int i = 0; i < m.nrad; ++i)
+            lc->rad[i] = m.rad[i];
+        return FFT3_OK;
+    }
+    if (n > kMaxLine) {
+        *err = "line length " + std::to_string(n) + " exceeds " + std::to_string(kMaxLine);
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    }
+    int k = factorize(n, order, lc->rad, kMaxStages);
+    if (k < 0) {
+        *err = "line length " + std::to_string(n) + " has a prime factor other than 2, 3, 5";
+        return k;
+    }
+    lc->fixed = -1;
+    lc->nst = k;
+    int maxr = 1;
+    for (int i = 0; i < k; ++i)
+        maxr = std::max(maxr, lc->rad[i]);
+    lc->T = std::max(1, n / maxr);
+    return FFT3_OK;
+}
+
+// Stage-major twiddle exponents of a line choice (fft_engine.cuh header).
+static void line_twiddles(const LineChoice &lc, std::vector<int64_t> *m)
+{
+    int NS = 1;
+    for (int s = 0; s < lc.nst; ++s) {
+        int R = lc.rad[s];
+        int64_t stride = lc.n / (NS * R);
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < NS; ++k)
+                m->push_back((int64_t)r * k * stride % lc.n);
+        NS *= R;
+    }
+}
+
+static int add_seg(Schedule *s, int n, std::vector<int64_t> m)
+{
+    TwSeg seg;
+    seg.n = n;
+    seg.m = std::move(m);
+    seg.off = s->tw_total;
+    s->tw_total += ((int64_t)seg.m.size() + 15) / 16 * 16;
+    s->tw.push_back(std::move(seg));
+    return (int)s->tw.size() - 1;
+}
+
+static int line_seg(Schedule *s, const LineChoice &lc)
+{
+    std::vector<int64_t> m;
+    line_twiddles(lc, &m);
+    if (m.empty())
+        m.push_back(0);
+    return add_seg(s, lc.n, std::move(m));
+}
+
+void generic_launch_shape(int n, int T, bool strided, int tw_len, int *lpt, int *threads, int *smem)
+{
+    int P = pitch_h(n);
+    int l = strided ? 16 : std::max(1, 256 / T);
+    while (l > 1 && T * l > 1024)
+        l /= 2;
+    auto bytes = [&](int ll) { return tw_slots_h(tw_len) * 8 + 2 * ll * P * 8; };
+    while (l > 1 && bytes(l) > kSmemLimit)
+        l /= 2;
+    *lpt = l;
+    *threads = std::max(32, std::min(1024, (T * l + 31) / 32 * 32));
+    *smem = bytes(l);
+}
+
+// --------------------------------------------------------- geometries ---- //
+static PassGeom geom_natural(int d, int64_t n0, int64_t n1, int64_t n2, int64_t batch)
+{
+    PassGeom g{};
+    int64_t N = n0 * n1 * n2;
+    if (d == 0) { // x lines: c = y, a = z, b = batch
+        g.C = n1; g.A = n2; g.B = batch;
+        g.ij = 1; g.ic = n0; g.ia = n0 * n1; g.ib = N;
+    } else if (d == 1) { // y lines: c = x, a = z, b = batch
+        g.C = n0; g.A = n2; g.B = batch;
+        g.ij = n0; g.ic = 1; g.ia = n0 * n1; g.ib = N;
+    } else { // z lines: c = x + n0*y, a = batch
+        g.C = n0 * n1; g.A = batch; g.B = 1;
+        g.ij = n0 * n1; g.ic = 1; g.ia = N; g.ib = 0;
+    }
+    g.ok = g.ij; g.oc = g.ic; g.oa = g.ia; g.ob = g.ib;
+    return g;
+}
+
+// Rotation xyz -> yzx -> zxy -> xyz (Section 2.4).  Pass d reads the layout in
+// which dimension d is fastest and writes the layout in which d+1 is fastest.
+static PassGeom geom_rotate(int d, int64_t n0, int64_t n1, int64_t n2, int64_t batch)
+{
+    int64_t n[3] = {n0, n1, n2};
+    int64_t da = n[d], db = n[(d + 1) % 3], dc = n[(d + 2) % 3];
+    PassGeom g{};
+    int64_t N = n0 * n1 * n2;
+    // input layout (da fastest, then db, then dc); lines along da:
+    // c = index along db, a = index along dc, b = batch
+    g.C = db; g.A = dc; g.B = batch;
+    g.ij = 1; g.ic = da; g.ia = da * db; g.ib = N;
+    // output layout (db fastest, then dc, then da)
+    g.oc = 1; g.oa = db; g.ok = db * dc; g.ob = N;
+    return g;
+}
+
+static void set_tiles(PassPlan *p)
+{
+    p->tiles_c = (p->g.C + p->lpt - 1) / p->lpt;
+    p->ntiles = p->tiles_c * p->g.A * p->g.B;
+}
+
+// A single 1D pass on dimension d with geometry g.
+static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rotate, int src, int dst,
+                          PassPlan *out, std::string *err)
+{
+    PassPlan p;
+    p.dim = d;
+    p.g = g;
+    p.src = src;
+    p.dst = dst;
+    int order = s->opts.radix_order;
+    int rc = choose_line(n, order, true, &p.line, err);
+    if (rc)
+        return rc;
+    const bool contig_in = g.ij == 1;
+    const bool strided_in = g.ic == 1 && g.oc == 1;
+    int want_c = s->opts.tile_lines == 8 ? 8 : 16;
+    if (p.line.fixed >= 0 && rotate && contig_in && g.oc == 1) {
+        p.kind = PK_JROT;
+        p.lpt = lpt_rot(p.line.T);
+    } else if (p.line.fixed >= 0 && !rotate && contig_in && g.ok == 1 && n > 1) {
+        p.kind = PK_J;
+        p.lpt = lpt_j(p.line.T);
+    } else if (p.line.fixed >= 0 && !rotate && strided_in && lpt_c(p.line.T, want_c) > 0 && n > 1) {
+        p.kind = PK_C;
+        p.lpt = lpt_c(p.line.T, want_c);
+    } else {
+        // runtime radix list (also used for n == 1 layout changes)
+        if (p.line.fixed >= 0) {
+            LineChoice lc;
+            rc = choose_line(n, order, false, &lc, err);
+            if (rc)
+                return rc;
+            p.line = lc;
+        }
+        p.kind = PK_G;
+    }
+    p.tw_seg[0] = line_seg(s, p.line);
+    int tw_len = (int)s->tw[p.tw_seg[0]].m.size();
+    if (p.kind == PK_G) {
+        generic_launch_shape(n, p.line.T, !contig_in, tw_len, &p.lpt, &p.threads, &p.smem_bytes);
+    } else if (p.kind == PK_J) {
+        p.threads = p.line.T * p.lpt;
+        p.smem_bytes = tw_slots_h(tw_len) * 8 + p.lpt * pitch_h(n) * 8;
+    } else if (p.kind == PK_JROT) {
+        p.threads = p.line.T * p.lpt;
+        p.smem_bytes = tw_slots_h(tw_len) * 8 + p.lpt * pitch_h(n) * 8;
+    } else {
+        p.threads = p.line.T * p.lpt;
+        p.smem_bytes = tw_slots_h(tw_len) * 8 + p.lpt * n * 8;
+    }
+    if (p.smem_bytes > kSmemLimit) {
+        *err = "pass needs more shared memory than a block has";
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    }
+    set_tiles(&p);
+    *out = p;
+    return FFT3_OK;
+}
+
+// Volumetric split of a line of length n over p blocks: n = a*b with p | a
+// and p | b (Section 3.2).  Prefers a close to sqrt(n).
+static bool volumetric_split(int n, int p, int *a, int *b)
+{
+    int best = -1;
+    for (int aa = p; aa <= n; aa += p) {
+        if (n % aa)
+            continue;
+        int bb = n / aa;
+        if (bb % p)
+            continue;
+        if (best < 0 || std::abs(aa - bb) < std::abs(best - n / best) ||
+            (std::abs(aa - bb) == std::abs(best - n / best) && aa > best))
+            best = aa;
+    }
+    if (best < 0)
+        return false;
+    *a = best;
+    *b = n / best;
+    return true;
+}
+
+static int vol_smem(int n, int p, int a, int b, int lpt, int twlen)
+{
+    int sub_b = lpt * (a / p) * pitch_h(b); // T0: lpt*(a/p) rows of length b
+    int sub_a = lpt * (b / p) * pitch_h(a); // T1: lpt*(b/p) columns of length a
+    int big = std::max(sub_a, sub_b);
+    return twlen * 8 + (sub_b + sub_a + big) * 8;
+}
+
+static int make_vol_pass(Schedule *s, int d, int n, int p, const PassGeom &g, int src, int dst,
+                         PassPlan *out, std::string *err)
+{
+    PassPlan q;
+    q.kind = PK_VOL;
+    q.dim = d;
+    q.g = g;
+    q.src = src;
+    q.dst = dst;
+    q.p = p;
+    if (!volumetric_split(n, p, &q.split_a, &q.split_b)) {
+        *err = "volumetric split of " + std::to_string(n) + " over " + std::to_string(p) +
+               " blocks needs n = a*b with p | a and p | b";
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    }
+    int rc = choose_line(q.split_b, s->opts.radix_order, false, &q.line, err); // rows: DFT_b
+    if (rc)
+        return rc;
+    rc = choose_line(q.split_a, s->opts.radix_order, false, &q.line2, err); // columns: DFT_a
+    if (rc)
+        return rc;
+    q.tw_seg[0] = line_seg(s, q.line);
+    q.tw_seg[1] = line_seg(s, q.line2);
+    std::vector<int64_t> m(n);
+    for (int i = 0; i < n; ++i)
+        m[i] = i; // w_n^i, indexed by (i0*k1) mod n
+    q.tw_seg[2] = add_seg(s, n, std::move(m));
+    int twlen = 0;
+    for (int k = 0; k < 3; ++k)
+        twlen += tw_slots_h((int)s->tw[q.tw_seg[k]].m.size());
+    const bool strided = g.ic == 1;
+    int lpt = strided ? (s->opts.tile_lines == 8 ? 8 : 16) : std::max(1, 512 / std::max(1, n / p / 4));
+    while (lpt > 1 && vol_smem(n, p, q.split_a, q.split_b, lpt, twlen) > kSmemLimit)
+        lpt /= 2;
+    q.lpt = lpt;
+    q.smem_bytes = vol_smem(n, p, q.split_a, q.split_b, lpt, twlen);
+    if (q.smem_bytes > kSmemLimit) {
+        *err = "volumetric pass does not fit in shared memory";
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    }
+    q.threads = std::max(256, (std::max(q.line.T, q.line2.T) + 31) / 32 * 32);
+    set_tiles(&q);
+    *out = q;
+    return FFT3_OK;
+}
+
+// Slab 2D pass in one block's shared memory: fits when two copies of the
+// padded slab fit.
+static int slab_smem(int n0, int n1, int twlen) { return twlen * 8 + 2 * n1 * pitch_h(n0) * 8; }
+
+static int make_slab_pass(Schedule *s, int n0, int n1, int64_t n2, int64_t batch, PassPlan *out,
+                          std::string *err)
+{
+    PassPlan q;
+    q.kind = PK_SLAB;
+    q.dim = 3;
+    q.src = BUF_IN;
+    q.dst = BUF_OUT;
+    int rc = choose_line(n0, s->opts.radix_order, false, &q.line, err);
+    if (rc)
+        return rc;
+    rc = choose_line(n1, s->opts.radix_order, false, &q.line2, err);
+    if (rc)
+        return rc;
+    q.tw_seg[0] = line_seg(s, q.line);
+    q.tw_seg[1] = line_seg(s, q.line2);
+    int twlen = tw_slots_h((int)s->tw[q.tw_seg[0]].m.size()) +
+                tw_slots_h((int)s->tw[q.tw_seg[1]].m.size());
+    q.smem_bytes = slab_smem(n0, n1, twlen);
+    if (q.smem_bytes > kSmemLimit)
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    int64_t N = (int64_t)n0 * n1 * n2;
+    // one slab per tile; slabs indexed by (a = z, b = batch)
+    q.g = PassGeom{};
+    q.g.C = 1; q.g.A = n2; q.g.B = batch;
+    q.g.ij = 1; q.g.ic = 0; q.g.ia = (int64_t)n0 * n1; q.g.ib = N;
+    q.g.ok = 1; q.g.oc = 0; q.g.oa = q.g.ia; q.g.ob = N;
+    q.lpt = 1;
+    int teams = std::max(1, std::max(n1, n0));
+    int T = std::max(q.line.T, q.line2.T);
+    // enough threads for one team of the longer line, up to 512 for the rest
+    q.threads = std::min(512, std::max(64, (teams * T + 31) / 32 * 32));
+    q.threads = std::max(q.threads, (T + 31) / 32 * 32);
+    set_tiles(&q);
+    *out = q;
+    return FFT3_OK;
+}
+
+// Slab pass with x and y tiles in one persistent launch, the slab kept in L2
+// between its x and y stages (compiled for square slabs with a fixed plan).
+static bool slab_l2_supported(int n0, int n1) { return n0 == n1 && (n0 == 1024 || n0 == 512 || n0 == 256); }
+
+static int make_slab_l2_pass(Schedule *s, int n0, int n1, int64_t n2, int64_t batch, PassPlan *out,
+                             std::string *err)
+{
+    PassPlan q;
+    q.kind = PK_SLABL2;
+    q.dim = 3;
+    q.src = BUF_IN;
+    q.dst = BUF_OUT;
+    int rc = choose_line(n0, s->opts.radix_order, true, &q.line, err);
+    if (rc)
+        return rc;
+    q.line2 = q.line;
+    if (q.line.fixed < 0)
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    q.tw_seg[0] = line_seg(s, q.line);
+    int twlen = tw_slots_h((int)s->tw[q.tw_seg[0]].m.size());
+    q.lpt = 16;
+    q.threads = q.line.T * q.lpt;
+    if (q.threads > 1024)
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    q.smem_bytes = twlen * 8 + q.lpt * pitch_h(n0) * 8;
+    int64_t N = (int64_t)n0 * n1 * n2;
+    q.g = PassGeom{};
+    q.g.C = n1; q.g.A = n2; q.g.B = batch;
+    q.g.ij = 1; q.g.ic = n0; q.g.ia = (int64_t)n0 * n1; q.g.ib = N;
+    q.g.ok = 1; q.g.oc = n0; q.g.oa = q.g.ia; q.g.ob = N;
+    q.tiles_c = n1 / q.lpt; // x tiles per slab (= y tiles per slab for square slabs)
+    q.ntiles = 2 * q.tiles_c * n2 * batch;
+    *out = q;
+    return FFT3_OK;
+}
+
+int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int direction,
+                   const fft3_options *opts, Schedule *out, std::string *err)
+{
+    init_meta();
+    if (n0 < 1 || n1 < 1 || n2 < 1 || batch < 1) {
+        *err = "sizes and batch must be positive";
+        return FFT3_ERR_INVALID_ARG;
+    }
+    if (direction != FFT3_FORWARD && direction != FFT3_INVERSE) {
+        *err = "direction must be FFT3_FORWARD (-1) or FFT3_INVERSE (+1)";
+        return FFT3_ERR_INVALID_ARG;
+    }
+    if (dtype != FFT3_C64_FP32 && dtype != FFT3_C64_SPLITBF16_TC) {
+        *err = "unknown dtype";
+        return FFT3_ERR_INVALID_ARG;
+    }
+    if (decomp < 0 || decomp > FFT3_AUTO) {
+        *err = "unknown decomposition";
+        return FFT3_ERR_INVALID_ARG;
+    }
+    int ns[3] = {n0, n1, n2};
+    for (int d = 0; d < 3; ++d) {
+        int e2, e3, e5;
+        if (!smooth235(ns[d], &e2, &e3, &e5)) {
+            *err = "dimension " + std::to_string(ns[d]) + " has a prime factor other than 2, 3, 5";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        if (ns[d] > kMaxLine) {
+            *err = "dimension " + std::to_string(ns[d]) + " exceeds " + std::to_string(kMaxLine);
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+    }
+    Schedule s;
+    s.n0 = n0; s.n1 = n1; s.n2 = n2; s.batch = batch;
+    s.dtype = dtype; s.direction = direction;
+    if (opts)
+        s.opts = *opts;
+    if (decomp == FFT3_AUTO) {
+        // Fixed default when no cost model is loaded: slab-pencil when the
+        // slab stage can be fused (fewest HBM sweeps), else pencil-pencil-pencil.
+        int twl = 2 * tw_slots_h(n0) + 2 * tw_slots_h(n1);
+        if (slab_smem(n0, n1, twl) <= kSmemLimit || slab_l2_supported(n0, n1))
+            decomp = FFT3_SLAB_PENCIL;
+        else
+            decomp = FFT3_PENCIL3;
+    }
+    s.decomp = decomp;
+    int64_t N = (int64_t)n0 * n1 * n2;
+    int rc = FFT3_OK;
+    int cur = BUF_IN;
+    auto add_nat = [&](int d) -> int {
+        if (ns[d] == 1)
+            return FFT3_OK;
+        PassPlan p;
+        int r = make_line_pass(&s, d, ns[d], geom_natural(d, n0, n1, n2, batch), false, cur, BUF_OUT,
+                               &p, err);
+        if (r)
+            return r;
+        s.passes.push_back(p);
+        cur = BUF_OUT;
+        return FFT3_OK;
+    };
+    if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_ROTATE) {
+        int bufs[3][2] = {{BUF_IN, BUF_OUT}, {BUF_OUT, BUF_WS}, {BUF_WS, BUF_OUT}};
+        for (int d = 0; d < 3; ++d) {
+            PassPlan p;
+            rc = make_line_pass(&s, d, ns[d], geom_rotate(d, n0, n1, n2, batch), true, bufs[d][0],
+                                bufs[d][1], &p, err);
+            if (rc)
+                return rc;
+            s.passes.push_back(p);
+        }
+        s.need_ws = true;
+    } else if (decomp == FFT3_PENCIL3) {
+        for (int d = 0; d < 3 && !rc; ++d)
+            rc = add_nat(d);
+    } else if (decomp == FFT3_SLAB_PENCIL) {
+        int mode = s.opts.slab_mode;
+        int twl = 2 * tw_slots_h(n0) + 2 * tw_slots_h(n1);
+        bool fits_smem = slab_smem(n0, n1, twl) <= kSmemLimit;
+        if (mode == 0)
+            mode = fits_smem ? 1 : (slab_l2_supported(n0, n1) ? 2 : 3);
+        PassPlan p;
+        if (mode == 1 && fits_smem) {
+            rc = make_slab_pass(&s, n0, n1, n2, batch, &p, err);
+            if (rc)
+                return rc;
+            s.passes.push_back(p);
+            cur = BUF_OUT;
+        } else if (mode == 2 && slab_l2_supported(n0, n1)) {
+            rc = make_slab_l2_pass(&s, n0, n1, n2, batch, &p, err);
+            if (rc)
+                return rc;
+            s.passes.push_back(p);
+            cur = BUF_OUT;
+        } else if (mode == 1 || mode == 2) {
+            *err = "requested slab mode is not available for this slab size";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        } else {
+            // unfused slab stage: x lines then y lines as two passes
+            rc = add_nat(0);
+            if (!rc)
+                rc = add_nat(1);
+        }
+        if (!rc)
+            rc = add_nat(2);
+    } else { // volumetric
+        for (int d = 0; d < 3 && !rc; ++d) {
+            if (ns[d] == 1)
+                continue;
+            int p = s.opts.mesh[d];
+            bool explicit_mesh = p > 0;
+            if (!explicit_mesh) {
+                p = 2; // the paper's smallest 3D mesh is 2 x 2 x 2
+                int a, b;
+                if (!volumetric_split(ns[d], p, &a, &b))
+                    p = 1;
+            }
+            if (p != 1 && p != 2 && p != 4 && p != 8) {
+                *err = "volumetric mesh extents must be 1, 2, 4 or 8";
+                return FFT3_ERR_INVALID_ARG;
+            }
+            PassGeom g = geom_natural(d, n0, n1, n2, batch);
+            PassPlan q;
+            if (p == 1) {
+                rc = make_line_pass(&s, d, ns[d], g, false, cur, BUF_OUT, &q, err);
+            } else {
+                rc = make_vol_pass(&s, d, ns[d], p, g, cur, BUF_OUT, &q, err);
+            }
+            if (rc)
+                return rc;
+            s.passes.push_back(q);
+            cur = BUF_OUT;
+        }
+    }
+    if (rc)
+        return rc;
+    if (s.passes.empty()) {
+        PassPlan p;
+        p.kind = PK_COPY;
+        p.src = BUF_IN;
+        p.dst = BUF_OUT;
+        p.g = PassGeom{};
+        p.g.C = N * batch;
+        p.g.A = 1; p.g.B = 1;
+        p.g.ij = 1; p.g.ok = 1;
+        p.threads = 256;
+        s.passes.push_back(p);
+    }
+    (void)N;
+    *out = std::move(s);
+    return FFT3_OK;
+}
+
+// ---------------------------------------------------------------- JSON --- //
+static const char *kind_name(int k)
+{
+    static const char *names[] = {"line_contig", "line_contig_rotate", "line_strided", "line_runtime",
+                                  "slab_smem", "slab_l2", "volumetric_split", "copy", "line_tc"};
+    return (k >= 0 && k <= 8) ? names[k] : "?";
+}
+static const char *buf_name(int b)
+{
+    return b == BUF_IN ? "in" : (b == BUF_OUT ? "out" : "workspace");
+}
+static const char *decomp_name(int d)
+{
+    return d == FFT3_SLAB_PENCIL ? "slab_pencil"
+           : d == FFT3_PENCIL3  ? "pencil_pencil_pencil"
+           : d == FFT3_VOLUMETRIC ? "volumetric" : "auto";
+}
+
+static void line_json(std::ostringstream &o, const LineChoice &l)
+{
+    o << "{\"n\":" << l.n << ",\"fixed\":" << l.fixed << ",\"T\":" << l.T << ",\"radices\":[";
+    for (int i = 0; i < l.nst; ++i)
+        o << (i ? "," : "") << l.rad[i];
+    o << "]}";
+}
+
+std::string Schedule::json() const
+{
+    std::ostringstream o;
+    int64_t N = (int64_t)n0 * n1 * n2 * batch;
+    o << "{\"dims\":[" << n0 << "," << n1 << "," << n2 << "],\"batch\":" << batch
+      << ",\"dtype\":" << dtype << ",\"direction\":" << direction << ",\"decomposition\":\""
+      << decomp_name(decomp) << "\",\"variant\":" << opts.variant
+      << ",\"workspace_bytes\":" << (need_ws ? N * 8 : 0) << ",\"hbm_sweeps\":" << passes.size()
+      << ",\"twiddle_entries\":" << tw_total << ",\"passes\":[";
+    for (size_t i = 0; i < passes.size(); ++i) {
+        const PassPlan &p = passes[i];
+        o << (i ? "," : "") << "{\"kind\":\"" << kind_name(p.kind) << "\",\"dim\":" << p.dim
+          << ",\"src\":\"" << buf_name(p.src) << "\",\"dst\":\"" << buf_name(p.dst)
+          << "\",\"line\":";
+        line_json(o, p.line);
+        if (p.kind == PK_SLAB || p.kind == PK_VOL || p.kind == PK_SLABL2) {
+            o << ",\"line2\":";
+            line_json(o, p.line2);
+        }
+        o << ",\"lpt\":" << p.lpt << ",\"threads\":" << p.threads << ",\"smem\":" << p.smem_bytes
+          << ",\"tiles\":" << p.ntiles;
+        if (p.kind == PK_VOL)
+            o << ",\"p\":" << p.p << ",\"a\":" << p.split_a << ",\"b\":" << p.split_b;
+        const PassGeom &g = p.g;
+        o << ",\"geom\":{\"C\":" << g.C << ",\"A\":" << g.A << ",\"B\":" << g.B << ",\"ij\":" << g.ij
+          << ",\"ic\":" << g.ic << ",\"ia\":" << g.ia << ",\"ib\":" << g.ib << ",\"ok\":" << g.ok
+          << ",\"oc\":" << g.oc << ",\"oa\":" << g.oa << ",\"ob\":" << g.ob << "}}";
+    }
+    o << "]}";
+    return o.str();
+}
+
+} // namespace fft3

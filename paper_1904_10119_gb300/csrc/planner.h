@@ -1,0 +1,86 @@
+// planner.h -- host-side lowering of a 3D DFT decomposition to a schedule of
+// passes with fused load/store maps (no CUDA calls; testable without a GPU).
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fft3.h"
+#include "geom.h"
+
+namespace fft3 {
+
+enum PassKind {
+    PK_J = 0,      // fixed plan, contiguous lines, direct store
+    PK_JROT = 1,   // fixed plan, contiguous lines, rotated (transposed) store
+    PK_C = 2,      // fixed plan, strided columns
+    PK_G = 3,      // runtime radix list, staged through shared memory
+    PK_SLAB = 4,   // 2D DFT of whole n0 x n1 slabs in one block's shared memory
+    PK_SLABL2 = 5, // 2D slab DFT: x and y tiles in one persistent launch, slab kept in L2
+    PK_VOL = 6,    // 1D DFT split n = a*b over a cluster of p blocks (DSMEM exchange)
+    PK_COPY = 7,   // all dimensions of length 1: plain copy
+    PK_TC = 8,     // split-BF16 tensor-core line pass
+};
+
+enum BufId { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };
+
+struct LineChoice {
+    int n = 1;
+    int fixed = -1; // fixed plan id, -1 = runtime radix list
+    int T = 1;      // threads per line
+    int nst = 0;
+    int rad[kMaxStages] = {0};
+};
+
+// Twiddle segment: w_n^{m} for the listed exponents, in order.
+struct TwSeg {
+    int n;
+    std::vector<int64_t> m;
+    int64_t off = 0; // element offset in the plan's device table
+};
+
+struct PassPlan {
+    int kind = PK_G;
+    int dim = 0; // 0/1/2 transformed dimension; 3 = slab (0 and 1)
+    LineChoice line; // 1D passes; slab: x lines
+    LineChoice line2; // slab: y lines; volumetric: the a-length sub-lines
+    PassGeom g{};
+    int src = BUF_IN, dst = BUF_OUT;
+    int lpt = 1;
+    int tw_seg[3] = {-1, -1, -1}; // segments used (line, line2, split twiddle)
+    // volumetric split
+    int p = 1, split_a = 1, split_b = 1;
+    int threads = 0;     // block size
+    int smem_bytes = 0;  // dynamic shared memory per block
+    int64_t ntiles = 0, tiles_c = 0;
+    int slabs_per_chunk = 0;
+};
+
+struct Schedule {
+    int n0 = 1, n1 = 1, n2 = 1, batch = 1;
+    int dtype = FFT3_C64_FP32, decomp = FFT3_PENCIL3, direction = FFT3_FORWARD;
+    fft3_options opts{};
+    std::vector<PassPlan> passes;
+    std::vector<TwSeg> tw;
+    int64_t tw_total = 0;
+    bool need_ws = false;
+    std::string json() const;
+};
+
+// Radix list for a line of length n under radix order `order` (runtime path).
+int factorize(int n, int order, int *rad, int cap);
+
+// Returns FFT3_OK or an FFT3_ERR_* code (message in *err).
+int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int direction,
+                   const fft3_options *opts, Schedule *out, std::string *err);
+
+// Lines per tile and shared memory of the runtime-radix kernel for a pass.
+void generic_launch_shape(int n, int T, bool strided, int tw_len, int *lpt, int *threads,
+                          int *smem);
+
+constexpr int kMaxLine = 4096;
+constexpr int kSmemLimit = 227 * 1024;
+
+} // namespace fft3

@@ -1,0 +1,69 @@
+// plans.h -- the line-transform plans compiled ahead of time.
+//
+// Each row: id, line length N, threads per line T, radix list (first stage
+// first).  The same list drives the device template instantiations
+// (k_fixed.cu) and the host planner's metadata (planner.cpp), so the two can
+// not disagree on a radix order.  Lengths without a row run through the
+// runtime-radix kernel (any 2*3*5-smooth length up to 4096).
+//
+// Candidates for one length are listed best-first by default; the planner's
+// `radix_order` option (and the autotuner) picks among them.
+#pragma once
+
+#define FFT3_FIXED_PLANS_A(X)          \
+    X(0, 1024, 64, 16, 16, 4)          \
+    X(1, 1024, 64, 4, 16, 16)          \
+    X(2, 1024, 32, 16, 16, 4)          \
+    X(3, 1024, 64, 8, 8, 16)           \
+    X(4, 512, 32, 16, 8, 4)            \
+    X(5, 512, 64, 8, 8, 8)             \
+    X(6, 512, 32, 4, 8, 16)
+
+#define FFT3_FIXED_PLANS_B(X)          \
+    X(7, 256, 16, 16, 16)              \
+    X(8, 256, 32, 8, 8, 4)             \
+    X(9, 256, 16, 4, 4, 16)            \
+    X(10, 128, 8, 16, 8)               \
+    X(11, 128, 16, 8, 16)              \
+    X(12, 64, 4, 16, 4)                \
+    X(13, 64, 8, 8, 8)                 \
+    X(14, 64, 16, 4, 4, 4)             \
+    X(15, 32, 4, 8, 4)                 \
+    X(16, 32, 2, 16, 2)                \
+    X(17, 16, 1, 16)                   \
+    X(18, 16, 4, 4, 4)                 \
+    X(19, 8, 1, 8)                     \
+    X(20, 4, 1, 4)                     \
+    X(21, 2, 1, 2)
+
+#define FFT3_FIXED_PLANS(X) FFT3_FIXED_PLANS_A(X) FFT3_FIXED_PLANS_B(X)
+
+namespace fft3 {
+
+struct FixedPlanMeta {
+    int id, n, T, nrad;
+    int rad[8];
+};
+
+// Host copy of the list above.
+int fixed_plan_count();
+const FixedPlanMeta &fixed_plan_meta(int id);
+
+// Device entry points compiled for one fixed plan (nullptr = not compiled).
+struct FixedKernels {
+    int id;
+    const void *j;    // k_pass_j, direct store
+    const void *jrot; // k_pass_j, rotated store
+    const void *c16;  // k_pass_c, 16 lines per tile
+    const void *c8;   // k_pass_c, 8 lines per tile
+    const void *l2;   // k_slab_l2 (square slabs), 0 if not compiled
+};
+const FixedKernels *fixed_kernels(int id);
+
+// Lines per tile of each compiled kernel kind for a plan with T threads per
+// line (0 = not compiled).
+constexpr int lpt_j(int T) { return T >= 256 ? 1 : 256 / T; }
+constexpr int lpt_rot(int T) { return T >= 64 ? 8 : (128 / T > 16 ? 128 / T : 16); }
+constexpr int lpt_c(int T, int want) { return T * want <= 1024 ? want : 0; }
+
+} // namespace fft3

@@ -1,0 +1,157 @@
+"""Host-side checks of the C-ABI library: it loads without a GPU, exports every
+entry point include/fft3.h declares, and its planner (pure host code) lowers
+each decomposition to the expected pass schedule."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from paper_1904_10119_gb300 import fft3
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return fft3.load()
+
+
+def test_library_exports_every_header_symbol(lib):
+    syms = fft3.header_symbols()
+    assert len(syms) >= 18
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_version(lib):
+    assert lib.fft3_version() >= 1
+
+
+@pytest.mark.parametrize("n,order,expect", [
+    (1024, 0, [16, 16, 4]), (1024, 1, [4, 16, 16]), (1024, 2, [4, 4, 4, 4, 4]), (1024, 3, [8, 8, 8, 2]),
+    (96, 0, [16, 2, 3]), (1000, 0, [8, 5, 5, 5]), (1, 0, []), (2, 0, [2]), (45, 0, [5, 3, 3])])
+def test_factorize(n, order, expect):
+    r = fft3.fft3_factorize(n, order)
+    assert r == expect
+    assert math.prod(r) == n
+
+
+def test_factorize_rejects_large_primes():
+    for n in (7, 14, 11 * 16, 1023):
+        with pytest.raises(fft3.Fft3Error) as e:
+            fft3.fft3_factorize(n)
+        assert e.value.code == -2
+
+
+def test_every_smooth_size_factorizes_into_supported_radices():
+    from paper_1904_10119_gb300 import synth
+    for n in synth.smooth_sizes(2, 4096):
+        for order in range(4):
+            r = fft3.fft3_factorize(n, order)
+            assert math.prod(r) == n and set(r) <= {2, 3, 4, 5, 8, 16}
+
+
+def _kinds(s):
+    return [p["kind"] for p in s["passes"]]
+
+
+def test_schedule_pencil3_natural():
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_PENCIL3, -1)
+    assert s["decomposition"] == "pencil_pencil_pencil"
+    assert _kinds(s) == ["line_contig", "line_strided", "line_strided"]
+    assert [p["dim"] for p in s["passes"]] == [0, 1, 2]
+    assert [(p["src"], p["dst"]) for p in s["passes"]] == [("in", "out"), ("out", "out"), ("out", "out")]
+    assert s["workspace_bytes"] == 0
+    # z pass: element stride n0*n1, columns contiguous
+    g = s["passes"][2]["geom"]
+    assert g["ij"] == 1024 * 1024 and g["ic"] == 1 and g["C"] == 1024 * 1024
+
+
+def test_schedule_pencil3_rotate_geometry():
+    n0, n1, n2 = 8, 12, 20
+    s = fft3.fft3_plan_schedule(n0, n1, n2, 1, 0, fft3.FFT3_PENCIL3, -1, fft3.make_options(variant=1))
+    assert [(p["src"], p["dst"]) for p in s["passes"]] == [("in", "out"), ("out", "workspace"),
+                                                          ("workspace", "out")]
+    assert s["workspace_bytes"] == n0 * n1 * n2 * 8
+    g0, g1, g2 = [p["geom"] for p in s["passes"]]
+    # x pass: reads xyz, writes yzx (y fastest, then z, then x)
+    assert (g0["ij"], g0["ic"], g0["ia"]) == (1, n0, n0 * n1)
+    assert (g0["oc"], g0["oa"], g0["ok"]) == (1, n1, n1 * n2)
+    # y pass: reads yzx, writes zxy
+    assert (g1["ij"], g1["ic"], g1["ia"]) == (1, n1, n1 * n2)
+    assert (g1["oc"], g1["oa"], g1["ok"]) == (1, n2, n2 * n0)
+    # z pass: reads zxy, writes xyz
+    assert (g2["ij"], g2["ic"], g2["ia"]) == (1, n2, n2 * n0)
+    assert (g2["oc"], g2["oa"], g2["ok"]) == (1, n0, n0 * n1)
+
+
+def test_schedule_slab_pencil_modes():
+    s = fft3.fft3_plan_schedule(64, 64, 64, 1, 0, fft3.FFT3_SLAB_PENCIL, -1)
+    assert _kinds(s) == ["slab_smem", "line_strided"]
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_SLAB_PENCIL, -1)
+    assert _kinds(s) == ["slab_l2", "line_strided"]
+    s = fft3.fft3_plan_schedule(1024, 1024, 64, 1, 0, fft3.FFT3_SLAB_PENCIL, -1,
+                                fft3.make_options(slab_mode=3))
+    assert _kinds(s) == ["line_contig", "line_strided", "line_strided"]
+    with pytest.raises(fft3.Fft3Error):
+        fft3.fft3_plan_schedule(640, 640, 8, 1, 0, fft3.FFT3_SLAB_PENCIL, -1, fft3.make_options(slab_mode=2))
+
+
+def test_schedule_volumetric_split_rule():
+    """One exchange per dimension needs n = a*b with p | a and p | b (Section 3.2)."""
+    s = fft3.fft3_plan_schedule(1024, 256, 64, 1, 0, fft3.FFT3_VOLUMETRIC, -1,
+                                fft3.make_options(mesh=(2, 4, 8)))
+    assert _kinds(s) == ["volumetric_split"] * 3
+    for p, mesh in zip(s["passes"], (2, 4, 8)):
+        assert p["p"] == mesh and p["a"] % mesh == 0 and p["b"] % mesh == 0
+        assert p["a"] * p["b"] == [1024, 256, 64][p["dim"]]
+    # 24 = a*b with 4 | a and 4 | b has no solution
+    with pytest.raises(fft3.Fft3Error) as e:
+        fft3.fft3_plan_schedule(24, 16, 16, 1, 0, fft3.FFT3_VOLUMETRIC, -1, fft3.make_options(mesh=(4, 2, 2)))
+    assert e.value.code == -2
+    # auto mesh falls back to an unsplit pass where p = 2 is infeasible (n = 6 = 2*3)
+    s = fft3.fft3_plan_schedule(6, 16, 16, 1, 0, fft3.FFT3_VOLUMETRIC, -1)
+    assert _kinds(s)[0] in ("line_runtime", "line_contig") and _kinds(s)[1] == "volumetric_split"
+
+
+def test_schedule_unit_dims_and_copy():
+    s = fft3.fft3_plan_schedule(1, 64, 1, 1, 0, fft3.FFT3_PENCIL3, -1)
+    assert [p["dim"] for p in s["passes"]] == [1] and s["passes"][0]["src"] == "in"
+    s = fft3.fft3_plan_schedule(1, 1, 1, 5, 0, fft3.FFT3_PENCIL3, -1)
+    assert _kinds(s) == ["copy"]
+
+
+@pytest.mark.parametrize("args,code", [
+    ((0, 4, 4, 1, 0, 1, -1), -1), ((4, 4, 4, 0, 0, 1, -1), -1), ((4, 4, 4, 1, 7, 1, -1), -1),
+    ((4, 4, 4, 1, 0, 9, -1), -1), ((4, 4, 4, 1, 0, 1, 0), -1), ((7, 4, 4, 1, 0, 1, -1), -2),
+    ((8192, 4, 4, 1, 0, 1, -1), -2)])
+def test_schedule_rejects_bad_arguments(args, code):
+    with pytest.raises(fft3.Fft3Error) as e:
+        fft3.fft3_plan_schedule(*args)
+    assert e.value.code == code
+
+
+def test_parallelism_limits_become_tile_counts():
+    """Section 2.5: slab parallelism is bounded by the slab count, pencil
+    parallelism by the number of lines; the planner's tile counts follow."""
+    s = fft3.fft3_plan_schedule(64, 32, 16, 2, 0, fft3.FFT3_SLAB_PENCIL, -1)
+    assert s["passes"][0]["tiles"] == 16 * 2                  # one tile per slab
+    s = fft3.fft3_plan_schedule(64, 32, 16, 1, 0, fft3.FFT3_PENCIL3, -1)
+    x, y, z = s["passes"]
+    assert x["tiles"] * x["lpt"] >= 32 * 16 and y["tiles"] * y["lpt"] >= 64 * 16
+    assert z["tiles"] * z["lpt"] >= 64 * 32
+
+
+def test_create_without_gpu_reports_no_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    h = ctypes.c_void_p()
+    rc = lib.fft3_plan_create(ctypes.byref(h), 8, 8, 8, 1, 0, 1, -1)
+    assert rc == -7 and not h.value
+    assert "device" in fft3.last_error()
+
+
+def test_null_arguments(lib):
+    assert lib.fft3_plan_create(None, 8, 8, 8, 1, 0, 1, -1) == -1
+    assert lib.fft3_plan_execute(None, None, None, None) == -1
+    assert lib.fft3_plan_destroy(None) == -1

@@ -1,0 +1,72 @@
+"""Parity at the benchmark's full sizes (256^3, 512^3, 1024^3 complex64,
+out-of-place, forward and inverse) in the launch configuration bench.py
+times.  256^3 is compared element by element with the oracle; at 512^3 and
+1024^3 the oracle computes a sample of outputs one by one (separable
+definition restricted to sampled frequencies), and Parseval's identity is
+checked over the whole array."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1904_10119_gb300 import fft3, synth
+from tests.gpu_util import MAXABS_TOL, REL_L2_TOL
+
+pytestmark = pytest.mark.gpu
+
+DECOMPS = [("slab_pencil", fft3.FFT3_SLAB_PENCIL, {}), ("ppp", fft3.FFT3_PENCIL3, {}),
+           ("ppp_rotate", fft3.FFT3_PENCIL3, {"variant": 1}), ("volumetric", fft3.FFT3_VOLUMETRIC, {})]
+
+
+def _run(n, x_dev, out_dev, decomp, direction, opts):
+    plan = fft3.Plan(n, n, n, 1, decomposition=decomp, direction=direction, **opts)
+    plan.execute(x_dev, out_dev)
+    torch.cuda.synchronize()
+    assert plan.check() == 0
+    plan.close()
+
+
+@pytest.mark.parametrize("name,decomp,opts", DECOMPS)
+def test_256cubed_elementwise(name, decomp, opts):
+    n = 256
+    x = synth.uniform_c64((1, n, n, n), 2)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    for direction in (fft3.FFT3_FORWARD, fft3.FFT3_INVERSE):
+        _run(n, xd, out, decomp, direction, opts)
+        ref = oracle.fft3(x.ravel(), n, n, n, sign=direction)
+        got = out.cpu().numpy()
+        assert oracle.rel_l2(got, ref) <= REL_L2_TOL and oracle.max_abs_ratio(got, ref) <= MAXABS_TOL
+
+
+def _sampled_check(x, got, n, direction, seed):
+    rng = np.random.default_rng(seed)
+    ks = [np.unique(np.concatenate([[0, n - 1, n // 2], rng.integers(0, n, 5)])) for _ in range(3)]
+    ref = oracle.dft3_sampled(x.reshape(n, n, n), n, n, n, ks[0], ks[1], ks[2], sign=direction)
+    g = got.reshape(n, n, n)[np.ix_(ks[2], ks[1], ks[0])].transpose(2, 1, 0)
+    rel = oracle.rel_l2(g, ref)
+    mx = float(np.max(np.abs(g - ref)) / np.max(np.abs(got)))
+    assert rel <= REL_L2_TOL and mx <= MAXABS_TOL, (rel, mx)
+    # Parseval over the whole array: sum |X|^2 = N sum |x|^2
+    N = float(n) ** 3
+    sx = float(np.sum(np.abs(x.astype(np.complex128)) ** 2))
+    sX = float(np.sum(np.abs(got.astype(np.complex128)) ** 2))
+    assert abs(sX - N * sx) <= 1e-5 * N * sx
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_fullsize_sampled(n):
+    x = synth.uniform_c64((1, n, n, n), 3 if n == 512 else 4)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    host = torch.empty(out.shape, dtype=torch.complex64).pin_memory()
+    for name, decomp, opts in DECOMPS + [("auto", fft3.FFT3_AUTO, {})]:
+        for direction in (fft3.FFT3_FORWARD, fft3.FFT3_INVERSE):
+            if direction == fft3.FFT3_INVERSE and name not in ("auto", "ppp"):
+                continue
+            out.fill_(float("nan"))
+            _run(n, xd, out, decomp, direction, opts)
+            host.copy_(out)
+            _sampled_check(x, host.numpy(), n, direction, 17 * len(name) + n)
+    del xd, out
+    torch.cuda.empty_cache()

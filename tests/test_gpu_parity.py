@@ -1,0 +1,168 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by
+element, at sizes that span several tiles and a ragged tail, for every
+decomposition, both directions, several radix orders and the degenerate
+shapes (unit dimensions, a single element)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1904_10119_gb300 import fft3, synth
+from tests.gpu_util import assert_parity, run_plan
+
+pytestmark = pytest.mark.gpu
+
+S, P, V = fft3.FFT3_SLAB_PENCIL, fft3.FFT3_PENCIL3, fft3.FFT3_VOLUMETRIC
+FWD, INV = fft3.FFT3_FORWARD, fft3.FFT3_INVERSE
+
+
+def test_config_64cubed_ppp_forward_against_direct_sum():
+    """64^3 forward, pencil-pencil-pencil, FP32, seed 1, direct-sum oracle."""
+    x = synth.uniform_c64((1, 64, 64, 64), 1)
+    x, got, plan = run_plan((64, 64, 64), 1, P, FWD, x=x)
+    ref = oracle.fft3(x.ravel(), 64, 64, 64, method=oracle.METHOD_DIRECT)
+    assert oracle.rel_l2(got, ref) <= 1e-5 and oracle.max_abs_ratio(got, ref) <= 1e-4
+    assert plan.launches() == 3
+
+
+SHAPES = [((64, 64, 64), 1), ((96, 80, 48), 2), ((30, 25, 18), 1), ((1024, 8, 6), 1), ((8, 1024, 6), 1),
+          ((6, 8, 1024), 1), ((512, 24, 10), 1), ((20, 512, 12), 1), ((256, 12, 40), 2),
+          ((16, 16, 16), 3), ((128, 36, 50), 1), ((45, 27, 75), 1)]
+
+
+@pytest.mark.parametrize("shape,batch", SHAPES)
+@pytest.mark.parametrize("decomp", [S, P, V])
+def test_forward_parity(shape, batch, decomp):
+    x, got, _ = run_plan(shape, batch, decomp, FWD, seed=sum(shape) + batch)
+    assert_parity(x, got, shape, batch, FWD)
+
+
+@pytest.mark.parametrize("shape,batch", [((64, 64, 64), 1), ((96, 80, 48), 2), ((1024, 8, 6), 1),
+                                         ((6, 8, 1024), 1), ((30, 25, 18), 1)])
+@pytest.mark.parametrize("decomp", [S, P, V])
+def test_inverse_parity(shape, batch, decomp):
+    x, got, _ = run_plan(shape, batch, decomp, INV, seed=7 + batch)
+    assert_parity(x, got, shape, batch, INV)
+
+
+@pytest.mark.parametrize("shape,batch", [((64, 64, 64), 1), ((96, 80, 48), 2), ((1024, 12, 10), 1),
+                                         ((10, 20, 1024), 1), ((16, 16, 16), 4), ((1, 32, 5), 2)])
+def test_pencil3_rotate_parity(shape, batch):
+    x, got, plan = run_plan(shape, batch, P, FWD, seed=3, variant=fft3.FFT3_PPP_ROTATE)
+    assert_parity(x, got, shape, batch, FWD)
+    assert fft3.fft3_plan_workspace_bytes(plan.handle) == np.prod(shape) * batch * 8
+    x, got, _ = run_plan(shape, batch, P, INV, seed=4, variant=fft3.FFT3_PPP_ROTATE)
+    assert_parity(x, got, shape, batch, INV)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [(1024, 16, 8), (512, 40, 6), (256, 256, 4), (64, 48, 96), (640, 6, 10)])
+def test_radix_orders(shape, order):
+    x, got, _ = run_plan(shape, 1, P, FWD, seed=order, radix_order=order)
+    assert_parity(x, got, shape)
+
+
+@pytest.mark.parametrize("mode,shape", [(1, (64, 64, 20)), (1, (96, 96, 8)), (2, (256, 256, 6)),
+                                        (2, (512, 512, 3)), (3, (256, 256, 6)), (3, (100, 60, 12))])
+def test_slab_modes(mode, shape):
+    x, got, plan = run_plan(shape, 1, S, FWD, seed=mode, slab_mode=mode)
+    assert_parity(x, got, shape)
+    kinds = [p["kind"] for p in plan.describe()["passes"]]
+    assert kinds[0] == {1: "slab_smem", 2: "slab_l2", 3: "line_contig"}[mode] or mode == 3
+
+
+@pytest.mark.parametrize("mesh,shape", [((2, 2, 2), (64, 64, 64)), ((4, 4, 4), (64, 64, 64)),
+                                        ((8, 2, 4), (256, 32, 64)), ((2, 8, 4), (36, 256, 16)),
+                                        ((4, 2, 8), (1024, 16, 64)), ((1, 4, 2), (30, 64, 36))])
+def test_volumetric_meshes(mesh, shape):
+    x, got, plan = run_plan(shape, 1, V, FWD, seed=11, mesh=mesh)
+    assert_parity(x, got, shape)
+    d = plan.describe()
+    for p in d["passes"]:
+        if p["kind"] == "volumetric_split":
+            assert p["a"] % p["p"] == 0 and p["b"] % p["p"] == 0
+
+
+@pytest.mark.parametrize("shape,batch", [((1, 64, 16), 1), ((64, 1, 1), 2), ((1, 1, 1), 3), ((1, 1, 96), 1),
+                                         ((2, 3, 5), 1), ((5, 1, 3), 4)])
+@pytest.mark.parametrize("decomp", [S, P, V])
+def test_degenerate_shapes(shape, batch, decomp):
+    x, got, _ = run_plan(shape, batch, decomp, FWD, seed=5)
+    assert_parity(x, got, shape, batch)
+
+
+def test_closed_forms_on_gpu():
+    n0, n1, n2 = 64, 48, 40
+    N = n0 * n1 * n2
+    x = np.zeros((1, n2, n1, n0), np.complex64)
+    x[0, 0, 0, 0] = 1
+    _, got, _ = run_plan((n0, n1, n2), 1, S, FWD, x=x)
+    assert np.max(np.abs(got - 1)) < 1e-6
+    x = np.full((1, n2, n1, n0), 0.5 + 0.25j, np.complex64)
+    _, got, _ = run_plan((n0, n1, n2), 1, P, FWD, x=x)
+    expect = np.zeros(N, np.complex128)
+    expect[0] = (0.5 + 0.25j) * N
+    assert np.max(np.abs(got.ravel() - expect)) < 1e-5 * N
+
+
+def test_round_trip_is_N_times_identity():
+    shape = (96, 64, 40)
+    N = int(np.prod(shape))
+    x = synth.uniform_c64((1, 40, 64, 96), 9)
+    _, y, _ = run_plan(shape, 1, S, FWD, x=x)
+    _, z, _ = run_plan(shape, 1, P, INV, x=y)
+    assert oracle.rel_l2(z / N, x) < 2e-6
+
+
+def test_hdr_inputs():
+    shape = (128, 64, 32)
+    x = synth.hdr_c64((1, 32, 64, 128), 6)
+    for d in (S, P, V):
+        _, got, _ = run_plan(shape, 1, d, FWD, x=x)
+        assert_parity(x, got, shape)
+
+
+def test_execute_host_buffers():
+    shape = (64, 40, 24)
+    x = synth.uniform_c64((2, 24, 40, 64), 12)
+    h = fft3.fft3_plan_create_ex(*shape, 2, 0, S, FWD, fft3.make_options())
+    try:
+        xin = torch.from_numpy(x).pin_memory()
+        out = torch.empty_like(xin).pin_memory()
+        fft3.fft3_plan_execute_host(h, xin.data_ptr(), out.data_ptr(), 0)
+        assert_parity(x, out.numpy(), shape, 2)
+    finally:
+        fft3.fft3_plan_destroy(h)
+
+
+def test_per_pass_execution_composes_to_the_transform():
+    shape = (256, 64, 32)
+    x = synth.uniform_c64((1, 32, 64, 256), 13)
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    plan = fft3.Plan(*shape, 1, decomposition=P, variant=fft3.FFT3_PPP_ROTATE)
+    for k in range(plan.launches()):
+        fft3.fft3_plan_execute_pass(plan.handle, k, xt.data_ptr(), out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert_parity(x, out.cpu().numpy(), shape)
+
+
+def test_error_paths():
+    xt = torch.zeros(8 * 8 * 8, dtype=torch.complex64, device="cuda")
+    h = fft3.fft3_plan_create(8, 8, 8, 1, 0, P, FWD)
+    try:
+        with pytest.raises(fft3.Fft3Error) as e:
+            fft3.fft3_plan_execute(h, xt.data_ptr(), xt.data_ptr(), 0)
+        assert e.value.code == -6
+        with pytest.raises(fft3.Fft3Error) as e:
+            fft3.fft3_plan_execute_pass(h, 99, xt.data_ptr(), xt.data_ptr() + 4096, 0)
+        assert e.value.code in (-1, -6)
+    finally:
+        fft3.fft3_plan_destroy(h)
+    for bad in [(7, 8, 8), (8, 8, 11 * 2), (8192, 2, 2)]:
+        with pytest.raises(fft3.Fft3Error) as e:
+            fft3.fft3_plan_create(*bad, 1, 0, P, FWD)
+        assert e.value.code == -2
+    # the context is still usable
+    x, got, _ = run_plan((16, 16, 16), 1, P, FWD)
+    assert_parity(x, got, (16, 16, 16))

@@ -364,3 +364,16 @@ def test_adam_first_step_moves_by_lr_times_sign():
     new_p, new_m, new_v = oracle.adam_step(p, g, m, v, t=1, lr=0.01)
     assert np.allclose(new_p[0], p[0] - 0.01 * np.sign(g[0]), rtol=0, atol=1e-7)
     assert np.allclose(new_m[0], 0.1 * g[0]) and np.allclose(new_v[0], 0.001 * g[0] ** 2)
+
+
+def test_sampled_outputs_equal_full_transform():
+    n0, n1, n2 = 24, 20, 18
+    x = _rand(n0 * n1 * n2, 31).reshape(n2, n1, n0)
+    full = oracle.fft3(x.ravel(), n0, n1, n2)
+    k0s, k1s, k2s = [0, 5, 23], [1, 19], [0, 7, 17]
+    got = oracle.dft3_sampled(x, n0, n1, n2, k0s, k1s, k2s, chunk_rows=37)
+    ref = full[np.ix_(k2s, k1s, k0s)].transpose(2, 1, 0)
+    assert oracle.rel_l2(got, ref) < 1e-14
+    gi = oracle.dft3_sampled(x, n0, n1, n2, k0s, k1s, k2s, sign=oracle.INVERSE)
+    fi = oracle.fft3(x.ravel(), n0, n1, n2, sign=oracle.INVERSE)
+    assert oracle.rel_l2(gi, fi[np.ix_(k2s, k1s, k0s)].transpose(2, 1, 0)) < 1e-14
