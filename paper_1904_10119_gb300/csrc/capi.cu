@@ -1,5 +1,7 @@
 // capi.cu -- the C ABI of libfft3 (include/fft3.h): plan objects, twiddle
 // generation at plan time, and the launch of each pass of a schedule.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -70,6 +72,7 @@ struct Launch {
     PassArgs args{};
     int src = BUF_IN, dst = BUF_OUT;
     bool reset_counters = false;
+    bool tma = false; // kernel takes two tensor maps after its PassArgs
     // identity probe of the same pass geometry
     PassGeom probe_g{};
     int probe_n = 1;
@@ -97,10 +100,58 @@ static int device_sms(int dev)
     return v > 0 ? v : 1;
 }
 
+// Raise the dynamic shared-memory cap of a kernel to the device's opt-in
+// maximum (the cap is per function, so it is never lowered by a later plan).
 static int prepare_func(const void *func, int smem)
 {
-    if (smem > 48 * 1024)
-        CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (smem > 48 * 1024) {
+        int dev = 0, optin = 0;
+        CUDA_TRY(cudaGetDevice(&dev));
+        CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (smem > optin)
+            return fail(FFT3_ERR_UNSUPPORTED_SIZE, "pass needs more shared memory than the device offers");
+        CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    }
+    return FFT3_OK;
+}
+
+// ------------------------------------------------------- tensor maps ----- //
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// The array seen by a strided pass as the 4D tensor {C, n, A, B} of 8-byte
+// elements; boxes of lpt columns x min(n, 256) line elements.
+static int encode_pass_map(CUtensorMap *m, const void *base, const PassGeom &g, int n, int lpt, bool output)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return fail(FFT3_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if ((uintptr_t)base & 15)
+        return fail(FFT3_ERR_INVALID_ARG, "this plan moves tiles with TMA: buffers must be 16-byte aligned");
+    const int64_t sj = output ? g.ok : g.ij, sa = output ? g.oa : g.ia, sb = output ? g.ob : g.ib;
+    cuuint64_t dims[4] = {(cuuint64_t)g.C, (cuuint64_t)n, (cuuint64_t)g.A, (cuuint64_t)g.B};
+    cuuint64_t strides[3] = {(cuuint64_t)sj * 8, (cuuint64_t)sa * 8,
+                             (cuuint64_t)(g.B > 1 ? sb : sa * g.A) * 8};
+    cuuint32_t box[4] = {(cuuint32_t)lpt, (cuuint32_t)(n < 256 ? n : 256), 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(FFT3_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
     return FFT3_OK;
 }
 
@@ -191,6 +242,10 @@ static int build_launches(fft3_plan_s *P)
         case PK_J: L.func = fk ? fk->j : nullptr; break;
         case PK_JROT: L.func = fk ? fk->jrot : nullptr; break;
         case PK_C: L.func = fk ? (p.lpt == 16 ? fk->c16 : fk->c8) : nullptr; break;
+        case PK_CTMA:
+            L.func = fk ? fk->ctma : nullptr;
+            L.tma = true;
+            break;
         case PK_G: L.func = (const void *)&k_pass_g; break;
         case PK_SLAB:
             L.func = (const void *)&k_slab;
@@ -428,6 +483,17 @@ static int launch_one(fft3_plan_s *P, const Launch &L, const void *func, PassArg
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
+    }
+    if (L.tma) {
+        CUtensorMap tin, tout;
+        int rc = encode_pass_map(&tin, a.in, a.g, L.probe_n, a.lpt, false);
+        if (!rc)
+            rc = encode_pass_map(&tout, a.out, a.g, L.probe_n, a.lpt, true);
+        if (rc)
+            return rc;
+        void *params[3] = {&a, &tin, &tout};
+        CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params));
+        return FFT3_OK;
     }
     void *params[1] = {&a};
     CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params));

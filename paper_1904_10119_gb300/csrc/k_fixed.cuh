@@ -5,6 +5,7 @@
 
 #include "pass_kernels.cuh"
 #include "plans.h"
+#include "pass_tma.cuh"
 #include "slab_l2.cuh"
 
 namespace fft3 {
@@ -30,6 +31,16 @@ constexpr const void *pass_c_ptr()
         return nullptr;
 }
 
+template <int N, int T, class Rad>
+constexpr const void *pass_ctma_ptr()
+{
+    constexpr int L = lpt_tma(N, T);
+    if constexpr (L > 0)
+        return (const void *)&k_pass_c_tma<N, T, Rad, L>;
+    else
+        return nullptr;
+}
+
 } // namespace fft3
 
 #define FFT3_KERNEL_ROW(ID, N, T, ...)                                                          \
@@ -38,4 +49,5 @@ constexpr const void *pass_c_ptr()
      (const void *)&fft3::k_pass_j<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_rot(T), true>,   \
      fft3::pass_c_ptr<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_c(T, 16)>(),                  \
      fft3::pass_c_ptr<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_c(T, 8)>(),                   \
-     fft3::slab_l2_ptr<N, T, fft3::Radices<__VA_ARGS__>>()},
+     fft3::slab_l2_ptr<N, T, fft3::Radices<__VA_ARGS__>>(),                                    \
+     fft3::pass_ctma_ptr<N, T, fft3::Radices<__VA_ARGS__>>()},

@@ -234,6 +234,22 @@ static void set_tiles(PassPlan *p)
     p->ntiles = p->tiles_c * p->g.A * p->g.B;
 }
 
+// The TMA-pipelined strided kernel needs the same geometry on both sides,
+// 16-byte multiples for every stride TMA walks, whole tiles and whole boxes.
+static bool tma_ok(const PassGeom &g, int n, int lpt)
+{
+    if (lpt <= 0 || g.ic != 1 || g.oc != 1 || g.ij != g.ok || g.ia != g.oa || g.ib != g.ob)
+        return false;
+    if (g.C % lpt || (g.ij * 8) % 16 || (g.ia * 8) % 16 || (g.B > 1 && (g.ib * 8) % 16))
+        return false;
+    int br = n < 256 ? n : 256;
+    if (n % br)
+        return false;
+    if (g.C > 0x7fffffff || g.A > 0x7fffffff || g.B > 0x7fffffff)
+        return false;
+    return 2 * n * lpt * 8 + 8192 * 8 <= kSmemLimit;
+}
+
 // A single 1D pass on dimension d with geometry g.
 static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rotate, int src, int dst,
                           PassPlan *out, std::string *err)
@@ -256,6 +272,10 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
     } else if (p.line.fixed >= 0 && !rotate && contig_in && g.ok == 1 && n > 1) {
         p.kind = PK_J;
         p.lpt = lpt_j(p.line.T);
+    } else if (p.line.fixed >= 0 && !rotate && strided_in && n > 1 && s->opts.tile_lines == 0 &&
+               tma_ok(g, n, lpt_tma(n, p.line.T))) {
+        p.kind = PK_CTMA;
+        p.lpt = lpt_tma(n, p.line.T);
     } else if (p.line.fixed >= 0 && !rotate && strided_in && lpt_c(p.line.T, want_c) > 0 && n > 1) {
         p.kind = PK_C;
         p.lpt = lpt_c(p.line.T, want_c);
@@ -280,6 +300,9 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
     } else if (p.kind == PK_JROT) {
         p.threads = p.line.T * p.lpt;
         p.smem_bytes = tw_slots_h(tw_len) * 8 + p.lpt * pitch_h(n) * 8;
+    } else if (p.kind == PK_CTMA) {
+        p.threads = p.line.T * p.lpt;
+        p.smem_bytes = tw_slots_h(tw_len) * 8 + 2 * p.lpt * n * 8;
     } else {
         p.threads = p.line.T * p.lpt;
         p.smem_bytes = tw_slots_h(tw_len) * 8 + p.lpt * n * 8;
@@ -605,8 +628,9 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
 static const char *kind_name(int k)
 {
     static const char *names[] = {"line_contig", "line_contig_rotate", "line_strided", "line_runtime",
-                                  "slab_smem", "slab_l2", "volumetric_split", "copy", "line_tc"};
-    return (k >= 0 && k <= 8) ? names[k] : "?";
+                                  "slab_smem", "slab_l2", "volumetric_split", "copy", "line_tc",
+                                  "line_strided_tma"};
+    return (k >= 0 && k <= 9) ? names[k] : "?";
 }
 static const char *buf_name(int b)
 {

@@ -22,6 +22,7 @@ enum PassKind {
     PK_VOL = 6,    // 1D DFT split n = a*b over a cluster of p blocks (DSMEM exchange)
     PK_COPY = 7,   // all dimensions of length 1: plain copy
     PK_TC = 8,     // split-BF16 tensor-core line pass
+    PK_CTMA = 9,   // fixed plan, strided columns, TMA double-buffered tiles
 };
 
 enum BufId { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };

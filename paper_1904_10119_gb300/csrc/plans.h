@@ -57,6 +57,7 @@ struct FixedKernels {
     const void *c16;  // k_pass_c, 16 lines per tile
     const void *c8;   // k_pass_c, 8 lines per tile
     const void *l2;   // k_slab_l2 (square slabs), 0 if not compiled
+    const void *ctma; // k_pass_c_tma (TMA-pipelined strided lines), 0 if not compiled
 };
 const FixedKernels *fixed_kernels(int id);
 
@@ -65,5 +66,7 @@ const FixedKernels *fixed_kernels(int id);
 constexpr int lpt_j(int T) { return T >= 256 ? 1 : 256 / T; }
 constexpr int lpt_rot(int T) { return T >= 64 ? 8 : (128 / T > 16 ? 128 / T : 16); }
 constexpr int lpt_c(int T, int want) { return T * want <= 1024 ? want : 0; }
+// TMA-pipelined strided pass: two tiles of N x LPT complex values in flight.
+constexpr int lpt_tma(int N, int T) { return (N >= 1024 ? 8 : 16) * T <= 1024 && N >= 16 ? (N >= 1024 ? 8 : 16) : 0; }
 
 } // namespace fft3
