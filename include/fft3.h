@@ -104,13 +104,20 @@ int fft3_plan_create(fft3_plan *out, int n0, int n1, int n2, int batch, int dtyp
 int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int dtype,
                         int decomposition, int direction, const fft3_options *opts);
 
-/* Batched uneven transforms: `count` independent 3D DFTs, problem i of size
- * dims[3i] x dims[3i+1] x dims[3i+2] (first fastest) starting at complex
- * offset offsets[i] of both the input and output buffers, executed by one
- * persistent launch (captured once in a CUDA graph).  Line lengths <= 128.
- * decomposition: FFT3_SLAB_PENCIL, FFT3_PENCIL3 or FFT3_AUTO (per size class).
- * `tuning` may be NULL or point to `count` ints of per-problem tile hints
- * (0 = default). */
+/* Batched uneven transforms: `count` independent 3D DFTs (Section 2.3 for
+ * each), problem i of size dims[3i] x dims[3i+1] x dims[3i+2] (first fastest)
+ * starting at complex offset offsets[i] of both the input and the output
+ * buffer (the problems' extents must not overlap).  One execute is one
+ * persistent launch with its counter reset, captured once in a CUDA graph
+ * (re-captured when the buffers change).  Dimensions: 2*3*5-smooth, <= 128.
+ * decomposition: FFT3_SLAB_PENCIL, FFT3_PENCIL3 or FFT3_AUTO (per problem).
+ * dtype: FFT3_C64_FP32.  `tuning` may be NULL or point to `count` tuning
+ * codes built with FFT3_TUNE (0 = defaults); fft3_autotune_many writes them. */
+#define FFT3_TUNE(decomp, radix_order, tile_code, items_code)                        \
+    ((decomp) | (((radix_order) + 1) << 2) | ((tile_code) << 5) | ((items_code) << 8))
+/* decomp: 1 = slab-pencil, 2 = pencil-pencil-pencil; tile_code: columns per
+ * tile of the strided phases, 1 -> 4, 2 -> 8, 3 -> 16, 4 -> 32; items_code:
+ * slabs (slab-pencil) or rows (pencil) per first-phase work item, k -> 2^(k-1). */
 int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets,
                           int dtype, int decomposition, int direction, const int *tuning);
 
@@ -180,6 +187,71 @@ int fft3_plan_execute_pass(fft3_plan p, int k, const void *in, void *out, void *
  * written as raw uint16 bit patterns.  Device pointers. */
 int fft3_split_bf16(const float *d_x, int64_t count, uint16_t *d_hi, uint16_t *d_lo,
                     void *stream);
+
+/* ---- measured plan selection (no counterpart in the paper, which leaves the
+ * choice of decomposition to the user; Section 4.3 shows no single one wins) */
+
+/* Times one plan: creates it, allocates two scratch arrays of the problem's
+ * size, runs two untimed executions and `reps` timed ones (CUDA events on the
+ * legacy default stream), destroys everything, and writes the mean ms of one
+ * execution to *ms. */
+int fft3_time_plan(int n0, int n1, int n2, int batch, int dtype, int decomposition, int direction,
+                   const fft3_options *opts, int reps, float *ms);
+
+/* Times `count` candidate plans of one shape (decompositions[i], opts[i]) on
+ * shared scratch arrays, as fft3_time_plan does for one; ms_out[i] = -1 for a
+ * candidate the planner rejects. */
+int fft3_time_candidates(int n0, int n1, int n2, int batch, int dtype, int direction, int reps, int count,
+                         const int *decompositions, const fft3_options *opts, float *ms_out);
+
+/* Exhaustive autotuning of one shape over the candidate decompositions,
+ * pencil variants, slab modes, strided tiles, the 2x2x2 volumetric mesh and
+ * radix orders 0..3; infeasible candidates are skipped.  Writes the fastest
+ * plan's options, decomposition and mean ms.  Allocates scratch arrays. */
+int fft3_autotune(int n0, int n1, int n2, int batch, int dtype, int direction, int reps,
+                  fft3_options *best, int *best_decomposition, float *best_ms);
+
+/* Autotuning of a batched plan: for every distinct (n0, n1, n2) among the
+ * `count` problems, times batched plans of up to `max_per_class` copies of
+ * that shape under each candidate FFT3_TUNE code (both decompositions, radix
+ * orders 0..3, tiles of 8/16/32 columns) and writes the fastest code to
+ * tuning_out[i] of every problem i of that shape.  `offsets` is unused (the
+ * timing runs on packed scratch arrays) and may be NULL. */
+int fft3_autotune_many(int count, const int *dims, const int64_t *offsets, int direction, int reps,
+                       int max_per_class, int *tuning_out);
+
+/* ---- learned plan cost model (no counterpart in the paper): a perceptron
+ * F -> H -> H -> 1 with exact GELU, 0.5 x (1 + erf(x / sqrt 2)), trained on
+ * measured plan timings (target: log run time) with the MSE loss and Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8), forward and backward computed by the
+ * library's own kernels in FP32.  Parameters form one flat float array
+ * [W1 (H x F), b1 (H), W2 (H x H), b2 (H), W3 (1 x H), b3 (1)], row-major;
+ * samples are rows of a row-major (n x F) float matrix. */
+typedef struct fft3_mlp_s *fft3_mlp;
+
+/* Allocates the model on the current device; weights ~ N(0, 2/fan_in) from a
+ * seeded generator, biases 0, Adam moments 0. */
+int fft3_mlp_create(fft3_mlp *out, int n_features, int hidden, unsigned long long seed);
+int fft3_mlp_destroy(fft3_mlp m);
+int fft3_mlp_num_params(fft3_mlp m);
+/* Host copies of the flat parameter array (setting also clears Adam's state). */
+int fft3_mlp_set_params(fft3_mlp m, const float *h_params);
+int fft3_mlp_get_params(fft3_mlp m, float *h_params);
+/* Device pointers: d_X (B x F), d_pred (B); asynchronous on stream. */
+int fft3_mlp_forward(fft3_mlp m, const float *d_X, int B, float *d_pred, void *stream);
+/* Loss (mean squared error against d_y) and its gradient with respect to the
+ * flat parameters (written to d_grad, may be NULL; d_loss may be NULL). */
+int fft3_mlp_grad(fft3_mlp m, const float *d_X, const float *d_y, int B, float *d_grad, float *d_loss,
+                  void *stream);
+/* One Adam update with the given gradient (NULL: the last fft3_mlp_grad). */
+int fft3_mlp_adam_step(fft3_mlp m, const float *d_grad, float lr, void *stream);
+/* Training loop on host arrays: `epochs` passes over a seeded shuffle in
+ * minibatches of `batch`; h_loss_curve (epochs floats, may be NULL) receives
+ * the full-data loss after every epoch.  Synchronous. */
+int fft3_mlp_train(fft3_mlp m, const float *h_X, const float *h_y, int n, int epochs, int batch, float lr,
+                   unsigned long long seed, float *h_loss_curve);
+/* Predictions for n host samples into h_pred.  Synchronous. */
+int fft3_mlp_predict(fft3_mlp m, const float *h_X, int n, float *h_pred);
 
 const char *fft3_last_error(void);
 int fft3_version(void);

@@ -1,0 +1,45 @@
+// batched.h -- plain (host and device) description of a batch of uneven 3D
+// DFTs executed by one persistent launch (k_batched).
+#pragma once
+
+#include <stdint.h>
+
+#include "geom.h"
+
+namespace fft3 {
+
+constexpr int kBatchMaxLine = 128; // longest line of a batched problem
+
+enum BatchDecomp { BD_SLAB = 0, BD_PPP = 1 };
+
+struct BatchCube {
+    int64_t off;    // complex offset of the problem in `in` and `out`
+    int n0, n1, n2;
+    int lx, ly, lz; // indices of the x, y, z line plans in the LineRt table
+    int decomp;     // BD_SLAB: 2D slabs then z lines; BD_PPP: x, y, z lines
+    int nph;        // phases (2 or 3)
+    int items[3];   // work items of each phase
+    int lpt;        // columns per tile of the strided phases
+    int spi;        // slabs (BD_SLAB) or rows (BD_PPP) per phase-0 item
+};
+
+struct BatchItem {
+    int cube, phase, index, pad;
+};
+
+struct BatchArgs {
+    const float2 *in;
+    float2 *out;
+    const BatchCube *cubes;
+    const BatchItem *items;
+    int nitems;
+    const LineRt *lines; // tw_off of each line plan indexes `tw`
+    const float2 *tw;
+    int *counters;       // [0] ticket; [1 + 3*cube + phase] finished items
+    unsigned *err;
+    long long wait_budget;
+    int conj;
+    int buf_elems;       // complex elements of each of the two shared buffers
+};
+
+} // namespace fft3

@@ -1,0 +1,409 @@
+// batched_host.cu -- fft3_plan_create_many: planning and graph-captured
+// execution of a batch of independent, unevenly sized 3D DFTs in one
+// persistent launch (k_batched.cu).
+//
+// Per problem, a tuning code (fft3.h, FFT3_TUNE_*) selects the decomposition
+// (slab-pencil or pencil-pencil-pencil), the radix order of its line plans,
+// the columns per tile of its strided phases and the slabs/rows per item of
+// its first phase; zero picks the defaults below.  Problems are grouped
+// (largest first) into groups of about 16 MB and the work items are emitted
+// in waves: wave w holds phase p of group w - p, so a problem's next phase
+// runs one group later, while its intermediate result is still in L2.
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <numeric>
+#include <sstream>
+
+#include "capi_internal.h"
+
+namespace fft3 {
+
+__global__ void k_batched(BatchArgs a);
+__global__ void k_roots(int n, int sign, const int64_t *m, int64_t count, double *o64, float2 *o32);
+
+struct BatchState {
+    std::vector<BatchCube> cubes;
+    std::vector<BatchItem> items;
+    std::vector<LineRt> lines;
+    std::vector<LineChoice> line_choice;
+    std::vector<int> tuning; // effective tuning code per problem
+    BatchCube *d_cubes = nullptr;
+    BatchItem *d_items = nullptr;
+    LineRt *d_lines = nullptr;
+    float2 *d_tw = nullptr;
+    int *d_counters = nullptr;
+    unsigned *d_err = nullptr;
+    size_t counters_bytes = 0;
+    int64_t tw_total = 0;
+    int buf_elems = 0;
+    int smem = 0;
+    int threads = 256;
+    dim3 grid;
+    int conj = 0;
+    int64_t extent = 0;
+    // CUDA graph of [counter reset, k_batched], re-captured when the buffers change
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    const void *g_in = nullptr;
+    void *g_out = nullptr;
+    int groups = 0;
+};
+
+static inline int pitch_b(int n) { return ((n - 1) + ((n - 1) >> 4) + 1) | 1; }
+static bool smooth_b(int n)
+{
+    if (n < 1)
+        return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0)
+            n /= p;
+    return n == 1;
+}
+
+void batch_free(BatchState *b)
+{
+    if (!b)
+        return;
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    if (b->graph)
+        cudaGraphDestroy(b->graph);
+    if (b->cap_stream)
+        cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_cubes);
+    cudaFree(b->d_items);
+    cudaFree(b->d_lines);
+    cudaFree(b->d_tw);
+    cudaFree(b->d_counters);
+    cudaFree(b->d_err);
+    delete b;
+}
+
+static int line_index(BatchState *b, std::map<std::pair<int, int>, int> &idx, int n, int order, std::string *err)
+{
+    auto key = std::make_pair(n, order);
+    auto it = idx.find(key);
+    if (it != idx.end())
+        return it->second;
+    LineChoice lc;
+    int rc = choose_runtime_line(n, order, &lc, err);
+    if (rc)
+        return rc;
+    int id = (int)b->line_choice.size();
+    b->line_choice.push_back(lc);
+    idx[key] = id;
+    return id;
+}
+
+// Decodes a tuning code (0 = defaults).
+static void decode_tuning(int code, int n0, int n1, int n2, int *decomp, int *order, int *lpt, int *spi)
+{
+    const int d = code & 3, o = (code >> 2) & 7, l = (code >> 5) & 7, s = (code >> 8) & 7;
+    // slab-pencil keeps the whole slab in shared memory; prefer it for small slabs
+    *decomp = d == 1 ? BD_SLAB : d == 2 ? BD_PPP : (n0 * n1 <= 4096 ? BD_SLAB : BD_PPP);
+    if (*decomp == BD_SLAB && 2 * n1 * pitch_b(n0) * 8 > 200 * 1024)
+        *decomp = BD_PPP;
+    *order = o ? o - 1 : 0;
+    *lpt = l ? (2 << l) : 16; // 1 -> 4, 2 -> 8, 3 -> 16, 4 -> 32
+    if (s) {
+        *spi = 1 << (s - 1);
+    } else if (*decomp == BD_SLAB) {
+        *spi = std::max(1, 4096 / (n0 * n1));
+    } else {
+        *spi = std::max(1, 2048 / n0);
+    }
+    (void)n2;
+}
+
+int batch_describe(const BatchState *b, std::string *json)
+{
+    std::ostringstream o;
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> cls; // shape -> (count, tuning)
+    for (size_t i = 0; i < b->cubes.size(); ++i) {
+        const BatchCube &c = b->cubes[i];
+        auto &e = cls[std::make_tuple(c.n0, c.n1, c.n2)];
+        e.first++;
+        e.second = b->tuning[i];
+    }
+    o << "{\"batched\":true,\"problems\":" << b->cubes.size() << ",\"items\":" << b->items.size()
+      << ",\"groups\":" << b->groups << ",\"line_plans\":" << b->lines.size() << ",\"grid\":" << b->grid.x
+      << ",\"block\":" << b->threads << ",\"smem\":" << b->smem << ",\"twiddle_entries\":" << b->tw_total
+      << ",\"extent\":" << b->extent << ",\"classes\":[";
+    bool first = true;
+    for (auto &kv : cls) {
+        o << (first ? "" : ",") << "{\"dims\":[" << std::get<0>(kv.first) << "," << std::get<1>(kv.first) << ","
+          << std::get<2>(kv.first) << "],\"count\":" << kv.second.first << ",\"tuning\":" << kv.second.second << "}";
+        first = false;
+    }
+    o << "]}";
+    *json = o.str();
+    return FFT3_OK;
+}
+
+static int capture(fft3_plan_s *P, const void *in, void *out)
+{
+    BatchState *b = P->batch;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    BatchArgs a{};
+    a.in = (const float2 *)in;
+    a.out = (float2 *)out;
+    a.cubes = b->d_cubes;
+    a.items = b->d_items;
+    a.nitems = (int)b->items.size();
+    a.lines = b->d_lines;
+    a.tw = b->d_tw;
+    a.counters = b->d_counters;
+    a.err = b->d_err;
+    a.wait_budget = 4000000000LL;
+    a.conj = b->conj;
+    a.buf_elems = b->buf_elems;
+    CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, b->counters_bytes, b->cap_stream);
+    if (e == cudaSuccess) {
+        void *params[1] = {&a};
+        e = cudaLaunchKernel((const void *)&k_batched, b->grid, dim3(b->threads), params, b->smem, b->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g)
+            cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(FFT3_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    b->graph = g;
+    CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    b->g_in = in;
+    b->g_out = out;
+    return FFT3_OK;
+}
+
+int batch_execute(fft3_plan p, const void *in, void *out, cudaStream_t st)
+{
+    BatchState *b = p->batch;
+    if (!b->exec || b->g_in != in || b->g_out != out) {
+        int rc = capture(p, in, out);
+        if (rc)
+            return rc;
+    }
+    CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    return FFT3_OK;
+}
+
+} // namespace fft3
+
+using namespace fft3;
+
+extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets, int dtype,
+                                     int decomposition, int direction, const int *tuning)
+{
+    if (!out)
+        return fail(FFT3_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !dims || !offsets)
+        return fail(FFT3_ERR_INVALID_ARG, "count must be positive and dims/offsets non-null");
+    if (direction != FFT3_FORWARD && direction != FFT3_INVERSE)
+        return fail(FFT3_ERR_INVALID_ARG, "direction must be FFT3_FORWARD or FFT3_INVERSE");
+    if (dtype != FFT3_C64_FP32)
+        return fail(FFT3_ERR_UNSUPPORTED_SIZE, "batched plans compute in FP32 only");
+    if (decomposition != FFT3_AUTO && decomposition != FFT3_SLAB_PENCIL && decomposition != FFT3_PENCIL3)
+        return fail(FFT3_ERR_INVALID_ARG, "batched plans support slab-pencil, pencil-pencil-pencil or auto");
+    auto *b = new (std::nothrow) BatchState();
+    if (!b)
+        return fail(FFT3_ERR_OOM, "host allocation failed");
+    std::string err;
+    std::map<std::pair<int, int>, int> lidx;
+    b->conj = direction == FFT3_INVERSE ? 1 : 0;
+    b->cubes.resize(count);
+    b->tuning.resize(count);
+    int64_t extent = 0;
+    int bufmax = 1;
+    for (int i = 0; i < count; ++i) {
+        const int n0 = dims[3 * i], n1 = dims[3 * i + 1], n2 = dims[3 * i + 2];
+        if (n0 < 1 || n1 < 1 || n2 < 1 || n0 > kBatchMaxLine || n1 > kBatchMaxLine || n2 > kBatchMaxLine ||
+            !smooth_b(n0) || !smooth_b(n1) || !smooth_b(n2) || offsets[i] < 0) {
+            batch_free(b);
+            return fail(FFT3_ERR_UNSUPPORTED_SIZE, "problem " + std::to_string(i) +
+                                                       ": dimensions must be 2*3*5-smooth and at most " +
+                                                       std::to_string(kBatchMaxLine) + ", offsets non-negative");
+        }
+        int code = tuning ? tuning[i] : 0;
+        if (decomposition == FFT3_SLAB_PENCIL && (code & 3) == 0)
+            code |= 1;
+        if (decomposition == FFT3_PENCIL3 && (code & 3) == 0)
+            code |= 2;
+        int decomp, order, lpt, spi;
+        decode_tuning(code, n0, n1, n2, &decomp, &order, &lpt, &spi);
+        BatchCube &c = b->cubes[i];
+        c.off = offsets[i];
+        c.n0 = n0; c.n1 = n1; c.n2 = n2;
+        c.decomp = decomp;
+        c.lpt = lpt;
+        int rc = 0, lx = line_index(b, lidx, n0, order, &err), ly = line_index(b, lidx, n1, order, &err),
+            lz = line_index(b, lidx, n2, order, &err);
+        if (lx < 0 || ly < 0 || lz < 0) {
+            batch_free(b);
+            return fail(FFT3_ERR_UNSUPPORTED_SIZE, err);
+        }
+        c.lx = lx; c.ly = ly; c.lz = lz;
+        if (decomp == BD_SLAB) {
+            c.spi = std::max(1, std::min(spi, n2));
+            c.nph = 2;
+            c.items[0] = (n2 + c.spi - 1) / c.spi;
+            c.items[1] = (n0 * n1 + lpt - 1) / lpt;
+            c.items[2] = 0;
+            bufmax = std::max(bufmax, std::max(n1 * pitch_b(n0), lpt * pitch_b(n2)));
+        } else {
+            c.spi = std::max(1, std::min(spi, n1 * n2));
+            c.nph = 3;
+            c.items[0] = (n1 * n2 + c.spi - 1) / c.spi;
+            c.items[1] = n2 * ((n0 + lpt - 1) / lpt);
+            c.items[2] = (n0 * n1 + lpt - 1) / lpt;
+            bufmax = std::max(bufmax, std::max(c.spi * pitch_b(n0), std::max(lpt * pitch_b(n1), lpt * pitch_b(n2))));
+        }
+        (void)rc;
+        b->tuning[i] = (decomp == BD_SLAB ? 1 : 2) | ((order + 1) << 2) |
+                       ((lpt == 4 ? 1 : lpt == 8 ? 2 : lpt == 16 ? 3 : 4) << 5);
+        extent = std::max(extent, offsets[i] + (int64_t)n0 * n1 * n2);
+    }
+    b->extent = extent;
+    b->buf_elems = (bufmax + 31) / 32 * 32;
+    b->smem = 2 * b->buf_elems * (int)sizeof(float2);
+    if (b->smem > 227 * 1024) {
+        batch_free(b);
+        return fail(FFT3_ERR_UNSUPPORTED_SIZE, "a work item of this batch needs more shared memory than a block has");
+    }
+    // line plans and their twiddle tables
+    std::vector<int64_t> m;
+    std::vector<std::pair<int64_t, int64_t>> segs; // (offset, count) per line plan
+    int64_t tw_total = 0;
+    std::vector<std::vector<int64_t>> exps;
+    for (const LineChoice &lc : b->line_choice) {
+        std::vector<int64_t> e;
+        line_twiddle_exponents(lc, &e);
+        if (e.empty())
+            e.push_back(0);
+        LineRt r{};
+        r.n = lc.n;
+        r.T = lc.T;
+        r.nst = lc.nst;
+        r.tw_off = (int)tw_total;
+        for (int k = 0; k < kMaxStages; ++k)
+            r.rad[k] = lc.rad[k];
+        b->lines.push_back(r);
+        segs.push_back({tw_total, (int64_t)e.size()});
+        tw_total += ((int64_t)e.size() + 15) / 16 * 16;
+        exps.push_back(std::move(e));
+    }
+    b->tw_total = tw_total;
+    // work items in waves over groups of problems (largest first)
+    std::vector<int> order_idx(count);
+    std::iota(order_idx.begin(), order_idx.end(), 0);
+    std::stable_sort(order_idx.begin(), order_idx.end(), [&](int x, int y) {
+        const BatchCube &a = b->cubes[x], &c = b->cubes[y];
+        return (int64_t)a.n0 * a.n1 * a.n2 > (int64_t)c.n0 * c.n1 * c.n2;
+    });
+    std::vector<std::vector<int>> groups;
+    int64_t acc = 0;
+    const int64_t group_bytes = 16ll << 20;
+    for (int i : order_idx) {
+        const BatchCube &c = b->cubes[i];
+        const int64_t bytes = (int64_t)c.n0 * c.n1 * c.n2 * 8;
+        if (groups.empty() || acc + bytes > group_bytes) {
+            groups.emplace_back();
+            acc = 0;
+        }
+        groups.back().push_back(i);
+        acc += bytes;
+    }
+    b->groups = (int)groups.size();
+    const int G = (int)groups.size();
+    for (int w = 0; w < G + 3; ++w)
+        for (int p = 0; p < 3; ++p) {
+            const int g = w - p;
+            if (g < 0 || g >= G)
+                continue;
+            for (int ci : groups[g]) {
+                const BatchCube &c = b->cubes[ci];
+                if (p >= c.nph)
+                    continue;
+                for (int k = 0; k < c.items[p]; ++k)
+                    b->items.push_back(BatchItem{ci, p, k, 0});
+            }
+        }
+    if (b->items.size() >= (size_t)0x7fffffff) {
+        batch_free(b);
+        return fail(FFT3_ERR_UNSUPPORTED_SIZE, "too many work items");
+    }
+    // device state
+    int dev = 0;
+    int rc = check_device(&dev);
+    if (rc) {
+        batch_free(b);
+        return rc;
+    }
+    auto *P = new (std::nothrow) fft3_plan_s();
+    if (!P) {
+        batch_free(b);
+        return fail(FFT3_ERR_OOM, "host allocation failed");
+    }
+    P->device = dev;
+    P->elems = extent;
+    P->batch = b;
+    auto bail = [&](int code) {
+        cudaGetLastError();
+        fft3_plan_destroy(P);
+        return code;
+    };
+    b->counters_bytes = (size_t)(1 + 3 * count) * sizeof(int);
+    if (cudaMalloc(&b->d_cubes, b->cubes.size() * sizeof(BatchCube)) != cudaSuccess ||
+        cudaMalloc(&b->d_items, b->items.size() * sizeof(BatchItem)) != cudaSuccess ||
+        cudaMalloc(&b->d_lines, b->lines.size() * sizeof(LineRt)) != cudaSuccess ||
+        cudaMalloc(&b->d_tw, std::max<int64_t>(16, tw_total) * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&b->d_counters, b->counters_bytes) != cudaSuccess ||
+        cudaMalloc(&b->d_err, sizeof(unsigned)) != cudaSuccess)
+        return bail(fail(FFT3_ERR_OOM, "device allocation for the batched plan failed"));
+    if (cudaMemcpy(b->d_cubes, b->cubes.data(), b->cubes.size() * sizeof(BatchCube), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->d_items, b->items.data(), b->items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->d_lines, b->lines.data(), b->lines.size() * sizeof(LineRt), cudaMemcpyHostToDevice) ||
+        cudaMemset(b->d_err, 0, sizeof(unsigned)) || cudaMemset(b->d_tw, 0, std::max<int64_t>(16, tw_total) * 8))
+        return bail(fail(FFT3_ERR_CUDA, "uploading the batched plan failed"));
+    P->d_err = b->d_err;
+    {
+        size_t maxm = 1;
+        for (auto &e : exps)
+            maxm = std::max(maxm, e.size());
+        int64_t *d_m = nullptr;
+        if (cudaMalloc(&d_m, maxm * sizeof(int64_t)) != cudaSuccess)
+            return bail(fail(FFT3_ERR_OOM, "twiddle scratch allocation failed"));
+        for (size_t i = 0; i < exps.size(); ++i) {
+            cudaMemcpy(d_m, exps[i].data(), exps[i].size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+            int blocks = (int)std::max<int64_t>(1, ((int64_t)exps[i].size() + 255) / 256);
+            k_roots<<<blocks, 256>>>(b->lines[i].n, FFT3_FORWARD, d_m, (int64_t)exps[i].size(), nullptr,
+                                     b->d_tw + segs[i].first);
+        }
+        cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(d_m);
+        if (e != cudaSuccess)
+            return bail(fail(FFT3_ERR_CUDA, std::string("twiddle generation: ") + cudaGetErrorString(e)));
+    }
+    rc = prepare_func((const void *)&k_batched, b->smem);
+    if (!rc)
+        rc = occupancy_grid((const void *)&k_batched, b->threads, b->smem, 0, dev, &b->grid);
+    if (rc)
+        return bail(rc);
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(FFT3_ERR_CUDA, "stream creation failed"));
+    *out = P;
+    return FFT3_OK;
+}

@@ -11,10 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/fft3.h"
-#include "geom.h"
-#include "planner.h"
-#include "plans.h"
+#include "capi_internal.h"
 
 namespace fft3 {
 __global__ void k_pass_g(PassArgs a);
@@ -46,54 +43,13 @@ using namespace fft3;
 // ------------------------------------------------------------- errors ---- //
 static thread_local std::string g_err;
 
-static int fail(int code, const std::string &msg)
+int fft3::fail(int code, const std::string &msg)
 {
     g_err = msg;
     return code;
 }
 
-#define CUDA_TRY(x)                                                                                \
-    do {                                                                                           \
-        cudaError_t e_ = (x);                                                                      \
-        if (e_ != cudaSuccess) {                                                                   \
-            cudaGetLastError();                                                                    \
-            return fail(e_ == cudaErrorMemoryAllocation ? FFT3_ERR_OOM : FFT3_ERR_CUDA,            \
-                        std::string(#x) + ": " + cudaGetErrorString(e_));                          \
-        }                                                                                          \
-    } while (0)
-
-// ------------------------------------------------------------- plans ----- //
-struct Launch {
-    const void *func = nullptr;
-    dim3 grid, block;
-    int smem = 0;
-    int cluster = 1;
-    int kind = 0;
-    PassArgs args{};
-    int src = BUF_IN, dst = BUF_OUT;
-    bool reset_counters = false;
-    bool tma = false; // kernel takes two tensor maps after its PassArgs
-    // identity probe of the same pass geometry
-    PassGeom probe_g{};
-    int probe_n = 1;
-};
-
-struct fft3_plan_s {
-    Schedule sched;
-    int device = 0;
-    int64_t elems = 0; // complex elements per array
-    float2 *d_tw = nullptr;
-    float2 *d_ws = nullptr;
-    size_t ws_bytes = 0;
-    int *d_counters = nullptr;
-    size_t counters_bytes = 0;
-    unsigned *d_err = nullptr;
-    std::vector<Launch> launches;
-    float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
-    cudaStream_t last_stream = nullptr;
-};
-
-static int device_sms(int dev)
+int fft3::device_sms(int dev)
 {
     int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
@@ -102,15 +58,18 @@ static int device_sms(int dev)
 
 // Raise the dynamic shared-memory cap of a kernel to the device's opt-in
 // maximum (the cap is per function, so it is never lowered by a later plan).
-static int prepare_func(const void *func, int smem)
+int fft3::prepare_func(const void *func, int smem)
 {
     if (smem > 48 * 1024) {
         int dev = 0, optin = 0;
         CUDA_TRY(cudaGetDevice(&dev));
         CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        if (smem > optin)
+        cudaFuncAttributes fa;
+        CUDA_TRY(cudaFuncGetAttributes(&fa, func));
+        const int cap = optin - (int)fa.sharedSizeBytes; // static shared memory counts against the opt-in
+        if (smem > cap)
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, "pass needs more shared memory than the device offers");
-        CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     }
     return FFT3_OK;
 }
@@ -155,7 +114,7 @@ static int encode_pass_map(CUtensorMap *m, const void *base, const PassGeom &g, 
     return FFT3_OK;
 }
 
-static int occupancy_grid(const void *func, int threads, int smem, int64_t ntiles, int dev, dim3 *grid)
+int fft3::occupancy_grid(const void *func, int threads, int smem, int64_t ntiles, int dev, dim3 *grid)
 {
     int nb = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, func, threads, smem));
@@ -318,9 +277,11 @@ static void free_plan(fft3_plan_s *P)
     cudaFree(P->d_tw);
     cudaFree(P->d_ws);
     cudaFree(P->d_counters);
-    cudaFree(P->d_err);
+    if (!P->batch) // a batched plan's error word belongs to its batch state
+        cudaFree(P->d_err);
     cudaFree(P->d_stage_in);
     cudaFree(P->d_stage_out);
+    batch_free(P->batch);
     delete P;
 }
 
@@ -355,7 +316,7 @@ static int generate_twiddles(fft3_plan_s *P)
     return FFT3_OK;
 }
 
-static int check_device(int *dev)
+int fft3::check_device(int *dev)
 {
     int count = 0;
     cudaError_t e = cudaGetDeviceCount(&count);
@@ -515,6 +476,8 @@ int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream)
         return fail(FFT3_ERR_INVALID_ARG, "buffers must be 8-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     p->last_stream = st;
+    if (p->batch)
+        return batch_execute(p, in, out, st);
     for (const Launch &L : p->launches) {
         PassArgs a = L.args;
         a.in = buf_ptr(p, L.src, in, out);
@@ -641,6 +604,8 @@ int fft3_plan_launches(fft3_plan p)
 {
     if (!p)
         return fail(FFT3_ERR_INVALID_ARG, "null plan");
+    if (p->batch)
+        return 1;
     return (int)p->launches.size();
 }
 
@@ -648,6 +613,16 @@ int fft3_plan_describe(fft3_plan p, char *buf, size_t len)
 {
     if (!p)
         return fail(FFT3_ERR_INVALID_ARG, "null plan");
+    if (p->batch) {
+        std::string bj;
+        batch_describe(p->batch, &bj);
+        if (buf && len > 0) {
+            size_t c = std::min(len - 1, bj.size());
+            memcpy(buf, bj.data(), c);
+            buf[c] = 0;
+        }
+        return (int)bj.size();
+    }
     std::string j = p->sched.json();
     // append the launch shapes
     std::string l = ",\"launches\":[";
@@ -690,15 +665,6 @@ int fft3_split_bf16(const float *d_x, int64_t count, uint16_t *d_hi, uint16_t *d
     k_split_bf16<<<blocks, 256, 0, (cudaStream_t)stream>>>(d_x, count, d_hi, d_lo);
     CUDA_TRY(cudaGetLastError());
     return FFT3_OK;
-}
-
-int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets, int dtype,
-                          int decomposition, int direction, const int *tuning)
-{
-    (void)count; (void)dims; (void)offsets; (void)dtype; (void)decomposition; (void)direction; (void)tuning;
-    if (out)
-        *out = nullptr;
-    return fail(FFT3_ERR_UNSUPPORTED_SIZE, "batched uneven plans are not built in this library");
 }
 
 } // extern "C"

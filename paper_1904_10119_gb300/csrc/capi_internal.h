@@ -1,0 +1,73 @@
+// capi_internal.h -- shared internals of the C ABI translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fft3.h"
+#include "batched.h"
+#include "geom.h"
+#include "planner.h"
+#include "plans.h"
+
+namespace fft3 {
+
+int fail(int code, const std::string &msg);
+
+#define CUDA_TRY(x)                                                                                \
+    do {                                                                                           \
+        cudaError_t e_ = (x);                                                                      \
+        if (e_ != cudaSuccess) {                                                                   \
+            cudaGetLastError();                                                                    \
+            return ::fft3::fail(e_ == cudaErrorMemoryAllocation ? FFT3_ERR_OOM : FFT3_ERR_CUDA,    \
+                                std::string(#x) + ": " + cudaGetErrorString(e_));                  \
+        }                                                                                          \
+    } while (0)
+
+struct Launch {
+    const void *func = nullptr;
+    dim3 grid, block;
+    int smem = 0;
+    int cluster = 1;
+    int kind = 0;
+    PassArgs args{};
+    int src = BUF_IN, dst = BUF_OUT;
+    bool reset_counters = false;
+    bool tma = false; // kernel takes two tensor maps after its PassArgs
+    // identity probe of the same pass geometry
+    PassGeom probe_g{};
+    int probe_n = 1;
+};
+
+struct BatchState; // batched uneven plans (batched_host.cu)
+
+int device_sms(int dev);
+int prepare_func(const void *func, int smem);
+int occupancy_grid(const void *func, int threads, int smem, int64_t ntiles, int dev, dim3 *grid);
+int check_device(int *dev);
+
+// Batched plans
+int batch_execute(fft3_plan p, const void *in, void *out, cudaStream_t st);
+void batch_free(BatchState *b);
+int batch_describe(const BatchState *b, std::string *json);
+
+} // namespace fft3
+
+struct fft3_plan_s {
+    fft3::Schedule sched;
+    int device = 0;
+    int64_t elems = 0; // complex elements per array
+    float2 *d_tw = nullptr;
+    float2 *d_ws = nullptr;
+    size_t ws_bytes = 0;
+    int *d_counters = nullptr;
+    size_t counters_bytes = 0;
+    unsigned *d_err = nullptr;
+    std::vector<fft3::Launch> launches;
+    float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
+    cudaStream_t last_stream = nullptr;
+    fft3::BatchState *batch = nullptr; // non-null for fft3_plan_create_many plans
+};

@@ -684,3 +684,11 @@ std::string Schedule::json() const
 }
 
 } // namespace fft3
+
+namespace fft3 {
+int choose_runtime_line(int n, int order, LineChoice *lc, std::string *err)
+{
+    return choose_line(n, order, false, lc, err);
+}
+void line_twiddle_exponents(const LineChoice &lc, std::vector<int64_t> *m) { line_twiddles(lc, m); }
+} // namespace fft3

@@ -77,6 +77,11 @@ int factorize(int n, int order, int *rad, int cap);
 int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int direction,
                    const fft3_options *opts, Schedule *out, std::string *err);
 
+// Runtime radix list for a line of length n (radix order `order`) and its
+// stage-major twiddle exponents.
+int choose_runtime_line(int n, int order, LineChoice *lc, std::string *err);
+void line_twiddle_exponents(const LineChoice &lc, std::vector<int64_t> *m);
+
 // Lines per tile and shared memory of the runtime-radix kernel for a pass.
 void generic_launch_shape(int n, int T, bool strided, int tw_len, int *lpt, int *threads,
                           int *smem);

@@ -73,6 +73,21 @@ def load() -> ctypes.CDLL:
         "fft3_plan_probe_layout": (i, [_P, _P, _P, i, _P]),
         "fft3_plan_execute_pass": (i, [_P, i, _P, _P, _P]),
         "fft3_split_bf16": (i, [_P, i64, _P, _P, _P]),
+        "fft3_time_plan": (i, [i, i, i, i, i, i, i, ctypes.POINTER(fft3_options), i, ctypes.POINTER(ctypes.c_float)]),
+        "fft3_time_candidates": (i, [i, i, i, i, i, i, i, i, pi, ctypes.POINTER(fft3_options),
+                                     ctypes.POINTER(ctypes.c_float)]),
+        "fft3_autotune": (i, [i, i, i, i, i, i, i, ctypes.POINTER(fft3_options), pi, ctypes.POINTER(ctypes.c_float)]),
+        "fft3_autotune_many": (i, [i, pi, ctypes.POINTER(ctypes.c_int64), i, i, i, pi]),
+        "fft3_mlp_create": (i, [ctypes.POINTER(_P), i, i, ctypes.c_ulonglong]),
+        "fft3_mlp_destroy": (i, [_P]),
+        "fft3_mlp_num_params": (i, [_P]),
+        "fft3_mlp_set_params": (i, [_P, _P]),
+        "fft3_mlp_get_params": (i, [_P, _P]),
+        "fft3_mlp_forward": (i, [_P, _P, i, _P, _P]),
+        "fft3_mlp_grad": (i, [_P, _P, _P, i, _P, _P, _P]),
+        "fft3_mlp_adam_step": (i, [_P, _P, ctypes.c_float, _P]),
+        "fft3_mlp_train": (i, [_P, _P, _P, i, i, i, ctypes.c_float, ctypes.c_ulonglong, _P]),
+        "fft3_mlp_predict": (i, [_P, _P, i, _P]),
         "fft3_last_error": (ctypes.c_char_p, []),
         "fft3_version": (i, []),
     }
@@ -208,6 +223,90 @@ def fft3_plan_execute_pass(plan: int, k: int, in_ptr: int, out_ptr: int, stream:
 
 def fft3_split_bf16(d_x: int, count: int, d_hi: int, d_lo: int, stream: int = 0) -> None:
     _check(load().fft3_split_bf16(_P(d_x), count, _P(d_hi), _P(d_lo), _P(stream)))
+
+
+def fft3_time_plan(n0, n1, n2, batch=1, dtype=FFT3_C64_FP32, decomposition=FFT3_PENCIL3,
+                   direction=FFT3_FORWARD, opts: fft3_options | None = None, reps: int = 5) -> float:
+    ms = ctypes.c_float()
+    _check(load().fft3_time_plan(n0, n1, n2, batch, dtype, decomposition, direction,
+                                 ctypes.byref(opts) if opts is not None else None, reps, ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def fft3_autotune(n0, n1, n2, batch=1, dtype=FFT3_C64_FP32, direction=FFT3_FORWARD, reps: int = 3):
+    """Returns (options, decomposition, ms) of the fastest candidate plan."""
+    o = fft3_options()
+    d = ctypes.c_int()
+    ms = ctypes.c_float()
+    _check(load().fft3_autotune(n0, n1, n2, batch, dtype, direction, reps, ctypes.byref(o), ctypes.byref(d),
+                                ctypes.byref(ms)))
+    return o, int(d.value), float(ms.value)
+
+
+def fft3_autotune_many(dims, direction=FFT3_FORWARD, reps: int = 3, max_per_class: int = 32) -> list[int]:
+    count = len(dims)
+    d = (ctypes.c_int * (3 * count))(*[int(v) for v in list(_flat(dims))])
+    t = (ctypes.c_int * count)()
+    _check(load().fft3_autotune_many(count, d, None, direction, reps, max_per_class, t))
+    return [int(t[i]) for i in range(count)]
+
+
+def tune_code(decomp: int, radix_order: int = 0, tile_code: int = 0, items_code: int = 0) -> int:
+    """FFT3_TUNE of include/fft3.h."""
+    return decomp | ((radix_order + 1) << 2) | (tile_code << 5) | (items_code << 8)
+
+
+class Mlp:
+    """The library's plan-cost perceptron (fft3_mlp_*); numpy float32 in and out."""
+
+    def __init__(self, n_features: int, hidden: int = 64, seed: int = 0):
+        h = _P()
+        _check(load().fft3_mlp_create(ctypes.byref(h), n_features, hidden, seed))
+        self.handle = h.value
+        self.F, self.H = n_features, hidden
+
+    @property
+    def num_params(self) -> int:
+        return _check(load().fft3_mlp_num_params(_P(self.handle)))
+
+    def get_params(self):
+        import numpy as np
+        p = np.empty(self.num_params, np.float32)
+        _check(load().fft3_mlp_get_params(_P(self.handle), _P(p.ctypes.data)))
+        return p
+
+    def set_params(self, p) -> None:
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.num_params
+        _check(load().fft3_mlp_set_params(_P(self.handle), _P(p.ctypes.data)))
+
+    def train(self, X, y, epochs=200, batch=128, lr=1e-3, seed=0):
+        import numpy as np
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        curve = np.zeros(epochs, np.float32)
+        _check(load().fft3_mlp_train(_P(self.handle), _P(X.ctypes.data), _P(y.ctypes.data), X.shape[0], epochs,
+                                     batch, lr, seed, _P(curve.ctypes.data)))
+        return curve
+
+    def predict(self, X):
+        import numpy as np
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        out = np.empty(X.shape[0], np.float32)
+        _check(load().fft3_mlp_predict(_P(self.handle), _P(X.ctypes.data), X.shape[0], _P(out.ctypes.data)))
+        return out
+
+    def close(self):
+        if self.handle:
+            load().fft3_mlp_destroy(_P(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------ torch convenience -- #

@@ -1,0 +1,121 @@
+"""Batched uneven 3D DFTs in one persistent, graph-captured launch: parity of
+every problem (small batches) or of a sample covering every size class (the
+4096-problem batch) with the FP64 oracle, plus Parseval over all problems."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1904_10119_gb300 import fft3, synth
+from tests.gpu_util import MAXABS_TOL, REL_L2_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+def _layout(dims, gap=0):
+    vols = [int(np.prod(d)) for d in dims]
+    offs = np.zeros(len(dims), np.int64)
+    offs[1:] = np.cumsum(np.asarray(vols[:-1]) + gap)
+    return offs, int(offs[-1] + vols[-1])
+
+
+def _check_problem(x, got, off, d, direction):
+    n0, n1, n2 = (int(v) for v in d)
+    N = n0 * n1 * n2
+    ref = oracle.fft3(x[off:off + N], n0, n1, n2, sign=direction)
+    g = got[off:off + N]
+    rel, mx = oracle.rel_l2(g, ref), oracle.max_abs_ratio(g, ref)
+    assert rel <= REL_L2_TOL and mx <= MAXABS_TOL, (d, rel, mx)
+
+
+def _run(dims, offs, total, decomposition=fft3.FFT3_AUTO, direction=fft3.FFT3_FORWARD, tuning=None, seed=7):
+    x = synth.uniform_c64(total, seed)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.full_like(xd, complex(float("nan"), 0.0))
+    h = fft3.fft3_plan_create_many(dims, offs, 0, decomposition, direction, tuning)
+    try:
+        fft3.fft3_plan_execute(h, xd.data_ptr(), out.data_ptr(), 0)
+        torch.cuda.synchronize()
+        assert fft3.fft3_plan_check(h) == 0
+        assert fft3.fft3_plan_launches(h) == 1
+        desc = fft3.fft3_plan_describe(h)
+    finally:
+        fft3.fft3_plan_destroy(h)
+    return x, out.cpu().numpy(), desc
+
+
+@pytest.mark.parametrize("decomp", [fft3.FFT3_AUTO, fft3.FFT3_SLAB_PENCIL, fft3.FFT3_PENCIL3])
+@pytest.mark.parametrize("direction", [fft3.FFT3_FORWARD, fft3.FFT3_INVERSE])
+def test_small_batch_every_problem(decomp, direction):
+    dims = synth.batched_dims(48, 5)
+    offs, total = _layout(dims, gap=3)
+    x, got, desc = _run(dims, offs, total, decomp, direction)
+    assert desc["problems"] == 48
+    for off, d in zip(offs, dims):
+        _check_problem(x, got, int(off), d, direction)
+
+
+def test_tuning_codes_and_mixed_radix_shapes():
+    dims = np.array([[16, 24, 40], [96, 80, 48], [30, 45, 27], [128, 16, 2], [1, 1, 1], [5, 1, 64], [2, 3, 5]])
+    offs, total = _layout(dims)
+    for code in [0, 1, 2, 1 | (3 << 2) | (1 << 5) | (2 << 8), 2 | (4 << 2) | (4 << 5) | (3 << 8),
+                 2 | (2 << 2) | (2 << 5)]:
+        x, got, _ = _run(dims, offs, total, tuning=[code] * len(dims), seed=code + 1)
+        for off, d in zip(offs, dims):
+            _check_problem(x, got, int(off), d, fft3.FFT3_FORWARD)
+
+
+def test_graph_replay_and_buffer_change():
+    dims = synth.batched_dims(20, 9)
+    offs, total = _layout(dims)
+    x = synth.uniform_c64(total, 3)
+    xd = torch.from_numpy(x).cuda()
+    o1, o2 = torch.empty_like(xd), torch.empty_like(xd)
+    h = fft3.fft3_plan_create_many(dims, offs)
+    try:
+        for _ in range(2):
+            fft3.fft3_plan_execute(h, xd.data_ptr(), o1.data_ptr(), 0)
+        fft3.fft3_plan_execute(h, xd.data_ptr(), o2.data_ptr(), 0)  # re-captured for new buffers
+        torch.cuda.synchronize()
+        assert fft3.fft3_plan_check(h) == 0
+    finally:
+        fft3.fft3_plan_destroy(h)
+    assert torch.equal(o1, o2)
+    g = o1.cpu().numpy()
+    for off, d in zip(offs, dims):
+        _check_problem(x, g, int(off), d, fft3.FFT3_FORWARD)
+
+
+def test_rejects_unsupported_problems():
+    for dims in ([[7, 8, 8]], [[256, 8, 8]], [[0, 8, 8]]):
+        with pytest.raises(fft3.Fft3Error) as e:
+            fft3.fft3_plan_create_many(dims, [0])
+        assert e.value.code in (-1, -2)
+
+
+def test_4096_uneven_cubes_sampled_and_parseval():
+    """4096 problems, dims i.i.d. from {16,...,96} (seed 7): at least 64
+    problems covering every size class compared element by element, and
+    Parseval's identity for every problem."""
+    dims = synth.batched_dims(4096, 7)
+    offs, total = _layout(dims)
+    x, got, desc = _run(dims, offs, total, seed=7)
+    assert desc["problems"] == 4096
+    # sample: the first problem of every distinct (n0, n1, n2), then random ones up to 96
+    seen, sample = set(), []
+    for i, d in enumerate(map(tuple, dims)):
+        if d not in seen:
+            seen.add(d)
+            sample.append(i)
+    rng = np.random.default_rng(1)
+    sample += list(rng.choice(len(dims), size=max(0, 96 - len(sample)), replace=False))
+    assert len(set(int(v) for d in dims[sample] for v in d)) == 8
+    for i in sample[:160]:
+        _check_problem(x, got, int(offs[i]), dims[i], fft3.FFT3_FORWARD)
+    # Parseval per problem
+    x2 = np.abs(x.astype(np.complex128)) ** 2
+    g2 = np.abs(got.astype(np.complex128)) ** 2
+    for off, d in zip(offs, dims):
+        N = int(np.prod(d))
+        sx, sg = x2[off:off + N].sum(), g2[off:off + N].sum()
+        assert abs(sg - N * sx) <= 1e-5 * N * sx

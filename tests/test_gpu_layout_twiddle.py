@@ -88,7 +88,8 @@ def test_twiddle_generator_fp64(n):
         # away from the tiny values the oracle's long-double evaluation leaves
         # at exact zeros of sin/cos, the float32 tables equal the oracle rounded
         big = (np.abs(ref.real) > 1e-6) & (np.abs(ref.imag) > 1e-6)
-        assert np.mean(g32[big] != ref[big].astype(np.complex64)) < 1e-3
+        if big.any():
+            assert np.mean(g32[big] != ref[big].astype(np.complex64)) < 1e-3
 
 
 def test_split_bf16_bit_exact():
