@@ -78,7 +78,8 @@ enum fft3_ppp_variant {
 typedef struct fft3_options {
     int variant;      /* fft3_ppp_variant for FFT3_PENCIL3 */
     int radix_order;  /* index into the candidate radix orders of each line length (0 = default) */
-    int tile_lines;   /* lines per tile of a strided pass, 8 or 16 (0 = default 16) */
+    int tile_lines;   /* lines per tile of a strided pass: 8 or 16 (0 = default 16);
+                         1 = tiles moved by TMA, double-buffered (8 or 16 lines by length) */
     int mesh[3];      /* volumetric: blocks cooperating on one line of dim d, 1/2/4/8 (0 = auto) */
     int slab_mode;    /* slab-pencil: 0 = auto, 1 = one block per slab in shared memory,
                          2 = L2-resident x/y stages in one persistent launch,

@@ -265,6 +265,8 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         return rc;
     const bool contig_in = g.ij == 1;
     const bool strided_in = g.ic == 1 && g.oc == 1;
+    // strided tiles: 16 adjacent columns (128-byte rows) unless 8 are asked for;
+    // tile_lines == kTileTma selects the TMA double-buffered kernel
     int want_c = s->opts.tile_lines == 8 ? 8 : 16;
     if (p.line.fixed >= 0 && rotate && contig_in && g.oc == 1) {
         p.kind = PK_JROT;
@@ -272,7 +274,7 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
     } else if (p.line.fixed >= 0 && !rotate && contig_in && g.ok == 1 && n > 1) {
         p.kind = PK_J;
         p.lpt = lpt_j(p.line.T);
-    } else if (p.line.fixed >= 0 && !rotate && strided_in && n > 1 && s->opts.tile_lines == 0 &&
+    } else if (p.line.fixed >= 0 && !rotate && strided_in && n > 1 && s->opts.tile_lines == kTileTma &&
                tma_ok(g, n, lpt_tma(n, p.line.T))) {
         p.kind = PK_CTMA;
         p.lpt = lpt_tma(n, p.line.T);

@@ -87,6 +87,7 @@ void generic_launch_shape(int n, int T, bool strided, int tw_len, int *lpt, int 
                           int *smem);
 
 constexpr int kMaxLine = 4096;
+constexpr int kTileTma = 1; // fft3_options.tile_lines value selecting the TMA strided kernel
 constexpr int kSmemLimit = 227 * 1024;
 
 } // namespace fft3

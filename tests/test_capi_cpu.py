@@ -57,7 +57,7 @@ def _kinds(s):
 def test_schedule_pencil3_natural():
     s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_PENCIL3, -1)
     assert s["decomposition"] == "pencil_pencil_pencil"
-    assert _kinds(s) == ["line_contig", "line_strided_tma", "line_strided_tma"]
+    assert _kinds(s) == ["line_contig", "line_strided", "line_strided"]
     assert [p["dim"] for p in s["passes"]] == [0, 1, 2]
     assert [(p["src"], p["dst"]) for p in s["passes"]] == [("in", "out"), ("out", "out"), ("out", "out")]
     assert s["workspace_bytes"] == 0
@@ -86,9 +86,9 @@ def test_schedule_pencil3_rotate_geometry():
 
 def test_schedule_slab_pencil_modes():
     s = fft3.fft3_plan_schedule(64, 64, 64, 1, 0, fft3.FFT3_SLAB_PENCIL, -1)
-    assert _kinds(s) == ["slab_smem", "line_strided_tma"]
+    assert _kinds(s) == ["slab_smem", "line_strided"]
     s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_SLAB_PENCIL, -1)
-    assert _kinds(s) == ["slab_l2", "line_strided_tma"]
+    assert _kinds(s) == ["slab_l2", "line_strided"]
     s = fft3.fft3_plan_schedule(1024, 1024, 64, 1, 0, fft3.FFT3_SLAB_PENCIL, -1,
                                 fft3.make_options(slab_mode=3, tile_lines=16))
     assert _kinds(s) == ["line_contig", "line_strided", "line_strided"]
@@ -115,11 +115,11 @@ def test_schedule_volumetric_split_rule():
 
 def test_tma_needs_16_byte_strides_and_whole_tiles():
     # 1024-point lines move in tiles of 8 columns, shorter lines in tiles of 16
-    s = fft3.fft3_plan_schedule(64, 1024, 256, 1, 0, fft3.FFT3_PENCIL3, -1)
+    s = fft3.fft3_plan_schedule(64, 1024, 256, 1, 0, fft3.FFT3_PENCIL3, -1, fft3.make_options(tile_lines=1))
     assert _kinds(s)[1:] == ["line_strided_tma"] * 2
     assert s["passes"][1]["lpt"] == 8 and s["passes"][2]["lpt"] == 16
     # odd n0: the y stride (n0 * 8 bytes) is not a multiple of 16 -> non-TMA kernel
-    s = fft3.fft3_plan_schedule(45, 256, 64, 1, 0, fft3.FFT3_PENCIL3, -1)
+    s = fft3.fft3_plan_schedule(45, 256, 64, 1, 0, fft3.FFT3_PENCIL3, -1, fft3.make_options(tile_lines=1))
     assert _kinds(s)[1] == "line_strided"
     # tile_lines forces the non-TMA kernel
     s = fft3.fft3_plan_schedule(64, 64, 64, 1, 0, fft3.FFT3_PENCIL3, -1, fft3.make_options(tile_lines=8))

@@ -166,3 +166,14 @@ def test_error_paths():
     # the context is still usable
     x, got, _ = run_plan((16, 16, 16), 1, P, FWD)
     assert_parity(x, got, (16, 16, 16))
+
+
+@pytest.mark.parametrize("shape,batch", [((64, 64, 64), 1), ((1024, 16, 16), 1), ((16, 1024, 32), 1),
+                                         ((32, 48, 1024), 2), ((128, 256, 80), 1), ((40, 40, 40), 1)])
+@pytest.mark.parametrize("direction", [FWD, INV])
+def test_tma_strided_pass(shape, batch, direction):
+    x, got, plan = run_plan(shape, batch, P, direction, seed=21, tile_lines=1)
+    assert_parity(x, got, shape, batch, direction)
+    kinds = [p["kind"] for p in plan.describe()["passes"]]
+    if shape != (40, 40, 40):
+        assert "line_strided_tma" in kinds
