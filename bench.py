@@ -167,36 +167,41 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--n", type=int, default=1024, help="cube edge (ignored with --shape)")
+    ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("N0", "N1", "N2"))
     ap.add_argument("--decomp", default="auto", choices=["auto", "slab_pencil", "ppp", "ppp_rotate", "volumetric"])
-    ap.add_argument("--no-extras", action="store_true", help="skip the per-decomposition table")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--tile-lines", type=int, default=0)
+    ap.add_argument("--slab-mode", type=int, default=0)
+    ap.add_argument("--radix-order", type=int, default=0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-decomposition and batched tables")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU oracle baseline")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    n = args.n
-    N = n ** 3
+    n0, n1, n2 = args.shape if args.shape else (args.n, args.n, args.n)
+    N = n0 * n1 * n2
     flops = 5.0 * N * math.log2(N)
-    workload = f"fft3d_c64_{n}x{n}x{n}_forward_out_of_place"
+    workload = f"fft3d_c64_{n0}x{n1}x{n2}_forward_out_of_place"
 
     if args.impl == "reference":
         if rank != 0:
             return 0
-        hbm, _ = _peaks()
+        assert n0 == n1 == n2, "the CPU reference arm samples cubic workloads"
         vals = []
         res = None
         for s in range(args.warmup + args.steps):
-            res = oracle_sample(n, max(1.0, args.cpu_seconds / max(1, args.steps)))
+            res = oracle_sample(n0, max(1.0, args.cpu_seconds / max(1, args.steps)))
             if s >= args.warmup:
                 vals.append(res["ms"])
         v = sum(vals) / len(vals)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload, "dims": [n, n, n], "batch": 1},
+                "config": {"workload": workload, "dims": [n0, n1, n2], "batch": 1},
                 "cpu_baseline": {"value": v, "unit": "ms", "cores": res["cores"], "kind": "oracle",
                                  "sample": res["sample"]},
                 "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -226,16 +231,15 @@ def main():
                   "volumetric": (fft3.FFT3_VOLUMETRIC, {})}
 
     # inputs: seeded uniform[-1,1) complex64, generated on the host into pinned memory
-    h_in = torch.empty((n, n, n), dtype=torch.complex64).pin_memory()
-    synth.uniform_c64((n, n, n), 4 + rank, out=h_in.numpy())
-    h_out = torch.empty_like(h_in).pin_memory()
+    h_in = torch.empty((n2, n1, n0), dtype=torch.complex64).pin_memory()
+    synth.uniform_c64((n2, n1, n0), 4 + rank, out=h_in.numpy())
     x = h_in.to("cuda")
     out = torch.empty_like(x)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
-    def time_plan(decomp, opts, steps, warmup, per_pass=False):
-        plan = fft3.Plan(n, n, n, 1, decomposition=decomp, **opts)
+    def time_plan(decomp, opts, steps, warmup):
+        plan = fft3.Plan(n0, n1, n2, 1, decomposition=decomp, **opts)
         npass = plan.launches()
         for _ in range(warmup):
             plan.execute(x, out)
@@ -254,10 +258,14 @@ def main():
         return plan, step_ms, pass_ms
 
     decomp, opts = decomp_map[args.decomp]
+    opts = dict(opts)
+    for k, v in (("tile_lines", args.tile_lines), ("slab_mode", args.slab_mode), ("radix_order", args.radix_order)):
+        if v:
+            opts[k] = v
     sampler = ClockSampler(dev)
     sampler.start()
     t_wall0 = time.perf_counter()
-    plan, step_ms, pass_ms = time_plan(decomp, opts, args.steps, args.warmup, per_pass=True)
+    plan, step_ms, pass_ms = time_plan(decomp, opts, args.steps, args.warmup)
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
     desc = plan.describe()
@@ -274,31 +282,35 @@ def main():
     alg_bytes = 2 * 8 * N  # each pass reads and writes the array once
     achieved = alg_bytes / (pass_ms[dom] * 1e-3) / 1e9
     dom_kind = desc["passes"][dom]["kind"]
-    traffic = _profiled_traffic(dom_kind)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": dom_kind, "peak_source": peak_kind,
+                "traffic": _profiled_traffic(dom_kind), "kernel": dom_kind, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": pass_ms[dom]}
     sweeps = len(pass_ms)
     whole = {"passes": sweeps, "bytes": sweeps * alg_bytes,
              "frac_of_plan_passes": sweeps * alg_bytes / (t_step * 1e-3) / 1e9 / hbm,
              "frac_of_3pass": 3 * alg_bytes / (t_step * 1e-3) / 1e9 / hbm,
-             "frac_of_3pass_nominal_8TBs": 3 * alg_bytes / (t_step * 1e-3) / 1e9 / 7900.0}
+             "frac_of_3pass_nominal_7900GBs": 3 * alg_bytes / (t_step * 1e-3) / 1e9 / 7900.0}
 
     # end to end through the C ABI with host buffers
-    eplan = fft3.fft3_plan_create_ex(n, n, n, 1, 0, decomp, -1, fft3.make_options(**opts))
-    fft3.fft3_plan_execute_host(eplan, h_in.data_ptr(), h_out.data_ptr(), sp)
-    e2e_steps = max(1, min(args.steps, 5))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e = None
+    if not args.no_e2e:
+        h_out = torch.empty_like(h_in).pin_memory()
+        eplan = fft3.fft3_plan_create_ex(n0, n1, n2, 1, 0, decomp, -1, fft3.make_options(**opts))
         fft3.fft3_plan_execute_host(eplan, h_in.data_ptr(), h_out.data_ptr(), sp)
-    barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    fft3.fft3_plan_destroy(eplan)
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = float(e2e_t.item()) / world
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            fft3.fft3_plan_execute_host(eplan, h_in.data_ptr(), h_out.data_ptr(), sp)
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+        fft3.fft3_plan_destroy(eplan)
+        del h_out
+        e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": float(e2e_t.item()) / world, "unit": "ms", "h2d_bytes_per_step": 8 * N,
+               "d2h_bytes_per_step": 8 * N}
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -312,10 +324,9 @@ def main():
                 p.close()
             except Exception as e:  # report, do not hide
                 extras[name] = {"error": str(e)}
-        # forward + inverse
         try:
-            pf = fft3.Plan(n, n, n, 1, decomposition=decomp, **opts)
-            pi = fft3.Plan(n, n, n, 1, decomposition=decomp, direction=fft3.FFT3_INVERSE, **opts)
+            pf = fft3.Plan(n0, n1, n2, 1, decomposition=decomp, **opts)
+            pi = fft3.Plan(n0, n1, n2, 1, decomposition=decomp, direction=fft3.FFT3_INVERSE, **opts)
             for _ in range(3):
                 pf.execute(x, out)
                 pi.execute(out, x)
@@ -333,11 +344,15 @@ def main():
             pi.close()
         except Exception as e:
             extras["forward_plus_inverse_ms"] = {"error": str(e)}
+        try:
+            extras["batched_4096_uneven"] = bench_batched(fft3, synth, torch, hbm)
+        except Exception as e:
+            extras["batched_4096_uneven"] = {"error": str(e)}
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_seconds > 0 and n0 == n1 == n2:
         try:
-            res = oracle_sample(n, args.cpu_seconds)
+            res = oracle_sample(n0, args.cpu_seconds)
             cpu = {"value": res["ms"], "unit": "ms", "cores": res["cores"], "kind": "oracle",
                    "sample": res["sample"]}
         except Exception as e:
@@ -348,12 +363,12 @@ def main():
             "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload, "dims": [n, n, n], "batch": 1,
+            "config": {"workload": workload, "dims": [n0, n1, n2], "batch": 1,
                        "decomposition": desc["decomposition"], "passes": [p["kind"] for p in desc["passes"]],
-                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "options": opts, "parallelism": f"replicas{world}" if world > 1 else "single",
                        "inputs": "uniform[-1,1) complex64, seed 4+rank",
-                       "l2": "no flush: each pass streams 8 GiB in and 8 GiB out, far larger than the 129 MB L2"},
-            "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+                       "l2": "no flush: each pass streams the whole array in and out, larger than the 129 MB L2"},
+            "e2e": e2e,
             "gpu_launches": len(pass_ms) * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -370,6 +385,43 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_batched(fft3, synth, torch, hbm):
+    """4096 independent 3D DFTs with dims drawn from {16..96} (seed 7) in one
+    graph-captured persistent launch: ms per batch, GB/s, roofline fractions."""
+    import numpy as np
+    dims = synth.batched_dims(4096, 7)
+    vols = dims.prod(axis=1)
+    offs = np.zeros(len(dims), np.int64)
+    offs[1:] = np.cumsum(vols[:-1])
+    total = int(vols.sum())
+    x = torch.empty(total, dtype=torch.complex64, device="cuda")
+    x.real.uniform_(-1, 1)
+    x.imag.uniform_(-1, 1)
+    out = torch.empty_like(x)
+    h = fft3.fft3_plan_create_many(dims, offs)
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        fft3.fft3_plan_execute(h, x.data_ptr(), out.data_ptr(), st.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(st)
+    for _ in range(reps):
+        fft3.fft3_plan_execute(h, x.data_ptr(), out.data_ptr(), st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    assert fft3.fft3_plan_check(h) == 0
+    desc = fft3.fft3_plan_describe(h)
+    fft3.fft3_plan_destroy(h)
+    one_sweep = 2 * 8 * total
+    return {"ms": ms, "elements": total, "problems": 4096, "items": desc["items"],
+            "GBps_one_sweep": one_sweep / (ms * 1e-3) / 1e9,
+            "frac_of_1_sweep": one_sweep / (ms * 1e-3) / 1e9 / hbm,
+            "frac_of_3_sweeps": 3 * one_sweep / (ms * 1e-3) / 1e9 / hbm,
+            "gflops": sum(5.0 * v * math.log2(v) for v in vols) / (ms * 1e-3) / 1e9}
 
 
 if __name__ == "__main__":
