@@ -189,6 +189,32 @@ int fft3_plan_execute_pass(fft3_plan p, int k, const void *in, void *out, void *
 int fft3_split_bf16(const float *d_x, int64_t count, uint16_t *d_hi, uint16_t *d_lo,
                     void *stream);
 
+/* ---- allocation-free transform (no counterpart in the paper) --------------
+ * For callers that must not allocate device memory: code embedded in a host
+ * application or framework that owns every device allocation and only hands
+ * out buffers, and latency-critical loops that cannot afford cudaMalloc and
+ * cudaFree, which may synchronise the whole device and can fail once memory is
+ * fragmented.  fft3_execute_noalloc computes the same transform as a
+ * pencil-pencil-pencil plan with FFT3_PPP_ROTATE, but its workspace and its
+ * twiddle tables live in fixed arrays inside the library (16 MiB + 128 KiB of
+ * device memory on every GPU that loads the library, held until the process
+ * exits) and it calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - in, out: device pointers to batch*n0*n1*n2 complex64 values (n0 fastest);
+ *     in is not modified; in == out returns FFT3_ERR_INPLACE_UNSUPPORTED.
+ *   - batch*n0*n1*n2 must not exceed FFT3_NOALLOC_MAX_ELEMENTS, otherwise the
+ *     call returns FFT3_ERR_UNSUPPORTED_SIZE and does nothing.
+ *   - The first call on a device looks up the arrays' device addresses on the
+ *     current device (cudaGetSymbolAddress); make that first call before any
+ *     stream capture.
+ *   - Every call shares the arrays: calls that overlap on the GPU (other
+ *     streams, other threads) race and corrupt each other's results; order
+ *     them on one stream or synchronise between them.
+ *   - Asynchronous on `stream` like fft3_plan_execute. */
+#define FFT3_NOALLOC_MAX_ELEMENTS (1 << 21)
+#define FFT3_NOALLOC_MAX_TWIDDLES (1 << 14)
+int fft3_execute_noalloc(int n0, int n1, int n2, int batch, int direction, const void *in, void *out,
+                         void *stream);
+
 /* ---- measured plan selection (no counterpart in the paper, which leaves the
  * choice of decomposition to the user; Section 4.3 shows no single one wins) */
 

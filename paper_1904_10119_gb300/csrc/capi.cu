@@ -668,3 +668,136 @@ int fft3_split_bf16(const float *d_x, int64_t count, uint16_t *d_hi, uint16_t *d
 }
 
 } // extern "C"
+
+// ---------------------------------------------- allocation-free transform -- //
+// fft3_execute_noalloc runs the rotated pencil-pencil-pencil schedule with its
+// workspace and its twiddle tables in the fixed device arrays below instead of
+// memory it allocates.  These arrays exist once per device for the life of the
+// process (the loader reserves them with the module), every call shares them,
+// and the data of the previous call stays in them; nothing in them needs to
+// start at zero, because every call writes the twiddles and the whole
+// workspace region it reads before reading it.
+static __device__ __align__(256) float2 g_noalloc_ws[FFT3_NOALLOC_MAX_ELEMENTS];
+static __device__ __align__(256) float2 g_noalloc_tw[FFT3_NOALLOC_MAX_TWIDDLES];
+static __device__ __align__(256) unsigned g_noalloc_err[64];
+
+namespace {
+
+struct NoallocDevice {
+    bool ready = false;
+    float2 *ws = nullptr, *tw = nullptr;
+    unsigned *err = nullptr;
+};
+std::mutex g_noalloc_mutex;
+NoallocDevice g_noalloc[64];
+
+// Host code cannot name a __device__ array's address directly: the symbol is a
+// host-side stand-in.  Ask the runtime for the device address, once per device
+// with that device current.
+int noalloc_setup(int dev, NoallocDevice **out)
+{
+    if (dev < 0 || dev >= 64)
+        return fail(FFT3_ERR_INVALID_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocDevice &d = g_noalloc[dev];
+    if (!d.ready) {
+        CUDA_TRY(cudaGetSymbolAddress((void **)&d.ws, g_noalloc_ws));
+        CUDA_TRY(cudaGetSymbolAddress((void **)&d.tw, g_noalloc_tw));
+        CUDA_TRY(cudaGetSymbolAddress((void **)&d.err, g_noalloc_err));
+        d.ready = true;
+    }
+    *out = &d;
+    return FFT3_OK;
+}
+
+} // namespace
+
+namespace fft3 {
+// Stage-major twiddles of one runtime line plan (fft_engine.cuh) computed on
+// the device from the plan itself, so no exponent list has to be uploaded:
+// entry e of stage s is w_n^{r*k*n/(NS*R)} with r = 1 + e' / NS, k = e' % NS.
+__global__ void k_noalloc_line_roots(LineRt L, float2 *out)
+{
+    int total = 0, NS = 1;
+    for (int s = 0; s < L.nst; ++s) {
+        total += (L.rad[s] - 1) * NS;
+        NS *= L.rad[s];
+    }
+    if (L.nst == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            out[0] = make_float2(1.f, 0.f);
+        return;
+    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        int s = 0, off = 0, ns = 1;
+        while ((L.rad[s] - 1) * ns <= e - off) {
+            off += (L.rad[s] - 1) * ns;
+            ns *= L.rad[s];
+            ++s;
+        }
+        const int idx = e - off, R = L.rad[s];
+        const int64_t r = 1 + idx / ns, k = idx % ns;
+        const int64_t m = r * k * (L.n / (ns * R)) % L.n;
+        const int64_t q = (4 * m) / L.n, rem = 4 * m - q * L.n;
+        double sn, cs;
+        sincospi((double)rem / (2.0 * (double)L.n), &sn, &cs);
+        double re, im;
+        switch (q & 3) {
+        case 0: re = cs; im = sn; break;
+        case 1: re = -sn; im = cs; break;
+        case 2: re = -cs; im = -sn; break;
+        default: re = sn; im = -cs; break;
+        }
+        out[e] = make_float2((float)re, (float)-im); // forward roots exp(-2 pi i m / n)
+    }
+}
+} // namespace fft3
+
+extern "C" int fft3_execute_noalloc(int n0, int n1, int n2, int batch, int direction, const void *in, void *out,
+                                    void *stream)
+{
+    if (!in || !out)
+        return fail(FFT3_ERR_INVALID_ARG, "null buffer");
+    if (in == out)
+        return fail(FFT3_ERR_INPLACE_UNSUPPORTED, "in-place execution is not supported (in == out)");
+    if (n0 < 1 || n1 < 1 || n2 < 1 || batch < 1)
+        return fail(FFT3_ERR_INVALID_ARG, "sizes and batch must be positive");
+    const int64_t elems = (int64_t)n0 * n1 * n2 * batch;
+    if (elems > FFT3_NOALLOC_MAX_ELEMENTS)
+        return fail(FFT3_ERR_UNSUPPORTED_SIZE,
+                    "fft3_execute_noalloc handles at most FFT3_NOALLOC_MAX_ELEMENTS (" +
+                        std::to_string((long long)FFT3_NOALLOC_MAX_ELEMENTS) + ") complex values per call; got " +
+                        std::to_string((long long)elems));
+    fft3_options o{};
+    o.variant = FFT3_PPP_ROTATE;
+    fft3_plan_s P; // host-side description only; every device pointer below is static
+    std::string err;
+    int rc = build_schedule(n0, n1, n2, batch, FFT3_C64_FP32, FFT3_PENCIL3, direction, &o, &P.sched, &err);
+    if (rc)
+        return fail(rc, err);
+    if (P.sched.tw_total > FFT3_NOALLOC_MAX_TWIDDLES)
+        return fail(FFT3_ERR_UNSUPPORTED_SIZE, "twiddle tables exceed FFT3_NOALLOC_MAX_TWIDDLES");
+    rc = check_device(&P.device);
+    if (rc)
+        return rc;
+    NoallocDevice *nd = nullptr;
+    rc = noalloc_setup(P.device, &nd);
+    if (rc)
+        return rc;
+    P.elems = elems;
+    P.d_tw = nd->tw;
+    P.d_ws = nd->ws;
+    P.ws_bytes = 0;
+    P.d_err = nd->err;
+    rc = build_launches(&P);
+    if (rc)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (const PassPlan &p : P.sched.passes) {
+        const TwSeg &sg = P.sched.tw[p.tw_seg[0]];
+        k_noalloc_line_roots<<<std::max(1, ((int)sg.m.size() + 255) / 256), 256, 0, st>>>(to_rt(p.line, 0),
+                                                                                          nd->tw + sg.off);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return fft3_plan_execute(&P, in, out, stream);
+}

@@ -88,6 +88,7 @@ def load() -> ctypes.CDLL:
         "fft3_mlp_adam_step": (i, [_P, _P, ctypes.c_float, _P]),
         "fft3_mlp_train": (i, [_P, _P, _P, i, i, i, ctypes.c_float, ctypes.c_ulonglong, _P]),
         "fft3_mlp_predict": (i, [_P, _P, i, _P]),
+        "fft3_execute_noalloc": (i, [i, i, i, i, i, _P, _P, _P]),
         "fft3_last_error": (ctypes.c_char_p, []),
         "fft3_version": (i, []),
     }
@@ -161,6 +162,15 @@ def _flat(dims):
 
 def fft3_plan_execute(plan: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
     _check(load().fft3_plan_execute(_P(plan), _P(in_ptr), _P(out_ptr), _P(stream)))
+
+
+FFT3_NOALLOC_MAX_ELEMENTS = 1 << 21
+
+
+def fft3_execute_noalloc(n0, n1, n2, batch, direction, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    """Transform without any device allocation (fixed library-owned scratch;
+    see include/fft3.h for the limits and the sharing rules)."""
+    _check(load().fft3_execute_noalloc(n0, n1, n2, batch, direction, _P(in_ptr), _P(out_ptr), _P(stream)))
 
 
 def fft3_plan_execute_host(plan: int, h_in: int, h_out: int, stream: int = 0) -> None:
