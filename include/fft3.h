@@ -84,6 +84,8 @@ typedef struct fft3_options {
     int slab_mode;    /* slab-pencil: 0 = auto, 1 = one block per slab in shared memory,
                          2 = L2-resident x/y stages in one persistent launch,
                          3 = x and y passes as two launches */
+    int tc_stages;    /* FFT3_C64_SPLITBF16_TC: 0 = every radix-16 stage on the tensor cores,
+                         1 = only the first radix-16 stage of each line */
     int reserved[8];  /* test hooks of the failure-detection tests, 0 in normal use:
                          [0] = s + 1 makes the x tiles of slab s never signal their
                          completion, so the waits of its y tiles expire;

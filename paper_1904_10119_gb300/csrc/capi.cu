@@ -222,6 +222,20 @@ static int build_launches(fft3_plan_s *P)
             L.cluster = p.p;
             L.probe_n = p.split_a * p.split_b;
             break;
+        case PK_VOLC: {
+            int cnt = 0;
+            const VolcKernel *vk = volc_kernels(&cnt);
+            L.func = (p.volc >= 0 && p.volc < cnt) ? vk[p.volc].func : nullptr;
+            L.cluster = p.p;
+            L.probe_n = p.split_a * p.split_b;
+            break;
+        }
+        case PK_JTC:
+            L.func = fk ? (p.tc_first_only ? fk->j_tc1 : fk->j_tc) : nullptr;
+            break;
+        case PK_CTC:
+            L.func = fk ? (p.tc_first_only ? fk->c_tc1 : fk->c_tc) : nullptr;
+            break;
         case PK_COPY:
             L.func = (const void *)&k_copy;
             L.probe_n = 1;
@@ -233,7 +247,7 @@ static int build_launches(fft3_plan_s *P)
         int rc = prepare_func(L.func, L.smem);
         if (rc)
             return rc;
-        if (p.kind == PK_VOL) {
+        if (p.kind == PK_VOL || p.kind == PK_VOLC) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -246,7 +260,7 @@ static int build_launches(fft3_plan_s *P)
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int ncl = 0;
-            CUDA_TRY(cudaOccupancyMaxActiveClusters(&ncl, (const void *)&k_vol, &cfg));
+            CUDA_TRY(cudaOccupancyMaxActiveClusters(&ncl, L.func, &cfg));
             if (ncl < 1)
                 return fail(FFT3_ERR_UNSUPPORTED_SIZE, "volumetric cluster does not fit on the GPU");
             int64_t g = std::min<int64_t>(ncl, p.ntiles);
@@ -375,10 +389,6 @@ int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int d
     if (rc) {
         delete P;
         return fail(rc, err);
-    }
-    if (dtype == FFT3_C64_SPLITBF16_TC) {
-        delete P;
-        return fail(FFT3_ERR_UNSUPPORTED_SIZE, "split-BF16 tensor-core path is not built in this library");
     }
     rc = check_device(&P->device);
     if (rc) {

@@ -5,6 +5,7 @@
 
 #include "pass_kernels.cuh"
 #include "plans.h"
+#include "pass_tc.cuh"
 #include "pass_tma.cuh"
 #include "slab_l2.cuh"
 
@@ -41,6 +42,26 @@ constexpr const void *pass_ctma_ptr()
         return nullptr;
 }
 
+template <int N, int T, class Rad, bool FIRST_ONLY>
+constexpr const void *pass_j_tc_ptr()
+{
+    constexpr int mask = FIRST_ONLY ? tc_mask_first(Rad{}) : tc_mask_all(Rad{});
+    if constexpr (mask != 0 && N >= 128 && T * lpt_j(T) <= 512 && (T * lpt_j(T)) % 32 == 0)
+        return (const void *)&k_pass_j_tc<N, T, Rad, lpt_j(T), mask>;
+    else
+        return nullptr;
+}
+
+template <int N, int T, class Rad, bool FIRST_ONLY>
+constexpr const void *pass_c_tc_ptr()
+{
+    constexpr int mask = FIRST_ONLY ? tc_mask_first(Rad{}) : tc_mask_all(Rad{});
+    if constexpr (mask != 0 && N >= 128 && T * 8 <= 512)
+        return (const void *)&k_pass_c_tc<N, T, Rad, 8, mask>;
+    else
+        return nullptr;
+}
+
 } // namespace fft3
 
 #define FFT3_KERNEL_ROW(ID, N, T, ...)                                                          \
@@ -50,4 +71,8 @@ constexpr const void *pass_ctma_ptr()
      fft3::pass_c_ptr<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_c(T, 16)>(),                  \
      fft3::pass_c_ptr<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_c(T, 8)>(),                   \
      fft3::slab_l2_ptr<N, T, fft3::Radices<__VA_ARGS__>>(),                                    \
-     fft3::pass_ctma_ptr<N, T, fft3::Radices<__VA_ARGS__>>()},
+     fft3::pass_ctma_ptr<N, T, fft3::Radices<__VA_ARGS__>>(),                                  \
+     fft3::pass_j_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, false>(),                            \
+     fft3::pass_j_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, true>(),                             \
+     fft3::pass_c_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, false>(),                            \
+     fft3::pass_c_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, true>()},

@@ -48,6 +48,16 @@ static void init_meta()
     done = true;
 }
 
+#define FFT3_VOLC_META(N, A, B, P, LPT, TA, RA, TB, RB) {N, A, B, P, LPT, LPT *(A / P) * TB, TA, TB, {RA}, {RB}, nullptr},
+static const VolcKernel g_volc_meta[] = {FFT3_VOLC_LIST(FFT3_VOLC_META)};
+#undef FFT3_VOLC_META
+
+const VolcKernel *volc_meta(int *count)
+{
+    *count = (int)(sizeof(g_volc_meta) / sizeof(g_volc_meta[0]));
+    return g_volc_meta;
+}
+
 int fixed_plan_count() { return g_nmeta; }
 const FixedPlanMeta &fixed_plan_meta(int id)
 {
@@ -265,6 +275,40 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         return rc;
     const bool contig_in = g.ij == 1;
     const bool strided_in = g.ic == 1 && g.oc == 1;
+    if (s->dtype == FFT3_C64_SPLITBF16_TC && !rotate && n >= 128) {
+        // prefer a candidate plan that has tensor-core kernels for this layout
+        std::vector<int> fc = fixed_candidates(n);
+        for (size_t k = 0; k < fc.size(); ++k) {
+            const FixedPlanMeta &m = g_meta[fc[(k + order) % fc.size()]];
+            bool has16 = false;
+            for (int i = 0; i < m.nrad; ++i)
+                has16 |= m.rad[i] == 16;
+            const bool jok = contig_in && g.ok == 1 && tc_j_ok(n, m.T, has16);
+            const bool cok = strided_in && tc_c_ok(n, m.T, has16);
+            if (!jok && !cok)
+                continue;
+            p.line.n = n;
+            p.line.fixed = m.id;
+            p.line.T = m.T;
+            p.line.nst = m.nrad;
+            for (int i = 0; i < m.nrad; ++i)
+                p.line.rad[i] = m.rad[i];
+            p.kind = jok ? PK_JTC : PK_CTC;
+            p.lpt = jok ? lpt_j(m.T) : lpt_c_tc();
+            p.tc_first_only = s->opts.tc_stages == 1;
+            p.tw_seg[0] = line_seg(s, p.line);
+            std::vector<int64_t> w16(16);
+            for (int i = 0; i < 16; ++i)
+                w16[i] = i;
+            p.tw_seg[2] = add_seg(s, 16, std::move(w16));
+            const int twl = tw_slots_h((int)s->tw[p.tw_seg[0]].m.size()) + 16;
+            p.threads = m.T * p.lpt;
+            p.smem_bytes = twl * 8 + 2 * p.lpt * (jok ? pitch_h(n) : n) * 8;
+            set_tiles(&p);
+            *out = p;
+            return FFT3_OK;
+        }
+    }
     // strided tiles: 16 adjacent columns (128-byte rows) unless 8 are asked for;
     // tile_lines == kTileTma selects the TMA double-buffered kernel
     int want_c = s->opts.tile_lines == 8 ? 8 : 16;
@@ -348,9 +392,66 @@ static int vol_smem(int n, int p, int a, int b, int lpt, int twlen)
     return twlen * 8 + (sub_b + sub_a + big) * 8;
 }
 
+static LineChoice fixed_line(int n, int T, const int *rad)
+{
+    LineChoice lc;
+    lc.n = n;
+    lc.fixed = -1;
+    lc.T = T;
+    lc.nst = 0;
+    while (lc.nst < 4 && rad[lc.nst] > 0) {
+        lc.rad[lc.nst] = rad[lc.nst];
+        ++lc.nst;
+    }
+    return lc;
+}
+
+// Compile-time split of a strided line when one is compiled for (n, p).
+static bool make_volc_pass(Schedule *s, int d, int n, int p, const PassGeom &g, int src, int dst, PassPlan *out)
+{
+    if (g.ic != 1 || g.oc != 1)
+        return false;
+    int cnt = 0;
+    const VolcKernel *vk = volc_meta(&cnt);
+    for (int i = 0; i < cnt; ++i) {
+        if (vk[i].n != n || vk[i].p != p)
+            continue;
+        PassPlan q;
+        q.kind = PK_VOLC;
+        q.volc = i;
+        q.dim = d;
+        q.g = g;
+        q.src = src;
+        q.dst = dst;
+        q.p = p;
+        q.split_a = vk[i].a;
+        q.split_b = vk[i].b;
+        q.line = fixed_line(vk[i].b, vk[i].tb, vk[i].rb);  // DFT_B on rows
+        q.line2 = fixed_line(vk[i].a, vk[i].ta, vk[i].ra); // DFT_A on columns
+        q.tw_seg[0] = line_seg(s, q.line);
+        q.tw_seg[1] = line_seg(s, q.line2);
+        std::vector<int64_t> m(n);
+        for (int k = 0; k < n; ++k)
+            m[k] = k;
+        q.tw_seg[2] = add_seg(s, n, std::move(m));
+        int twlen = 0;
+        for (int k = 0; k < 3; ++k)
+            twlen += tw_slots_h((int)s->tw[q.tw_seg[k]].m.size());
+        q.lpt = vk[i].lpt;
+        q.threads = vk[i].threads;
+        q.smem_bytes = twlen * 8 + 2 * (n / p) * q.lpt * 8;
+        set_tiles(&q);
+        *out = q;
+        return true;
+    }
+    return false;
+}
+
 static int make_vol_pass(Schedule *s, int d, int n, int p, const PassGeom &g, int src, int dst,
                          PassPlan *out, std::string *err)
 {
+    if (make_volc_pass(s, d, n, p, g, src, dst, out))
+        return FFT3_OK;
     PassPlan q;
     q.kind = PK_VOL;
     q.dim = d;
@@ -509,6 +610,8 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
     s.dtype = dtype; s.direction = direction;
     if (opts)
         s.opts = *opts;
+    if (decomp == FFT3_AUTO && dtype == FFT3_C64_SPLITBF16_TC)
+        decomp = FFT3_PENCIL3;
     if (decomp == FFT3_AUTO) {
         // Fixed default when no cost model is loaded: slab-pencil when the
         // slab stage can be fused (fewest HBM sweeps), else pencil-pencil-pencil.
@@ -517,6 +620,12 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
             decomp = FFT3_SLAB_PENCIL;
         else
             decomp = FFT3_PENCIL3;
+    }
+    if (dtype == FFT3_C64_SPLITBF16_TC) {
+        if (decomp != FFT3_PENCIL3 || s.opts.variant != FFT3_PPP_NATURAL) {
+            *err = "the split-BF16 tensor-core path runs the pencil-pencil-pencil decomposition (natural layout)";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
     }
     s.decomp = decomp;
     int64_t N = (int64_t)n0 * n1 * n2;
@@ -585,9 +694,18 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
             int p = s.opts.mesh[d];
             bool explicit_mesh = p > 0;
             if (!explicit_mesh) {
-                p = 2; // the paper's smallest 3D mesh is 2 x 2 x 2
+                // Automatic mesh: the contiguous dimension stays whole (a split
+                // of it buys no coalescing on one GPU); a strided dimension is
+                // split over 4 blocks where a compiled split exists, else over 2
+                // (the paper's smallest mesh extent).
+                int cnt = 0;
+                const VolcKernel *vk = volc_meta(&cnt);
+                p = 2;
+                for (int i = 0; i < cnt; ++i)
+                    if (vk[i].n == ns[d] && vk[i].p == 4)
+                        p = 4;
                 int a, b;
-                if (!volumetric_split(ns[d], p, &a, &b))
+                if (d == 0 || !volumetric_split(ns[d], p, &a, &b))
                     p = 1;
             }
             if (p != 1 && p != 2 && p != 4 && p != 8) {
@@ -631,8 +749,9 @@ static const char *kind_name(int k)
 {
     static const char *names[] = {"line_contig", "line_contig_rotate", "line_strided", "line_runtime",
                                   "slab_smem", "slab_l2", "volumetric_split", "copy", "line_tc",
-                                  "line_strided_tma"};
-    return (k >= 0 && k <= 9) ? names[k] : "?";
+                                  "line_strided_tma", "line_contig_tc", "line_strided_tc",
+                                  "volumetric_split_fixed"};
+    return (k >= 0 && k <= 12) ? names[k] : "?";
 }
 static const char *buf_name(int b)
 {
@@ -668,13 +787,13 @@ std::string Schedule::json() const
           << ",\"src\":\"" << buf_name(p.src) << "\",\"dst\":\"" << buf_name(p.dst)
           << "\",\"line\":";
         line_json(o, p.line);
-        if (p.kind == PK_SLAB || p.kind == PK_VOL || p.kind == PK_SLABL2) {
+        if (p.kind == PK_SLAB || p.kind == PK_VOL || p.kind == PK_SLABL2 || p.kind == PK_VOLC) {
             o << ",\"line2\":";
             line_json(o, p.line2);
         }
         o << ",\"lpt\":" << p.lpt << ",\"threads\":" << p.threads << ",\"smem\":" << p.smem_bytes
           << ",\"tiles\":" << p.ntiles;
-        if (p.kind == PK_VOL)
+        if (p.kind == PK_VOL || p.kind == PK_VOLC)
             o << ",\"p\":" << p.p << ",\"a\":" << p.split_a << ",\"b\":" << p.split_b;
         const PassGeom &g = p.g;
         o << ",\"geom\":{\"C\":" << g.C << ",\"A\":" << g.A << ",\"B\":" << g.B << ",\"ij\":" << g.ij

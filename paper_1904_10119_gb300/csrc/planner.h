@@ -23,6 +23,9 @@ enum PassKind {
     PK_COPY = 7,   // all dimensions of length 1: plain copy
     PK_TC = 8,     // split-BF16 tensor-core line pass
     PK_CTMA = 9,   // fixed plan, strided columns, TMA double-buffered tiles
+    PK_JTC = 10,   // split-BF16 tensor-core radix-16 stages, contiguous lines
+    PK_CTC = 11,   // split-BF16 tensor-core radix-16 stages, strided columns
+    PK_VOLC = 12,  // compile-time volumetric split of strided lines (k_volc.cu)
 };
 
 enum BufId { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };
@@ -57,6 +60,8 @@ struct PassPlan {
     int smem_bytes = 0;  // dynamic shared memory per block
     int64_t ntiles = 0, tiles_c = 0;
     int slabs_per_chunk = 0;
+    bool tc_first_only = false; // PK_JTC / PK_CTC: only the first radix-16 stage on tensor cores
+    int volc = -1;              // PK_VOLC: index into the compiled volumetric list
 };
 
 struct Schedule {

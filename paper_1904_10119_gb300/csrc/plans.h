@@ -38,7 +38,30 @@
 
 #define FFT3_FIXED_PLANS(X) FFT3_FIXED_PLANS_A(X) FFT3_FIXED_PLANS_B(X)
 
+// Compile-time volumetric splits of strided lines (k_volc.cu): line length N =
+// A * B over a cluster of P blocks, LPT columns per tile, sub-line plans
+// (TA threads, radix list RA) for DFT_A and (TB, RB) for DFT_B.
+#define FFT3_COMMA ,
+#define FFT3_VOLC_LIST(X)                                              \
+    X(1024, 32, 32, 4, 16, 2, 16 FFT3_COMMA 2, 2, 16 FFT3_COMMA 2)      \
+    X(1024, 32, 32, 2, 16, 2, 16 FFT3_COMMA 2, 2, 16 FFT3_COMMA 2)      \
+    X(1024, 32, 32, 8, 16, 2, 16 FFT3_COMMA 2, 2, 16 FFT3_COMMA 2)      \
+    X(512, 16, 32, 4, 16, 1, 16, 2, 16 FFT3_COMMA 2)                    \
+    X(512, 16, 32, 2, 16, 1, 16, 2, 16 FFT3_COMMA 2)                    \
+    X(256, 16, 16, 4, 16, 1, 16, 1, 16)                                 \
+    X(256, 16, 16, 2, 16, 1, 16, 1, 16)
+
 namespace fft3 {
+
+struct VolcKernel {
+    int n, a, b, p, lpt, threads, ta, tb;
+    int ra[4], rb[4];
+    const void *func; // nullptr in the host-only metadata
+};
+// Compiled list (device translation unit) and its size.
+const VolcKernel *volc_kernels(int *count);
+// Host-only metadata: the same list without kernel pointers.
+const VolcKernel *volc_meta(int *count);
 
 struct FixedPlanMeta {
     int id, n, T, nrad;
@@ -58,6 +81,9 @@ struct FixedKernels {
     const void *c8;   // k_pass_c, 8 lines per tile
     const void *l2;   // k_slab_l2 (square slabs), 0 if not compiled
     const void *ctma; // k_pass_c_tma (TMA-pipelined strided lines), 0 if not compiled
+    // split-BF16 tensor-core variants: every radix-16 stage / the first one only
+    const void *j_tc, *j_tc1; // contiguous lines, lpt_j(T) lines per tile
+    const void *c_tc, *c_tc1; // strided lines, 8 lines per tile
 };
 const FixedKernels *fixed_kernels(int id);
 
@@ -66,6 +92,13 @@ const FixedKernels *fixed_kernels(int id);
 constexpr int lpt_j(int T) { return T >= 256 ? 1 : 256 / T; }
 constexpr int lpt_rot(int T) { return T >= 64 ? 8 : (128 / T > 16 ? 128 / T : 16); }
 constexpr int lpt_c(int T, int want) { return T * want <= 1024 ? want : 0; }
+// Split-BF16 tensor-core variants exist for plans with a radix-16 stage and
+// N >= 128, with at most 512 threads per block (k_fixed.cuh instantiates the
+// same conditions).
+constexpr int lpt_c_tc() { return 8; }
+constexpr bool tc_j_ok(int N, int T, bool has16) { return has16 && N >= 128 && T * lpt_j(T) <= 512 && (T * lpt_j(T)) % 32 == 0; }
+constexpr bool tc_c_ok(int N, int T, bool has16) { return has16 && N >= 128 && T * lpt_c_tc() <= 512; }
+
 // TMA-pipelined strided pass: two tiles of N x LPT complex values in flight.
 constexpr int lpt_tma(int N, int T) { return (N >= 1024 ? 8 : 16) * T <= 1024 && N >= 16 ? (N >= 1024 ? 8 : 16) : 0; }
 

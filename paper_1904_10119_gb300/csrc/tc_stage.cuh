@@ -78,80 +78,68 @@ __device__ __forceinline__ void tc_build_w(TcW &w, const float2 *w16)
             }
 }
 
-// One radix-16 stage over `nbf` butterflies (nbf a multiple of 8) of lines of
-// N points; butterfly b of the stage is (line, q).  GROUP_LINES: a group of 8
-// butterflies is 8 adjacent lines at one q (column tiles) instead of 8
-// adjacent q of one line (line tiles).  Src/Dst: accessors acc(line, pos)
-// returning float2 (load) / storing.  All loads of the stage happen before a
-// block barrier and all stores after it, so Src and Dst may alias.
-template <int N, int NS, int LPT, bool GROUP_LINES, int MAXG, class Src, class Dst>
+// Butterfly (line, q) of group `grp`, lane group g (GROUP_LINES: a group is
+// 8 adjacent lines at one q; otherwise 8 adjacent q of one line).
+template <int NB, int LPT, bool GROUP_LINES>
+__device__ __forceinline__ void tc_butterfly(int grp, int n, int &line, int &q)
+{
+    if constexpr (GROUP_LINES) {
+        q = grp / (LPT / 8);
+        line = (grp % (LPT / 8)) * 8 + n;
+    } else {
+        line = grp / (NB / 8);
+        q = (grp % (NB / 8)) * 8 + n;
+    }
+}
+
+// One radix-16 stage of lines of N points on the tensor cores: the NB*LPT
+// butterflies (line, q) of a tile, in groups of 8, each warp taking every
+// nwarps-th group.  Src and Dst are tile accessors acc(line, pos) and must not
+// alias (the stage streams group by group; the caller ping-pongs buffers).
+template <int N, int NS, int LPT, bool GROUP_LINES, class Src, class Dst>
 __device__ __forceinline__ void tc_stage16(const Src &src, const Dst &dst, const float2 *tw, const TcW &w)
 {
     constexpr int NB = N / 16;
-    constexpr int NBF = NB * LPT;
-    constexpr int NGROUPS = NBF / 8;
+    constexpr int NGROUPS = NB * LPT / 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int r4[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
-    float2 v[MAXG][4];
+    for (int grp = warp; grp < NGROUPS; grp += nwarps) {
+        int line, q;
+        tc_butterfly<NB, LPT, GROUP_LINES>(grp, g, line, q);
+        float2 v[4];
 #pragma unroll
-    for (int gi = 0; gi < MAXG; ++gi) {
-        const int grp = warp + gi * nwarps;
-        if (grp < NGROUPS) {
-            int line, q;
-            if constexpr (GROUP_LINES) {
-                q = grp / (LPT / 8);
-                line = (grp % (LPT / 8)) * 8 + g;
-            } else {
-                line = grp / (NB / 8);
-                q = (grp % (NB / 8)) * 8 + g;
+        for (int e = 0; e < 4; ++e) {
+            const int r = 2 * t + (e & 1) + ((e & 2) ? 8 : 0);
+            float2 x = src(line, q + r * NB);
+            if constexpr (NS > 1) {
+                if (r > 0)
+                    x = cmul(x, tw[(r - 1) * NS + (q % NS)]);
             }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                float2 x = src(line, q + r4[e] * NB);
-                if constexpr (NS > 1) {
-                    if (r4[e] > 0)
-                        x = cmul(x, tw[(r4[e] - 1) * NS + (q % NS)]);
-                }
-                v[gi][e] = x;
-            }
+            v[e] = x;
         }
-    }
-    __syncthreads();
+        uint32_t bh[2][2], bl[2][2]; // [xr|xi][register]
+        split_pair(v[0].x, v[1].x, bh[0][0], bl[0][0]);
+        split_pair(v[2].x, v[3].x, bh[0][1], bl[0][1]);
+        split_pair(v[0].y, v[1].y, bh[1][0], bl[1][0]);
+        split_pair(v[2].y, v[3].y, bh[1][1], bl[1][1]);
+        float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-    for (int gi = 0; gi < MAXG; ++gi) {
-        const int grp = warp + gi * nwarps;
-        if (grp < NGROUPS) {
-            uint32_t bh[2][2], bl[2][2]; // [xr|xi][register]
-            split_pair(v[gi][0].x, v[gi][1].x, bh[0][0], bl[0][0]);
-            split_pair(v[gi][2].x, v[gi][3].x, bh[0][1], bl[0][1]);
-            split_pair(v[gi][0].y, v[gi][1].y, bh[1][0], bl[1][0]);
-            split_pair(v[gi][2].y, v[gi][3].y, bh[1][1], bl[1][1]);
-            float d[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        for (int mb = 0; mb < 2; ++mb)
 #pragma unroll
-            for (int mb = 0; mb < 2; ++mb)
-#pragma unroll
-                for (int kb = 0; kb < 2; ++kb) {
-                    mma_bf16_16816(d[mb], w.lo[mb][kb], bh[kb][0], bh[kb][1]);
-                    mma_bf16_16816(d[mb], w.hi[mb][kb], bl[kb][0], bl[kb][1]);
-                    mma_bf16_16816(d[mb], w.hi[mb][kb], bh[kb][0], bh[kb][1]);
-                }
-            // outputs k in {g, g+8} of butterflies n in {2t, 2t+1} of the group
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int k = g + ((e & 2) ? 8 : 0);
-                const int n = 2 * t + (e & 1);
-                int line, q;
-                if constexpr (GROUP_LINES) {
-                    q = grp / (LPT / 8);
-                    line = (grp % (LPT / 8)) * 8 + n;
-                } else {
-                    line = grp / (NB / 8);
-                    q = (grp % (NB / 8)) * 8 + n;
-                }
-                const int base = (NS == 1) ? q * 16 : (q / NS) * NS * 16 + (q % NS);
-                dst(line, base + k * NS, make_float2(d[0][e], d[1][e]));
+            for (int kb = 0; kb < 2; ++kb) {
+                // small products first, the hi x hi product last
+                mma_bf16_16816(d[mb], w.lo[mb][kb], bh[kb][0], bh[kb][1]);
+                mma_bf16_16816(d[mb], w.hi[mb][kb], bl[kb][0], bl[kb][1]);
+                mma_bf16_16816(d[mb], w.hi[mb][kb], bh[kb][0], bh[kb][1]);
             }
+        // this lane holds outputs k in {g, g+8} of butterflies n in {2t, 2t+1}
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = g + ((e & 2) ? 8 : 0);
+            int ol, oq;
+            tc_butterfly<NB, LPT, GROUP_LINES>(grp, 2 * t + (e & 1), ol, oq);
+            const int base = (NS == 1) ? oq * 16 : (oq / NS) * NS * 16 + (oq % NS);
+            dst(ol, base + k * NS, make_float2(d[0][e], d[1][e]));
         }
     }
 }

@@ -39,7 +39,8 @@ class Fft3Error(RuntimeError):
 
 class fft3_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("radix_order", ctypes.c_int), ("tile_lines", ctypes.c_int),
-                ("mesh", ctypes.c_int * 3), ("slab_mode", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("mesh", ctypes.c_int * 3), ("slab_mode", ctypes.c_int), ("tc_stages", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
 
 
 _lib = None
@@ -116,7 +117,7 @@ def _check(rc: int) -> int:
     return rc
 
 
-def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mode=0) -> fft3_options:
+def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mode=0, tc_stages=0) -> fft3_options:
     o = fft3_options()
     o.variant = int(variant)
     o.radix_order = int(radix_order)
@@ -124,6 +125,7 @@ def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mo
     for k in range(3):
         o.mesh[k] = int(mesh[k])
     o.slab_mode = int(slab_mode)
+    o.tc_stages = int(tc_stages)
     return o
 
 

@@ -100,7 +100,9 @@ def test_schedule_volumetric_split_rule():
     """One exchange per dimension needs n = a*b with p | a and p | b (Section 3.2)."""
     s = fft3.fft3_plan_schedule(1024, 256, 64, 1, 0, fft3.FFT3_VOLUMETRIC, -1,
                                 fft3.make_options(mesh=(2, 4, 8)))
-    assert _kinds(s) == ["volumetric_split"] * 3
+    # the strided 256-point lines over 4 blocks have a compiled split; the
+    # others run the runtime-radix split
+    assert _kinds(s) == ["volumetric_split", "volumetric_split_fixed", "volumetric_split"]
     for p, mesh in zip(s["passes"], (2, 4, 8)):
         assert p["p"] == mesh and p["a"] % mesh == 0 and p["b"] % mesh == 0
         assert p["a"] * p["b"] == [1024, 256, 64][p["dim"]]
@@ -168,3 +170,23 @@ def test_null_arguments(lib):
     assert lib.fft3_plan_create(None, 8, 8, 8, 1, 0, 1, -1) == -1
     assert lib.fft3_plan_execute(None, None, None, None) == -1
     assert lib.fft3_plan_destroy(None) == -1
+
+
+def test_volumetric_automatic_mesh_and_compiled_splits():
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_VOLUMETRIC, -1)
+    assert _kinds(s) == ["line_contig", "volumetric_split_fixed", "volumetric_split_fixed"]
+    for p in s["passes"][1:]:
+        assert p["p"] == 4 and p["a"] == 32 and p["b"] == 32 and p["lpt"] == 16 and p["threads"] == 256
+    s = fft3.fft3_plan_schedule(256, 512, 1024, 1, 0, fft3.FFT3_VOLUMETRIC, -1, fft3.make_options(mesh=(0, 2, 8)))
+    assert "p" not in s["passes"][0] and s["passes"][1]["p"] == 2 and s["passes"][2]["p"] == 8
+
+
+def test_tensor_core_schedule():
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_AUTO, -1)
+    assert _kinds(s) == ["line_contig_tc", "line_strided_tc", "line_strided_tc"]
+    assert all(16 in p["line"]["radices"] for p in s["passes"])
+    # short lines fall back to the FP32 kernels; other decompositions are FP32 only
+    s = fft3.fft3_plan_schedule(64, 1024, 32, 1, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_PENCIL3, -1)
+    assert _kinds(s) == ["line_contig", "line_strided_tc", "line_strided"]
+    with pytest.raises(fft3.Fft3Error):
+        fft3.fft3_plan_schedule(64, 64, 64, 1, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_SLAB_PENCIL, -1)
