@@ -19,7 +19,8 @@ struct BatchCube {
     int decomp;     // BD_SLAB: 2D slabs then z lines; BD_PPP: x, y, z lines
     int nph;        // phases (2 or 3)
     int items[3];   // work items of each phase
-    int lpt;        // columns per tile of the strided phases
+    int lpt;        // columns per tile of the z phase
+    int lpty;       // columns per tile of the y phase (pencil-pencil-pencil)
     int spi;        // slabs (BD_SLAB) or rows (BD_PPP) per phase-0 item
 };
 

@@ -98,24 +98,34 @@ static int line_index(BatchState *b, std::map<std::pair<int, int>, int> &idx, in
     return id;
 }
 
-// Decodes a tuning code (0 = defaults).
-static void decode_tuning(int code, int n0, int n1, int n2, int *decomp, int *order, int *lpt, int *spi)
+// Elements per shared buffer that keep four blocks of 256 threads on an SM.
+constexpr int kBatchBufTarget = 3072;
+
+// Decodes a tuning code (0 = defaults): items of roughly 2-4 thousand
+// elements, buffers of at most kBatchBufTarget elements unless a slab needs more.
+static void decode_tuning(int code, int n0, int n1, int n2, int *decomp, int *order, int *lpt, int *lpty,
+                          int *spi)
 {
     const int d = code & 3, o = (code >> 2) & 7, l = (code >> 5) & 7, s = (code >> 8) & 7;
     // slab-pencil keeps the whole slab in shared memory; prefer it for small slabs
-    *decomp = d == 1 ? BD_SLAB : d == 2 ? BD_PPP : (n0 * n1 <= 4096 ? BD_SLAB : BD_PPP);
+    *decomp = d == 1 ? BD_SLAB : d == 2 ? BD_PPP : (n1 * pitch_b(n0) <= kBatchBufTarget ? BD_SLAB : BD_PPP);
     if (*decomp == BD_SLAB && 2 * n1 * pitch_b(n0) * 8 > 200 * 1024)
         *decomp = BD_PPP;
     *order = o ? o - 1 : 0;
-    *lpt = l ? (2 << l) : 16; // 1 -> 4, 2 -> 8, 3 -> 16, 4 -> 32
+    if (l) {
+        *lpt = 2 << l; // 1 -> 4, 2 -> 8, 3 -> 16, 4 -> 32, 5 -> 64, 6 -> 128
+        *lpty = std::min(n0, *lpt);
+    } else {
+        *lpt = std::max(16, std::min(4096 / n2, kBatchBufTarget / pitch_b(n2)) / 16 * 16);
+        *lpty = std::max(1, std::min(n0, kBatchBufTarget / pitch_b(n1)));
+    }
     if (s) {
         *spi = 1 << (s - 1);
     } else if (*decomp == BD_SLAB) {
         *spi = std::max(1, 4096 / (n0 * n1));
     } else {
-        *spi = std::max(1, 2048 / n0);
+        *spi = std::max(1, kBatchBufTarget / pitch_b(n0));
     }
-    (void)n2;
 }
 
 int batch_describe(const BatchState *b, std::string *json)
@@ -242,13 +252,14 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
             code |= 1;
         if (decomposition == FFT3_PENCIL3 && (code & 3) == 0)
             code |= 2;
-        int decomp, order, lpt, spi;
-        decode_tuning(code, n0, n1, n2, &decomp, &order, &lpt, &spi);
+        int decomp, order, lpt, lpty, spi;
+        decode_tuning(code, n0, n1, n2, &decomp, &order, &lpt, &lpty, &spi);
         BatchCube &c = b->cubes[i];
         c.off = offsets[i];
         c.n0 = n0; c.n1 = n1; c.n2 = n2;
         c.decomp = decomp;
         c.lpt = lpt;
+        c.lpty = lpty;
         int rc = 0, lx = line_index(b, lidx, n0, order, &err), ly = line_index(b, lidx, n1, order, &err),
             lz = line_index(b, lidx, n2, order, &err);
         if (lx < 0 || ly < 0 || lz < 0) {
@@ -267,9 +278,9 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
             c.spi = std::max(1, std::min(spi, n1 * n2));
             c.nph = 3;
             c.items[0] = (n1 * n2 + c.spi - 1) / c.spi;
-            c.items[1] = n2 * ((n0 + lpt - 1) / lpt);
+            c.items[1] = n2 * ((n0 + lpty - 1) / lpty);
             c.items[2] = (n0 * n1 + lpt - 1) / lpt;
-            bufmax = std::max(bufmax, std::max(c.spi * pitch_b(n0), std::max(lpt * pitch_b(n1), lpt * pitch_b(n2))));
+            bufmax = std::max(bufmax, std::max(c.spi * pitch_b(n0), std::max(lpty * pitch_b(n1), lpt * pitch_b(n2))));
         }
         (void)rc;
         b->tuning[i] = (decomp == BD_SLAB ? 1 : 2) | ((order + 1) << 2) |

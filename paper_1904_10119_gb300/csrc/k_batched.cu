@@ -121,9 +121,9 @@ __global__ void __launch_bounds__(256) k_batched(BatchArgs a)
             const int nl = (int)min((int64_t)cb.spi, n1 * n2 - r0);
             batch_lines(src + r0 * n0, dst + r0 * n0, !first, a.lines[cb.lx], a.tw, nl, n0, 1, A, B, conj);
         } else if (dim == 1) { // columns x in slab z, element stride n0
-            const int per = (int)((n0 + cb.lpt - 1) / cb.lpt);
-            const int64_t z = it.index / per, c0 = (int64_t)(it.index % per) * cb.lpt;
-            const int nl = (int)min((int64_t)cb.lpt, n0 - c0);
+            const int per = (int)((n0 + cb.lpty - 1) / cb.lpty);
+            const int64_t z = it.index / per, c0 = (int64_t)(it.index % per) * cb.lpty;
+            const int nl = (int)min((int64_t)cb.lpty, n0 - c0);
             const int64_t base = z * n0 * n1 + c0;
             batch_lines(src + base, dst + base, !first, a.lines[cb.ly], a.tw, nl, 1, n0, A, B, conj);
         } else { // columns c of the n0*n1 plane, element stride n0*n1

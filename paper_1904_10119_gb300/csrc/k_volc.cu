@@ -76,13 +76,23 @@ __global__ void __launch_bounds__(LPT *(A / P) * TB) k_volc(PassArgs a)
             T0[e] = cmul(T0[e], W[(i0 * k1) % N]);
         }
         cluster.sync();
-        // (III) T1[(v*A + i0)*LPT + l] = T0 of block (i0 mod P) at row (i0/P)*B + k1, k1 = r + P*v
-#pragma unroll 4
-        for (int e = tid; e < BP * A * LPT; e += THREADS) {
-            const int row = e / LPT, v = row / A, i0 = row - v * A;
-            const int owner = i0 % P, k1 = r + P * v;
-            const float2 *src = cluster.map_shared_rank(T0, owner);
-            T1[e] = src[((i0 / P) * B + k1) * LPT + l];
+        // (III) T1[(v*A + i0)*LPT + l] = T0 of block (i0 mod P) at row (i0/P)*B + k1, k1 = r + P*v.
+        // All of a thread's remote loads are issued before any local store.
+        {
+            constexpr int PER = BP * A * LPT / THREADS;
+            static_assert(PER * THREADS == BP * A * LPT, "exchange divides evenly");
+            float2 stage[PER];
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int e = tid + k * THREADS;
+                const int row = e / LPT, v = row / A, i0 = row - v * A;
+                const int owner = i0 % P, k1 = r + P * v;
+                const float2 *src = cluster.map_shared_rank(T0, owner);
+                stage[k] = src[((i0 / P) * B + k1) * LPT + l];
+            }
+#pragma unroll
+            for (int k = 0; k < PER; ++k)
+                T1[tid + k * THREADS] = stage[k];
         }
         cluster.sync();
         { // (IV) DFT_A on sub-lines (v, l)

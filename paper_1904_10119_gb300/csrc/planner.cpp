@@ -414,7 +414,8 @@ static bool make_volc_pass(Schedule *s, int d, int n, int p, const PassGeom &g, 
     int cnt = 0;
     const VolcKernel *vk = volc_meta(&cnt);
     for (int i = 0; i < cnt; ++i) {
-        if (vk[i].n != n || vk[i].p != p)
+        // tile_lines (16, 32 or 64) picks the tile width; 0 takes the first compiled one
+        if (vk[i].n != n || vk[i].p != p || (s->opts.tile_lines > 1 && vk[i].lpt != s->opts.tile_lines))
             continue;
         PassPlan q;
         q.kind = PK_VOLC;

@@ -46,6 +46,9 @@
     X(1024, 32, 32, 4, 16, 2, 16 FFT3_COMMA 2, 2, 16 FFT3_COMMA 2)      \
     X(1024, 32, 32, 2, 16, 2, 16 FFT3_COMMA 2, 2, 16 FFT3_COMMA 2)      \
     X(1024, 32, 32, 8, 16, 2, 16 FFT3_COMMA 2, 2, 16 FFT3_COMMA 2)      \
+    X(1024, 32, 32, 8, 32, 2, 16 FFT3_COMMA 2, 2, 16 FFT3_COMMA 2)      \
+    X(1024, 32, 32, 4, 32, 2, 16 FFT3_COMMA 2, 2, 16 FFT3_COMMA 2)      \
+    X(1024, 32, 32, 8, 64, 2, 16 FFT3_COMMA 2, 2, 16 FFT3_COMMA 2)      \
     X(512, 16, 32, 4, 16, 1, 16, 2, 16 FFT3_COMMA 2)                    \
     X(512, 16, 32, 2, 16, 1, 16, 2, 16 FFT3_COMMA 2)                    \
     X(256, 16, 16, 4, 16, 1, 16, 1, 16)                                 \

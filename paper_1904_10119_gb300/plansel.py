@@ -23,7 +23,7 @@ import numpy as np
 from . import fft3
 
 SIZES = (16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024)
-N_FEATURES = 16
+N_FEATURES = 20
 
 
 def candidates():
@@ -42,11 +42,20 @@ def candidates():
     return out
 
 
-def features(shape, batch, decomp, opts) -> np.ndarray:
-    """16 features of a (shape, plan) pair."""
+def features(shape, batch, decomp, opts, schedule=None) -> np.ndarray:
+    """20 features of a (shape, plan) pair: sizes, the plan's options, the
+    radix stages per dimension, and what the host planner lowers it to (HBM
+    sweeps, runtime-radix passes, cluster passes)."""
     n0, n1, n2 = shape
     order = opts.get("radix_order", 0)
+    if schedule is None:
+        schedule = fft3.fft3_plan_schedule(*shape, batch, 0, decomp, -1, fft3.make_options(**opts))
+    kinds = [p["kind"] for p in schedule["passes"]]
     f = np.zeros(N_FEATURES, np.float32)
+    f[16] = len(kinds)
+    f[17] = sum(k == "line_runtime" for k in kinds)
+    f[18] = sum(k.startswith("volumetric") for k in kinds)
+    f[19] = sum(k.startswith("slab") for k in kinds)
     f[0:3] = [math.log2(n0), math.log2(n1), math.log2(n2)]
     f[3] = math.log2(batch)
     f[4] = 0.0  # dtype: FP32
