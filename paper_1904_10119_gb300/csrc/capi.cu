@@ -60,7 +60,7 @@ int fft3::device_sms(int dev)
 // maximum (the cap is per function, so it is never lowered by a later plan).
 int fft3::prepare_func(const void *func, int smem)
 {
-    if (smem > 48 * 1024) {
+    if (smem > 0) {
         int dev = 0, optin = 0;
         CUDA_TRY(cudaGetDevice(&dev));
         CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -69,7 +69,8 @@ int fft3::prepare_func(const void *func, int smem)
         const int cap = optin - (int)fa.sharedSizeBytes; // static shared memory counts against the opt-in
         if (smem > cap)
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, "pass needs more shared memory than the device offers");
-        CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        if (smem + (int)fa.sharedSizeBytes > 48 * 1024)
+            CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     }
     return FFT3_OK;
 }
