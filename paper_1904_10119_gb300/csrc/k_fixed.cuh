@@ -12,13 +12,13 @@
 namespace fft3 {
 
 template <int N, int T>
-constexpr bool has_slab_l2() { return (N == 1024 || N == 512 || N == 256) && T * 16 <= 1024; }
+constexpr bool has_slab_l2() { return (N == 1024 || N == 512 || N == 256) && T * kSlabL2Lpt <= 1024; }
 
 template <int N, int T, class Rad>
 constexpr const void *slab_l2_ptr()
 {
     if constexpr (has_slab_l2<N, T>())
-        return (const void *)&k_slab_l2<N, T, Rad>;
+        return (const void *)&k_slab_l2<N, T, Rad, kSlabL2Lpt>;
     else
         return nullptr;
 }

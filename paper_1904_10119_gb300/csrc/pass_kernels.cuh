@@ -45,11 +45,6 @@ struct TileId {
     int64_t c0, a, b;
 };
 
-__device__ __forceinline__ void prefetch_l2(const void *p)
-{
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 __device__ __forceinline__ TileId decode_tile(int64_t tile, int64_t tiles_c, int64_t A, int lpt)
 {
     TileId id;
@@ -131,16 +126,6 @@ __global__ void __launch_bounds__(T *LPT) k_pass_j(PassArgs a)
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         __syncthreads();
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, LPT);
-        if (tile + gridDim.x < a.ntiles) { // next tile's lines into L2, 128 bytes per prefetch
-            const TileId nx = decode_tile(tile + gridDim.x, a.tiles_c, a.g.A, LPT);
-            const float2 *nb = a.in + nx.c0 * a.g.ic + nx.a * a.g.ia + nx.b * a.g.ib;
-            const int64_t nl = min((int64_t)LPT, a.g.C - nx.c0);
-            for (int k = threadIdx.x; k < LPT * N / 16; k += T * LPT) {
-                const int ln = (k * 16) / N, off = (k * 16) % N;
-                if (ln < nl)
-                    prefetch_l2(nb + ln * a.g.ic + off);
-            }
-        }
         const int64_t c = id.c0 + l;
         const bool valid = c < a.g.C;
         GLoad1 src{a.in + c * a.g.ic + id.a * a.g.ia + id.b * a.g.ib, valid, conj};
@@ -178,15 +163,6 @@ __global__ void __launch_bounds__(T *LPT) k_pass_c(PassArgs a)
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         __syncthreads();
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, LPT);
-        // pull the next tile's rows into L2 while this tile is transformed, so
-        // its loads find their data on chip (one block per SM cannot overlap
-        // two tiles otherwise)
-        if (tile + gridDim.x < a.ntiles) {
-            const TileId nx = decode_tile(tile + gridDim.x, a.tiles_c, a.g.A, LPT);
-            const float2 *nb = a.in + nx.c0 * a.g.ic + nx.a * a.g.ia + nx.b * a.g.ib;
-            for (int j = threadIdx.x; j < N; j += T * LPT)
-                prefetch_l2(nb + (int64_t)j * a.g.ij);
-        }
         const int64_t c = id.c0 + l;
         const bool valid = c < a.g.C;
         GLoad src{a.in + c * a.g.ic + id.a * a.g.ia + id.b * a.g.ib, a.g.ij, valid, conj};

@@ -558,7 +558,7 @@ static int make_slab_l2_pass(Schedule *s, int n0, int n1, int64_t n2, int64_t ba
         return FFT3_ERR_UNSUPPORTED_SIZE;
     q.tw_seg[0] = line_seg(s, q.line);
     int twlen = tw_slots_h((int)s->tw[q.tw_seg[0]].m.size());
-    q.lpt = 16;
+    q.lpt = kSlabL2Lpt;
     q.threads = q.line.T * q.lpt;
     if (q.threads > 1024)
         return FFT3_ERR_UNSUPPORTED_SIZE;

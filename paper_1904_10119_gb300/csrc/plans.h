@@ -92,6 +92,8 @@ const FixedKernels *fixed_kernels(int id);
 
 // Lines per tile of each compiled kernel kind for a plan with T threads per
 // line (0 = not compiled).
+// rows (x tiles) and columns (y tiles) per tile of the L2-resident slab kernel
+constexpr int kSlabL2Lpt = 4;
 constexpr int lpt_j(int T) { return T >= 256 ? 1 : 256 / T; }
 constexpr int lpt_rot(int T) { return T >= 64 ? 8 : (128 / T > 16 ? 128 / T : 16); }
 constexpr int lpt_c(int T, int want) { return T * want <= 1024 ? want : 0; }

@@ -38,6 +38,15 @@ struct GLoadCG { // strided, L2-only loads (data written earlier in this launch)
     }
 };
 
+// Column layout with padded positions: element j of column l at
+// p[padpos(j)*LPT + l] (conflict free also for narrow tiles).
+template <int LPT>
+struct SmemColPad {
+    float2 *p; // buf + l
+    __device__ __forceinline__ float2 operator()(int j) const { return p[padpos(j) * LPT]; }
+    __device__ __forceinline__ void operator()(int k, float2 v) const { p[padpos(k) * LPT] = v; }
+};
+
 struct SlabTicket {
     int64_t slab;
     int tile;
@@ -77,12 +86,13 @@ __device__ __forceinline__ SlabTicket decode_slab_ticket(int64_t q, int64_t nsla
 
 constexpr long long kWaitBudgetCycles = 4000000000LL; // about two seconds
 
-// N x N slabs, fixed plan (N, T, Rad), 16 lines per tile, blockDim = 16*T.
+// N x N slabs, fixed plan (N, T, Rad), LPT rows (x tiles) or columns (y
+// tiles) per tile, blockDim = LPT*T.  Small tiles let several blocks share an
+// SM; the y tiles read L2-resident data, where narrow rows cost little.
 // counters[0] = ticket, counters[1 + s] = finished x tiles of slab s.
-template <int N, int T, class Rad>
-__global__ void __launch_bounds__(T * 16) k_slab_l2(PassArgs a)
+template <int N, int T, class Rad, int LPT>
+__global__ void __launch_bounds__(T *LPT) k_slab_l2(PassArgs a)
 {
-    constexpr int LPT = 16;
     constexpr int S = line_pitch(N);
     constexpr int TPS = N / LPT;
     extern __shared__ float2 smem[];
@@ -137,7 +147,7 @@ __global__ void __launch_bounds__(T * 16) k_slab_l2(PassArgs a)
             const int64_t col = (int64_t)tk.tile * LPT + l;
             GLoadCG src{a.out + slab_off + col, a.g.ic, conj};
             GStore dst{a.out + slab_off + col, a.g.oc, true, conj};
-            SmemCol<LPT> sm{buf + l};
+            SmemColPad<LPT> sm{buf + l};
             EngineFixed<N, T, 1, Rad>::template run<true, false>(t, src, sm, dst, tw);
         }
     }
