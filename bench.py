@@ -80,7 +80,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -164,7 +164,7 @@ def oracle_sample(n: int, target_s: float, threads: int | None = None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024, help="cube edge (ignored with --shape)")
@@ -172,6 +172,7 @@ def main():
     ap.add_argument("--decomp", default="auto", choices=["auto", "slab_pencil", "ppp", "ppp_rotate", "volumetric"])
     ap.add_argument("--tile-lines", type=int, default=0)
     ap.add_argument("--slab-mode", type=int, default=0)
+    ap.add_argument("--slab-chunk", type=int, default=0)
     ap.add_argument("--radix-order", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true", help="skip the per-decomposition and batched tables")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
@@ -227,6 +228,7 @@ def main():
         torch.cuda.synchronize()
 
     decomp_map = {"auto": (fft3.FFT3_AUTO, {}), "slab_pencil": (fft3.FFT3_SLAB_PENCIL, {}),
+                  "slab_pencil_pipelined": (fft3.FFT3_SLAB_PENCIL, {"slab_mode": 4}),
                   "ppp": (fft3.FFT3_PENCIL3, {}), "ppp_rotate": (fft3.FFT3_PENCIL3, {"variant": 1}),
                   "volumetric": (fft3.FFT3_VOLUMETRIC, {})}
 
@@ -259,7 +261,8 @@ def main():
 
     decomp, opts = decomp_map[args.decomp]
     opts = dict(opts)
-    for k, v in (("tile_lines", args.tile_lines), ("slab_mode", args.slab_mode), ("radix_order", args.radix_order)):
+    for k, v in (("tile_lines", args.tile_lines), ("slab_mode", args.slab_mode), ("slab_chunk", args.slab_chunk),
+                 ("radix_order", args.radix_order)):
         if v:
             opts[k] = v
     sampler = ClockSampler(dev)
@@ -280,11 +283,15 @@ def main():
     hbm, peak_kind = _peaks()
     dom = max(range(len(pass_ms)), key=lambda k: pass_ms[k])
     alg_bytes = 2 * 8 * N  # each pass reads and writes the array once
-    achieved = alg_bytes / (pass_ms[dom] * 1e-3) / 1e9
-    dom_kind = desc["passes"][dom]["kind"]
+    # a pipelined pair (x and y lines chunk by chunk on two streams) is timed as
+    # one entry and needs to read and write the array once in all
+    pair = desc["passes"][dom].get("pipelined_with") == "next"
+    dom_bytes = alg_bytes
+    achieved = dom_bytes / (pass_ms[dom] * 1e-3) / 1e9
+    dom_kind = desc["passes"][dom]["kind"] + ("+" + desc["passes"][dom + 1]["kind"] if pair else "")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": _profiled_traffic(dom_kind), "kernel": dom_kind, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": pass_ms[dom]}
+                "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": pass_ms[dom]}
     sweeps = len(pass_ms)
     whole = {"passes": sweeps, "bytes": sweeps * alg_bytes,
              "frac_of_plan_passes": sweeps * alg_bytes / (t_step * 1e-3) / 1e9 / hbm,
@@ -369,7 +376,7 @@ def main():
                        "inputs": "uniform[-1,1) complex64, seed 4+rank",
                        "l2": "no flush: each pass streams the whole array in and out, larger than the 129 MB L2"},
             "e2e": e2e,
-            "gpu_launches": len(pass_ms) * args.steps,
+            "gpu_launches": plan.kernel_launches() * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -83,9 +83,16 @@ typedef struct fft3_options {
     int mesh[3];      /* volumetric: blocks cooperating on one line of dim d, 1/2/4/8 (0 = auto) */
     int slab_mode;    /* slab-pencil: 0 = auto, 1 = one block per slab in shared memory,
                          2 = L2-resident x/y stages in one persistent launch,
-                         3 = x and y passes as two launches */
+                         3 = x and y passes as two launches,
+                         4 = x and y passes pipelined over chunks of slabs on two
+                             streams: the y lines of a chunk run on the plan's side
+                             stream while the x lines of the next chunk run on the
+                             caller's stream, so the y pass reads what the x pass
+                             has just left in L2; the side stream joins the caller's
+                             stream before the z pass */
     int tc_stages;    /* FFT3_C64_SPLITBF16_TC: 0 = every radix-16 stage on the tensor cores,
                          1 = only the first radix-16 stage of each line */
+    int slab_chunk;   /* slab_mode 4: slabs per chunk (0 = about 32 MiB of slabs) */
     int reserved[8];  /* test hooks of the failure-detection tests, 0 in normal use:
                          [0] = s + 1 makes the x tiles of slab s never signal their
                          completion, so the waits of its y tiles expire;
@@ -146,8 +153,14 @@ int fft3_plan_destroy(fft3_plan p);
 /* Device bytes the plan owns besides its twiddle tables (workspace). */
 size_t fft3_plan_workspace_bytes(fft3_plan p);
 
-/* Number of kernel launches one fft3_plan_execute issues. */
+/* Number of passes of the schedule: the valid indices of fft3_plan_execute_pass.
+ * Without pipelined pairs (slab_mode 4) it is also the number of kernel
+ * launches one fft3_plan_execute issues; a batched plan counts as one. */
 int fft3_plan_launches(fft3_plan p);
+
+/* Number of kernel launches one fft3_plan_execute issues (a pipelined pair
+ * of passes launches each of its two kernels once per chunk). */
+int fft3_plan_kernel_launches(fft3_plan p);
 
 /* JSON description of the pass schedule (decomposition, passes, kernels,
  * line lengths, radix lists, layouts, bytes moved).  Returns the length

@@ -151,6 +151,7 @@ int fft3_autotune(int n0, int n1, int n2, int batch, int dtype, int direction, i
         add(FFT3_SLAB_PENCIL, 0, order, 0, 1, 0, 0, 0);
         add(FFT3_SLAB_PENCIL, 0, order, 0, 2, 0, 0, 0);
         add(FFT3_SLAB_PENCIL, 0, order, 0, 3, 0, 0, 0);
+        add(FFT3_SLAB_PENCIL, 0, order, 0, 4, 0, 0, 0);
         add(FFT3_VOLUMETRIC, 0, order, 0, 0, 2, 2, 2);
     }
     Scratch s;

@@ -196,6 +196,8 @@ static int build_launches(fft3_plan_s *P)
         L.probe_g = p.g;
         L.probe_n = p.line.n;
         L.smem = p.smem_bytes;
+        L.chunk = p.chunk;
+        L.pair_next = p.pair_next;
         L.block = dim3(std::max(1, p.threads));
         const FixedKernels *fk = p.line.fixed >= 0 ? fixed_kernels(p.line.fixed) : nullptr;
         switch (p.kind) {
@@ -282,6 +284,14 @@ static int build_launches(fft3_plan_s *P)
         }
         P->launches.push_back(L);
     }
+    bool pair = false;
+    for (size_t i = 0; i + 1 < P->launches.size(); ++i)
+        pair = pair || (P->launches[i].pair_next && P->launches[i].chunk > 0);
+    if (pair) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    }
     return FFT3_OK;
 }
 
@@ -296,6 +306,12 @@ static void free_plan(fft3_plan_s *P)
         cudaFree(P->d_err);
     cudaFree(P->d_stage_in);
     cudaFree(P->d_stage_out);
+    if (P->side)
+        cudaStreamDestroy(P->side);
+    if (P->ev_fork)
+        cudaEventDestroy(P->ev_fork);
+    if (P->ev_join)
+        cudaEventDestroy(P->ev_join);
     batch_free(P->batch);
     delete P;
 }
@@ -477,6 +493,43 @@ static float2 *buf_ptr(fft3_plan_s *P, int id, const void *in, void *out)
     return id == BUF_IN ? (float2 *)in : (id == BUF_OUT ? (float2 *)out : P->d_ws);
 }
 
+static bool pair_head(const fft3_plan_s *P, size_t k)
+{
+    return k + 1 < P->launches.size() && P->launches[k].pair_next && P->launches[k].chunk > 0;
+}
+
+// Two passes over the same slabs, pipelined in chunks of `chunk` values of a:
+// chunk c of the first pass runs on the caller's stream, chunk c of the second
+// on the plan's side stream once the first has finished it, so the second
+// pass reads a chunk the first has just written (still in L2) while the first
+// moves on to chunk c+1.  The side stream joins the caller's stream at the end.
+static int run_pair(fft3_plan_s *P, size_t k, const void *in, void *out, cudaStream_t st)
+{
+    const Launch &X = P->launches[k], &Y = P->launches[k + 1];
+    const int64_t na_total = X.args.g.A, K = X.chunk;
+    for (int64_t a0 = 0; a0 < na_total; a0 += K) {
+        const int64_t na = std::min(K, na_total - a0);
+        for (int w = 0; w < 2; ++w) {
+            const Launch &L = w ? Y : X;
+            PassArgs a = L.args;
+            a.in = buf_ptr(P, L.src, in, out) + a0 * a.g.ia;
+            a.out = buf_ptr(P, L.dst, in, out) + a0 * a.g.oa;
+            a.g.A = na;
+            a.ntiles = a.tiles_c * na * a.g.B;
+            int rc = launch_one(P, L, L.func, a, w ? P->side : st);
+            if (rc)
+                return rc;
+            if (!w) {
+                CUDA_TRY(cudaEventRecord(P->ev_fork, st));
+                CUDA_TRY(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+            }
+        }
+    }
+    CUDA_TRY(cudaEventRecord(P->ev_join, P->side));
+    CUDA_TRY(cudaStreamWaitEvent(st, P->ev_join, 0));
+    return FFT3_OK;
+}
+
 int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream)
 {
     if (!p || !in || !out)
@@ -489,7 +542,15 @@ int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream)
     p->last_stream = st;
     if (p->batch)
         return batch_execute(p, in, out, st);
-    for (const Launch &L : p->launches) {
+    for (size_t k = 0; k < p->launches.size(); ++k) {
+        const Launch &L = p->launches[k];
+        if (pair_head(p, k)) {
+            int rc = run_pair(p, k, in, out, st);
+            if (rc)
+                return rc;
+            ++k;
+            continue;
+        }
         PassArgs a = L.args;
         a.in = buf_ptr(p, L.src, in, out);
         a.out = buf_ptr(p, L.dst, in, out);
@@ -554,6 +615,10 @@ int fft3_plan_execute_pass(fft3_plan p, int k, const void *in, void *out, void *
         return fail(FFT3_ERR_INVALID_ARG, "pass index out of range");
     cudaStream_t st = (cudaStream_t)stream;
     p->last_stream = st;
+    if (pair_head(p, (size_t)k))
+        return run_pair(p, (size_t)k, in, out, st);
+    if (k > 0 && pair_head(p, (size_t)k - 1))
+        return FFT3_OK; // ran with the pass before it
     const Launch &L = p->launches[k];
     PassArgs a = L.args;
     a.in = buf_ptr(p, L.src, in, out);
@@ -618,6 +683,25 @@ int fft3_plan_launches(fft3_plan p)
     if (p->batch)
         return 1;
     return (int)p->launches.size();
+}
+
+int fft3_plan_kernel_launches(fft3_plan p)
+{
+    if (!p)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan");
+    if (p->batch)
+        return 1;
+    int n = 0;
+    for (size_t k = 0; k < p->launches.size(); ++k) {
+        if (pair_head(p, k)) {
+            const int64_t K = p->launches[k].chunk, na = p->launches[k].args.g.A;
+            n += 2 * (int)((na + K - 1) / K);
+            ++k;
+        } else {
+            n += 1;
+        }
+    }
+    return n;
 }
 
 int fft3_plan_describe(fft3_plan p, char *buf, size_t len)

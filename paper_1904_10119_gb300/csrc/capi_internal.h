@@ -37,6 +37,11 @@ struct Launch {
     int src = BUF_IN, dst = BUF_OUT;
     bool reset_counters = false;
     bool tma = false; // kernel takes two tensor maps after its PassArgs
+    // two-stream pipelined pair: this pass (on the caller's stream) and the
+    // next one (on the plan's side stream) run over chunks of `chunk` values
+    // of a, the next pass's chunk c after this pass's chunk c
+    int chunk = 0;
+    bool pair_next = false;
     // identity probe of the same pass geometry
     PassGeom probe_g{};
     int probe_n = 1;
@@ -69,5 +74,7 @@ struct fft3_plan_s {
     std::vector<fft3::Launch> launches;
     float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
     cudaStream_t last_stream = nullptr;
+    cudaStream_t side = nullptr;                        // second stream of a pipelined pair
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // chunk hand-over and final join
     fft3::BatchState *batch = nullptr; // non-null for fft3_plan_create_many plans
 };

@@ -680,6 +680,22 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         } else if (mode == 1 || mode == 2) {
             *err = "requested slab mode is not available for this slab size";
             return FFT3_ERR_UNSUPPORTED_SIZE;
+        } else if (mode == 4 && n0 > 1 && n1 > 1) {
+            // x lines and y lines of chunks of slabs, pipelined on two streams:
+            // the y lines of chunk c (read back from L2) run beside the x lines
+            // of chunk c+1.  Chunks of about 32 MiB.
+            rc = add_nat(0);
+            if (!rc)
+                rc = add_nat(1);
+            if (!rc) {
+                const int64_t slab_bytes = (int64_t)n0 * n1 * 8;
+                const int64_t want = s.opts.slab_chunk > 0 ? s.opts.slab_chunk : (32ll << 20) / slab_bytes;
+                const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(n2, want));
+                PassPlan &px = s.passes[s.passes.size() - 2], &py = s.passes.back();
+                px.chunk = chunk;
+                py.chunk = chunk;
+                px.pair_next = true;
+            }
         } else {
             // unfused slab stage: x lines then y lines as two passes
             rc = add_nat(0);
@@ -796,6 +812,9 @@ std::string Schedule::json() const
           << ",\"tiles\":" << p.ntiles;
         if (p.kind == PK_VOL || p.kind == PK_VOLC)
             o << ",\"p\":" << p.p << ",\"a\":" << p.split_a << ",\"b\":" << p.split_b;
+        if (p.chunk > 0)
+            o << ",\"chunk\":" << p.chunk << ",\"pipelined_with\":\"" << (p.pair_next ? "next" : "previous")
+              << "\"";
         const PassGeom &g = p.g;
         o << ",\"geom\":{\"C\":" << g.C << ",\"A\":" << g.A << ",\"B\":" << g.B << ",\"ij\":" << g.ij
           << ",\"ic\":" << g.ic << ",\"ia\":" << g.ia << ",\"ib\":" << g.ib << ",\"ok\":" << g.ok

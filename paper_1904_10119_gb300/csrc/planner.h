@@ -62,6 +62,8 @@ struct PassPlan {
     int slabs_per_chunk = 0;
     bool tc_first_only = false; // PK_JTC / PK_CTC: only the first radix-16 stage on tensor cores
     int volc = -1;              // PK_VOLC: index into the compiled volumetric list
+    int chunk = 0;              // slabs per chunk of a two-stream pipelined slab stage (0 = one launch)
+    bool pair_next = false;     // this pass and the next run chunk-interleaved on two streams
 };
 
 struct Schedule {

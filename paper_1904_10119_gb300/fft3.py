@@ -40,7 +40,7 @@ class Fft3Error(RuntimeError):
 class fft3_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("radix_order", ctypes.c_int), ("tile_lines", ctypes.c_int),
                 ("mesh", ctypes.c_int * 3), ("slab_mode", ctypes.c_int), ("tc_stages", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("slab_chunk", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
 
 
 _lib = None
@@ -67,6 +67,7 @@ def load() -> ctypes.CDLL:
         "fft3_plan_destroy": (i, [_P]),
         "fft3_plan_workspace_bytes": (sz, [_P]),
         "fft3_plan_launches": (i, [_P]),
+        "fft3_plan_kernel_launches": (i, [_P]),
         "fft3_plan_describe": (i, [_P, ctypes.c_char_p, sz]),
         "fft3_plan_schedule": (i, [i, i, i, i, i, i, i, ctypes.POINTER(fft3_options), ctypes.c_char_p, sz]),
         "fft3_factorize": (i, [i, i, pi, i]),
@@ -117,7 +118,8 @@ def _check(rc: int) -> int:
     return rc
 
 
-def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mode=0, tc_stages=0) -> fft3_options:
+def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mode=0, tc_stages=0,
+                 slab_chunk=0) -> fft3_options:
     o = fft3_options()
     o.variant = int(variant)
     o.radix_order = int(radix_order)
@@ -126,6 +128,7 @@ def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mo
         o.mesh[k] = int(mesh[k])
     o.slab_mode = int(slab_mode)
     o.tc_stages = int(tc_stages)
+    o.slab_chunk = int(slab_chunk)
     return o
 
 
@@ -193,6 +196,10 @@ def fft3_plan_workspace_bytes(plan: int) -> int:
 
 def fft3_plan_launches(plan: int) -> int:
     return _check(load().fft3_plan_launches(_P(plan)))
+
+
+def fft3_plan_kernel_launches(plan: int) -> int:
+    return _check(load().fft3_plan_kernel_launches(_P(plan)))
 
 
 def fft3_plan_describe(plan: int) -> dict:
@@ -344,6 +351,9 @@ class Plan:
 
     def launches(self) -> int:
         return fft3_plan_launches(self.handle)
+
+    def kernel_launches(self) -> int:
+        return fft3_plan_kernel_launches(self.handle)
 
     def check(self) -> int:
         return fft3_plan_check(self.handle)

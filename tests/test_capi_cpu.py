@@ -96,6 +96,23 @@ def test_schedule_slab_pencil_modes():
         fft3.fft3_plan_schedule(640, 640, 8, 1, 0, fft3.FFT3_SLAB_PENCIL, -1, fft3.make_options(slab_mode=2))
 
 
+def test_schedule_slab_pipelined_pair():
+    """slab_mode 4: the x and y passes carry the same chunk of slabs (about
+    32 MiB by default, or slab_chunk), the x pass marked as running with the next."""
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_SLAB_PENCIL, -1, fft3.make_options(slab_mode=4))
+    assert _kinds(s)[0] == "line_contig" and len(s["passes"]) == 3
+    px, py, pz = s["passes"]
+    assert px["chunk"] == py["chunk"] == 4 and "chunk" not in pz
+    assert (px["pipelined_with"], py["pipelined_with"]) == ("next", "previous")
+    assert py["src"] == py["dst"] == "out"
+    s = fft3.fft3_plan_schedule(96, 80, 10, 2, 0, fft3.FFT3_SLAB_PENCIL, -1,
+                                fft3.make_options(slab_mode=4, slab_chunk=3))
+    assert s["passes"][0]["chunk"] == 3
+    s = fft3.fft3_plan_schedule(64, 64, 5, 1, 0, fft3.FFT3_SLAB_PENCIL, -1,
+                                fft3.make_options(slab_mode=4, slab_chunk=99))
+    assert s["passes"][0]["chunk"] == 5
+
+
 def test_schedule_volumetric_split_rule():
     """One exchange per dimension needs n = a*b with p | a and p | b (Section 3.2)."""
     s = fft3.fft3_plan_schedule(1024, 256, 64, 1, 0, fft3.FFT3_VOLUMETRIC, -1,

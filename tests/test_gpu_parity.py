@@ -71,6 +71,29 @@ def test_slab_modes(mode, shape):
     assert kinds[0] == {1: "slab_smem", 2: "slab_l2", 3: "line_contig"}[mode] or mode == 3
 
 
+@pytest.mark.parametrize("shape,batch,chunk,direction", [((64, 64, 64), 1, 0, FWD), ((96, 80, 10), 2, 3, FWD),
+                                                         ((256, 256, 12), 1, 5, INV), ((100, 60, 9), 1, 1, FWD),
+                                                         ((1024, 16, 9), 1, 4, INV), ((30, 25, 18), 3, 18, FWD)])
+def test_slab_pipelined_chunks(shape, batch, chunk, direction):
+    """slab_mode 4: x and y passes interleaved chunk by chunk on two streams,
+    including a ragged last chunk and a batch."""
+    x, got, plan = run_plan(shape, batch, S, direction, seed=chunk + batch, slab_mode=4, slab_chunk=chunk)
+    assert_parity(x, got, shape, batch, direction)
+    passes = plan.describe()["passes"]
+    K = passes[0]["chunk"]
+    assert passes[0]["pipelined_with"] == "next" and passes[1]["pipelined_with"] == "previous"
+    assert K == (chunk if chunk else min(shape[2], max(1, (32 << 20) // (shape[0] * shape[1] * 8))))
+    nchunks = -(-shape[2] // K)
+    assert plan.kernel_launches() == 2 * nchunks + 1 and plan.launches() == 3
+    # per-pass execution: the pair runs at its first index, the second index is empty
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    for k in range(plan.launches()):
+        fft3.fft3_plan_execute_pass(plan.handle, k, xt.data_ptr(), out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert_parity(x, out.cpu().numpy(), shape, batch, direction)
+
+
 @pytest.mark.parametrize("mesh,shape", [((2, 2, 2), (64, 64, 64)), ((4, 4, 4), (64, 64, 64)),
                                         ((8, 2, 4), (256, 32, 64)), ((2, 8, 4), (36, 256, 16)),
                                         ((4, 2, 8), (1024, 16, 64)), ((1, 4, 2), (30, 64, 36))])
