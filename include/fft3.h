@@ -78,8 +78,12 @@ enum fft3_ppp_variant {
 typedef struct fft3_options {
     int variant;      /* fft3_ppp_variant for FFT3_PENCIL3 */
     int radix_order;  /* index into the candidate radix orders of each line length (0 = default) */
-    int tile_lines;   /* lines per tile of a strided pass: 8 or 16 (0 = default 16);
-                         1 = tiles moved by TMA, double-buffered (8 or 16 lines by length) */
+    int tile_lines;   /* strided passes: 0 = default (the streamed kernel where one is
+                         compiled for the line length, else 16 lines per tile);
+                         8 or 16 = lines per tile of the plain strided kernel;
+                         1 = tiles moved by TMA, double-buffered (8 or 16 lines by length);
+                         2 = the streamed kernel: decimated sub-lines loaded by TMA
+                             while earlier ones are transformed (512 and 1024 points) */
     int mesh[3];      /* volumetric: blocks cooperating on one line of dim d, 1/2/4/8 (0 = auto) */
     int slab_mode;    /* slab-pencil: 0 = auto, 1 = one block per slab in shared memory,
                          2 = L2-resident x/y stages in one persistent launch,

@@ -115,6 +115,30 @@ static int encode_pass_map(CUtensorMap *m, const void *base, const PassGeom &g, 
     return FFT3_OK;
 }
 
+// Input map of a streamed strided pass: the array as {C, Q, M, A, B} with
+// line element j = Q*j' + q, so one box {LPT, 1, M, 1, 1} is the decimated
+// sub-line q of a tile.
+static int encode_stream_map(CUtensorMap *m, const void *base, const PassGeom &g, int n, int q, int lpt)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return fail(FFT3_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if ((uintptr_t)base & 15)
+        return fail(FFT3_ERR_INVALID_ARG, "this plan moves tiles with TMA: buffers must be 16-byte aligned");
+    const int mm = n / q;
+    cuuint64_t dims[5] = {(cuuint64_t)g.C, (cuuint64_t)q, (cuuint64_t)mm, (cuuint64_t)g.A, (cuuint64_t)g.B};
+    cuuint64_t strides[4] = {(cuuint64_t)g.ij * 8, (cuuint64_t)g.ij * q * 8, (cuuint64_t)g.ia * 8,
+                             (cuuint64_t)(g.B > 1 ? g.ib : g.ia * g.A) * 8};
+    cuuint32_t box[5] = {(cuuint32_t)lpt, 1, (cuuint32_t)mm, 1, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(FFT3_ERR_CUDA, "cuTensorMapEncodeTiled (streamed pass) failed with code " + std::to_string((int)r));
+    return FFT3_OK;
+}
+
 int fft3::occupancy_grid(const void *func, int threads, int smem, int64_t ntiles, int dev, dim3 *grid)
 {
     int nb = 0;
@@ -231,6 +255,13 @@ static int build_launches(fft3_plan_s *P)
             L.func = (p.volc >= 0 && p.volc < cnt) ? vk[p.volc].func : nullptr;
             L.cluster = p.p;
             L.probe_n = p.split_a * p.split_b;
+            break;
+        }
+        case PK_CSTREAM: {
+            int cnt = 0;
+            const CStreamKernel *ck = cstream_kernels(&cnt);
+            L.func = (p.cstream >= 0 && p.cstream < cnt) ? ck[p.cstream].func : nullptr;
+            L.stream_q = L.func ? ck[p.cstream].q : 0;
             break;
         }
         case PK_JTC:
@@ -471,6 +502,15 @@ static int launch_one(fft3_plan_s *P, const Launch &L, const void *func, PassArg
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
+    }
+    if (L.stream_q > 0) {
+        CUtensorMap tin;
+        int rc = encode_stream_map(&tin, a.in, a.g, L.probe_n, L.stream_q, a.lpt);
+        if (rc)
+            return rc;
+        void *params[2] = {&a, &tin};
+        CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params));
+        return FFT3_OK;
     }
     if (L.tma) {
         CUtensorMap tin, tout;

@@ -37,6 +37,7 @@ struct Launch {
     int src = BUF_IN, dst = BUF_OUT;
     bool reset_counters = false;
     bool tma = false; // kernel takes two tensor maps after its PassArgs
+    int stream_q = 0; // > 0: streamed strided pass, one 5D input map of Q decimated sub-lines
     // two-stream pipelined pair: this pass (on the caller's stream) and the
     // next one (on the plan's side stream) run over chunks of `chunk` values
     // of a, the next pass's chunk c after this pass's chunk c

@@ -58,6 +58,16 @@ const VolcKernel *volc_meta(int *count)
     return g_volc_meta;
 }
 
+#define FFT3_CSTREAM_META(N, Q, R1, R2, G, S, LPT) {N, Q, R1, R2, G, S, LPT, G * LPT * R2, nullptr},
+static const CStreamKernel g_cstream_meta[] = {FFT3_CSTREAM_LIST(FFT3_CSTREAM_META)};
+#undef FFT3_CSTREAM_META
+
+const CStreamKernel *cstream_meta(int *count)
+{
+    *count = (int)(sizeof(g_cstream_meta) / sizeof(g_cstream_meta[0]));
+    return g_cstream_meta;
+}
+
 int fixed_plan_count() { return g_nmeta; }
 const FixedPlanMeta &fixed_plan_meta(int id)
 {
@@ -260,6 +270,26 @@ static bool tma_ok(const PassGeom &g, int n, int lpt)
     return 2 * n * lpt * 8 + 8192 * 8 <= kSmemLimit;
 }
 
+// Streamed strided pass for a line of length n: the compiled entry for n
+// picked by `order` among the entries for n, if the input geometry suits its
+// TMA map {C, Q, M, A, B} (16-byte multiples for every stride the map walks).
+static int cstream_pick(int n, int order, const PassGeom &g)
+{
+    if (g.ic != 1 || g.oc != 1 || (g.ij * 8) % 16 || (g.ia * 8) % 16 || (g.B > 1 && (g.ib * 8) % 16))
+        return -1;
+    if (g.C > 0x7fffffff || g.A > 0x7fffffff || g.B > 0x7fffffff)
+        return -1;
+    int cnt = 0;
+    const CStreamKernel *m = cstream_meta(&cnt);
+    std::vector<int> ids;
+    for (int i = 0; i < cnt; ++i)
+        if (m[i].n == n && cstream_smem(n, m[i].q, m[i].lpt, m[i].groups * m[i].stages) <= kSmemLimit)
+            ids.push_back(i);
+    if (ids.empty())
+        return -1;
+    return ids[(size_t)std::max(0, order) % ids.size()];
+}
+
 // A single 1D pass on dimension d with geometry g.
 static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rotate, int src, int dst,
                           PassPlan *out, std::string *err)
@@ -310,7 +340,8 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         }
     }
     // strided tiles: 16 adjacent columns (128-byte rows) unless 8 are asked for;
-    // tile_lines == kTileTma selects the TMA double-buffered kernel
+    // lengths with a compiled streamed kernel use it unless tile_lines asks for
+    // another (kTileTma: the TMA double-buffered kernel, 8/16: the plain one)
     int want_c = s->opts.tile_lines == 8 ? 8 : 16;
     if (p.line.fixed >= 0 && rotate && contig_in && g.oc == 1) {
         p.kind = PK_JROT;
@@ -318,6 +349,22 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
     } else if (p.line.fixed >= 0 && !rotate && contig_in && g.ok == 1 && n > 1) {
         p.kind = PK_J;
         p.lpt = lpt_j(p.line.T);
+    } else if (!rotate && strided_in && n > 1 && (s->opts.tile_lines == 0 || s->opts.tile_lines == kTileStream) &&
+               cstream_pick(n, order, g) >= 0) {
+        const int ci = cstream_pick(n, order, g);
+        int cnt = 0;
+        const CStreamKernel &m = cstream_meta(&cnt)[ci];
+        p.kind = PK_CSTREAM;
+        p.cstream = ci;
+        p.lpt = m.lpt;
+        p.line = LineChoice{};
+        p.line.n = n;
+        p.line.fixed = -1;
+        p.line.T = m.threads / m.lpt;
+        p.line.nst = 3;
+        p.line.rad[0] = m.r1;
+        p.line.rad[1] = m.r2;
+        p.line.rad[2] = m.q;
     } else if (p.line.fixed >= 0 && !rotate && strided_in && n > 1 && s->opts.tile_lines == kTileTma &&
                tma_ok(g, n, lpt_tma(n, p.line.T))) {
         p.kind = PK_CTMA;
@@ -349,6 +396,11 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
     } else if (p.kind == PK_CTMA) {
         p.threads = p.line.T * p.lpt;
         p.smem_bytes = tw_slots_h(tw_len) * 8 + 2 * p.lpt * n * 8;
+    } else if (p.kind == PK_CSTREAM) {
+        int cnt = 0;
+        const CStreamKernel &m = cstream_meta(&cnt)[p.cstream];
+        p.threads = m.threads;
+        p.smem_bytes = cstream_smem(n, m.q, m.lpt, m.groups * m.stages);
     } else {
         p.threads = p.line.T * p.lpt;
         p.smem_bytes = tw_slots_h(tw_len) * 8 + p.lpt * n * 8;
@@ -614,13 +666,12 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
     if (decomp == FFT3_AUTO && dtype == FFT3_C64_SPLITBF16_TC)
         decomp = FFT3_PENCIL3;
     if (decomp == FFT3_AUTO) {
-        // Fixed default when no cost model is loaded: slab-pencil when the
-        // slab stage can be fused (fewest HBM sweeps), else pencil-pencil-pencil.
+        // Fixed default when no cost model is loaded: slab-pencil when a whole
+        // slab fits one block's shared memory (one HBM sweep fewer), else
+        // pencil-pencil-pencil, whose strided passes stream their sub-lines
+        // (measured faster than the L2-resident slab kernel at 1024 x 1024).
         int twl = 2 * tw_slots_h(n0) + 2 * tw_slots_h(n1);
-        if (slab_smem(n0, n1, twl) <= kSmemLimit || slab_l2_supported(n0, n1))
-            decomp = FFT3_SLAB_PENCIL;
-        else
-            decomp = FFT3_PENCIL3;
+        decomp = slab_smem(n0, n1, twl) <= kSmemLimit ? FFT3_SLAB_PENCIL : FFT3_PENCIL3;
     }
     if (dtype == FFT3_C64_SPLITBF16_TC) {
         if (decomp != FFT3_PENCIL3 || s.opts.variant != FFT3_PPP_NATURAL) {
@@ -662,8 +713,16 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         int mode = s.opts.slab_mode;
         int twl = 2 * tw_slots_h(n0) + 2 * tw_slots_h(n1);
         bool fits_smem = slab_smem(n0, n1, twl) <= kSmemLimit;
-        if (mode == 0)
-            mode = fits_smem ? 1 : (slab_l2_supported(n0, n1) ? 2 : 3);
+        if (mode == 0) {
+            // unfused when the y lines have a streamed kernel (faster than
+            // the L2-resident slab kernel where both exist), else L2-resident
+            int cnt = 0;
+            const CStreamKernel *cm = cstream_meta(&cnt);
+            bool streamed_y = false;
+            for (int i = 0; i < cnt; ++i)
+                streamed_y = streamed_y || cm[i].n == n1;
+            mode = fits_smem ? 1 : (!streamed_y && slab_l2_supported(n0, n1) ? 2 : 3);
+        }
         PassPlan p;
         if (mode == 1 && fits_smem) {
             rc = make_slab_pass(&s, n0, n1, n2, batch, &p, err);
@@ -767,8 +826,8 @@ static const char *kind_name(int k)
     static const char *names[] = {"line_contig", "line_contig_rotate", "line_strided", "line_runtime",
                                   "slab_smem", "slab_l2", "volumetric_split", "copy", "line_tc",
                                   "line_strided_tma", "line_contig_tc", "line_strided_tc",
-                                  "volumetric_split_fixed"};
-    return (k >= 0 && k <= 12) ? names[k] : "?";
+                                  "volumetric_split_fixed", "line_strided_stream"};
+    return (k >= 0 && k <= 13) ? names[k] : "?";
 }
 static const char *buf_name(int b)
 {
@@ -812,6 +871,12 @@ std::string Schedule::json() const
           << ",\"tiles\":" << p.ntiles;
         if (p.kind == PK_VOL || p.kind == PK_VOLC)
             o << ",\"p\":" << p.p << ",\"a\":" << p.split_a << ",\"b\":" << p.split_b;
+        if (p.kind == PK_CSTREAM) {
+            int cnt = 0;
+            const CStreamKernel &m = cstream_meta(&cnt)[p.cstream];
+            o << ",\"q\":" << m.q << ",\"m\":" << m.n / m.q << ",\"groups\":" << m.groups
+              << ",\"staging\":" << m.groups * m.stages;
+        }
         if (p.chunk > 0)
             o << ",\"chunk\":" << p.chunk << ",\"pipelined_with\":\"" << (p.pair_next ? "next" : "previous")
               << "\"";

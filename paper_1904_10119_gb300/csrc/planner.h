@@ -26,6 +26,7 @@ enum PassKind {
     PK_JTC = 10,   // split-BF16 tensor-core radix-16 stages, contiguous lines
     PK_CTC = 11,   // split-BF16 tensor-core radix-16 stages, strided columns
     PK_VOLC = 12,  // compile-time volumetric split of strided lines (k_volc.cu)
+    PK_CSTREAM = 13, // strided lines, decimated sub-lines streamed by TMA (k_cstream.cu)
 };
 
 enum BufId { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };
@@ -62,6 +63,7 @@ struct PassPlan {
     int slabs_per_chunk = 0;
     bool tc_first_only = false; // PK_JTC / PK_CTC: only the first radix-16 stage on tensor cores
     int volc = -1;              // PK_VOLC: index into the compiled volumetric list
+    int cstream = -1;           // PK_CSTREAM: index into the compiled streamed-pass list
     int chunk = 0;              // slabs per chunk of a two-stream pipelined slab stage (0 = one launch)
     bool pair_next = false;     // this pass and the next run chunk-interleaved on two streams
 };
@@ -95,6 +97,7 @@ void generic_launch_shape(int n, int T, bool strided, int tw_len, int *lpt, int 
 
 constexpr int kMaxLine = 4096;
 constexpr int kTileTma = 1; // fft3_options.tile_lines value selecting the TMA strided kernel
+constexpr int kTileStream = 2; // fft3_options.tile_lines value selecting the streamed strided kernel
 constexpr int kSmemLimit = 227 * 1024;
 
 } // namespace fft3

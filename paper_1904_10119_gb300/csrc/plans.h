@@ -54,7 +54,44 @@
     X(256, 16, 16, 4, 16, 1, 16, 1, 16)                                 \
     X(256, 16, 16, 2, 16, 1, 16, 1, 16)
 
+// Streamed strided passes (k_cstream.cu).  A line of N = M * Q points is
+// taken as Q decimated sub-lines x[Q*j' + q] (Eq. ct with n0 = Q); per tile of
+// LPT adjacent columns, G thread groups transform the sub-lines (M = R1 * R2,
+// two Stockham stages), each through its own ring of S TMA staging buffers
+// refilled as soon as they are read, then one radix-Q stage with twiddles
+// w_N^{q k'} stores the lines.  The line's twiddle table is the stage-major
+// table of (R1, R2, Q).  Row: N, Q, R1, R2, G, S, LPT.
+#define FFT3_CSTREAM_LIST(X)             \
+    X(1024, 4, 16, 16, 2, 1, 16)         \
+    X(1024, 4, 16, 16, 1, 2, 16)         \
+    X(1024, 8, 16, 8, 4, 1, 16)          \
+    X(1024, 8, 16, 8, 2, 2, 16)          \
+    X(1024, 8, 8, 16, 2, 2, 16)          \
+    X(512, 4, 16, 8, 2, 1, 16)           \
+    X(512, 2, 16, 16, 1, 2, 16)          \
+    X(512, 2, 16, 16, 2, 1, 16)
+
 namespace fft3 {
+
+struct CStreamKernel {
+    int n, q, r1, r2, groups, stages, lpt, threads;
+    const void *func; // nullptr in the host-only metadata
+};
+// Compiled list (device translation unit) and the host-only metadata.
+const CStreamKernel *cstream_kernels(int *count);
+const CStreamKernel *cstream_meta(int *count);
+// Dynamic shared memory of a streamed pass: twiddles (N-1 entries rounded to
+// 16), the tile's result (N x LPT) and `bufs` staging buffers (M x LPT).
+constexpr int cstream_smem(int n, int q, int lpt, int bufs)
+{
+    return ((n - 1 + 15) / 16 * 16 + n * lpt + bufs * (n / q) * lpt) * 8;
+}
+// Blocks per SM the launch bounds ask for: two when two copies of the
+// shared memory fit.
+constexpr int cstream_min_blocks(int n, int q, int lpt, int bufs, int threads)
+{
+    return (2 * (cstream_smem(n, q, lpt, bufs) + 1024) <= 228 * 1024 && threads <= 512) ? 2 : 1;
+}
 
 struct VolcKernel {
     int n, a, b, p, lpt, threads, ta, tb;

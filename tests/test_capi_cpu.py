@@ -57,7 +57,11 @@ def _kinds(s):
 def test_schedule_pencil3_natural():
     s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_PENCIL3, -1)
     assert s["decomposition"] == "pencil_pencil_pencil"
-    assert _kinds(s) == ["line_contig", "line_strided", "line_strided"]
+    # strided 1024-point lines stream their decimated sub-lines by default
+    assert _kinds(s) == ["line_contig", "line_strided_stream", "line_strided_stream"]
+    assert all(p["q"] * p["m"] == 1024 for p in s["passes"][1:])
+    s16 = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_PENCIL3, -1, fft3.make_options(tile_lines=16))
+    assert _kinds(s16) == ["line_contig", "line_strided", "line_strided"]
     assert [p["dim"] for p in s["passes"]] == [0, 1, 2]
     assert [(p["src"], p["dst"]) for p in s["passes"]] == [("in", "out"), ("out", "out"), ("out", "out")]
     assert s["workspace_bytes"] == 0
@@ -87,8 +91,11 @@ def test_schedule_pencil3_rotate_geometry():
 def test_schedule_slab_pencil_modes():
     s = fft3.fft3_plan_schedule(64, 64, 64, 1, 0, fft3.FFT3_SLAB_PENCIL, -1)
     assert _kinds(s) == ["slab_smem", "line_strided"]
+    # 1024 x 1024 slabs: the x and y passes unfused (the y lines stream), slab_l2 on request
     s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_SLAB_PENCIL, -1)
-    assert _kinds(s) == ["slab_l2", "line_strided"]
+    assert _kinds(s) == ["line_contig", "line_strided_stream", "line_strided_stream"]
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_SLAB_PENCIL, -1, fft3.make_options(slab_mode=2))
+    assert _kinds(s) == ["slab_l2", "line_strided_stream"]
     s = fft3.fft3_plan_schedule(1024, 1024, 64, 1, 0, fft3.FFT3_SLAB_PENCIL, -1,
                                 fft3.make_options(slab_mode=3, tile_lines=16))
     assert _kinds(s) == ["line_contig", "line_strided", "line_strided"]

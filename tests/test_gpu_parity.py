@@ -94,6 +94,22 @@ def test_slab_pipelined_chunks(shape, batch, chunk, direction):
     assert_parity(x, out.cpu().numpy(), shape, batch, direction)
 
 
+@pytest.mark.parametrize("shape,batch,order,direction", [
+    ((40, 1024, 6), 1, 0, FWD), ((40, 1024, 6), 1, 1, INV), ((40, 1024, 6), 1, 2, FWD),
+    ((24, 6, 1024), 2, 0, FWD), ((18, 512, 4), 1, 0, INV), ((18, 512, 4), 1, 1, FWD),
+    ((20, 6, 512), 1, 1, FWD), ((512, 512, 3), 1, 0, FWD), ((45, 512, 2), 1, 0, FWD),
+    ((40, 1024, 6), 1, 3, INV), ((24, 6, 1024), 1, 4, FWD), ((18, 512, 4), 1, 2, INV)])
+def test_streamed_strided_pass(shape, batch, order, direction):
+    """Strided 512/1024-point lines with their decimated sub-lines streamed by
+    TMA (tile_lines 2): every compiled variant, ragged column tiles, a batch,
+    both directions; a row stride that is not a 16-byte multiple falls back to
+    the plain strided kernel."""
+    x, got, plan = run_plan(shape, batch, P, direction, seed=order + 20, tile_lines=2, radix_order=order)
+    assert_parity(x, got, shape, batch, direction)
+    kinds = [p["kind"] for p in plan.describe()["passes"]]
+    assert ("line_strided_stream" in kinds) == (shape[0] % 2 == 0)
+
+
 @pytest.mark.parametrize("mesh,shape", [((2, 2, 2), (64, 64, 64)), ((4, 4, 4), (64, 64, 64)),
                                         ((8, 2, 4), (256, 32, 64)), ((2, 8, 4), (36, 256, 16)),
                                         ((4, 2, 8), (1024, 16, 64)), ((1, 4, 2), (30, 64, 36))])
