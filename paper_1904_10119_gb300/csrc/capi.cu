@@ -262,6 +262,7 @@ static int build_launches(fft3_plan_s *P)
             const CStreamKernel *ck = cstream_kernels(&cnt);
             L.func = (p.cstream >= 0 && p.cstream < cnt) ? ck[p.cstream].func : nullptr;
             L.stream_q = L.func ? ck[p.cstream].q : 0;
+            L.cluster = p.p;
             break;
         }
         case PK_JTC:
@@ -281,7 +282,7 @@ static int build_launches(fft3_plan_s *P)
         int rc = prepare_func(L.func, L.smem);
         if (rc)
             return rc;
-        if (p.kind == PK_VOL || p.kind == PK_VOLC) {
+        if (p.kind == PK_VOL || p.kind == PK_VOLC || (p.kind == PK_CSTREAM && p.p > 1)) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -18,12 +18,24 @@
 // whole ring (G*S sub-lines, across tile boundaries) is in flight while the
 // groups compute and while the block stores the previous tile.
 //
+// With P = 2 a cluster of two blocks shares a tile twice as wide (LPT = 32
+// columns, 256-byte rows): block r loads and transforms the sub-lines
+// q in [r*Q/2, (r+1)*Q/2) into its own slots, and in the final stage computes
+// the outputs k' in [r*M/2, (r+1)*M/2) of all LPT columns, reading the other
+// block's slots through distributed shared memory.  Rows of 256 bytes are what
+// lines strided by whole planes (z lines) need to reach full DRAM throughput;
+// a single block can not hold a 32-column tile's result.
+//
 // Twiddles: the stage-major table of the radix list (R1, R2, Q) for length
 // N.  Its first M-1 entries are the M-point table of (R1, R2) (an entry
 // w_N^{r k N/(NS R)} depends on NS*R only) and the last (Q-1)*M entries are
 // w_N^{r k'}, the twiddles (II) of the final stage.
+#include <cooperative_groups.h>
+
 #include "pass_tma.cuh"
 #include "plans.h"
+
+namespace cg = cooperative_groups;
 
 namespace fft3 {
 
@@ -75,39 +87,62 @@ __device__ __forceinline__ void group_sync(int g)
     }
 }
 
-template <int N, int Q, int R1, int R2, int G, int S, int LPT>
-__global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(N, Q, LPT, G *S, G *LPT *R2))
+// Block barrier (P = 1) or cluster barrier (P = 2, with the release /
+// acquire ordering that makes the slots visible to the other block).
+template <int P>
+__device__ __forceinline__ void tile_sync()
+{
+    if constexpr (P == 1)
+        __syncthreads();
+    else
+        cg::this_cluster().sync();
+}
+
+template <int N, int Q, int R1, int R2, int G, int S, int LPT, int P>
+__global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(N, Q, Q / P, LPT, G *S), G *LPT *R2))
     k_cstream(PassArgs a, const __grid_constant__ CUtensorMap tin)
 {
     constexpr int M = R1 * R2;
     constexpr int T1 = M / R1;          // threads per column in a group (= first-stage butterflies)
     constexpr int GT = LPT * T1;        // threads per group
     constexpr int THREADS = G * GT;
-    constexpr int W = Q / G;            // sub-lines per group per tile
+    constexpr int QP = Q / P;           // sub-lines (slots) per block
+    constexpr int W = QP / G;           // sub-lines per group per tile
+    constexpr int MP = M / P;           // final-stage outputs k' per block
     constexpr int NB2 = M / R2;         // second-stage butterflies per column
     constexpr int BPT2 = (NB2 + T1 - 1) / T1;
     constexpr int TF = THREADS / LPT;   // threads per column in the final stage
     constexpr uint32_t SUB_BYTES = (uint32_t)M * LPT * 8u;
-    static_assert(M * Q == N && Q % G == 0 && GT % 32 == 0, "N = M * Q, whole warps per group");
-    static_assert(M <= 256 && (LPT * 8) % 16 == 0, "a sub-line is one TMA box");
+    static_assert(M * Q == N && Q % P == 0 && QP % G == 0 && M % P == 0 && GT % 32 == 0,
+                  "N = M * Q, whole sub-lines per block and group, whole warps per group");
+    static_assert(M <= 256 && LPT <= 256 && (LPT * 8) % 16 == 0, "a sub-line is one TMA box");
+    static_assert(P == 1 || P == 2, "one block or a pair");
     extern __shared__ __align__(128) float2 smem[];
     __shared__ __align__(8) uint64_t bars[G * S];
     float2 *tw = smem;
-    float2 *res = smem + tw_slots(a.tw_len); // Q slots of M x LPT, slot q at q*M*LPT
-    float2 *stg = res + N * LPT;             // G*S staging buffers of M x LPT; group g owns g*S .. g*S+S-1
+    float2 *res = smem + tw_slots(a.tw_len); // QP slots of M x LPT, slot s at s*M*LPT
+    float2 *stg = res + QP * M * LPT;        // G*S staging buffers of M x LPT; group g owns g*S .. g*S+S-1
     load_twiddles(tw, a.tw, a.tw_len);
     const int tid = threadIdx.x, g = tid / GT, gtid = tid % GT;
     const int l = gtid % LPT, t1 = gtid / LPT;
     const bool conj = a.conj != 0;
+    int r = 0;
+    const float2 *peer = res; // the other block's slots (P = 2)
+    if constexpr (P > 1) {
+        cg::cluster_group cluster = cg::this_cluster();
+        r = (int)cluster.block_rank();
+        peer = cluster.map_shared_rank(res, r ^ 1);
+    }
+    const int64_t cid = blockIdx.x / P, ncl = gridDim.x / P;
     if (tid == 0) {
         for (int b = 0; b < G * S; ++b)
             mbar_init(&bars[b], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    // The k-th sub-line of group g: tile blockIdx.x + (k / W) * gridDim.x, q = g + G*(k % W),
-    // staging buffer g*S + k % S, mbarrier phase (k / S) & 1.
-    auto tile_of = [&](int64_t k) { return (int64_t)blockIdx.x + (k / W) * (int64_t)gridDim.x; };
+    // The k-th sub-line of group g: tile cid + (k / W) * ncl, local slot g + G*(k % W)
+    // (sub-line q = r*QP + slot), staging buffer g*S + k % S, mbarrier phase (k / S) & 1.
+    auto tile_of = [&](int64_t k) { return cid + (k / W) * ncl; };
     auto issue = [&](int64_t k) {
         const int64_t tile = tile_of(k);
         if (tile >= a.ntiles)
@@ -115,8 +150,8 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(N, Q, LPT, G *S
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, LPT);
         const int b = g * S + (int)(k % S);
         mbar_expect_tx(&bars[b], SUB_BYTES);
-        tma_load_5d(stg + b * M * LPT, &tin, (int)id.c0, g + G * (int)(k % W), 0, (int)id.a, (int)id.b,
-                    &bars[b]);
+        tma_load_5d(stg + b * M * LPT, &tin, (int)id.c0, r * QP + g + G * (int)(k % W), 0, (int)id.a,
+                    (int)id.b, &bars[b]);
     };
     if (gtid == 0) {
         for (int k = 0; k < S; ++k)
@@ -129,11 +164,11 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(N, Q, LPT, G *S
     bool failed = false;
     int64_t k_fail = 0;
     int64_t k = 0;
-    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    for (int64_t tile = cid; tile < a.ntiles; tile += ncl) {
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, LPT);
 #pragma unroll 1
         for (int w = 0; w < W; ++w, ++k) {
-            const int q = g + G * w;
+            const int q = g + G * w; // local slot
             const int b = g * S + (int)(k % S);
             const bool late = !failed && !mbar_wait(&bars[b], (uint32_t)((k / S) & 1), a.wait_budget);
             // (I) first stage, radix R1, NS = 1: inputs x_q[t1 + r*T1] of column l
@@ -185,7 +220,7 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(N, Q, LPT, G *S
                 }
             }
         }
-        __syncthreads(); // every slot of the tile is complete
+        tile_sync<P>(); // every slot of the tile (of both blocks) is complete
         // (II)+(IV): radix-Q stage with NS = M over the Q slots, stored to global
         {
             const int lf = tid % LPT, tf = tid / LPT;
@@ -194,23 +229,25 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(N, Q, LPT, G *S
             float2 *op = a.out + c * a.g.oc + id.a * a.g.oa + id.b * a.g.ob;
             const float2 *twf = tw + (M - 1);
 #pragma unroll 2
-            for (int kk = tf; kk < M; kk += TF) {
+            for (int kk = r * MP + tf; kk < (r + 1) * MP; kk += TF) {
                 float2 z[Q];
 #pragma unroll
-                for (int r = 0; r < Q; ++r)
-                    z[r] = res[(kk + r * M) * LPT + lf];
+                for (int s = 0; s < Q; ++s) {
+                    const float2 *src = (s / QP == r) ? res : peer;
+                    z[s] = src[((s % QP) * M + kk) * LPT + lf];
+                }
 #pragma unroll
-                for (int r = 1; r < Q; ++r)
-                    z[r] = cmul(z[r], twf[(r - 1) * M + kk]);
+                for (int s = 1; s < Q; ++s)
+                    z[s] = cmul(z[s], twf[(s - 1) * M + kk]);
                 Bfly<Q>::run(z);
                 if (valid) {
 #pragma unroll
-                    for (int r = 0; r < Q; ++r)
-                        op[(int64_t)(kk + r * M) * a.g.ok] = conj ? cconj(z[r]) : z[r];
+                    for (int s = 0; s < Q; ++s)
+                        op[(int64_t)(kk + s * M) * a.g.ok] = conj ? cconj(z[s]) : z[s];
                 }
             }
         }
-        __syncthreads(); // the next tile's first stages overwrite the slots
+        tile_sync<P>(); // the next tile's first stages overwrite the slots
     }
     if (failed && gtid == 0) {
         atomicOr(a.err, kErrWaitTimeout);
@@ -220,8 +257,8 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(N, Q, LPT, G *S
     }
 }
 
-#define FFT3_CSTREAM_ROW(N, Q, R1, R2, G, S, LPT) \
-    {N, Q, R1, R2, G, S, LPT, G * LPT * R2, (const void *)&k_cstream<N, Q, R1, R2, G, S, LPT>},
+#define FFT3_CSTREAM_ROW(N, Q, R1, R2, G, S, LPT, P) \
+    {N, Q, R1, R2, G, S, LPT, P, G * LPT * R2, (const void *)&k_cstream<N, Q, R1, R2, G, S, LPT, P>},
 
 static const CStreamKernel g_cstream_kernels[] = {FFT3_CSTREAM_LIST(FFT3_CSTREAM_ROW)};
 

@@ -58,7 +58,7 @@ const VolcKernel *volc_meta(int *count)
     return g_volc_meta;
 }
 
-#define FFT3_CSTREAM_META(N, Q, R1, R2, G, S, LPT) {N, Q, R1, R2, G, S, LPT, G * LPT * R2, nullptr},
+#define FFT3_CSTREAM_META(N, Q, R1, R2, G, S, LPT, P) {N, Q, R1, R2, G, S, LPT, P, G * LPT * R2, nullptr},
 static const CStreamKernel g_cstream_meta[] = {FFT3_CSTREAM_LIST(FFT3_CSTREAM_META)};
 #undef FFT3_CSTREAM_META
 
@@ -273,7 +273,10 @@ static bool tma_ok(const PassGeom &g, int n, int lpt)
 // Streamed strided pass for a line of length n: the compiled entry for n
 // picked by `order` among the entries for n, if the input geometry suits its
 // TMA map {C, Q, M, A, B} (16-byte multiples for every stride the map walks).
-static int cstream_pick(int n, int order, const PassGeom &g)
+// `pair` = 1 keeps each line in one block (a pencil pass); `pair` = 2 takes
+// the entries whose line is split over a cluster of two blocks (a volumetric
+// split of the line, Section 3.2).
+static int cstream_pick(int n, int order, const PassGeom &g, int pair)
 {
     if (g.ic != 1 || g.oc != 1 || (g.ij * 8) % 16 || (g.ia * 8) % 16 || (g.B > 1 && (g.ib * 8) % 16))
         return -1;
@@ -283,11 +286,33 @@ static int cstream_pick(int n, int order, const PassGeom &g)
     const CStreamKernel *m = cstream_meta(&cnt);
     std::vector<int> ids;
     for (int i = 0; i < cnt; ++i)
-        if (m[i].n == n && cstream_smem(n, m[i].q, m[i].lpt, m[i].groups * m[i].stages) <= kSmemLimit)
+        if (m[i].n == n && m[i].pair == pair &&
+            cstream_smem_p(n, m[i].q, m[i].q / m[i].pair, m[i].lpt, m[i].groups * m[i].stages) <= kSmemLimit)
             ids.push_back(i);
     if (ids.empty())
         return -1;
     return ids[(size_t)std::max(0, order) % ids.size()];
+}
+
+// Kind, tile, line and launch shape of a streamed pass with compiled entry ci.
+static void set_cstream(PassPlan *p, int ci)
+{
+    int cnt = 0;
+    const CStreamKernel &m = cstream_meta(&cnt)[ci];
+    p->kind = PK_CSTREAM;
+    p->cstream = ci;
+    p->lpt = m.lpt;
+    p->p = m.pair;
+    p->line = LineChoice{};
+    p->line.n = m.n;
+    p->line.fixed = -1;
+    p->line.T = m.threads / m.lpt;
+    p->line.nst = 3;
+    p->line.rad[0] = m.r1;
+    p->line.rad[1] = m.r2;
+    p->line.rad[2] = m.q;
+    p->threads = m.threads;
+    p->smem_bytes = cstream_smem_p(m.n, m.q, m.q / m.pair, m.lpt, m.groups * m.stages);
 }
 
 // A single 1D pass on dimension d with geometry g.
@@ -350,21 +375,8 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         p.kind = PK_J;
         p.lpt = lpt_j(p.line.T);
     } else if (!rotate && strided_in && n > 1 && (s->opts.tile_lines == 0 || s->opts.tile_lines == kTileStream) &&
-               cstream_pick(n, order, g) >= 0) {
-        const int ci = cstream_pick(n, order, g);
-        int cnt = 0;
-        const CStreamKernel &m = cstream_meta(&cnt)[ci];
-        p.kind = PK_CSTREAM;
-        p.cstream = ci;
-        p.lpt = m.lpt;
-        p.line = LineChoice{};
-        p.line.n = n;
-        p.line.fixed = -1;
-        p.line.T = m.threads / m.lpt;
-        p.line.nst = 3;
-        p.line.rad[0] = m.r1;
-        p.line.rad[1] = m.r2;
-        p.line.rad[2] = m.q;
+               cstream_pick(n, order, g, 1) >= 0) {
+        set_cstream(&p, cstream_pick(n, order, g, 1));
     } else if (p.line.fixed >= 0 && !rotate && strided_in && n > 1 && s->opts.tile_lines == kTileTma &&
                tma_ok(g, n, lpt_tma(n, p.line.T))) {
         p.kind = PK_CTMA;
@@ -397,10 +409,7 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         p.threads = p.line.T * p.lpt;
         p.smem_bytes = tw_slots_h(tw_len) * 8 + 2 * p.lpt * n * 8;
     } else if (p.kind == PK_CSTREAM) {
-        int cnt = 0;
-        const CStreamKernel &m = cstream_meta(&cnt)[p.cstream];
-        p.threads = m.threads;
-        p.smem_bytes = cstream_smem(n, m.q, m.lpt, m.groups * m.stages);
+        // launch shape set with the kind
     } else {
         p.threads = p.line.T * p.lpt;
         p.smem_bytes = tw_slots_h(tw_len) * 8 + p.lpt * n * 8;
@@ -503,6 +512,22 @@ static bool make_volc_pass(Schedule *s, int d, int n, int p, const PassGeom &g, 
 static int make_vol_pass(Schedule *s, int d, int n, int p, const PassGeom &g, int src, int dst,
                          PassPlan *out, std::string *err)
 {
+    // a strided line split over a cluster pair whose halves of the decimated
+    // sub-lines stream in by TMA (k_cstream.cu), unless tile_lines asks for
+    // the compiled splits of k_volc.cu
+    const int ci = p == 2 && s->opts.tile_lines <= kTileStream ? cstream_pick(n, s->opts.radix_order, g, 2) : -1;
+    if (ci >= 0) {
+        PassPlan q;
+        q.dim = d;
+        q.g = g;
+        q.src = src;
+        q.dst = dst;
+        set_cstream(&q, ci);
+        q.tw_seg[0] = line_seg(s, q.line);
+        set_tiles(&q);
+        *out = q;
+        return FFT3_OK;
+    }
     if (make_volc_pass(s, d, n, p, g, src, dst, out))
         return FFT3_OK;
     PassPlan q;
@@ -774,12 +799,16 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
                 // of it buys no coalescing on one GPU); a strided dimension is
                 // split over 4 blocks where a compiled split exists, else over 2
                 // (the paper's smallest mesh extent).
+                // The streamed cluster-pair split (measured faster than the
+                // compiled 4-block splits) comes first.
                 int cnt = 0;
                 const VolcKernel *vk = volc_meta(&cnt);
                 p = 2;
                 for (int i = 0; i < cnt; ++i)
                     if (vk[i].n == ns[d] && vk[i].p == 4)
                         p = 4;
+                if (cstream_pick(ns[d], 0, geom_natural(d, n0, n1, n2, batch), 2) >= 0)
+                    p = 2;
                 int a, b;
                 if (d == 0 || !volumetric_split(ns[d], p, &a, &b))
                     p = 1;
@@ -871,11 +900,13 @@ std::string Schedule::json() const
           << ",\"tiles\":" << p.ntiles;
         if (p.kind == PK_VOL || p.kind == PK_VOLC)
             o << ",\"p\":" << p.p << ",\"a\":" << p.split_a << ",\"b\":" << p.split_b;
+        if (p.kind == PK_CSTREAM && p.p > 1)
+            o << ",\"p\":" << p.p;
         if (p.kind == PK_CSTREAM) {
             int cnt = 0;
             const CStreamKernel &m = cstream_meta(&cnt)[p.cstream];
             o << ",\"q\":" << m.q << ",\"m\":" << m.n / m.q << ",\"groups\":" << m.groups
-              << ",\"staging\":" << m.groups * m.stages;
+              << ",\"staging\":" << m.groups * m.stages << ",\"cluster\":" << m.pair;
         }
         if (p.chunk > 0)
             o << ",\"chunk\":" << p.chunk << ",\"pipelined_with\":\"" << (p.pair_next ? "next" : "previous")

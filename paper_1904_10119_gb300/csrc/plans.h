@@ -59,38 +59,44 @@
 // LPT adjacent columns, G thread groups transform the sub-lines (M = R1 * R2,
 // two Stockham stages), each through its own ring of S TMA staging buffers
 // refilled as soon as they are read, then one radix-Q stage with twiddles
-// w_N^{q k'} stores the lines.  The line's twiddle table is the stage-major
-// table of (R1, R2, Q).  Row: N, Q, R1, R2, G, S, LPT.
+// w_N^{q k'} stores the lines.  With P = 2 a cluster of two blocks shares a
+// tile of LPT = 32 columns, each block holding half of the sub-lines.  The
+// line's twiddle table is the stage-major table of (R1, R2, Q).
+// Row: N, Q, R1, R2, G, S, LPT, P.
 #define FFT3_CSTREAM_LIST(X)             \
-    X(1024, 4, 16, 16, 2, 1, 16)         \
-    X(1024, 4, 16, 16, 1, 2, 16)         \
-    X(1024, 8, 16, 8, 4, 1, 16)          \
-    X(1024, 8, 16, 8, 2, 2, 16)          \
-    X(1024, 8, 8, 16, 2, 2, 16)          \
-    X(512, 4, 16, 8, 2, 1, 16)           \
-    X(512, 2, 16, 16, 1, 2, 16)          \
-    X(512, 2, 16, 16, 2, 1, 16)
+    X(1024, 4, 16, 16, 2, 1, 16, 1)      \
+    X(1024, 8, 16, 8, 2, 1, 32, 2)       \
+    X(1024, 4, 16, 16, 1, 2, 16, 1)      \
+    X(1024, 8, 16, 8, 4, 1, 16, 1)       \
+    X(1024, 8, 16, 8, 2, 2, 16, 1)       \
+    X(1024, 8, 8, 16, 2, 2, 16, 1)       \
+    X(512, 4, 16, 8, 2, 1, 16, 1)        \
+    X(512, 2, 16, 16, 1, 2, 16, 1)       \
+    X(512, 2, 16, 16, 2, 1, 16, 1)       \
+    X(512, 4, 16, 8, 2, 1, 32, 2)
 
 namespace fft3 {
 
 struct CStreamKernel {
-    int n, q, r1, r2, groups, stages, lpt, threads;
+    int n, q, r1, r2, groups, stages, lpt, pair, threads;
     const void *func; // nullptr in the host-only metadata
 };
 // Compiled list (device translation unit) and the host-only metadata.
 const CStreamKernel *cstream_kernels(int *count);
 const CStreamKernel *cstream_meta(int *count);
-// Dynamic shared memory of a streamed pass: twiddles (N-1 entries rounded to
-// 16), the tile's result (N x LPT) and `bufs` staging buffers (M x LPT).
-constexpr int cstream_smem(int n, int q, int lpt, int bufs)
+// Dynamic shared memory of one block of a streamed pass: twiddles (N-1
+// entries rounded to 16), its qp slots of the tile's result (M x LPT each)
+// and `bufs` staging buffers (M x LPT); M = n / q.
+constexpr int cstream_smem_p(int n, int q, int qp, int lpt, int bufs)
 {
-    return ((n - 1 + 15) / 16 * 16 + n * lpt + bufs * (n / q) * lpt) * 8;
+    return ((n - 1 + 15) / 16 * 16 + (qp + bufs) * (n / q) * lpt) * 8;
 }
+constexpr int cstream_smem(int n, int q, int lpt, int bufs) { return cstream_smem_p(n, q, q, lpt, bufs); }
 // Blocks per SM the launch bounds ask for: two when two copies of the
 // shared memory fit.
-constexpr int cstream_min_blocks(int n, int q, int lpt, int bufs, int threads)
+constexpr int cstream_min_blocks(int smem_bytes, int threads)
 {
-    return (2 * (cstream_smem(n, q, lpt, bufs) + 1024) <= 228 * 1024 && threads <= 512) ? 2 : 1;
+    return (2 * (smem_bytes + 1024) <= 228 * 1024 && threads <= 512) ? 2 : 1;
 }
 
 struct VolcKernel {

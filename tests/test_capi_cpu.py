@@ -197,7 +197,14 @@ def test_null_arguments(lib):
 
 
 def test_volumetric_automatic_mesh_and_compiled_splits():
+    # automatic mesh: the strided 1024-point lines split over a cluster pair,
+    # each block streaming half of the decimated sub-lines
     s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_VOLUMETRIC, -1)
+    assert _kinds(s) == ["line_contig", "line_strided_stream", "line_strided_stream"]
+    for p in s["passes"][1:]:
+        assert p["p"] == 2 and p["cluster"] == 2 and p["lpt"] == 32 and p["q"] % 2 == 0
+    # a 4-block mesh takes the compiled splits
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_VOLUMETRIC, -1, fft3.make_options(mesh=(0, 4, 4)))
     assert _kinds(s) == ["line_contig", "volumetric_split_fixed", "volumetric_split_fixed"]
     for p in s["passes"][1:]:
         assert p["p"] == 4 and p["a"] == 32 and p["b"] == 32 and p["lpt"] == 16 and p["threads"] == 256

@@ -96,14 +96,16 @@ def test_slab_pipelined_chunks(shape, batch, chunk, direction):
 
 @pytest.mark.parametrize("shape,batch,order,direction", [
     ((40, 1024, 6), 1, 0, FWD), ((40, 1024, 6), 1, 1, INV), ((40, 1024, 6), 1, 2, FWD),
-    ((24, 6, 1024), 2, 0, FWD), ((18, 512, 4), 1, 0, INV), ((18, 512, 4), 1, 1, FWD),
-    ((20, 6, 512), 1, 1, FWD), ((512, 512, 3), 1, 0, FWD), ((45, 512, 2), 1, 0, FWD),
-    ((40, 1024, 6), 1, 3, INV), ((24, 6, 1024), 1, 4, FWD), ((18, 512, 4), 1, 2, INV)])
+    ((40, 1024, 6), 1, 3, INV), ((40, 1024, 6), 1, 4, FWD), ((40, 1024, 6), 1, 5, FWD),
+    ((24, 6, 1024), 2, 0, FWD), ((24, 6, 1024), 2, 1, INV), ((24, 6, 1024), 1, 4, FWD),
+    ((18, 512, 4), 1, 0, INV), ((18, 512, 4), 1, 1, FWD), ((18, 512, 4), 1, 2, INV), ((18, 512, 4), 2, 3, FWD),
+    ((20, 6, 512), 1, 1, FWD), ((20, 6, 512), 1, 3, INV), ((512, 512, 3), 1, 0, FWD), ((45, 512, 2), 1, 0, FWD)])
 def test_streamed_strided_pass(shape, batch, order, direction):
     """Strided 512/1024-point lines with their decimated sub-lines streamed by
-    TMA (tile_lines 2): every compiled variant, ragged column tiles, a batch,
-    both directions; a row stride that is not a 16-byte multiple falls back to
-    the plain strided kernel."""
+    TMA (tile_lines 2): every compiled variant (one block, or a cluster pair
+    sharing 32-column tiles), ragged column tiles, a batch, both directions; a
+    row stride that is not a 16-byte multiple falls back to the plain strided
+    kernel."""
     x, got, plan = run_plan(shape, batch, P, direction, seed=order + 20, tile_lines=2, radix_order=order)
     assert_parity(x, got, shape, batch, direction)
     kinds = [p["kind"] for p in plan.describe()["passes"]]
