@@ -177,6 +177,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the per-decomposition and batched tables")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU oracle baseline")
+    ap.add_argument("--batched", type=int, default=0, metavar="COUNT",
+                    help="only time the batched executor on COUNT uneven cubes (seed 7) and print its line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -226,6 +228,11 @@ def main():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+
+    if args.batched > 0:
+        hbm, _ = _peaks()
+        print(json.dumps({"batched": bench_batched(fft3, synth, torch, hbm, args.batched)}), flush=True)
+        return 0
 
     decomp_map = {"auto": (fft3.FFT3_AUTO, {}), "slab_pencil": (fft3.FFT3_SLAB_PENCIL, {}),
                   "slab_pencil_pipelined": (fft3.FFT3_SLAB_PENCIL, {"slab_mode": 4}),
@@ -321,7 +328,13 @@ def main():
 
     extras = {}
     if not args.no_extras and rank == 0:
-        for name, (d, o) in decomp_map.items():
+        variants = dict(decomp_map)
+        variants["volumetric_mesh4_compiled"] = (fft3.FFT3_VOLUMETRIC, {"mesh": (1, 4, 4), "tile_lines": 16})
+        variants["ppp_plain_strided_kernel"] = (fft3.FFT3_PENCIL3, {"tile_lines": 16})
+        variants["split_bf16_tc"] = (fft3.FFT3_PENCIL3, {"dtype": fft3.FFT3_C64_SPLITBF16_TC})
+        variants["split_bf16_tc_first_stage"] = (fft3.FFT3_PENCIL3, {"dtype": fft3.FFT3_C64_SPLITBF16_TC,
+                                                                      "tc_stages": 1})
+        for name, (d, o) in variants.items():
             if name == "auto":
                 continue
             try:
@@ -355,6 +368,11 @@ def main():
             extras["batched_4096_uneven"] = bench_batched(fft3, synth, torch, hbm)
         except Exception as e:
             extras["batched_4096_uneven"] = {"error": str(e)}
+        if n0 == n1 == n2 == 1024:
+            try:
+                extras["smaller_cubes"] = size_table(fft3, synth, torch, (256, 512), decomp_map)
+            except Exception as e:
+                extras["smaller_cubes"] = {"error": str(e)}
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0 and n0 == n1 == n2:
@@ -394,11 +412,46 @@ def main():
     return 0
 
 
-def bench_batched(fft3, synth, torch, hbm):
-    """4096 independent 3D DFTs with dims drawn from {16..96} (seed 7) in one
+def size_table(fft3, synth, torch, sizes, decomp_map):
+    """Forward and inverse ms of n^3 (one transform, out of place) under each
+    decomposition, CUDA events over 10 back-to-back executions."""
+    table = {}
+    st = torch.cuda.current_stream()
+    for n in sizes:
+        x = torch.empty((n, n, n), dtype=torch.complex64).pin_memory()
+        synth.uniform_c64((n, n, n), 2, out=x.numpy())
+        x = x.to("cuda")
+        out = torch.empty_like(x)
+        row = {}
+        for name, (d, o) in decomp_map.items():
+            if name == "auto":
+                continue
+            ent = {}
+            for dname, direction in (("fwd_ms", fft3.FFT3_FORWARD), ("inv_ms", fft3.FFT3_INVERSE)):
+                p = fft3.Plan(n, n, n, 1, decomposition=d, direction=direction, **o)
+                for _ in range(3):
+                    p.execute(x, out)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(10):
+                    p.execute(x, out)
+                e1.record(st)
+                torch.cuda.synchronize()
+                assert p.check() == 0, fft3.last_error()
+                ent[dname] = e0.elapsed_time(e1) / 10
+                ent["kinds"] = [q["kind"] for q in p.describe()["passes"]]
+                p.close()
+            row[name] = ent
+        table[f"{n}^3"] = row
+        del x, out
+    return table
+
+
+def bench_batched(fft3, synth, torch, hbm, count=4096):
+    """`count` independent 3D DFTs with dims drawn from {16..96} (seed 7) in one
     graph-captured persistent launch: ms per batch, GB/s, roofline fractions."""
     import numpy as np
-    dims = synth.batched_dims(4096, 7)
+    dims = synth.batched_dims(count, 7)
     vols = dims.prod(axis=1)
     offs = np.zeros(len(dims), np.int64)
     offs[1:] = np.cumsum(vols[:-1])
@@ -424,7 +477,7 @@ def bench_batched(fft3, synth, torch, hbm):
     desc = fft3.fft3_plan_describe(h)
     fft3.fft3_plan_destroy(h)
     one_sweep = 2 * 8 * total
-    return {"ms": ms, "elements": total, "problems": 4096, "items": desc["items"],
+    return {"ms": ms, "elements": total, "problems": count, "items": desc["items"],
             "GBps_one_sweep": one_sweep / (ms * 1e-3) / 1e9,
             "frac_of_1_sweep": one_sweep / (ms * 1e-3) / 1e9 / hbm,
             "frac_of_3_sweeps": 3 * one_sweep / (ms * 1e-3) / 1e9 / hbm,
