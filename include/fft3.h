@@ -94,8 +94,10 @@ typedef struct fft3_options {
                              caller's stream, so the y pass reads what the x pass
                              has just left in L2; the side stream joins the caller's
                              stream before the z pass */
-    int tc_stages;    /* FFT3_C64_SPLITBF16_TC: 0 = every radix-16 stage on the tensor cores,
-                         1 = only the first radix-16 stage of each line */
+    int tc_stages;    /* FFT3_C64_SPLITBF16_TC: which radix-16 stages run on the tensor cores:
+                         0 = the first radix-16 stage of each line (the fastest; default),
+                         1 = the radix-16 stages whose operands are both in shared memory,
+                         2 = every radix-16 stage */
     int slab_chunk;   /* slab_mode 4: slabs per chunk (0 = about 32 MiB of slabs) */
     int reserved[8];  /* test hooks of the failure-detection tests, 0 in normal use:
                          [0] = s + 1 makes the x tiles of slab s never signal their

@@ -260,16 +260,18 @@ static int build_launches(fft3_plan_s *P)
         case PK_CSTREAM: {
             int cnt = 0;
             const CStreamKernel *ck = cstream_kernels(&cnt);
-            L.func = (p.cstream >= 0 && p.cstream < cnt) ? ck[p.cstream].func : nullptr;
+            L.func = (p.cstream >= 0 && p.cstream < cnt)
+                         ? (p.tc_mode < 0 ? ck[p.cstream].func : ck[p.cstream].func_tc[p.tc_mode == 0 ? 0 : 1])
+                         : nullptr;
             L.stream_q = L.func ? ck[p.cstream].q : 0;
             L.cluster = p.p;
             break;
         }
         case PK_JTC:
-            L.func = fk ? (p.tc_first_only ? fk->j_tc1 : fk->j_tc) : nullptr;
+            L.func = fk && p.tc_mode >= 0 ? fk->j_tc[p.tc_mode] : nullptr;
             break;
         case PK_CTC:
-            L.func = fk ? (p.tc_first_only ? fk->c_tc1 : fk->c_tc) : nullptr;
+            L.func = fk && p.tc_mode >= 0 ? fk->c_tc[p.tc_mode] : nullptr;
             break;
         case PK_COPY:
             L.func = (const void *)&k_copy;

@@ -32,6 +32,7 @@
 // w_N^{r k'}, the twiddles (II) of the final stage.
 #include <cooperative_groups.h>
 
+#include "pass_tc.cuh"
 #include "pass_tma.cuh"
 #include "plans.h"
 
@@ -98,10 +99,26 @@ __device__ __forceinline__ void tile_sync()
         cg::this_cluster().sync();
 }
 
-template <int N, int Q, int R1, int R2, int G, int S, int LPT, int P>
+// Staging buffer as a tile accessor (line = column, position = row of the
+// sub-line), conjugating on load for the inverse transform.
+template <int LPT>
+struct StageTile {
+    const float2 *p;
+    bool conj;
+    __device__ __forceinline__ float2 operator()(int l, int j) const
+    {
+        const float2 v = p[j * LPT + l];
+        return conj ? cconj(v) : v;
+    }
+};
+
+// TC = 0: FP32 sub-line stages.  TC = 1: the first 16-point stage of every
+// sub-line on the tensor cores in split BF16 (tc_stage.cuh); TC = 2: both.
+template <int N, int Q, int R1, int R2, int G, int S, int LPT, int P, int TC>
 __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(N, Q, Q / P, LPT, G *S), G *LPT *R2))
     k_cstream(PassArgs a, const __grid_constant__ CUtensorMap tin)
 {
+    static_assert(TC == 0 || (R1 == 16 && R2 == 16 && P == 1), "tensor-core sub-lines are 16 x 16");
     constexpr int M = R1 * R2;
     constexpr int T1 = M / R1;          // threads per column in a group (= first-stage butterflies)
     constexpr int GT = LPT * T1;        // threads per group
@@ -134,6 +151,11 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
         peer = cluster.map_shared_rank(res, r ^ 1);
     }
     const int64_t cid = blockIdx.x / P, ncl = gridDim.x / P;
+    TcW wtc;
+    if constexpr (TC > 0) {
+        __syncthreads(); // twiddles, including w_16^m at tw_split_off
+        tc_build_w(wtc, tw + a.tw_split_off);
+    }
     if (tid == 0) {
         for (int b = 0; b < G * S; ++b)
             mbar_init(&bars[b], 1);
@@ -171,26 +193,46 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
             const int q = g + G * w; // local slot
             const int b = g * S + (int)(k % S);
             const bool late = !failed && !mbar_wait(&bars[b], (uint32_t)((k / S) & 1), a.wait_budget);
-            // (I) first stage, radix R1, NS = 1: inputs x_q[t1 + r*T1] of column l
-            float2 x[R1];
             const float2 *sb = stg + b * M * LPT;
-#pragma unroll
-            for (int r = 0; r < R1; ++r) {
-                const float2 e = sb[(t1 + r * T1) * LPT + l];
-                x[r] = conj ? cconj(e) : e;
-            }
-            if (group_sync_or<G, GT>(g, late) && !failed) {
-                failed = true;
-                k_fail = k;
-            }
-            if (gtid == 0 && !failed)
-                issue(k + S); // the staging buffer is read out: refill it
-            Bfly<R1>::run(x);
             float2 *slot = res + q * M * LPT;
+            if constexpr (TC > 0) {
+                // (I) first 16-point stage on the tensor cores: staging buffer -> slot q
+                tc_stage16<M, 1, LPT, true>(StageTile<LPT>{sb, conj}, TileColSmem<LPT>{slot}, tw, wtc,
+                                            gtid >> 5, GT / 32);
+                if (group_sync_or<G, GT>(g, late) && !failed) {
+                    failed = true;
+                    k_fail = k;
+                }
+                if (gtid == 0 && !failed)
+                    issue(k + S); // the staging buffer is read out: refill it
+            } else {
+                // (I) first stage, radix R1, NS = 1: inputs x_q[t1 + r*T1] of column l
+                float2 x[R1];
 #pragma unroll
-            for (int r = 0; r < R1; ++r)
-                slot[(t1 * R1 + r) * LPT + l] = x[r];
-            group_sync<G, GT>(g);
+                for (int r = 0; r < R1; ++r) {
+                    const float2 e = sb[(t1 + r * T1) * LPT + l];
+                    x[r] = conj ? cconj(e) : e;
+                }
+                if (group_sync_or<G, GT>(g, late) && !failed) {
+                    failed = true;
+                    k_fail = k;
+                }
+                if (gtid == 0 && !failed)
+                    issue(k + S); // the staging buffer is read out: refill it
+                Bfly<R1>::run(x);
+#pragma unroll
+                for (int r = 0; r < R1; ++r)
+                    slot[(t1 * R1 + r) * LPT + l] = x[r];
+                group_sync<G, GT>(g);
+            }
+            if constexpr (TC == 2) {
+                // (I) second 16-point stage on the tensor cores, in place in slot q: with
+                // NS = 16 and M = 256 the outputs of a butterfly are its own inputs'
+                // positions, and a warp reads all its inputs before its MMAs
+                tc_stage16<M, R1, LPT, true>(TileColSmem<LPT>{slot}, TileColSmem<LPT>{slot}, tw + (R1 - 1), wtc,
+                                             gtid >> 5, GT / 32);
+                continue;
+            }
             // (I) second stage, radix R2, NS = R1, in place in slot q
             float2 y[BPT2][R2];
 #pragma unroll
@@ -257,8 +299,18 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
     }
 }
 
-#define FFT3_CSTREAM_ROW(N, Q, R1, R2, G, S, LPT, P) \
-    {N, Q, R1, R2, G, S, LPT, P, G * LPT * R2, (const void *)&k_cstream<N, Q, R1, R2, G, S, LPT, P>},
+template <int N, int Q, int R1, int R2, int G, int S, int LPT, int P, int TC>
+constexpr const void *cstream_tc_ptr()
+{
+    if constexpr (R1 == 16 && R2 == 16 && P == 1)
+        return (const void *)&k_cstream<N, Q, R1, R2, G, S, LPT, P, TC>;
+    else
+        return nullptr;
+}
+
+#define FFT3_CSTREAM_ROW(N, Q, R1, R2, G, S, LPT, P)                                      \
+    {N, Q, R1, R2, G, S, LPT, P, G * LPT * R2, (const void *)&k_cstream<N, Q, R1, R2, G, S, LPT, P, 0>, \
+     {cstream_tc_ptr<N, Q, R1, R2, G, S, LPT, P, 1>(), cstream_tc_ptr<N, Q, R1, R2, G, S, LPT, P, 2>()}},
 
 static const CStreamKernel g_cstream_kernels[] = {FFT3_CSTREAM_LIST(FFT3_CSTREAM_ROW)};
 

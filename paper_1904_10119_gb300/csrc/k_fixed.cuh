@@ -42,20 +42,20 @@ constexpr const void *pass_ctma_ptr()
         return nullptr;
 }
 
-template <int N, int T, class Rad, bool FIRST_ONLY>
+template <int N, int T, class Rad, int MODE>
 constexpr const void *pass_j_tc_ptr()
 {
-    constexpr int mask = FIRST_ONLY ? tc_mask_first(Rad{}) : tc_mask_all(Rad{});
+    constexpr int mask = tc_mask_mode<Rad>(MODE);
     if constexpr (mask != 0 && N >= 128 && T * lpt_j(T) <= 512 && (T * lpt_j(T)) % 32 == 0)
         return (const void *)&k_pass_j_tc<N, T, Rad, lpt_j(T), mask>;
     else
         return nullptr;
 }
 
-template <int N, int T, class Rad, bool FIRST_ONLY>
+template <int N, int T, class Rad, int MODE>
 constexpr const void *pass_c_tc_ptr()
 {
-    constexpr int mask = FIRST_ONLY ? tc_mask_first(Rad{}) : tc_mask_all(Rad{});
+    constexpr int mask = tc_mask_mode<Rad>(MODE);
     if constexpr (mask != 0 && N >= 128 && T * 8 <= 512)
         return (const void *)&k_pass_c_tc<N, T, Rad, 8, mask>;
     else
@@ -72,7 +72,9 @@ constexpr const void *pass_c_tc_ptr()
      fft3::pass_c_ptr<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_c(T, 8)>(),                   \
      fft3::slab_l2_ptr<N, T, fft3::Radices<__VA_ARGS__>>(),                                    \
      fft3::pass_ctma_ptr<N, T, fft3::Radices<__VA_ARGS__>>(),                                  \
-     fft3::pass_j_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, false>(),                            \
-     fft3::pass_j_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, true>(),                             \
-     fft3::pass_c_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, false>(),                            \
-     fft3::pass_c_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, true>()},
+     {fft3::pass_j_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, 0>(),                               \
+      fft3::pass_j_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, 1>(),                               \
+      fft3::pass_j_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, 2>()},                              \
+     {fft3::pass_c_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, 0>(),                               \
+      fft3::pass_c_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, 1>(),                               \
+      fft3::pass_c_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, 2>()}},

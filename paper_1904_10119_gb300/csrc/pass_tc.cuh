@@ -156,5 +156,19 @@ __host__ __device__ constexpr int tc_mask_first(Radices<Rs...> r)
     const int all = tc_mask_all(r);
     return all & (-all);
 }
+// The radix-16 stages whose operands are both in shared memory (neither the
+// first stage, which reads global memory, nor the last, which writes it).
+template <int... Rs>
+__host__ __device__ constexpr int tc_mask_inner(Radices<Rs...> r)
+{
+    return tc_mask_all(r) & ~1 & ~(1 << ((int)sizeof...(Rs) - 1));
+}
+// tc_stages option: 0 = the first radix-16 stage, 1 = the radix-16 stages
+// with both operands in shared memory, 2 = every radix-16 stage.
+template <class Rad>
+__host__ __device__ constexpr int tc_mask_mode(int mode)
+{
+    return mode == 0 ? tc_mask_first(Rad{}) : mode == 1 ? tc_mask_inner(Rad{}) : tc_mask_all(Rad{});
+}
 
 } // namespace fft3

@@ -58,7 +58,7 @@ const VolcKernel *volc_meta(int *count)
     return g_volc_meta;
 }
 
-#define FFT3_CSTREAM_META(N, Q, R1, R2, G, S, LPT, P) {N, Q, R1, R2, G, S, LPT, P, G * LPT * R2, nullptr},
+#define FFT3_CSTREAM_META(N, Q, R1, R2, G, S, LPT, P) {N, Q, R1, R2, G, S, LPT, P, G * LPT * R2, nullptr, {nullptr, nullptr}},
 static const CStreamKernel g_cstream_meta[] = {FFT3_CSTREAM_LIST(FFT3_CSTREAM_META)};
 #undef FFT3_CSTREAM_META
 
@@ -330,14 +330,36 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         return rc;
     const bool contig_in = g.ij == 1;
     const bool strided_in = g.ic == 1 && g.oc == 1;
+    const int tc_mode = std::min(2, std::max(0, s->opts.tc_stages));
+    if (s->dtype == FFT3_C64_SPLITBF16_TC && !rotate && strided_in && n > 1 && s->opts.tile_lines == 0) {
+        // streamed strided pass whose 16 x 16 sub-line transforms run on the tensor cores
+        int cnt = 0;
+        const CStreamKernel *cm = cstream_meta(&cnt);
+        const int ci = cstream_pick(n, order, g, 1);
+        int tci = -1;
+        for (int i = 0; i < cnt && tci < 0; ++i)
+            if (cm[i].n == n && cm[i].pair == 1 && cm[i].r1 == 16 && cm[i].r2 == 16 && ci >= 0)
+                tci = i;
+        if (tci >= 0) {
+            set_cstream(&p, tci);
+            p.tc_mode = tc_mode;
+            p.tw_seg[0] = line_seg(s, p.line);
+            std::vector<int64_t> w16(16);
+            for (int i = 0; i < 16; ++i)
+                w16[i] = i;
+            p.tw_seg[2] = add_seg(s, 16, std::move(w16)); // w_16^m for the DFT_16 matrix
+            p.smem_bytes += 16 * 8;
+            set_tiles(&p);
+            *out = p;
+            return FFT3_OK;
+        }
+    }
     if (s->dtype == FFT3_C64_SPLITBF16_TC && !rotate && n >= 128) {
         // prefer a candidate plan that has tensor-core kernels for this layout
         std::vector<int> fc = fixed_candidates(n);
         for (size_t k = 0; k < fc.size(); ++k) {
             const FixedPlanMeta &m = g_meta[fc[(k + order) % fc.size()]];
-            bool has16 = false;
-            for (int i = 0; i < m.nrad; ++i)
-                has16 |= m.rad[i] == 16;
+            const bool has16 = tc_mask_host(m.rad, m.nrad, tc_mode) != 0;
             const bool jok = contig_in && g.ok == 1 && tc_j_ok(n, m.T, has16);
             const bool cok = strided_in && tc_c_ok(n, m.T, has16);
             if (!jok && !cok)
@@ -350,7 +372,7 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
                 p.line.rad[i] = m.rad[i];
             p.kind = jok ? PK_JTC : PK_CTC;
             p.lpt = jok ? lpt_j(m.T) : lpt_c_tc();
-            p.tc_first_only = s->opts.tc_stages == 1;
+            p.tc_mode = tc_mode;
             p.tw_seg[0] = line_seg(s, p.line);
             std::vector<int64_t> w16(16);
             for (int i = 0; i < 16; ++i)
@@ -738,16 +760,8 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         int mode = s.opts.slab_mode;
         int twl = 2 * tw_slots_h(n0) + 2 * tw_slots_h(n1);
         bool fits_smem = slab_smem(n0, n1, twl) <= kSmemLimit;
-        if (mode == 0) {
-            // unfused when the y lines have a streamed kernel (faster than
-            // the L2-resident slab kernel where both exist), else L2-resident
-            int cnt = 0;
-            const CStreamKernel *cm = cstream_meta(&cnt);
-            bool streamed_y = false;
-            for (int i = 0; i < cnt; ++i)
-                streamed_y = streamed_y || cm[i].n == n1;
-            mode = fits_smem ? 1 : (!streamed_y && slab_l2_supported(n0, n1) ? 2 : 3);
-        }
+        if (mode == 0) // the L2-resident slab kernel measured slower than x and y passes (256^2 to 1024^2)
+            mode = fits_smem ? 1 : 3;
         PassPlan p;
         if (mode == 1 && fits_smem) {
             rc = make_slab_pass(&s, n0, n1, n2, batch, &p, err);
@@ -888,7 +902,9 @@ std::string Schedule::json() const
       << ",\"twiddle_entries\":" << tw_total << ",\"passes\":[";
     for (size_t i = 0; i < passes.size(); ++i) {
         const PassPlan &p = passes[i];
-        o << (i ? "," : "") << "{\"kind\":\"" << kind_name(p.kind) << "\",\"dim\":" << p.dim
+        o << (i ? "," : "") << "{\"kind\":\""
+          << (p.kind == PK_CSTREAM && p.tc_mode >= 0 ? "line_strided_stream_tc" : kind_name(p.kind))
+          << "\",\"dim\":" << p.dim
           << ",\"src\":\"" << buf_name(p.src) << "\",\"dst\":\"" << buf_name(p.dst)
           << "\",\"line\":";
         line_json(o, p.line);
@@ -902,6 +918,8 @@ std::string Schedule::json() const
             o << ",\"p\":" << p.p << ",\"a\":" << p.split_a << ",\"b\":" << p.split_b;
         if (p.kind == PK_CSTREAM && p.p > 1)
             o << ",\"p\":" << p.p;
+        if (p.kind == PK_JTC || p.kind == PK_CTC || (p.kind == PK_CSTREAM && p.tc_mode >= 0))
+            o << ",\"tc_stages\":" << p.tc_mode;
         if (p.kind == PK_CSTREAM) {
             int cnt = 0;
             const CStreamKernel &m = cstream_meta(&cnt)[p.cstream];

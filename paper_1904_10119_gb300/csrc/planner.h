@@ -61,7 +61,7 @@ struct PassPlan {
     int smem_bytes = 0;  // dynamic shared memory per block
     int64_t ntiles = 0, tiles_c = 0;
     int slabs_per_chunk = 0;
-    bool tc_first_only = false; // PK_JTC / PK_CTC: only the first radix-16 stage on tensor cores
+    int tc_mode = -1;           // split-BF16 tensor-core stages (tc_stages option); -1 = FP32 pass
     int volc = -1;              // PK_VOLC: index into the compiled volumetric list
     int cstream = -1;           // PK_CSTREAM: index into the compiled streamed-pass list
     int chunk = 0;              // slabs per chunk of a two-stream pipelined slab stage (0 = one launch)

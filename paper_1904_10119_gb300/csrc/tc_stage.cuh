@@ -96,12 +96,19 @@ __device__ __forceinline__ void tc_butterfly(int grp, int n, int &line, int &q)
 // butterflies (line, q) of a tile, in groups of 8, each warp taking every
 // nwarps-th group.  Src and Dst are tile accessors acc(line, pos) and must not
 // alias (the stage streams group by group; the caller ping-pongs buffers).
+// `warp` / `nwarps`: this warp's index among the warps sharing the stage (by
+// default every warp of the block).
 template <int N, int NS, int LPT, bool GROUP_LINES, class Src, class Dst>
-__device__ __forceinline__ void tc_stage16(const Src &src, const Dst &dst, const float2 *tw, const TcW &w)
+__device__ __forceinline__ void tc_stage16(const Src &src, const Dst &dst, const float2 *tw, const TcW &w,
+                                           int warp = -1, int nwarps = 0)
 {
     constexpr int NB = N / 16;
     constexpr int NGROUPS = NB * LPT / 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp < 0) {
+        warp = threadIdx.x >> 5;
+        nwarps = blockDim.x >> 5;
+    }
     const int g = lane >> 2, t = lane & 3;
     for (int grp = warp; grp < NGROUPS; grp += nwarps) {
         int line, q;
