@@ -8,7 +8,7 @@ The paper leaves the choice of decomposition to the user and shows that none
 wins everywhere (Section 4.3); this module makes the choice from measurements.
 
 Command line (runs on a GPU):
-  python -m paper_1904_10119_gb300.plansel --train-shapes 70 --test-shapes 200 --out plansel.json
+  python -m paper_1904_10119_gb300.plansel --train-shapes 120 --test-shapes 200 --out plansel.json
 """
 from __future__ import annotations
 
@@ -23,50 +23,65 @@ import numpy as np
 from . import fft3
 
 SIZES = (16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024)
-N_FEATURES = 20
+
+KINDS = ("line_contig", "line_contig_rotate", "line_strided", "line_runtime", "slab_smem", "slab_l2",
+         "volumetric_split", "volumetric_split_fixed", "line_strided_stream", "line_strided_tma")
+N_FEATURES = 12 + len(KINDS) + 10
 
 
 def candidates():
     """(decomposition, options kwargs) of every candidate plan; index 0 is the
-    fixed default (pencil-pencil-pencil, natural layout, radix order 0)."""
+    fixed default (pencil-pencil-pencil, natural layout, radix order 0,
+    streamed strided kernels where compiled)."""
     out = []
     for order in range(4):
         out.append((fft3.FFT3_PENCIL3, dict(radix_order=order)))
-        out.append((fft3.FFT3_PENCIL3, dict(radix_order=order, tile_lines=8)))
         out.append((fft3.FFT3_PENCIL3, dict(radix_order=order, tile_lines=16)))
+    for order in range(2):
         out.append((fft3.FFT3_PENCIL3, dict(radix_order=order, variant=1)))
         out.append((fft3.FFT3_SLAB_PENCIL, dict(radix_order=order, slab_mode=1)))
         out.append((fft3.FFT3_SLAB_PENCIL, dict(radix_order=order, slab_mode=2)))
-        out.append((fft3.FFT3_SLAB_PENCIL, dict(radix_order=order, slab_mode=3)))
-        out.append((fft3.FFT3_VOLUMETRIC, dict(radix_order=order, mesh=(2, 2, 2))))
+        out.append((fft3.FFT3_SLAB_PENCIL, dict(radix_order=order, slab_mode=3, tile_lines=8)))
+        out.append((fft3.FFT3_VOLUMETRIC, dict(radix_order=order)))
+    out.append((fft3.FFT3_SLAB_PENCIL, dict(slab_mode=4)))
+    out.append((fft3.FFT3_VOLUMETRIC, dict(mesh=(2, 2, 2))))
+    out.append((fft3.FFT3_VOLUMETRIC, dict(mesh=(1, 4, 4), tile_lines=16)))
     return out
 
 
 def features(shape, batch, decomp, opts, schedule=None) -> np.ndarray:
-    """20 features of a (shape, plan) pair: sizes, the plan's options, the
-    radix stages per dimension, and what the host planner lowers it to (HBM
-    sweeps, runtime-radix passes, cluster passes)."""
+    """Features of a (shape, plan) pair: sizes, the plan's options, and what
+    the host planner lowers it to (passes by kernel kind, line lengths, radix
+    stages, lines per tile, launches)."""
     n0, n1, n2 = shape
     order = opts.get("radix_order", 0)
     if schedule is None:
         schedule = fft3.fft3_plan_schedule(*shape, batch, 0, decomp, -1, fft3.make_options(**opts))
-    kinds = [p["kind"] for p in schedule["passes"]]
+    passes = schedule["passes"]
     f = np.zeros(N_FEATURES, np.float32)
-    f[16] = len(kinds)
-    f[17] = sum(k == "line_runtime" for k in kinds)
-    f[18] = sum(k.startswith("volumetric") for k in kinds)
-    f[19] = sum(k.startswith("slab") for k in kinds)
     f[0:3] = [math.log2(n0), math.log2(n1), math.log2(n2)]
     f[3] = math.log2(batch)
-    f[4] = 0.0  # dtype: FP32
+    f[4] = math.log2(n0 * n1 * n2 * batch)
     f[5 + {fft3.FFT3_SLAB_PENCIL: 0, fft3.FFT3_PENCIL3: 1, fft3.FFT3_VOLUMETRIC: 2}[decomp]] = 1.0
     f[8] = float(opts.get("variant", 0))
-    f[9] = opts.get("slab_mode", 0) / 3.0
+    f[9] = opts.get("slab_mode", 0) / 4.0
     f[10] = opts.get("tile_lines", 0) / 16.0
     f[11] = order / 3.0
-    f[12] = math.log2(n0 * n1 * n2 * batch)
-    for d, n in enumerate(shape):
-        f[13 + d] = len(fft3.fft3_factorize(n, order)) if n > 1 else 0.0
+    for p in passes:
+        if p["kind"] in KINDS:
+            f[12 + KINDS.index(p["kind"])] += 1.0
+    k = 12 + len(KINDS)
+    f[k] = len(passes)
+    f[k + 1] = sum(p.get("chunk", 0) > 0 for p in passes)
+    stages = [len(p["line"]["radices"]) for p in passes]
+    f[k + 2] = float(sum(stages))
+    f[k + 3] = float(max(stages) if stages else 0)
+    f[k + 4] = float(sum(16 in p["line"]["radices"] for p in passes))
+    f[k + 5] = float(np.mean([math.log2(max(1, p["lpt"])) for p in passes]))
+    f[k + 6] = float(np.mean([p["threads"] / 1024.0 for p in passes]))
+    f[k + 7] = float(np.mean([p["smem"] / (227.0 * 1024) for p in passes]))
+    f[k + 8] = float(np.log2(max(1, min(p["tiles"] for p in passes))))
+    f[k + 9] = float(schedule["hbm_sweeps"] + (0.5 if schedule["decomposition"] == "volumetric" else 0.0))
     return f
 
 
@@ -108,13 +123,20 @@ def collect(shapes, batch=1, reps=3):
 
 
 def to_xy(table, batch=1):
+    """Features and targets: the log run time of each feasible candidate
+    relative to the mean log run time of the shape's candidates (only the
+    ranking within a shape matters for the choice)."""
     cands = candidates()
     X, y = [], []
     for shape, ms in table:
-        for (d, o), t in zip(cands, ms):
-            if t > 0:
-                X.append(features(shape, batch, d, o))
-                y.append(math.log(t))
+        valid = [(i, t) for i, t in enumerate(ms) if t > 0]
+        if not valid:
+            continue
+        mean_log = float(np.mean([math.log(t) for _, t in valid]))
+        for i, t in valid:
+            d, o = cands[i]
+            X.append(features(shape, batch, d, o))
+            y.append(math.log(t) - mean_log)
     return np.asarray(X, np.float32), np.asarray(y, np.float32)
 
 
@@ -136,9 +158,9 @@ class CostModel:
     def predict(self, X):
         return self.mlp.predict((X - self.mu) / self.sd)
 
-    def choose(self, shape, batch=1):
-        """Index of the candidate with the lowest predicted run time among the
-        ones the planner accepts for this shape."""
+    def ranking(self, shape, batch=1):
+        """Candidate indices the planner accepts for this shape, best
+        predicted first."""
         cands = candidates()
         ok = []
         for i, (d, o) in enumerate(cands):
@@ -148,31 +170,39 @@ class CostModel:
             except fft3.Fft3Error:
                 pass
         X = np.stack([features(shape, batch, *cands[i]) for i in ok])
-        return ok[int(np.argmin(self.predict(X)))]
+        return [ok[j] for j in np.argsort(self.predict(X), kind="stable")]
+
+    def choose(self, shape, batch=1):
+        return self.ranking(shape, batch)[0]
 
 
-def analytic_choice(shape, batch=1):
-    """Baseline without the model: fewest HBM sweeps (passes of the plan),
-    ties broken by candidate order."""
-    best, best_cost = 0, None
+def analytic_ranking(shape, batch=1):
+    """Baseline without the model: fewest HBM sweeps (passes of the plan,
+    volumetric penalised by half a sweep for its exchange), ties broken by
+    candidate order."""
+    scored = []
     for i, (d, o) in enumerate(candidates()):
         try:
             s = fft3.fft3_plan_schedule(*shape, batch, 0, d, -1, fft3.make_options(**o))
         except fft3.Fft3Error:
             continue
-        cost = s["hbm_sweeps"] + (0.5 if s["decomposition"] == "volumetric" else 0.0)
-        if best_cost is None or cost < best_cost:
-            best, best_cost = i, cost
-    return best
+        scored.append((s["hbm_sweeps"] + (0.5 if s["decomposition"] == "volumetric" else 0.0), i))
+    return [i for _, i in sorted(scored)]
 
 
-def regrets(table, chooser):
+def regrets(table, ranker):
+    """regret = t(chosen) / t(best) - 1 per shape, where the chosen plan is the
+    first of the ranking that can be created on the GPU (a proposal whose
+    creation fails falls through to the next one at no measured cost)."""
     out = []
     for shape, ms in table:
         valid = ms > 0
         best = ms[valid].min()
-        c = chooser(shape)
-        t = ms[c] if ms[c] > 0 else np.inf
+        t = np.inf
+        for c in ranker(shape):
+            if ms[c] > 0:
+                t = ms[c]
+                break
         out.append(float(t / best - 1.0))
     return np.asarray(out)
 
@@ -182,7 +212,7 @@ def summarize(r):
             "max": float(np.max(r)), "zero_regret_frac": float(np.mean(r <= 1e-9))}
 
 
-def run(train_shapes=70, test_shapes=200, seed=8, max_volume=1 << 24, reps=3, epochs=200):
+def run(train_shapes=120, test_shapes=200, seed=8, max_volume=1 << 24, reps=3, epochs=400):
     t0 = time.perf_counter()
     train = sample_shapes(train_shapes, seed, max_volume)
     test = sample_shapes(test_shapes, seed + 1000, max_volume, exclude=train)
@@ -196,9 +226,9 @@ def run(train_shapes=70, test_shapes=200, seed=8, max_volume=1 << 24, reps=3, ep
         "train_shapes": len(train), "test_shapes": len(test), "train_plans": int(X.shape[0]),
         "candidates": len(candidates()), "collect_seconds": t_collect,
         "loss_first": float(curve[0]), "loss_last": float(curve[-1]),
-        "regret_mlp": summarize(regrets(tab_test, lambda s: model.choose(s))),
-        "regret_fixed_default": summarize(regrets(tab_test, lambda s: 0)),
-        "regret_analytic": summarize(regrets(tab_test, analytic_choice)),
+        "regret_mlp": summarize(regrets(tab_test, lambda s: model.ranking(s))),
+        "regret_fixed_default": summarize(regrets(tab_test, lambda s: [0])),
+        "regret_analytic": summarize(regrets(tab_test, analytic_ranking)),
         "exhaustive_ms_per_shape": float(np.mean([ms[ms > 0].sum() for _, ms in tab_test])),
     }
     model.mlp.close()
@@ -207,11 +237,11 @@ def run(train_shapes=70, test_shapes=200, seed=8, max_volume=1 << 24, reps=3, ep
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train-shapes", type=int, default=70)
+    ap.add_argument("--train-shapes", type=int, default=120)
     ap.add_argument("--test-shapes", type=int, default=200)
     ap.add_argument("--seed", type=int, default=8)
     ap.add_argument("--max-volume", type=int, default=1 << 24)
-    ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     res = run(a.train_shapes, a.test_shapes, a.seed, a.max_volume, epochs=a.epochs)
