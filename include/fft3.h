@@ -150,6 +150,20 @@ int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream);
  * staging buffers are allocated on the first call and kept by the plan. */
 int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *stream);
 
+/* `count` transforms from and to HOST memory, pipelined: transform i reads
+ * h_in[i] and writes h_out[i] (arrays of `count` host pointers, each to one
+ * plan-sized complex64 array; h_out[i] must not overlap any h_in[j]).  Two
+ * sets of plan-owned device staging buffers alternate, so the host-to-device
+ * copy of transform i+1, the transform of i and the device-to-host copy of
+ * i-1 run at the same time on three plan-owned streams.  Returns after the
+ * last result is in h_out[count-1] (every h_out[i] is complete); `stream` is
+ * ordered before the first copy.  The staging buffers (four plan-sized
+ * arrays) are allocated on the first call and kept by the plan.  The paper
+ * has no host-memory interface; this is the end-to-end form of the transform
+ * for callers whose data live in host memory. */
+int fft3_plan_execute_host_pipelined(fft3_plan p, const void *const *h_in, void *const *h_out, int count,
+                                     void *stream);
+
 /* Reads and clears the plan's device error flag (set when a bounded wait in a
  * persistent kernel expired).  Synchronises the plan's last stream. */
 int fft3_plan_check(fft3_plan p);

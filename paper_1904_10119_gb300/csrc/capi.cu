@@ -340,6 +340,15 @@ static void free_plan(fft3_plan_s *P)
         cudaFree(P->d_err);
     cudaFree(P->d_stage_in);
     cudaFree(P->d_stage_out);
+    cudaFree(P->d_stage_in2);
+    cudaFree(P->d_stage_out2);
+    for (int i = 0; i < 3; ++i)
+        if (P->pipe_st[i])
+            cudaStreamDestroy(P->pipe_st[i]);
+    for (int b = 0; b < 2; ++b)
+        for (int e = 0; e < 3; ++e)
+            if (P->pipe_ev[b][e])
+                cudaEventDestroy(P->pipe_ev[b][e]);
     if (P->side)
         cudaStreamDestroy(P->side);
     if (P->ev_fork)
@@ -690,6 +699,60 @@ int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *str
         return rc;
     CUDA_TRY(cudaMemcpyAsync(h_out, p->d_stage_out, bytes, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    return FFT3_OK;
+}
+
+int fft3_plan_execute_host_pipelined(fft3_plan p, const void *const *h_in, void *const *h_out, int count,
+                                     void *stream)
+{
+    if (!p || !h_in || !h_out || count < 0)
+        return fail(FFT3_ERR_INVALID_ARG, "null plan or pointer arrays, or negative count");
+    for (int i = 0; i < count; ++i)
+        if (!h_in[i] || !h_out[i])
+            return fail(FFT3_ERR_INVALID_ARG, "null host buffer in the pointer arrays");
+    if (count == 0)
+        return FFT3_OK;
+    const size_t bytes = (size_t)p->elems * sizeof(float2);
+    if (!p->d_stage_in) {
+        CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
+        CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
+    }
+    if (!p->d_stage_in2) {
+        CUDA_TRY(cudaMalloc(&p->d_stage_in2, bytes));
+        CUDA_TRY(cudaMalloc(&p->d_stage_out2, bytes));
+        for (int i = 0; i < 3; ++i)
+            CUDA_TRY(cudaStreamCreateWithFlags(&p->pipe_st[i], cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b)
+            for (int e = 0; e < 3; ++e)
+                CUDA_TRY(cudaEventCreateWithFlags(&p->pipe_ev[b][e], cudaEventDisableTiming));
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    cudaStream_t h2d = p->pipe_st[0], comp = p->pipe_st[1], d2h = p->pipe_st[2];
+    float2 *din[2] = {p->d_stage_in, p->d_stage_in2}, *dout[2] = {p->d_stage_out, p->d_stage_out2};
+    // everything the caller queued on `stream` comes first
+    CUDA_TRY(cudaEventRecord(p->pipe_ev[0][0], user));
+    for (int i = 0; i < 3; ++i)
+        CUDA_TRY(cudaStreamWaitEvent(p->pipe_st[i], p->pipe_ev[0][0], 0));
+    for (int i = 0; i < count; ++i) {
+        const int b = i & 1;
+        cudaEvent_t *ev = p->pipe_ev[b];
+        if (i >= 2) // the transform of i-2 has read din[b]
+            CUDA_TRY(cudaStreamWaitEvent(h2d, ev[1], 0));
+        CUDA_TRY(cudaMemcpyAsync(din[b], h_in[i], bytes, cudaMemcpyHostToDevice, h2d));
+        CUDA_TRY(cudaEventRecord(ev[0], h2d));
+        CUDA_TRY(cudaStreamWaitEvent(comp, ev[0], 0));
+        if (i >= 2) // the copy-out of i-2 has drained dout[b]
+            CUDA_TRY(cudaStreamWaitEvent(comp, ev[2], 0));
+        int rc = fft3_plan_execute(p, din[b], dout[b], comp);
+        if (rc)
+            return rc;
+        CUDA_TRY(cudaEventRecord(ev[1], comp)); // din[b] read, dout[b] written
+        CUDA_TRY(cudaStreamWaitEvent(d2h, ev[1], 0));
+        CUDA_TRY(cudaMemcpyAsync(h_out[i], dout[b], bytes, cudaMemcpyDeviceToHost, d2h));
+        CUDA_TRY(cudaEventRecord(ev[2], d2h));
+    }
+    CUDA_TRY(cudaStreamSynchronize(d2h));
+    p->last_stream = comp;
     return FFT3_OK;
 }
 

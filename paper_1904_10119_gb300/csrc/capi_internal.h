@@ -74,6 +74,11 @@ struct fft3_plan_s {
     unsigned *d_err = nullptr;
     std::vector<fft3::Launch> launches;
     float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
+    // pipelined host execution: a second set of staging buffers, the copy and
+    // compute streams, and per-set events (input consumed, output produced, output drained)
+    float2 *d_stage_in2 = nullptr, *d_stage_out2 = nullptr;
+    cudaStream_t pipe_st[3] = {nullptr, nullptr, nullptr}; // H2D, compute, D2H
+    cudaEvent_t pipe_ev[2][3] = {};                        // [set][input loaded, transform done, output drained]
     cudaStream_t last_stream = nullptr;
     cudaStream_t side = nullptr;                        // second stream of a pipelined pair
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // chunk hand-over and final join

@@ -68,6 +68,7 @@ def load() -> ctypes.CDLL:
         "fft3_plan_workspace_bytes": (sz, [_P]),
         "fft3_plan_launches": (i, [_P]),
         "fft3_plan_kernel_launches": (i, [_P]),
+        "fft3_plan_execute_host_pipelined": (i, [_P, _P, _P, ctypes.c_int, _P]),
         "fft3_plan_describe": (i, [_P, ctypes.c_char_p, sz]),
         "fft3_plan_schedule": (i, [i, i, i, i, i, i, i, ctypes.POINTER(fft3_options), ctypes.c_char_p, sz]),
         "fft3_factorize": (i, [i, i, pi, i]),
@@ -196,6 +197,14 @@ def fft3_plan_workspace_bytes(plan: int) -> int:
 
 def fft3_plan_launches(plan: int) -> int:
     return _check(load().fft3_plan_launches(_P(plan)))
+
+
+def fft3_plan_execute_host_pipelined(plan: int, h_in_ptrs, h_out_ptrs, stream: int = 0) -> None:
+    count = len(h_in_ptrs)
+    assert len(h_out_ptrs) == count
+    arr_in = (_P * max(1, count))(*[int(v) for v in h_in_ptrs])
+    arr_out = (_P * max(1, count))(*[int(v) for v in h_out_ptrs])
+    _check(load().fft3_plan_execute_host_pipelined(_P(plan), arr_in, arr_out, count, _P(stream)))
 
 
 def fft3_plan_kernel_launches(plan: int) -> int:

@@ -176,6 +176,24 @@ def test_execute_host_buffers():
         fft3.fft3_plan_destroy(h)
 
 
+def test_execute_host_pipelined():
+    """Five transforms of different inputs from and to host memory with the
+    copies of neighbouring transforms overlapping; every output is checked."""
+    shape = (64, 40, 24)
+    xs = [synth.uniform_c64((1, 24, 40, 64), 30 + i) for i in range(5)]
+    h = fft3.fft3_plan_create_ex(*shape, 1, 0, P, FWD, fft3.make_options())
+    try:
+        hin = [torch.from_numpy(x).pin_memory() for x in xs]
+        hout = [torch.empty_like(t).pin_memory() for t in hin]
+        fft3.fft3_plan_execute_host_pipelined(h, [t.data_ptr() for t in hin], [t.data_ptr() for t in hout], 0)
+        assert fft3.fft3_plan_check(h) == 0
+        for x, o in zip(xs, hout):
+            assert_parity(x, o.numpy(), shape)
+        fft3.fft3_plan_execute_host_pipelined(h, [], [], 0)  # count 0 is a no-op
+    finally:
+        fft3.fft3_plan_destroy(h)
+
+
 def test_per_pass_execution_composes_to_the_transform():
     shape = (256, 64, 32)
     x = synth.uniform_c64((1, 32, 64, 256), 13)
