@@ -99,10 +99,11 @@ struct FlatPlan {
     X(128, 16, 8) X(20, 4, 5) X(60, 4, 5, 3) X(120, 8, 5, 3) X(8, 8) X(12, 4, 3) X(4, 4)
 
 // Transforms nl lines (COLS = false) or columns (COLS = true) of length L.n
-// held in A; returns the buffer (A or B) holding the result.
+// held in A; returns the buffer (A or B) holding the result.  Every compiled
+// sequence is tried (one out-of-line copy per layout).
 template <bool COLS>
-__device__ __forceinline__ float2 *batch_stages(const LineRt &L, int nl, int pitch, float2 *A, float2 *B,
-                                                const float2 *tw)
+__device__ __noinline__ float2 *batch_stages_all(const LineRt &L, int nl, int pitch, float2 *A, float2 *B,
+                                                 const float2 *tw)
 {
 #define FFT3_FLAT_TRY(N, ...)                                                    \
     if (FlatPlan<N, __VA_ARGS__>::match(L))                                      \
@@ -110,6 +111,26 @@ __device__ __forceinline__ float2 *batch_stages(const LineRt &L, int nl, int pit
     FFT3_FLAT_PLANS(FFT3_FLAT_TRY)
 #undef FFT3_FLAT_TRY
     return COLS ? run_stages_cols(L, nl, pitch, A, B, tw) : run_stages_lines(L, nl, pitch, A, B, tw);
+}
+
+// The same when the line length is known at compile time (NF > 0): only the
+// sequences of that length are tried inline; NF = 0 calls batch_stages_all.
+template <bool COLS, int NF>
+__device__ __forceinline__ float2 *batch_stages(const LineRt &L, int nl, int pitch, float2 *A, float2 *B,
+                                                const float2 *tw)
+{
+    if constexpr (NF == 0) {
+        return batch_stages_all<COLS>(L, nl, pitch, A, B, tw);
+    } else {
+#define FFT3_FLAT_TRY(N, ...)                                                    \
+        if constexpr (N == NF) {                                                 \
+            if (FlatPlan<N, __VA_ARGS__>::match(L))                              \
+                return FlatPlan<N, __VA_ARGS__>::template run<COLS>(nl, pitch, A, B, tw); \
+        }
+        FFT3_FLAT_PLANS(FFT3_FLAT_TRY)
+#undef FFT3_FLAT_TRY
+        return batch_stages_all<COLS>(L, nl, pitch, A, B, tw);
+    }
 }
 
 } // namespace fft3

@@ -40,7 +40,8 @@ struct BatchArgs {
     unsigned *err;
     long long wait_budget;
     int conj;
-    int buf_elems;       // complex elements of each of the two shared buffers
+    int buf_elems;       // complex elements of each of the shared buffers
+    int prefetch;        // 1: a third buffer stages the next item's first tile (cp.async)
 };
 
 } // namespace fft3

@@ -38,6 +38,7 @@ struct BatchState {
     size_t counters_bytes = 0;
     int64_t tw_total = 0;
     int buf_elems = 0;
+    int prefetch = 0;
     int smem = 0;
     int threads = 256;
     dim3 grid;
@@ -140,7 +141,7 @@ int batch_describe(const BatchState *b, std::string *json)
     }
     o << "{\"batched\":true,\"problems\":" << b->cubes.size() << ",\"items\":" << b->items.size()
       << ",\"groups\":" << b->groups << ",\"line_plans\":" << b->lines.size() << ",\"grid\":" << b->grid.x
-      << ",\"block\":" << b->threads << ",\"smem\":" << b->smem << ",\"twiddle_entries\":" << b->tw_total
+      << ",\"block\":" << b->threads << ",\"smem\":" << b->smem << ",\"prefetch\":" << b->prefetch << ",\"twiddle_entries\":" << b->tw_total
       << ",\"extent\":" << b->extent << ",\"classes\":[";
     bool first = true;
     for (auto &kv : cls) {
@@ -177,6 +178,7 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
     a.wait_budget = 4000000000LL;
     a.conj = b->conj;
     a.buf_elems = b->buf_elems;
+    a.prefetch = b->prefetch;
     CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, b->counters_bytes, b->cap_stream);
     if (e == cudaSuccess) {
@@ -289,7 +291,9 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
     }
     b->extent = extent;
     b->buf_elems = (bufmax + 31) / 32 * 32;
-    b->smem = 2 * b->buf_elems * (int)sizeof(float2);
+    // a third buffer stages the next item's first tile when it still fits
+    b->prefetch = 3 * b->buf_elems * (int)sizeof(float2) <= 200 * 1024 ? 1 : 0;
+    b->smem = (2 + b->prefetch) * b->buf_elems * (int)sizeof(float2);
     if (b->smem > 227 * 1024) {
         batch_free(b);
         return fail(FFT3_ERR_UNSUPPORTED_SIZE, "a work item of this batch needs more shared memory than a block has");
