@@ -99,6 +99,13 @@ __device__ __forceinline__ void tile_sync()
         cg::this_cluster().sync();
 }
 
+// The two halves of a cluster barrier (P = 2): every thread of both blocks
+// arrives after its last read of the tile's slots, and waits before its first
+// write of the next tile's slots, so the barrier's latency overlaps the next
+// tile's first load.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 // Staging buffer as a tile accessor (line = column, position = row of the
 // sub-line), conjugating on load for the inverse transform.
 template <int LPT>
@@ -186,6 +193,7 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
     bool failed = false;
     int64_t k_fail = 0;
     int64_t k = 0;
+    bool armed = false; // P = 2: this thread arrived after the previous tile's final stage
     for (int64_t tile = cid; tile < a.ntiles; tile += ncl) {
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, LPT);
 #pragma unroll 1
@@ -220,6 +228,12 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
                 if (gtid == 0 && !failed)
                     issue(k + S); // the staging buffer is read out: refill it
                 Bfly<R1>::run(x);
+                if constexpr (P > 1) {
+                    if (armed) { // both blocks are done reading the previous tile's slots
+                        cluster_wait();
+                        armed = false;
+                    }
+                }
 #pragma unroll
                 for (int r = 0; r < R1; ++r)
                     slot[(t1 * R1 + r) * LPT + l] = x[r];
@@ -289,7 +303,16 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
                 }
             }
         }
-        tile_sync<P>(); // the next tile's first stages overwrite the slots
+        if constexpr (P > 1) {
+            cluster_arrive(); // waited for before this thread's next slot write
+            armed = true;
+        } else {
+            __syncthreads(); // the next tile's first stages overwrite the slots
+        }
+    }
+    if constexpr (P > 1) {
+        if (armed)
+            cluster_wait(); // the other block has finished reading this block's slots
     }
     if (failed && gtid == 0) {
         atomicOr(a.err, kErrWaitTimeout);
