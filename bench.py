@@ -174,6 +174,9 @@ def main():
     ap.add_argument("--slab-mode", type=int, default=0)
     ap.add_argument("--slab-chunk", type=int, default=0)
     ap.add_argument("--radix-order", type=int, default=0)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "splitbf16"],
+                    help="splitbf16: radix-16 stages on the tensor cores (hi+lo BF16, FP32 accumulation)")
+    ap.add_argument("--tc-stages", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true", help="skip the per-decomposition and batched tables")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU oracle baseline")
@@ -272,6 +275,9 @@ def main():
                  ("radix_order", args.radix_order)):
         if v:
             opts[k] = v
+    if args.dtype == "splitbf16":
+        opts["dtype"] = fft3.FFT3_C64_SPLITBF16_TC
+        opts["tc_stages"] = args.tc_stages
     sampler = ClockSampler(dev)
     sampler.start()
     t_wall0 = time.perf_counter()
@@ -309,7 +315,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         h_out = torch.empty_like(h_in).pin_memory()
-        eplan = fft3.fft3_plan_create_ex(n0, n1, n2, 1, 0, decomp, -1, fft3.make_options(**opts))
+        eplan = fft3.fft3_plan_create_ex(n0, n1, n2, 1, opts.get("dtype", 0), decomp, -1,
+                                         fft3.make_options(**{k: v for k, v in opts.items() if k != "dtype"}))
         # every step copies its input from pinned host memory, transforms, and copies
         # the result back (fft3_plan_execute_host, synchronous per call)
         fft3.fft3_plan_execute_host(eplan, h_in.data_ptr(), h_out.data_ptr(), sp)
@@ -399,7 +406,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.dtype == "f32" else "bf16x3_f32acc", "data": "synthetic",
             "config": {"workload": workload, "dims": [n0, n1, n2], "batch": 1,
                        "decomposition": desc["decomposition"], "passes": [p["kind"] for p in desc["passes"]],
                        "options": opts, "parallelism": f"replicas{world}" if world > 1 else "single",
