@@ -39,7 +39,7 @@ def test_256cubed_elementwise(name, decomp, opts):
         assert oracle.rel_l2(got, ref) <= REL_L2_TOL and oracle.max_abs_ratio(got, ref) <= MAXABS_TOL
 
 
-def _sampled_check(x, got, n, direction, seed):
+def _sampled_check(x, got, n, direction, seed, parseval_tol=1e-5):
     rng = np.random.default_rng(seed)
     ks = [np.unique(np.concatenate([[0, n - 1, n // 2], rng.integers(0, n, 5)])) for _ in range(3)]
     ref = oracle.dft3_sampled(x.reshape(n, n, n), n, n, n, ks[0], ks[1], ks[2], sign=direction)
@@ -51,7 +51,8 @@ def _sampled_check(x, got, n, direction, seed):
     N = float(n) ** 3
     sx = float(np.sum(np.abs(x.astype(np.complex128)) ** 2))
     sX = float(np.sum(np.abs(got.astype(np.complex128)) ** 2))
-    assert abs(sX - N * sx) <= 1e-5 * N * sx
+    assert abs(sX - N * sx) <= parseval_tol * N * sx
+    return rel, mx
 
 
 @pytest.mark.parametrize("n", [512, 1024])
@@ -62,11 +63,34 @@ def test_fullsize_sampled(n):
     host = torch.empty(out.shape, dtype=torch.complex64).pin_memory()
     for name, decomp, opts in DECOMPS + [("auto", fft3.FFT3_AUTO, {})]:
         for direction in (fft3.FFT3_FORWARD, fft3.FFT3_INVERSE):
-            if direction == fft3.FFT3_INVERSE and name not in ("auto", "ppp"):
+            if direction == fft3.FFT3_INVERSE and name == "auto":
                 continue
             out.fill_(float("nan"))
             _run(n, xd, out, decomp, direction, opts)
             host.copy_(out)
             _sampled_check(x, host.numpy(), n, direction, 17 * len(name) + n)
+    del xd, out
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+@pytest.mark.parametrize("inputs", ["uniform", "hdr"])
+def test_fullsize_tensor_cores_sampled(n, inputs):
+    """The split-BF16 tensor-core path at the bench's full sizes, uniform and
+    high-dynamic-range inputs: sampled outputs within the FP32 bound (rel-L2
+    1e-5) and Parseval over the whole array."""
+    shape = (1, n, n, n)
+    x = synth.uniform_c64(shape, 5) if inputs == "uniform" else synth.hdr_c64(shape, 6)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.full_like(xd, complex(float("nan"), float("nan")))
+    plan = fft3.Plan(n, n, n, 1, decomposition=fft3.FFT3_PENCIL3, dtype=fft3.FFT3_C64_SPLITBF16_TC)
+    assert any(p["kind"].endswith("_tc") for p in plan.describe()["passes"])
+    plan.execute(xd, out)
+    torch.cuda.synchronize()
+    assert plan.check() == 0
+    plan.close()
+    host = out.cpu().numpy()
+    rel, mx = _sampled_check(x, host, n, fft3.FFT3_FORWARD, 31 + n, parseval_tol=5e-5)
+    print(f"TC {n}^3 {inputs}: sampled rel-L2 {rel:.3e} max-abs {mx:.3e}")
     del xd, out
     torch.cuda.empty_cache()
