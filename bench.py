@@ -169,7 +169,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024, help="cube edge (ignored with --shape)")
     ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("N0", "N1", "N2"))
-    ap.add_argument("--decomp", default="auto", choices=["auto", "slab_pencil", "ppp", "ppp_rotate", "volumetric"])
+    ap.add_argument("--decomp", default="auto",
+                    choices=["auto", "slab_pencil", "slab_pencil_pipelined", "ppp", "ppp_rotate", "ppp_blocked",
+                             "volumetric"])
     ap.add_argument("--tile-lines", type=int, default=0)
     ap.add_argument("--slab-mode", type=int, default=0)
     ap.add_argument("--slab-chunk", type=int, default=0)
@@ -240,6 +242,7 @@ def main():
     decomp_map = {"auto": (fft3.FFT3_AUTO, {}), "slab_pencil": (fft3.FFT3_SLAB_PENCIL, {}),
                   "slab_pencil_pipelined": (fft3.FFT3_SLAB_PENCIL, {"slab_mode": 4}),
                   "ppp": (fft3.FFT3_PENCIL3, {}), "ppp_rotate": (fft3.FFT3_PENCIL3, {"variant": 1}),
+                  "ppp_blocked": (fft3.FFT3_PENCIL3, {"variant": 2}),
                   "volumetric": (fft3.FFT3_VOLUMETRIC, {})}
 
     # inputs: seeded uniform[-1,1) complex64, generated on the host into pinned memory

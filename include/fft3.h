@@ -71,7 +71,12 @@ enum fft3_status {
 /* Pencil-pencil-pencil variants (options.variant). */
 enum fft3_ppp_variant {
     FFT3_PPP_NATURAL = 0, /* x pass out-of-place, y and z passes in place on strided lines */
-    FFT3_PPP_ROTATE = 1   /* each pass stores its result rotated xyz -> yzx -> zxy -> xyz (Section 2.4) */
+    FFT3_PPP_ROTATE = 1,  /* each pass stores its result rotated xyz -> yzx -> zxy -> xyz (Section 2.4) */
+    FFT3_PPP_BLOCKED = 2  /* the y pass stores into a workspace blocked as [x/16][z][y][x%16], so each
+                             16-column tile of the y pass is one contiguous block and the z pass reads
+                             rows 16*n1 values apart instead of n0*n1; the z pass restores natural order.
+                             Needs n0 % 16 == 0, batch 1 and streamed kernels for n1 and n2; otherwise the
+                             natural variant is used */
 };
 
 /* Optional planner controls.  Zero-initialise and set what you need. */

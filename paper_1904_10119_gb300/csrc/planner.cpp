@@ -1,12 +1,17 @@
 // planner.cpp -- lowers a decomposition of the 3D DFT to a schedule of passes.
 //
 // Decompositions (paper Sections 2.3, 2.4 and 3.2):
-//   pencil-pencil-pencil  DFT_{n0}, then DFT_{n1}, then DFT_{n2}.  Two variants:
+//   pencil-pencil-pencil  DFT_{n0}, then DFT_{n1}, then DFT_{n2}.  Three variants:
 //     natural: the x pass writes `out`, the y and z passes run in place on
 //              strided lines of `out` (tiles of adjacent columns);
 //     rotate:  each pass reads contiguous lines and stores its result rotated,
 //              xyz -> yzx -> zxy -> xyz (Section 2.4), so the next pass's lines
-//              are contiguous again; the rotation is the store epilogue.
+//              are contiguous again; the rotation is the store epilogue;
+//     blocked: the y pass stores into a workspace laid out [x/16][z][y][x%16]
+//              (a redistribution fused into its store, Section 3.1), so each of
+//              its 16-column tiles is one contiguous block and the z pass reads
+//              rows 16*n1 values apart instead of n0*n1; the z pass stores the
+//              natural layout.  The default of FFT3_AUTO where it applies.
 //   slab-pencil           2D DFT of every n0 x n1 slab (x lines then y lines
 //                         on data kept on chip or in L2), then DFT_{n2}.
 //   volumetric            every dimension's 1D DFT split n = a*b (Eq. ct) over
@@ -719,6 +724,9 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         // (measured faster than the L2-resident slab kernel at 1024 x 1024).
         int twl = 2 * tw_slots_h(n0) + 2 * tw_slots_h(n1);
         decomp = slab_smem(n0, n1, twl) <= kSmemLimit ? FFT3_SLAB_PENCIL : FFT3_PENCIL3;
+        // and with the blocked intermediate when it applies (measured 8.76 against 9.49 ms at 1024^3)
+        if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_NATURAL)
+            s.opts.variant = FFT3_PPP_BLOCKED;
     }
     if (dtype == FFT3_C64_SPLITBF16_TC) {
         if (decomp != FFT3_PENCIL3 || s.opts.variant != FFT3_PPP_NATURAL) {
@@ -742,7 +750,47 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         cur = BUF_OUT;
         return FFT3_OK;
     };
-    if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_ROTATE) {
+    // Blocked intermediate (FFT3_PPP_BLOCKED): x pass natural, y pass from `out`
+    // into the workspace laid out as [x/16][z][y][x%16] (a 16-column tile of y
+    // lines is one contiguous block), z pass from the workspace back to `out`.
+    auto blocked_ok = [&]() {
+        if (!(decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED && batch == 1 && n0 % 16 == 0 &&
+              n1 > 1 && n2 > 1 && dtype == FFT3_C64_FP32 && (s.opts.tile_lines == 0 || s.opts.tile_lines == kTileStream)))
+            return false;
+        int cnt = 0;
+        const CStreamKernel *cm = cstream_meta(&cnt);
+        bool y = false, z = false;
+        for (int i = 0; i < cnt; ++i) {
+            y = y || (cm[i].n == n1 && cm[i].pair == 1 && cm[i].lpt == 16);
+            z = z || (cm[i].n == n2 && cm[i].pair == 1 && cm[i].lpt == 16);
+        }
+        return y && z;
+    };
+    if (blocked_ok()) {
+        const int64_t X = n0, Y = n1, Z = n2;
+        PassPlan p;
+        rc = make_line_pass(&s, 0, n0, geom_natural(0, n0, n1, n2, batch), false, BUF_IN, BUF_OUT, &p, err);
+        if (rc)
+            return rc;
+        s.passes.push_back(p);
+        PassGeom gy{}; // columns x%16, lines y, a = x/16, b = z
+        gy.C = 16; gy.A = X / 16; gy.B = Z;
+        gy.ij = X; gy.ic = 1; gy.ia = 16; gy.ib = X * Y;
+        gy.ok = 16; gy.oc = 1; gy.oa = Z * Y * 16; gy.ob = Y * 16;
+        rc = make_line_pass(&s, 1, n1, gy, false, BUF_OUT, BUF_WS, &p, err);
+        if (rc)
+            return rc;
+        s.passes.push_back(p);
+        PassGeom gz{}; // columns x%16, lines z, a = y, b = x/16
+        gz.C = 16; gz.A = Y; gz.B = X / 16;
+        gz.ij = Y * 16; gz.ic = 1; gz.ia = 16; gz.ib = Z * Y * 16;
+        gz.ok = X * Y; gz.oc = 1; gz.oa = X; gz.ob = 16;
+        rc = make_line_pass(&s, 2, n2, gz, false, BUF_WS, BUF_OUT, &p, err);
+        if (rc)
+            return rc;
+        s.passes.push_back(p);
+        s.need_ws = true;
+    } else if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_ROTATE) {
         int bufs[3][2] = {{BUF_IN, BUF_OUT}, {BUF_OUT, BUF_WS}, {BUF_WS, BUF_OUT}};
         for (int d = 0; d < 3; ++d) {
             PassPlan p;

@@ -20,7 +20,7 @@ FFT3_C64_FP32 = 0
 FFT3_C64_SPLITBF16_TC = 1
 FFT3_SLAB_PENCIL, FFT3_PENCIL3, FFT3_VOLUMETRIC, FFT3_AUTO = 0, 1, 2, 3
 FFT3_FORWARD, FFT3_INVERSE = -1, 1
-FFT3_PPP_NATURAL, FFT3_PPP_ROTATE = 0, 1
+FFT3_PPP_NATURAL, FFT3_PPP_ROTATE, FFT3_PPP_BLOCKED = 0, 1, 2
 
 STATUS = {
     0: "FFT3_OK", -1: "FFT3_ERR_INVALID_ARG", -2: "FFT3_ERR_UNSUPPORTED_SIZE", -3: "FFT3_ERR_OOM",

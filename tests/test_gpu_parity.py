@@ -112,6 +112,17 @@ def test_streamed_strided_pass(shape, batch, order, direction):
     assert ("line_strided_stream" in kinds) == (shape[0] % 2 == 0)
 
 
+@pytest.mark.parametrize("shape,direction", [((16, 512, 512), FWD), ((48, 1024, 512), INV), ((32, 512, 1024), FWD)])
+def test_pencil3_blocked_intermediate(shape, direction):
+    """FFT3_PPP_BLOCKED: the y pass stores [x/16][z][y][x%16] into the workspace
+    and the z pass reads it back to natural order."""
+    x, got, plan = run_plan(shape, 1, P, direction, seed=41, variant=fft3.FFT3_PPP_BLOCKED)
+    assert_parity(x, got, shape, 1, direction)
+    d = plan.describe()
+    assert [(p["src"], p["dst"]) for p in d["passes"]] == [("in", "out"), ("out", "workspace"), ("workspace", "out")]
+    assert fft3.fft3_plan_workspace_bytes(plan.handle) == np.prod(shape) * 8
+
+
 @pytest.mark.parametrize("mesh,shape", [((2, 2, 2), (64, 64, 64)), ((4, 4, 4), (64, 64, 64)),
                                         ((8, 2, 4), (256, 32, 64)), ((2, 8, 4), (36, 256, 16)),
                                         ((4, 2, 8), (1024, 16, 64)), ((1, 4, 2), (30, 64, 36))])
