@@ -753,9 +753,9 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
     // Blocked intermediate (FFT3_PPP_BLOCKED): x pass natural, y pass from `out`
     // into the workspace laid out as [x/16][z][y][x%16] (a 16-column tile of y
     // lines is one contiguous block), z pass from the workspace back to `out`.
-    auto blocked_ok = [&]() {
-        if (!(decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED && batch == 1 && n0 % 16 == 0 &&
-              n1 > 1 && n2 > 1 && dtype == FFT3_C64_FP32 && (s.opts.tile_lines == 0 || s.opts.tile_lines == kTileStream)))
+    auto blocked_fits = [&]() {
+        if (!(batch == 1 && n0 % 16 == 0 && n1 > 1 && n2 > 1 && dtype == FFT3_C64_FP32 &&
+              (s.opts.tile_lines == 0 || s.opts.tile_lines == kTileStream)))
             return false;
         int cnt = 0;
         const CStreamKernel *cm = cstream_meta(&cnt);
@@ -766,7 +766,7 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         }
         return y && z;
     };
-    if (blocked_ok()) {
+    auto emit_blocked = [&]() -> int {
         const int64_t X = n0, Y = n1, Z = n2;
         PassPlan p;
         rc = make_line_pass(&s, 0, n0, geom_natural(0, n0, n1, n2, batch), false, BUF_IN, BUF_OUT, &p, err);
@@ -790,6 +790,12 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
             return rc;
         s.passes.push_back(p);
         s.need_ws = true;
+        return FFT3_OK;
+    };
+    if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED && blocked_fits()) {
+        rc = emit_blocked();
+        if (rc)
+            return rc;
     } else if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_ROTATE) {
         int bufs[3][2] = {{BUF_IN, BUF_OUT}, {BUF_OUT, BUF_WS}, {BUF_WS, BUF_OUT}};
         for (int d = 0; d < 3; ++d) {
@@ -805,6 +811,7 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         for (int d = 0; d < 3 && !rc; ++d)
             rc = add_nat(d);
     } else if (decomp == FFT3_SLAB_PENCIL) {
+        bool z_done = false;
         int mode = s.opts.slab_mode;
         int twl = 2 * tw_slots_h(n0) + 2 * tw_slots_h(n1);
         bool fits_smem = slab_smem(n0, n1, twl) <= kSmemLimit;
@@ -842,13 +849,20 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
                 py.chunk = chunk;
                 px.pair_next = true;
             }
+        } else if (blocked_fits()) {
+            // slab stage as x and y passes; the y pass stores the slabs redistributed
+            // into z pencils ([x/16][z][y][x%16]), the z pass reads them back
+            rc = emit_blocked();
+            if (rc)
+                return rc;
+            z_done = true;
         } else {
             // unfused slab stage: x lines then y lines as two passes
             rc = add_nat(0);
             if (!rc)
                 rc = add_nat(1);
         }
-        if (!rc)
+        if (!rc && !z_done)
             rc = add_nat(2);
     } else { // volumetric
         for (int d = 0; d < 3 && !rc; ++d) {
