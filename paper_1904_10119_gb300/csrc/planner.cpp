@@ -929,7 +929,7 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
 static const char *kind_name(int k)
 {
     static const char *names[] = {"line_contig", "line_contig_rotate", "line_strided", "line_runtime",
-                                  "slab_smem", "slab_l2", "volumetric_split", "copy", "line_tc",
+                                  "slab_smem", "slab_l2", "volumetric_split", "copy", "unused",
                                   "line_strided_tma", "line_contig_tc", "line_strided_tc",
                                   "volumetric_split_fixed", "line_strided_stream"};
     return (k >= 0 && k <= 13) ? names[k] : "?";

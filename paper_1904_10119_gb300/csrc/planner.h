@@ -21,7 +21,6 @@ enum PassKind {
     PK_SLABL2 = 5, // 2D slab DFT: x and y tiles in one persistent launch, slab kept in L2
     PK_VOL = 6,    // 1D DFT split n = a*b over a cluster of p blocks (DSMEM exchange)
     PK_COPY = 7,   // all dimensions of length 1: plain copy
-    PK_TC = 8,     // split-BF16 tensor-core line pass
     PK_CTMA = 9,   // fixed plan, strided columns, TMA double-buffered tiles
     PK_JTC = 10,   // split-BF16 tensor-core radix-16 stages, contiguous lines
     PK_CTC = 11,   // split-BF16 tensor-core radix-16 stages, strided columns
@@ -60,7 +59,6 @@ struct PassPlan {
     int threads = 0;     // block size
     int smem_bytes = 0;  // dynamic shared memory per block
     int64_t ntiles = 0, tiles_c = 0;
-    int slabs_per_chunk = 0;
     int tc_mode = -1;           // split-BF16 tensor-core stages (tc_stages option); -1 = FP32 pass
     int volc = -1;              // PK_VOLC: index into the compiled volumetric list
     int cstream = -1;           // PK_CSTREAM: index into the compiled streamed-pass list
