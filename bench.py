@@ -41,11 +41,16 @@ def _peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+# Host-only sources (planning, launching, the C ABI): they do not change what a kernel reads or writes.
+_HOST_SOURCES = ("planner.cpp", "planner.h", "capi.cu", "capi_internal.h", "autotune.cu", "batched_host.cu")
+
+
 def _csrc_sha() -> str:
+    """Hash of the device-code sources (kernels, their headers and argument structs)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1904_10119_gb300", "csrc")
     for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")) and name not in _HOST_SOURCES:
             with open(os.path.join(d, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
