@@ -100,8 +100,9 @@ typedef struct fft3_options {
                              has just left in L2; the side stream joins the caller's
                              stream before the z pass */
     int tc_stages;    /* FFT3_C64_SPLITBF16_TC: which radix-16 stages run on the tensor cores:
-                         0 = the first radix-16 stage of each line (the fastest; default),
-                         1 = the radix-16 stages whose operands are both in shared memory,
+                         0 = per line, the first radix-16 stage whose operands are both in
+                             shared memory (the fastest; default; lines without one stay FP32),
+                         1 = every radix-16 stage whose operands are both in shared memory,
                          2 = every radix-16 stage */
     int slab_chunk;   /* slab_mode 4: slabs per chunk (0 = about 32 MiB of slabs) */
     int reserved[8];  /* test hooks of the failure-detection tests, 0 in normal use:

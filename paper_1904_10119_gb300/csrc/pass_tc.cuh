@@ -163,12 +163,14 @@ __host__ __device__ constexpr int tc_mask_inner(Radices<Rs...> r)
 {
     return tc_mask_all(r) & ~1 & ~(1 << ((int)sizeof...(Rs) - 1));
 }
-// tc_stages option: 0 = the first radix-16 stage, 1 = the radix-16 stages
-// with both operands in shared memory, 2 = every radix-16 stage.
+// tc_stages option: 0 = the first radix-16 stage with both operands in shared
+// memory, 1 = every radix-16 stage with both operands in shared memory, 2 =
+// every radix-16 stage.
 template <class Rad>
 __host__ __device__ constexpr int tc_mask_mode(int mode)
 {
-    return mode == 0 ? tc_mask_first(Rad{}) : mode == 1 ? tc_mask_inner(Rad{}) : tc_mask_all(Rad{});
+    return mode == 0 ? (tc_mask_inner(Rad{}) & -tc_mask_inner(Rad{})) : mode == 1 ? tc_mask_inner(Rad{})
+                                                                                  : tc_mask_all(Rad{});
 }
 
 } // namespace fft3

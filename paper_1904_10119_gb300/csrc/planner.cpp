@@ -715,8 +715,11 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
     s.dtype = dtype; s.direction = direction;
     if (opts)
         s.opts = *opts;
-    if (decomp == FFT3_AUTO && dtype == FFT3_C64_SPLITBF16_TC)
+    if (decomp == FFT3_AUTO && dtype == FFT3_C64_SPLITBF16_TC) {
         decomp = FFT3_PENCIL3;
+        if (s.opts.variant == FFT3_PPP_NATURAL)
+            s.opts.variant = FFT3_PPP_BLOCKED;
+    }
     if (decomp == FFT3_AUTO) {
         // Fixed default when no cost model is loaded: slab-pencil when a whole
         // slab fits one block's shared memory (one HBM sweep fewer), else
@@ -729,8 +732,8 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
             s.opts.variant = FFT3_PPP_BLOCKED;
     }
     if (dtype == FFT3_C64_SPLITBF16_TC) {
-        if (decomp != FFT3_PENCIL3 || s.opts.variant != FFT3_PPP_NATURAL) {
-            *err = "the split-BF16 tensor-core path runs the pencil-pencil-pencil decomposition (natural layout)";
+        if (decomp != FFT3_PENCIL3 || s.opts.variant == FFT3_PPP_ROTATE) {
+            *err = "the split-BF16 tensor-core path runs the pencil-pencil-pencil decomposition (natural or blocked)";
             return FFT3_ERR_UNSUPPORTED_SIZE;
         }
     }
@@ -754,7 +757,7 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
     // into the workspace laid out as [x/16][z][y][x%16] (a 16-column tile of y
     // lines is one contiguous block), z pass from the workspace back to `out`.
     auto blocked_fits = [&]() {
-        if (!(batch == 1 && n0 % 16 == 0 && n1 > 1 && n2 > 1 && dtype == FFT3_C64_FP32 &&
+        if (!(batch == 1 && n0 % 16 == 0 && n1 > 1 && n2 > 1 &&
               (s.opts.tile_lines == 0 || s.opts.tile_lines == kTileStream)))
             return false;
         int cnt = 0;

@@ -81,7 +81,8 @@ struct CStreamKernel {
     int n, q, r1, r2, groups, stages, lpt, pair, threads;
     const void *func;      // nullptr in the host-only metadata
     const void *func_tc[2]; // split-BF16 tensor-core sub-line stages: [0] the first, [1] both (R1 = R2 = 16)
-                            // (tc_stages 0 takes [0]; 1 and 2 take [1]: both stages work in shared memory)
+                            // (tc_stages 0 takes [0]; 1 and 2 take [1]: both stages work in shared memory,
+                            // the staging buffer and the result slot)
 };
 // Compiled list (device translation unit) and the host-only metadata.
 const CStreamKernel *cstream_kernels(int *count);
@@ -129,8 +130,8 @@ struct FixedKernels {
     const void *c8;   // k_pass_c, 8 lines per tile
     const void *l2;   // k_slab_l2 (square slabs), 0 if not compiled
     const void *ctma; // k_pass_c_tma (TMA-pipelined strided lines), 0 if not compiled
-    // split-BF16 tensor-core variants by tc_stages mode: [0] the first radix-16
-    // stage, [1] the radix-16 stages with both operands in shared memory, [2] every one
+    // split-BF16 tensor-core variants by tc_stages mode: [0] the first radix-16 stage
+    // with both operands in shared memory, [1] every such stage, [2] every radix-16 stage
     const void *j_tc[3]; // contiguous lines, lpt_j(T) lines per tile
     const void *c_tc[3]; // strided lines, 8 lines per tile
 };
@@ -150,17 +151,18 @@ constexpr int lpt_c_tc() { return 8; }
 constexpr bool tc_j_ok(int N, int T, bool has16) { return has16 && N >= 128 && T * lpt_j(T) <= 512 && (T * lpt_j(T)) % 32 == 0; }
 constexpr bool tc_c_ok(int N, int T, bool has16) { return has16 && N >= 128 && T * lpt_c_tc() <= 512; }
 // Host copy of the stage mask of a radix list for a tc_stages mode (0: the
-// first radix-16 stage, 1: radix-16 stages that are neither first nor last,
-// 2: all).
+// first radix-16 stage that is neither the first nor the last stage, 1: every
+// such stage, 2: all radix-16 stages).
 inline int tc_mask_host(const int *rad, int nrad, int mode)
 {
     int all = 0;
     for (int s = 0; s < nrad; ++s)
         all |= (rad[s] == 16 ? 1 : 0) << s;
+    const int inner = all & ~1 & ~(1 << (nrad - 1));
     if (mode == 0)
-        return all & (-all);
+        return inner & (-inner);
     if (mode == 1)
-        return all & ~1 & ~(1 << (nrad - 1));
+        return inner;
     return all;
 }
 

@@ -7,14 +7,14 @@ same for the DFT_16 matrix, and the dropped lo x lo product is of the same
 order, so one tensor-core stage adds an RMS relative error of about 5e-6.
 The errors of successive stages add in quadrature: with every radix-16 stage
 on the tensor cores (two per 1024-point line, six per 3D transform) the
-expected rel-L2 is about 1.3e-5; with the first radix-16 stage of each line
-only (three per transform, tc_stages 0, the default) about 9e-6.  Mode 1
-puts the radix-16 stages whose operands are both in shared memory on the
-tensor cores: one per contiguous 1024-point line, both 16-point stages of
-each decimated sub-line of a streamed strided line.  The bounds below follow
-from that (2.5e-5 for modes 1 and 2, the task's 1e-5 for mode 0); measured
-errors are 3-6e-6 in every mode.  The FP32 path is held to 1e-5 as
-elsewhere.
+expected rel-L2 is about 1.3e-5; with one radix-16 stage per line (three
+per transform) about 9e-6.  The default mode (tc_stages 0) puts, per line,
+the first radix-16 stage whose operands are both in shared memory on the
+tensor cores (the middle stage of a contiguous 16 x 16 x 4 line, the first
+16-point stage of each decimated sub-line of a streamed strided line); mode 1
+every such stage, mode 2 every radix-16 stage.  The bounds below follow from
+that (2.5e-5 for modes 1 and 2, the task's 1e-5 for mode 0); measured errors
+are 3-6e-6 in every mode.  The FP32 path is held to 1e-5 as elsewhere.
 """
 import numpy as np
 import pytest
@@ -54,7 +54,7 @@ def test_tc_radix16_stages(shape, batch, direction, mode):
 
 
 @pytest.mark.parametrize("shape", [(1024, 16, 8), (8, 16, 1024), (256, 256, 16), (128, 128, 128)])
-def test_tc_first_stage_only_meets_fp32_bar(shape):
+def test_tc_default_mode_meets_fp32_bar(shape):
     n0, n1, n2 = shape
     x = synth.uniform_c64((1, n2, n1, n0), 5)
     h = fft3.fft3_plan_create_ex(n0, n1, n2, 1, TC, P, -1, _opts_first())
@@ -68,7 +68,7 @@ def test_tc_first_stage_only_meets_fp32_bar(shape):
     finally:
         fft3.fft3_plan_destroy(h)
     rel, mx = _err(x, got, shape, 1, -1)
-    print(f"TC first stage {shape}: rel-L2 {rel:.3e} max-abs {mx:.3e}")
+    print(f"TC default mode {shape}: rel-L2 {rel:.3e} max-abs {mx:.3e}")
     assert rel <= 1e-5 and mx <= 1e-4
 
 
