@@ -186,6 +186,15 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
         for (int k = 0; k < S; ++k)
             issue(k);
     }
+    // With one second-stage butterfly per thread (q2 = t1) its twiddles
+    // w^{r (q2 mod R1)} are the same for every sub-line and tile: kept in registers.
+    float2 w2[R2];
+    if constexpr (BPT2 == 1) {
+        __syncthreads(); // twiddles in shared memory
+#pragma unroll
+        for (int r = 1; r < R2; ++r)
+            w2[r] = t1 < NB2 ? tw[(R1 - 1) + (r - 1) * R1 + t1 % R1] : make_float2(1.f, 0.f);
+    }
     // A wait that runs out of budget marks the group failed: it stops waiting
     // and loading but keeps every barrier (the other groups and the block
     // barriers stay matched), and at the end waits, bounded, for the copies it
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
                     const int kk = q2 % R1;
 #pragma unroll
                     for (int r = 1; r < R2; ++r)
-                        y[bb][r] = cmul(y[bb][r], tw2[(r - 1) * R1 + kk]);
+                        y[bb][r] = cmul(y[bb][r], BPT2 == 1 ? w2[r] : tw2[(r - 1) * R1 + kk]);
                     Bfly<R2>::run(y[bb]);
                     const int base = (q2 / R1) * M + kk;
 #pragma unroll
