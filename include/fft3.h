@@ -52,7 +52,9 @@ enum fft3_decomp {
     FFT3_SLAB_PENCIL = 0, /* 2D DFT on n0 x n1 slabs, then DFT_{n2} (Section 2.3, Fig. 3ddftopt a) */
     FFT3_PENCIL3 = 1,     /* DFT_{n0}, DFT_{n1}, DFT_{n2} (Section 2.3, Fig. 3ddftopt b) */
     FFT3_VOLUMETRIC = 2,  /* every 1D DFT split over p cooperating blocks (Section 3.2) */
-    FFT3_AUTO = 3         /* the planner's choice (cost model, else a fixed default) */
+    FFT3_AUTO = 3         /* the planner's fixed rule: slab-pencil when a slab fits one block's shared
+                             memory, else pencil-pencil-pencil with the blocked intermediate where it
+                             applies; fft3_autotune and the learned chooser pick by measurement */
 };
 
 enum fft3_direction { FFT3_FORWARD = -1, FFT3_INVERSE = +1 }; /* sign of the exponent */
