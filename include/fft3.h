@@ -281,12 +281,17 @@ int fft3_time_candidates(int n0, int n1, int n2, int batch, int dtype, int direc
 int fft3_autotune(int n0, int n1, int n2, int batch, int dtype, int direction, int reps,
                   fft3_options *best, int *best_decomposition, float *best_ms);
 
-/* Autotuning of a batched plan: for every distinct (n0, n1, n2) among the
- * `count` problems, times batched plans of up to `max_per_class` copies of
- * that shape under each candidate FFT3_TUNE code (both decompositions, radix
- * orders 0..3, tiles of 8/16/32 columns) and writes the fastest code to
- * tuning_out[i] of every problem i of that shape.  `offsets` is unused (the
- * timing runs on packed scratch arrays) and may be NULL. */
+/* Autotuning of a batched plan: times the whole batch (packed into scratch
+ * arrays) under the default codes and under each candidate FFT3_TUNE code
+ * (both decompositions, radix orders 0..3, tiles of 8/16/32 columns) applied
+ * to every problem whose shared-buffer need stays within the default
+ * buffers; then, for three size classes (thirds of the batch by problem
+ * volume) in turn, the code that makes the whole batch fastest (kept when it
+ * gains at least 1%).  Writes the assignment to tuning_out.  The batch is
+ * timed as a whole because the executor's buffers, blocks per SM and item
+ * order depend on all its problems (per-shape timings in isolation chose
+ * codes that made the mixed batch slower).  `offsets` and `max_per_class`
+ * are unused and may be NULL / 0. */
 int fft3_autotune_many(int count, const int *dims, const int64_t *offsets, int direction, int reps,
                        int max_per_class, int *tuning_out);
 

@@ -186,53 +186,90 @@ int fft3_autotune_many(int count, const int *dims, const int64_t *offsets, int d
                        int max_per_class, int *tuning_out)
 {
     (void)offsets;
+    (void)max_per_class;
     if (count < 1 || !dims || !tuning_out || reps < 1)
         return fail(FFT3_ERR_INVALID_ARG, "bad argument to fft3_autotune_many");
-    std::map<std::vector<int>, std::vector<int>> cls;
-    for (int i = 0; i < count; ++i)
-        cls[{dims[3 * i], dims[3 * i + 1], dims[3 * i + 2]}].push_back(i);
+    // The executor's shared buffers, blocks per SM, item order and L2 reuse are
+    // properties of the whole batch, so candidates are timed on the whole
+    // batch (packed into scratch arrays): the default codes, and each code
+    // applied to every problem whose buffer need stays within the default
+    // buffers (the others keep the default).
     std::vector<int> codes;
     for (int d = 1; d <= 2; ++d)
         for (int order = 0; order < 4; ++order)
             for (int tile = 2; tile <= 4; ++tile)
                 codes.push_back(FFT3_TUNE(d, order, tile, 0));
+    int budget = 1;
+    for (int i = 0; i < count; ++i)
+        budget = std::max(budget, batch_buffer_need(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], 0));
+    std::vector<int64_t> off(count);
+    int64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        off[i] = total;
+        total += (int64_t)dims[3 * i] * dims[3 * i + 1] * dims[3 * i + 2];
+    }
     Scratch s;
-    for (auto &kv : cls) {
-        const int n0 = kv.first[0], n1 = kv.first[1], n2 = kv.first[2];
-        const int m = std::max(1, std::min((int)kv.second.size(), max_per_class > 0 ? max_per_class : 32));
-        const int64_t vol = (int64_t)n0 * n1 * n2;
-        std::vector<int> d(3 * m);
-        std::vector<int64_t> off(m);
-        for (int i = 0; i < m; ++i) {
-            d[3 * i] = n0;
-            d[3 * i + 1] = n1;
-            d[3 * i + 2] = n2;
-            off[i] = i * vol;
+    int rc = s.ensure((size_t)total * 8);
+    if (rc)
+        return rc;
+    auto fits = [&](int i, int code) {
+        return code == 0 || batch_buffer_need(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], code) <= budget;
+    };
+    auto time_assignment = [&](const std::vector<int> &tune, float *t) -> int {
+        fft3_plan p = nullptr;
+        if (fft3_plan_create_many(&p, count, dims, off.data(), FFT3_C64_FP32, FFT3_AUTO, direction, tune.data())) {
+            *t = 3.4e38f; // infeasible assignment
+            return FFT3_OK;
         }
-        int rc = s.ensure((size_t)(m * vol) * 8);
-        if (rc)
+        int r = time_plan(p, s.in, s.out, reps, t);
+        fft3_plan_destroy(p);
+        return r;
+    };
+    std::vector<int> tune(count), best(count, 0);
+    std::vector<int> order_codes(1, 0);
+    order_codes.insert(order_codes.end(), codes.begin(), codes.end());
+    // 1) one code for every problem it fits
+    float bt = 3.4e38f;
+    for (int code : order_codes) {
+        for (int i = 0; i < count; ++i)
+            tune[i] = fits(i, code) ? code : 0;
+        float t = 0.f;
+        if ((rc = time_assignment(tune, &t)))
             return rc;
-        float bt = 3.4e38f;
-        int best = 0;
-        for (int code : codes) {
-            std::vector<int> tune(m, code);
-            fft3_plan p = nullptr;
-            if (fft3_plan_create_many(&p, m, d.data(), off.data(), FFT3_C64_FP32, FFT3_AUTO, direction,
-                                      tune.data()))
+        if (t < bt) {
+            bt = t;
+            best = tune;
+        }
+    }
+    // 2) size classes (problem volume in thirds of the batch, smallest first):
+    // each class in turn takes the code that makes the whole batch fastest,
+    // kept when it gains at least 1%
+    std::vector<int> idx(count);
+    for (int i = 0; i < count; ++i)
+        idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        return (int64_t)dims[3 * x] * dims[3 * x + 1] * dims[3 * x + 2] <
+               (int64_t)dims[3 * y] * dims[3 * y + 1] * dims[3 * y + 2];
+    });
+    for (int c = 0; c < 3; ++c) {
+        const int lo = count * c / 3, hi = count * (c + 1) / 3;
+        for (int code : order_codes) {
+            tune = best;
+            for (int k = lo; k < hi; ++k)
+                tune[idx[k]] = fits(idx[k], code) ? code : 0;
+            if (tune == best)
                 continue;
             float t = 0.f;
-            int r = time_plan(p, s.in, s.out, reps, &t);
-            fft3_plan_destroy(p);
-            if (r)
-                return r;
-            if (t < bt) {
+            if ((rc = time_assignment(tune, &t)))
+                return rc;
+            if (t < 0.99f * bt) {
                 bt = t;
-                best = code;
+                best = tune;
             }
         }
-        for (int i : kv.second)
-            tuning_out[i] = best;
     }
+    for (int i = 0; i < count; ++i)
+        tuning_out[i] = best[i];
     return FFT3_OK;
 }
 

@@ -129,6 +129,18 @@ static void decode_tuning(int code, int n0, int n1, int n2, int *decomp, int *or
     }
 }
 
+// Shared-buffer elements one problem needs under a tuning code (the batch's
+// buffers are sized by the largest need over its problems).
+int batch_buffer_need(int n0, int n1, int n2, int code)
+{
+    int decomp, order, lpt, lpty, spi;
+    decode_tuning(code, n0, n1, n2, &decomp, &order, &lpt, &lpty, &spi);
+    if (decomp == BD_SLAB)
+        return std::max(n1 * pitch_b(n0), lpt * pitch_b(n2));
+    spi = std::max(1, std::min(spi, n1 * n2));
+    return std::max(spi * pitch_b(n0), std::max(lpty * pitch_b(n1), lpt * pitch_b(n2)));
+}
+
 int batch_describe(const BatchState *b, std::string *json)
 {
     std::ostringstream o;
