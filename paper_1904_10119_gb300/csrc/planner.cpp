@@ -717,7 +717,7 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         s.opts = *opts;
     if (decomp == FFT3_AUTO && dtype == FFT3_C64_SPLITBF16_TC) {
         decomp = FFT3_PENCIL3;
-        if (s.opts.variant == FFT3_PPP_NATURAL)
+        if (s.opts.variant == FFT3_PPP_NATURAL && (int64_t)n0 * n1 * 8 >= (4ll << 20))
             s.opts.variant = FFT3_PPP_BLOCKED;
     }
     if (decomp == FFT3_AUTO) {
@@ -727,8 +727,10 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         // (measured faster than the L2-resident slab kernel at 1024 x 1024).
         int twl = 2 * tw_slots_h(n0) + 2 * tw_slots_h(n1);
         decomp = slab_smem(n0, n1, twl) <= kSmemLimit ? FFT3_SLAB_PENCIL : FFT3_PENCIL3;
-        // and with the blocked intermediate when it applies (measured 8.76 against 9.49 ms at 1024^3)
-        if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_NATURAL)
+        // and with the blocked intermediate when it applies and the natural z lines
+        // would be at least 4 MiB apart (1024^3: 8.68 against 9.41 ms; at 512^3, 2 MiB
+        // apart, the natural layout measured 1.053 against 1.067 ms)
+        if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_NATURAL && (int64_t)n0 * n1 * 8 >= (4ll << 20))
             s.opts.variant = FFT3_PPP_BLOCKED;
     }
     if (dtype == FFT3_C64_SPLITBF16_TC) {
