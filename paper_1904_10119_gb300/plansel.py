@@ -2,7 +2,7 @@
 kernels) predicts the log run time of a candidate plan for a shape; the
 candidate with the lowest prediction is proposed.  Exhaustive timing of all
 candidates (fft3_time_candidates / fft3_autotune) stays the fallback and is
-the judge of the model's regret, regret = t(chosen) / t(best) - 1.
+the yardstick of the model's regret, regret = t(chosen) / t(best) - 1.
 
 The paper leaves the choice of decomposition to the user and shows that none
 wins everywhere (Section 4.3); this module makes the choice from measurements.
