@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
     // The k-th sub-line of group g: tile cid + (k / W) * ncl, local slot g + G*(k % W)
     // (sub-line q = r*QP + slot), staging buffer g*S + k % S, mbarrier phase (k / S) & 1.
     auto tile_of = [&](int64_t k) { return cid + (k / W) * ncl; };
+    const bool prefetch_l2 = a.g.ij * 8 <= (1 << 20);
     auto issue = [&](int64_t k) {
         const int64_t tile = tile_of(k);
         if (tile >= a.ntiles)
@@ -181,6 +182,15 @@ __global__ void __launch_bounds__(G *LPT *R2, cstream_min_blocks(cstream_smem_p(
         mbar_expect_tx(&bars[b], SUB_BYTES);
         tma_load_5d(stg + b * M * LPT, &tin, (int)id.c0, r * QP + g + G * (int)(k % W), 0, (int)id.a,
                     (int)id.b, &bars[b]);
+        // the group's following sub-line goes to L2 now, so its load into the
+        // staging buffer (issued once the buffer is free) finds it there; not
+        // for rows megabytes apart (every row its own page: measured slower)
+        const int64_t kp = k + S;
+        const int64_t tp = tile_of(kp);
+        if (prefetch_l2 && tp < a.ntiles) {
+            const TileId ip = decode_tile(tp, a.tiles_c, a.g.A, LPT);
+            tma_prefetch_5d(&tin, (int)ip.c0, r * QP + g + G * (int)(kp % W), 0, (int)ip.a, (int)ip.b);
+        }
     };
     if (gtid == 0) {
         for (int k = 0; k < S; ++k)

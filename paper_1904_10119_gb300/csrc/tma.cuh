@@ -73,6 +73,14 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, i
                  : "memory");
 }
 
+// Prefetch of a 5D box into L2 (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_5d(const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];" ::"l"(map), "r"(c0),
+                 "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                              const void *src)
 {
