@@ -854,9 +854,10 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
                 py.chunk = chunk;
                 px.pair_next = true;
             }
-        } else if (blocked_fits()) {
+        } else if (blocked_fits() && (int64_t)n0 * n1 * 8 >= (4ll << 20)) {
             // slab stage as x and y passes; the y pass stores the slabs redistributed
-            // into z pencils ([x/16][z][y][x%16]), the z pass reads them back
+            // into z pencils ([x/16][z][y][x%16]), the z pass reads them back (where
+            // the natural z lines would be at least 4 MiB apart, as for FFT3_AUTO)
             rc = emit_blocked();
             if (rc)
                 return rc;
