@@ -175,11 +175,12 @@ def main():
     ap.add_argument("--n", type=int, default=1024, help="cube edge (ignored with --shape)")
     ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("N0", "N1", "N2"))
     ap.add_argument("--decomp", default="auto",
-                    choices=["auto", "slab_pencil", "slab_pencil_pipelined", "ppp", "ppp_rotate", "ppp_blocked",
-                             "volumetric"])
+                    choices=["auto", "slab_pencil", "slab_pencil_pipelined", "slab_pencil_fused", "ppp", "ppp_rotate",
+                             "ppp_blocked", "volumetric"])
     ap.add_argument("--tile-lines", type=int, default=0)
     ap.add_argument("--slab-mode", type=int, default=0)
     ap.add_argument("--slab-chunk", type=int, default=0)
+    ap.add_argument("--slab-lines", type=int, default=0)
     ap.add_argument("--radix-order", type=int, default=0)
     ap.add_argument("--dtype", default="f32", choices=["f32", "splitbf16"],
                     help="splitbf16: radix-16 stages on the tensor cores (hi+lo BF16, FP32 accumulation)")
@@ -246,6 +247,7 @@ def main():
 
     decomp_map = {"auto": (fft3.FFT3_AUTO, {}), "slab_pencil": (fft3.FFT3_SLAB_PENCIL, {}),
                   "slab_pencil_pipelined": (fft3.FFT3_SLAB_PENCIL, {"slab_mode": 4}),
+                  "slab_pencil_fused": (fft3.FFT3_SLAB_PENCIL, {"slab_mode": 5}),
                   "ppp": (fft3.FFT3_PENCIL3, {}), "ppp_rotate": (fft3.FFT3_PENCIL3, {"variant": 1}),
                   "ppp_blocked": (fft3.FFT3_PENCIL3, {"variant": 2}),
                   "volumetric": (fft3.FFT3_VOLUMETRIC, {})}
@@ -280,7 +282,7 @@ def main():
     decomp, opts = decomp_map[args.decomp]
     opts = dict(opts)
     for k, v in (("tile_lines", args.tile_lines), ("slab_mode", args.slab_mode), ("slab_chunk", args.slab_chunk),
-                 ("radix_order", args.radix_order)):
+                 ("slab_lines", args.slab_lines), ("radix_order", args.radix_order)):
         if v:
             opts[k] = v
     if args.dtype == "splitbf16":

@@ -100,13 +100,20 @@ typedef struct fft3_options {
                              stream while the x lines of the next chunk run on the
                              caller's stream, so the y pass reads what the x pass
                              has just left in L2; the side stream joins the caller's
-                             stream before the z pass */
+                             stream before the z pass,
+                         5 = x and y tiles of every slab in one persistent launch that
+                             stores the slabs as z pencils ([x/16][z][y][x%16] in the
+                             workspace) with the intermediate kept in L2 (one HBM
+                             sweep for the 2D slab stage; tiles loaded by TMA), then
+                             the z pass back to natural order.  Square 256, 512 or
+                             1024 slabs, batch 1, n2 > 1; the workspace is array-sized */
     int tc_stages;    /* FFT3_C64_SPLITBF16_TC: which radix-16 stages run on the tensor cores:
                          0 = per line, the first radix-16 stage whose operands are both in
                              shared memory (the fastest; default; lines without one stay FP32),
                          1 = every radix-16 stage whose operands are both in shared memory,
                          2 = every radix-16 stage */
     int slab_chunk;   /* slab_mode 4: slabs per chunk (0 = about 32 MiB of slabs) */
+    int slab_lines;   /* slab_mode 5: rows per x tile and columns per y tile, 4 or 8 (0 = 4) */
     int reserved[8];  /* test hooks of the failure-detection tests, 0 in normal use:
                          [0] = s + 1 makes the x tiles of slab s never signal their
                          completion, so the waits of its y tiles expire;

@@ -115,6 +115,28 @@ static int encode_pass_map(CUtensorMap *m, const void *base, const PassGeom &g, 
     return FFT3_OK;
 }
 
+// The blocked workspace of the fused slab stage as rows of 16 values; boxes of
+// lpt columns x min(n, 256) rows.
+static int encode_blocked_map(CUtensorMap *m, const void *base, int64_t elems, int n, int lpt)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return fail(FFT3_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if ((uintptr_t)base & 15)
+        return fail(FFT3_ERR_INVALID_ARG, "this plan moves tiles with TMA: buffers must be 16-byte aligned");
+    cuuint64_t dims[2] = {16, (cuuint64_t)(elems / 16)};
+    cuuint64_t strides[1] = {16 * 8};
+    cuuint32_t box[2] = {(cuuint32_t)lpt, (cuuint32_t)(n < 256 ? n : 256)};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(FFT3_ERR_CUDA, "cuTensorMapEncodeTiled (blocked workspace) failed with code " +
+                                       std::to_string((int)r));
+    return FFT3_OK;
+}
+
 // Input map of a streamed strided pass: the array as {C, Q, M, A, B} with
 // line element j = Q*j' + q, so one box {LPT, 1, M, 1, 1} is the decimated
 // sub-line q of a tile.
@@ -244,6 +266,13 @@ static int build_launches(fft3_plan_s *P)
             L.probe_g = natural_x(s);
             L.probe_n = s.n0;
             break;
+        case PK_SLABBLK:
+            L.func = fk ? fk->l2blk[p.lpt == 8 ? 1 : 0] : nullptr;
+            L.reset_counters = true;
+            L.slab_map = true;
+            L.probe_g = natural_x(s);
+            L.probe_n = s.n0;
+            break;
         case PK_VOL:
             L.func = (const void *)&k_vol;
             L.cluster = p.p;
@@ -305,7 +334,7 @@ static int build_launches(fft3_plan_s *P)
         } else if (p.kind == PK_COPY) {
             L.grid = dim3((unsigned)std::min<int64_t>(4096, (P->elems + 255) / 256 + 1));
             L.block = dim3(256);
-        } else if (p.kind == PK_SLABL2) {
+        } else if (p.kind == PK_SLABL2 || p.kind == PK_SLABBLK) {
             rc = occupancy_grid(L.func, L.block.x, L.smem, 0, P->device, &L.grid);
             if (rc)
                 return rc;
@@ -521,6 +550,17 @@ static int launch_one(fft3_plan_s *P, const Launch &L, const void *func, PassArg
         if (rc)
             return rc;
         void *params[2] = {&a, &tin};
+        CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params));
+        return FFT3_OK;
+    }
+    if (L.slab_map) {
+        if ((uintptr_t)a.in & 15)
+            return fail(FFT3_ERR_INVALID_ARG, "this plan moves tiles with TMA: buffers must be 16-byte aligned");
+        CUtensorMap tws;
+        int rc = encode_blocked_map(&tws, a.out, P->elems, L.probe_n, a.lpt);
+        if (rc)
+            return rc;
+        void *params[2] = {&a, &tws};
         CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params));
         return FFT3_OK;
     }

@@ -36,6 +36,7 @@ struct Launch {
     PassArgs args{};
     int src = BUF_IN, dst = BUF_OUT;
     bool reset_counters = false;
+    bool slab_map = false; // k_slab_tma: 2D tensor map of the blocked workspace
     bool tma = false; // kernel takes two tensor maps after its PassArgs
     int stream_q = 0; // > 0: streamed strided pass, one 5D input map of Q decimated sub-lines
     // two-stream pipelined pair: this pass (on the caller's stream) and the

@@ -207,11 +207,23 @@ __host__ __device__ __forceinline__ constexpr int padpos(int pos) { return pos +
 // reading one position of 16 consecutive lines is conflict free too.
 __host__ __device__ constexpr int line_pitch(int n) { return (padpos(n - 1) + 1) | 1; }
 
+// Barrier of the threads running the line transforms: the whole block
+// (BAR = 0), or the NT threads of named barrier BAR when other warps of the
+// block do other work.
+template <int BAR, int NT>
+__device__ __forceinline__ void lines_sync()
+{
+    if constexpr (BAR == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+}
+
 // One compile-time Stockham stage (see the file header).  `src(j)` returns
 // element j of this thread's line, `dst(k, v)` stores element k.  When the
-// source and destination alias, SYNC_MID places a block barrier between
-// reading every input and writing any output.
-template <int N, int T, int R, int NS, bool SYNC_MID, class Src, class Dst>
+// source and destination alias, SYNC_MID places a barrier between reading
+// every input and writing any output.
+template <int N, int T, int R, int NS, bool SYNC_MID, int BAR = 0, int NT = 0, class Src, class Dst>
 __device__ __forceinline__ void stage_fixed(int t, const Src &src, const Dst &dst, const float2 *tw)
 {
     constexpr int NB = N / R;
@@ -228,7 +240,7 @@ __device__ __forceinline__ void stage_fixed(int t, const Src &src, const Dst &ds
         }
     }
     if constexpr (SYNC_MID)
-        __syncthreads();
+        lines_sync<BAR, NT>();
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         const int q = t + b * T;
@@ -254,33 +266,55 @@ struct Radices {
     static constexpr int count = sizeof...(Rs);
 };
 
-template <int N, int T, int NS, class Rad>
+// BAR, NT: the barrier of the transforming threads (lines_sync).
+template <int N, int T, int NS, class Rad, int BAR = 0, int NT = 0>
 struct EngineFixed;
 
 // Last stage: source is shared memory (or global for a single-stage line),
 // destination is the caller's sink.
-template <int N, int T, int NS, int R>
-struct EngineFixed<N, T, NS, Radices<R>> {
+template <int N, int T, int NS, int R, int BAR, int NT>
+struct EngineFixed<N, T, NS, Radices<R>, BAR, NT> {
     template <bool FIRST, bool SINK_ALIASES, class Src, class Smem, class Dst>
     __device__ __forceinline__ static void run(int t, const Src &src, const Smem &, const Dst &dst,
                                                const float2 *tw)
     {
-        stage_fixed<N, T, R, NS, SINK_ALIASES>(t, src, dst, tw);
+        stage_fixed<N, T, R, NS, SINK_ALIASES, BAR, NT>(t, src, dst, tw);
     }
 };
 
-template <int N, int T, int NS, int R, int R2, int... Rest>
-struct EngineFixed<N, T, NS, Radices<R, R2, Rest...>> {
+template <int N, int T, int NS, int R, int R2, int... Rest, int BAR, int NT>
+struct EngineFixed<N, T, NS, Radices<R, R2, Rest...>, BAR, NT> {
     template <bool FIRST, bool SINK_ALIASES, class Src, class Smem, class Dst>
     __device__ __forceinline__ static void run(int t, const Src &src, const Smem &sm, const Dst &dst,
                                                const float2 *tw)
     {
         // The first stage reads its own source; later stages read the shared
         // buffer they also write, so they need the mid-stage barrier.
-        stage_fixed<N, T, R, NS, !FIRST>(t, src, sm, tw);
-        __syncthreads();
-        EngineFixed<N, T, NS * R, Radices<R2, Rest...>>::template run<false, SINK_ALIASES>(
+        stage_fixed<N, T, R, NS, !FIRST, BAR, NT>(t, src, sm, tw);
+        lines_sync<BAR, NT>();
+        EngineFixed<N, T, NS * R, Radices<R2, Rest...>, BAR, NT>::template run<false, SINK_ALIASES>(
             t, sm, sm, dst, tw + (R - 1) * NS);
+    }
+};
+
+// The first stage (source -> shared buffer), then `between()` after the
+// barrier that ends it (the source has been read by every thread), then the
+// remaining stages (shared buffer -> sink).
+template <int N, int T, class Rad, int BAR, int NT>
+struct EngineSplitFirst;
+
+template <int N, int T, int R, int... Rest, int BAR, int NT>
+struct EngineSplitFirst<N, T, Radices<R, Rest...>, BAR, NT> {
+    static_assert(sizeof...(Rest) > 0, "at least two stages");
+    template <class Src, class Smem, class Dst, class Between>
+    __device__ __forceinline__ static void run(int t, const Src &src, const Smem &sm, const Dst &dst,
+                                               const float2 *tw, const Between &between)
+    {
+        stage_fixed<N, T, R, 1, false, BAR, NT>(t, src, sm, tw);
+        lines_sync<BAR, NT>();
+        between();
+        EngineFixed<N, T, R, Radices<Rest...>, BAR, NT>::template run<false, false>(t, sm, sm, dst,
+                                                                                  tw + (R - 1));
     }
 };
 

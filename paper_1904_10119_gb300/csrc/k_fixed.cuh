@@ -24,6 +24,16 @@ constexpr const void *slab_l2_ptr()
 }
 
 template <int N, int T, class Rad, int LPT>
+constexpr const void *slab_blk_ptr()
+{
+    if constexpr (has_slab_l2<N, T>() && T * LPT + 32 <= 1024 &&
+                  slab_tma_smem(N, LPT) <= 227 * 1024)
+        return (const void *)&k_slab_tma<N, T, Rad, LPT, kSlabTmaBufs>;
+    else
+        return nullptr;
+}
+
+template <int N, int T, class Rad, int LPT>
 constexpr const void *pass_c_ptr()
 {
     if constexpr (LPT > 0)
@@ -71,6 +81,8 @@ constexpr const void *pass_c_tc_ptr()
      fft3::pass_c_ptr<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_c(T, 16)>(),                  \
      fft3::pass_c_ptr<N, T, fft3::Radices<__VA_ARGS__>, fft3::lpt_c(T, 8)>(),                   \
      fft3::slab_l2_ptr<N, T, fft3::Radices<__VA_ARGS__>>(),                                    \
+     {fft3::slab_blk_ptr<N, T, fft3::Radices<__VA_ARGS__>, 4>(),                               \
+      fft3::slab_blk_ptr<N, T, fft3::Radices<__VA_ARGS__>, 8>()},                              \
      fft3::pass_ctma_ptr<N, T, fft3::Radices<__VA_ARGS__>>(),                                  \
      {fft3::pass_j_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, 0>(),                               \
       fft3::pass_j_tc_ptr<N, T, fft3::Radices<__VA_ARGS__>, 1>(),                               \

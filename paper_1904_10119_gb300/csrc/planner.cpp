@@ -678,6 +678,38 @@ static int make_slab_l2_pass(Schedule *s, int n0, int n1, int64_t n2, int64_t ba
     return FFT3_OK;
 }
 
+// Slab stage fused with the slab-to-pencil redistribution: x and y tiles of
+// every square slab in one persistent launch (k_slab_blk), from `in` into the
+// workspace laid out as z pencils [x/16][z][y][x%16].
+static int make_slab_blk_pass(Schedule *s, int n0, int n1, int64_t n2, PassPlan *out, std::string *err)
+{
+    PassPlan q;
+    int rc = make_slab_l2_pass(s, n0, n1, n2, 1, &q, err);
+    if (rc)
+        return rc;
+    q.kind = PK_SLABBLK;
+    q.dst = BUF_WS;
+    q.g.ok = 1; q.g.oc = 16; q.g.oa = (int64_t)n1 * 16; q.g.ob = (int64_t)n1 * 16 * n2;
+    // rows per x tile = columns per y tile; transforming warps + one producer
+    // warp; twiddles, the padded work buffer and the ring of landing buffers
+    // (k_slab_tma)
+    const int want = s->opts.slab_lines;
+    if (want != 0 && want != 4 && want != 8) {
+        *err = "slab_lines must be 0, 4 or 8";
+        return FFT3_ERR_INVALID_ARG;
+    }
+    q.lpt = want == 8 ? 8 : 4;
+    q.threads = q.line.T * q.lpt + 32;
+    const int twlen = tw_slots_h((int)s->tw[q.tw_seg[0]].m.size());
+    q.smem_bytes = (twlen + (q.lpt * pitch_h(n0) + 15) / 16 * 16 + kSlabTmaBufs * q.lpt * n0) * 8;
+    if (q.smem_bytes > kSmemLimit || q.threads > 1024)
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    q.tiles_c = n1 / q.lpt;
+    q.ntiles = 2 * q.tiles_c * n2;
+    *out = q;
+    return FFT3_OK;
+}
+
 int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int direction,
                    const fft3_options *opts, Schedule *out, std::string *err)
 {
@@ -771,6 +803,20 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         }
         return y && z;
     };
+    auto emit_blocked_z = [&]() -> int {
+        const int64_t X = n0, Y = n1, Z = n2;
+        PassPlan p;
+        PassGeom gz{}; // columns x%16, lines z, a = y, b = x/16
+        gz.C = 16; gz.A = Y; gz.B = X / 16;
+        gz.ij = Y * 16; gz.ic = 1; gz.ia = 16; gz.ib = Z * Y * 16;
+        gz.ok = X * Y; gz.oc = 1; gz.oa = X; gz.ob = 16;
+        rc = make_line_pass(&s, 2, n2, gz, false, BUF_WS, BUF_OUT, &p, err);
+        if (rc)
+            return rc;
+        s.passes.push_back(p);
+        s.need_ws = true;
+        return FFT3_OK;
+    };
     auto emit_blocked = [&]() -> int {
         const int64_t X = n0, Y = n1, Z = n2;
         PassPlan p;
@@ -786,16 +832,7 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         if (rc)
             return rc;
         s.passes.push_back(p);
-        PassGeom gz{}; // columns x%16, lines z, a = y, b = x/16
-        gz.C = 16; gz.A = Y; gz.B = X / 16;
-        gz.ij = Y * 16; gz.ic = 1; gz.ia = 16; gz.ib = Z * Y * 16;
-        gz.ok = X * Y; gz.oc = 1; gz.oa = X; gz.ob = 16;
-        rc = make_line_pass(&s, 2, n2, gz, false, BUF_WS, BUF_OUT, &p, err);
-        if (rc)
-            return rc;
-        s.passes.push_back(p);
-        s.need_ws = true;
-        return FFT3_OK;
+        return emit_blocked_z();
     };
     if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED && blocked_fits()) {
         rc = emit_blocked();
@@ -835,7 +872,16 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
                 return rc;
             s.passes.push_back(p);
             cur = BUF_OUT;
-        } else if (mode == 1 || mode == 2) {
+        } else if (mode == 5 && slab_l2_supported(n0, n1) && batch == 1 && n2 > 1) {
+            rc = make_slab_blk_pass(&s, n0, n1, n2, &p, err);
+            if (rc)
+                return rc;
+            s.passes.push_back(p);
+            rc = emit_blocked_z();
+            if (rc)
+                return rc;
+            z_done = true;
+        } else if (mode == 1 || mode == 2 || mode == 5) {
             *err = "requested slab mode is not available for this slab size";
             return FFT3_ERR_UNSUPPORTED_SIZE;
         } else if (mode == 4 && n0 > 1 && n1 > 1) {
@@ -937,8 +983,8 @@ static const char *kind_name(int k)
     static const char *names[] = {"line_contig", "line_contig_rotate", "line_strided", "line_runtime",
                                   "slab_smem", "slab_l2", "volumetric_split", "copy", "unused",
                                   "line_strided_tma", "line_contig_tc", "line_strided_tc",
-                                  "volumetric_split_fixed", "line_strided_stream"};
-    return (k >= 0 && k <= 13) ? names[k] : "?";
+                                  "volumetric_split_fixed", "line_strided_stream", "slab_l2_blocked"};
+    return (k >= 0 && k <= 14) ? names[k] : "?";
 }
 static const char *buf_name(int b)
 {
@@ -976,7 +1022,8 @@ std::string Schedule::json() const
           << ",\"src\":\"" << buf_name(p.src) << "\",\"dst\":\"" << buf_name(p.dst)
           << "\",\"line\":";
         line_json(o, p.line);
-        if (p.kind == PK_SLAB || p.kind == PK_VOL || p.kind == PK_SLABL2 || p.kind == PK_VOLC) {
+        if (p.kind == PK_SLAB || p.kind == PK_VOL || p.kind == PK_SLABL2 || p.kind == PK_VOLC ||
+            p.kind == PK_SLABBLK) {
             o << ",\"line2\":";
             line_json(o, p.line2);
         }

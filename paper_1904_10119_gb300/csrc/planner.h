@@ -26,6 +26,7 @@ enum PassKind {
     PK_CTC = 11,   // split-BF16 tensor-core radix-16 stages, strided columns
     PK_VOLC = 12,  // compile-time volumetric split of strided lines (k_volc.cu)
     PK_CSTREAM = 13, // strided lines, decimated sub-lines streamed by TMA (k_cstream.cu)
+    PK_SLABBLK = 14, // 2D slab DFT in one persistent launch, stored as blocked z pencils (k_slab_blk)
 };
 
 enum BufId { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };

@@ -129,6 +129,7 @@ struct FixedKernels {
     const void *c16;  // k_pass_c, 16 lines per tile
     const void *c8;   // k_pass_c, 8 lines per tile
     const void *l2;   // k_slab_l2 (square slabs), 0 if not compiled
+    const void *l2blk[2]; // k_slab_tma (square slabs, blocked output), 4 and 8 lines per tile
     const void *ctma; // k_pass_c_tma (TMA-pipelined strided lines), 0 if not compiled
     // split-BF16 tensor-core variants by tc_stages mode: [0] the first radix-16 stage
     // with both operands in shared memory, [1] every such stage, [2] every radix-16 stage
@@ -141,6 +142,15 @@ const FixedKernels *fixed_kernels(int id);
 // line (0 = not compiled).
 // rows (x tiles) and columns (y tiles) per tile of the L2-resident slab kernel
 constexpr int kSlabL2Lpt = 4;
+// landing buffers of the fused slab kernel (k_slab_tma) and its dynamic
+// shared memory: twiddles (n-1 rounded to 16), the padded work buffer, the
+// ring of landing buffers
+constexpr int kSlabTmaBufs = 2;
+constexpr int slab_tma_smem(int n, int lpt)
+{
+    return ((n - 1 + 15) / 16 * 16 + (lpt * ((n - 1 + (n - 1) / 16 + 1) | 1) + 15) / 16 * 16 +
+            kSlabTmaBufs * lpt * n) * 8;
+}
 constexpr int lpt_j(int T) { return T >= 256 ? 1 : 256 / T; }
 constexpr int lpt_rot(int T) { return T >= 64 ? 8 : (128 / T > 16 ? 128 / T : 16); }
 constexpr int lpt_c(int T, int want) { return T * want <= 1024 ? want : 0; }

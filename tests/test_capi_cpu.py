@@ -103,6 +103,32 @@ def test_schedule_slab_pencil_modes():
         fft3.fft3_plan_schedule(640, 640, 8, 1, 0, fft3.FFT3_SLAB_PENCIL, -1, fft3.make_options(slab_mode=2))
 
 
+def test_schedule_slab_fused_blocked():
+    """slab_mode 5: one fused slab launch from `in` into the blocked workspace
+    ([x/16][z][y][x%16]: rows of 16 values, slab stride 16*n1, block stride
+    16*n1*n2), then the z pass from the workspace back to natural order."""
+    for lines, threads in ((0, 64 * 4 + 32), (8, 64 * 8 + 32)):
+        s = fft3.fft3_plan_schedule(1024, 1024, 512, 1, 0, fft3.FFT3_SLAB_PENCIL, -1,
+                                    fft3.make_options(slab_mode=5, slab_lines=lines))
+        assert _kinds(s) == ["slab_l2_blocked", "line_strided_stream"]
+        ps, pz = s["passes"]
+        assert (ps["src"], ps["dst"], pz["src"], pz["dst"]) == ("in", "workspace", "workspace", "out")
+        g = ps["geom"]
+        assert (g["ic"], g["ia"], g["oc"], g["oa"], g["ob"]) == (1024, 1024 * 1024, 16, 16 * 1024, 16 * 1024 * 512)
+        assert ps["lpt"] == (lines or 4) and ps["threads"] == threads
+        assert ps["tiles"] == 2 * (1024 // ps["lpt"]) * 512 and s["workspace_bytes"] == 1024 * 1024 * 512 * 8
+        gz = pz["geom"]
+        assert (gz["ij"], gz["ia"], gz["ib"], gz["ok"], gz["oa"], gz["ob"]) == \
+            (16 * 1024, 16, 16 * 1024 * 512, 1024 * 1024, 1024, 16)
+    s = fft3.fft3_plan_schedule(256, 256, 64, 1, 0, fft3.FFT3_SLAB_PENCIL, -1, fft3.make_options(slab_mode=5))
+    assert _kinds(s)[0] == "slab_l2_blocked"
+    bad = [((640, 640, 8, 1), {}), ((1024, 1024, 8, 2), {}), ((1024, 1024, 1, 1), {}),
+           ((1024, 1024, 8, 1), {"slab_lines": 6})]
+    for dims, extra in bad:
+        with pytest.raises(fft3.Fft3Error):
+            fft3.fft3_plan_schedule(*dims, 0, fft3.FFT3_SLAB_PENCIL, -1, fft3.make_options(slab_mode=5, **extra))
+
+
 def test_schedule_slab_pipelined_pair():
     """slab_mode 4: the x and y passes carry the same chunk of slabs (about
     32 MiB by default, or slab_chunk), the x pass marked as running with the next."""

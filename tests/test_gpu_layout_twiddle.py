@@ -108,15 +108,17 @@ def test_split_bf16_bit_exact():
     assert np.array_equal(gl, l_ref.view(np.uint32))
 
 
-def test_bounded_wait_expires_and_reports_timeout():
+@pytest.mark.parametrize("mode", [2, 5])
+def test_bounded_wait_expires_and_reports_timeout(mode):
     """A slab whose x tiles never signal makes its y tiles' waits run out: the
     kernel records the timeout and returns, the host reads FFT3_ERR_TIMEOUT,
-    and the context stays usable."""
+    and the context stays usable (slab_mode 2: L2-resident slab kernel;
+    5: the fused kernel with TMA loads, whose producer waits)."""
     shape = (256, 256, 4)
     x = synth.uniform_c64((1, 4, 256, 256), 2)
     xt = torch.from_numpy(x).cuda()
     out = torch.empty_like(xt)
-    opts = fft3.make_options(slab_mode=2)
+    opts = fft3.make_options(slab_mode=mode)
     opts.reserved[0] = 1 + 1      # slab 1 never signals
     opts.reserved[1] = 2000       # each wait gives up after 2e6 cycles (about a millisecond)
     h = fft3.fft3_plan_create_ex(*shape, 1, 0, fft3.FFT3_SLAB_PENCIL, -1, opts)
@@ -128,5 +130,5 @@ def test_bounded_wait_expires_and_reports_timeout():
     finally:
         fft3.fft3_plan_destroy(h)
     from tests.gpu_util import assert_parity, run_plan
-    x, got, _ = run_plan(shape, 1, fft3.FFT3_SLAB_PENCIL, -1, x=x, slab_mode=2)
+    x, got, _ = run_plan(shape, 1, fft3.FFT3_SLAB_PENCIL, -1, x=x, slab_mode=mode)
     assert_parity(x, got, shape)

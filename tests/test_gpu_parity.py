@@ -71,6 +71,26 @@ def test_slab_modes(mode, shape):
     assert kinds[0] == {1: "slab_smem", 2: "slab_l2", 3: "line_contig"}[mode] or mode == 3
 
 
+@pytest.mark.parametrize("shape,direction,lines", [((256, 256, 6), FWD, 0), ((256, 256, 5), INV, 8),
+                                                   ((512, 512, 3), FWD, 4), ((512, 512, 4), INV, 8),
+                                                   ((1024, 1024, 2), INV, 0), ((1024, 1024, 5), FWD, 8),
+                                                   ((256, 256, 1), FWD, 0)])
+def test_slab_fused_blocked(shape, direction, lines):
+    """slab_mode 5: x and y tiles of every slab in one persistent launch (TMA
+    loads by a producer warp), stored as blocked z pencils in the workspace,
+    then the z pass back to natural order; 4 and 8 lines per tile, fewer slabs
+    than the ticket lag (3), and a single slab (refused: no z pass)."""
+    if shape[2] == 1:
+        with pytest.raises(fft3.Fft3Error):
+            fft3.Plan(*shape, 1, decomposition=S, slab_mode=5)
+        return
+    x, got, plan = run_plan(shape, 1, S, direction, seed=sum(shape), slab_mode=5, slab_lines=lines)
+    assert_parity(x, got, shape, 1, direction)
+    passes = plan.describe()["passes"]
+    assert [p["kind"] for p in passes][0] == "slab_l2_blocked" and len(passes) == 2
+    assert passes[0]["dst"] == "workspace" and passes[1]["src"] == "workspace"
+
+
 @pytest.mark.parametrize("shape,batch,chunk,direction", [((64, 64, 64), 1, 0, FWD), ((96, 80, 10), 2, 3, FWD),
                                                          ((256, 256, 12), 1, 5, INV), ((100, 60, 9), 1, 1, FWD),
                                                          ((1024, 16, 9), 1, 4, INV), ((30, 25, 18), 3, 18, FWD)])
