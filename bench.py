@@ -358,6 +358,8 @@ def main():
         variants = dict(decomp_map)
         variants["volumetric_mesh4_compiled"] = (fft3.FFT3_VOLUMETRIC, {"mesh": (1, 4, 4), "tile_lines": 16})
         variants["ppp_plain_strided_kernel"] = (fft3.FFT3_PENCIL3, {"tile_lines": 16})
+        variants["permuted_output_pencils"] = (fft3.FFT3_AUTO, {"layout": fft3.FFT3_LAYOUT_PENCILS})
+        variants["permuted_output_rotated"] = (fft3.FFT3_PENCIL3, {"layout": fft3.FFT3_LAYOUT_ROTATED})
         tc = fft3.FFT3_C64_SPLITBF16_TC
         variants["split_bf16_tc_one_stage_per_line"] = (fft3.FFT3_AUTO, {"dtype": tc})
         variants["split_bf16_tc_shared_memory_stages"] = (fft3.FFT3_AUTO, {"dtype": tc, "tc_stages": 1})

@@ -81,6 +81,22 @@ enum fft3_ppp_variant {
                              natural variant is used */
 };
 
+/* Layout of the spectrum (options.layout): where a forward plan writes X[k0,k1,k2]
+ * of batch b and where an inverse plan reads it.  Section 2.4: applications that
+ * only need the spectrum in some known order (convolutions, PDE solvers) can skip
+ * the last redistribution and keep the data shuffled.  fft3_layout_positions
+ * gives the position of every element, N = n0*n1*n2:
+ *   NATURAL  k0 + n0*(k1 + n1*k2) + N*b;
+ *   ROTATED  the paper's shuffled order after the rotations xyz -> yzx -> zxy with
+ *            the final rotation back to xyz dropped: k2 + n2*(k0 + n0*k1) + N*b;
+ *   PENCILS  z pencils blocked by 16 columns of x, [k0/16][k2][k1][k0%16]:
+ *            (k0/16)*16*n1*n2 + k2*16*n1 + k1*16 + k0%16 (batch 1, n0 % 16 == 0);
+ *            the layout the default schedule's z pass reads, so a forward plan
+ *            saves that pass's redistribution and an inverse plan starts from it.
+ * Permuted layouts need every dimension > 1 and a slab-pencil, pencil-pencil-pencil
+ * or automatic decomposition (FFT3_LAYOUT_PENCILS also with the split-BF16 dtype). */
+enum fft3_layout { FFT3_LAYOUT_NATURAL = 0, FFT3_LAYOUT_ROTATED = 1, FFT3_LAYOUT_PENCILS = 2 };
+
 /* Optional planner controls.  Zero-initialise and set what you need. */
 typedef struct fft3_options {
     int variant;      /* fft3_ppp_variant for FFT3_PENCIL3 */
@@ -114,6 +130,7 @@ typedef struct fft3_options {
                          2 = every radix-16 stage */
     int slab_chunk;   /* slab_mode 4: slabs per chunk (0 = about 32 MiB of slabs) */
     int slab_lines;   /* slab_mode 5: rows per x tile and columns per y tile, 4 or 8 (0 = 4) */
+    int layout;       /* fft3_layout of the forward output / inverse input (0 = natural) */
     int reserved[8];  /* test hooks of the failure-detection tests, 0 in normal use:
                          [0] = s + 1 makes the x tiles of slab s never signal their
                          completion, so the waits of its y tiles expire;
@@ -206,6 +223,16 @@ int fft3_plan_describe(fft3_plan p, char *buf, size_t len);
  * fft3_plan_create_ex would build.  Same return convention as describe. */
 int fft3_plan_schedule(int n0, int n1, int n2, int batch, int dtype, int decomposition,
                        int direction, const fft3_options *opts, char *buf, size_t len);
+
+/* Host-only: positions of spectrum elements in a permuted layout (fft3_layout,
+ * Section 2.4).  For each natural flat index idx[i] = k0 + n0*(k1 + n1*k2) + N*b
+ * (0 <= idx[i] < N*batch) writes pos[i], its offset in complex elements in the
+ * buffer a forward plan with that layout writes (and an inverse plan reads).
+ * idx and pos are host arrays of `count` entries owned by the caller.  Returns
+ * FFT3_OK, FFT3_ERR_INVALID_ARG (null pointer, bad layout, index out of range) or
+ * FFT3_ERR_UNSUPPORTED_SIZE (the layout does not exist for these sizes). */
+int fft3_layout_positions(int layout, int n0, int n1, int n2, int batch, const int64_t *idx, int64_t *pos,
+                          int64_t count);
 
 /* Host-only: the radix list the planner uses for a line of length n under
  * radix_order `order`; returns the number of stages (<= cap) or a negative

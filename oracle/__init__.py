@@ -22,7 +22,9 @@ Multi-Dimensional DFTs"):
   dimension of a cube distributed cyclically on a 3D mesh (the volumetric
   decomposition of Fig. cuboid): ``volumetric3_sim``.
 * Section 2.4 -- the data rotations xyz -> yzx -> zxy of the
-  pencil-pencil-pencil algorithm: ``rotation_dst_index``.
+  pencil-pencil-pencil algorithm: ``rotation_dst_index``; the shuffled
+  spectrum left when the last redistribution is dropped, and the blocked
+  z-pencil order: ``layout_positions``.
 
 Parity is pinned for every function here by ``tests/test_oracle_*.py``
 against closed forms, invariants, brute force and an independent library
@@ -321,6 +323,28 @@ def rotation_dst_index(n0: int, n1: int, n2: int, kind: str) -> np.ndarray:
     ic, ib, ia = np.meshgrid(np.arange(dc), np.arange(db), np.arange(da), indexing="ij")
     dst = ib + db * (ic + dc * ia)
     return dst.ravel().astype(np.int64)
+
+
+def layout_positions(layout: str, n0: int, n1: int, n2: int, batch: int = 1) -> np.ndarray:
+    """Position of every natural flat index (k0 + n0*(k1 + n1*k2) + N*b) in a
+    permuted spectrum.  'rotated' (Section 2.4): the cube after the rotations
+    xyz -> yzx -> zxy with the redistribution back to xyz dropped, i.e. the
+    two rotations of ``rotation_dst_index`` applied in turn.  'pencils': z
+    pencils grouped by 16 columns of x, element (k0, k1, k2) at block k0 // 16,
+    then k2, then k1, then k0 % 16 (n0 a multiple of 16, batch 1)."""
+    N = n0 * n1 * n2
+    if layout == "rotated":
+        first = rotation_dst_index(n0, n1, n2, "xyz")
+        second = rotation_dst_index(n0, n1, n2, "yzx")
+        one = second[first]
+        return (one[None, :] + N * np.arange(batch)[:, None]).ravel().astype(np.int64)
+    if layout == "pencils":
+        if batch != 1 or n0 % 16:
+            raise ValueError("pencils: batch 1 and n0 % 16 == 0")
+        k2, k1, k0 = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
+        pos = (k0 // 16) * (n2 * n1 * 16) + k2 * (n1 * 16) + k1 * 16 + k0 % 16
+        return pos.ravel().astype(np.int64)
+    raise ValueError(layout)
 
 
 # --------------------------------------------------------------------------- #

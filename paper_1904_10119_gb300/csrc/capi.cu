@@ -447,6 +447,23 @@ int fft3_factorize(int n, int order, int *radices, int cap)
     return r;
 }
 
+int fft3_layout_positions(int layout, int n0, int n1, int n2, int batch, const int64_t *idx, int64_t *pos,
+                          int64_t count)
+{
+    if (!idx || !pos || count < 0 || n0 < 1 || n1 < 1 || n2 < 1 || batch < 1)
+        return fail(FFT3_ERR_INVALID_ARG, "bad argument to fft3_layout_positions");
+    if (layout < FFT3_LAYOUT_NATURAL || layout > FFT3_LAYOUT_PENCILS)
+        return fail(FFT3_ERR_INVALID_ARG, "unknown layout");
+    for (int64_t i = 0; i < count; ++i) {
+        int rc = layout_position(layout, n0, n1, n2, batch, idx[i], &pos[i]);
+        if (rc == FFT3_ERR_UNSUPPORTED_SIZE)
+            return fail(rc, "the pencils layout needs batch 1 and n0 % 16 == 0");
+        if (rc)
+            return fail(rc, "index " + std::to_string(idx[i]) + " outside the array");
+    }
+    return FFT3_OK;
+}
+
 int fft3_plan_schedule(int n0, int n1, int n2, int batch, int dtype, int decomposition, int direction,
                        const fft3_options *opts, char *buf, size_t len)
 {

@@ -710,6 +710,25 @@ static int make_slab_blk_pass(Schedule *s, int n0, int n1, int64_t n2, PassPlan 
     return FFT3_OK;
 }
 
+int layout_position(int layout, int64_t n0, int64_t n1, int64_t n2, int64_t batch, int64_t idx, int64_t *pos)
+{
+    const int64_t N = n0 * n1 * n2;
+    if (idx < 0 || idx >= N * batch)
+        return FFT3_ERR_INVALID_ARG;
+    const int64_t b = idx / N, r = idx % N;
+    const int64_t k0 = r % n0, k1 = (r / n0) % n1, k2 = r / (n0 * n1);
+    switch (layout) {
+    case FFT3_LAYOUT_NATURAL: *pos = idx; return FFT3_OK;
+    case FFT3_LAYOUT_ROTATED: *pos = k2 + n2 * (k0 + n0 * k1) + N * b; return FFT3_OK;
+    case FFT3_LAYOUT_PENCILS:
+        if (batch != 1 || n0 % 16)
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        *pos = (k0 / 16) * 16 * n1 * n2 + k2 * 16 * n1 + k1 * 16 + k0 % 16;
+        return FFT3_OK;
+    default: return FFT3_ERR_INVALID_ARG;
+    }
+}
+
 int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int direction,
                    const fft3_options *opts, Schedule *out, std::string *err)
 {
@@ -834,7 +853,95 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         s.passes.push_back(p);
         return emit_blocked_z();
     };
-    if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED && blocked_fits()) {
+    const int layout = s.opts.layout;
+    if (layout < FFT3_LAYOUT_NATURAL || layout > FFT3_LAYOUT_PENCILS) {
+        *err = "unknown layout";
+        return FFT3_ERR_INVALID_ARG;
+    }
+    if (layout != FFT3_LAYOUT_NATURAL) {
+        // Permuted spectrum (Section 2.4): the forward plan leaves out the last
+        // redistribution, the inverse plan starts from the permuted layout.
+        if (decomp == FFT3_VOLUMETRIC) {
+            *err = "permuted layouts come from the slab-pencil and pencil-pencil-pencil schedules";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        if (n0 < 2 || n1 < 2 || n2 < 2) {
+            *err = "permuted layouts need every dimension > 1";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        const bool fwd = direction == FFT3_FORWARD;
+        auto push = [&](int d, int n, const PassGeom &g, bool rot, int src, int dst) -> int {
+            PassPlan p;
+            int r = make_line_pass(&s, d, n, g, rot, src, dst, &p, err);
+            if (!r)
+                s.passes.push_back(p);
+            return r;
+        };
+        if (layout == FFT3_LAYOUT_ROTATED) {
+            if (dtype == FFT3_C64_SPLITBF16_TC) {
+                *err = "the rotated layout has no split-BF16 tensor-core schedule";
+                return FFT3_ERR_UNSUPPORTED_SIZE;
+            }
+            if (fwd) {
+                // x and y passes rotate (xyz -> yzx -> zxy); the z pass transforms the
+                // contiguous z lines of zxy in place of the final rotation
+                rc = push(0, n0, geom_rotate(0, n0, n1, n2, batch), true, BUF_IN, BUF_OUT);
+                if (!rc)
+                    rc = push(1, n1, geom_rotate(1, n0, n1, n2, batch), true, BUF_OUT, BUF_WS);
+                if (!rc)
+                    rc = push(2, n2, geom_natural(0, n2, n0, n1, batch), false, BUF_WS, BUF_OUT);
+            } else {
+                // z lines are contiguous in zxy: transform them and rotate zxy -> xyz,
+                // then the natural x and y passes
+                rc = push(2, n2, geom_rotate(2, n0, n1, n2, batch), true, BUF_IN, BUF_WS);
+                if (!rc)
+                    rc = push(0, n0, geom_natural(0, n0, n1, n2, batch), false, BUF_WS, BUF_OUT);
+                if (!rc)
+                    rc = push(1, n1, geom_natural(1, n0, n1, n2, batch), false, BUF_OUT, BUF_OUT);
+            }
+        } else {
+            if (batch != 1 || n0 % 16) {
+                *err = "the pencils layout needs batch 1 and n0 % 16 == 0";
+                return FFT3_ERR_UNSUPPORTED_SIZE;
+            }
+            const int64_t X = n0, Y = n1, Z = n2;
+            PassGeom gb{}; // z lines of the blocked layout on both sides: columns x%16, a = y, b = x/16
+            gb.C = 16; gb.A = Y; gb.B = X / 16;
+            gb.ij = Y * 16; gb.ic = 1; gb.ia = 16; gb.ib = Z * Y * 16;
+            gb.ok = gb.ij; gb.oc = 1; gb.oa = 16; gb.ob = gb.ib;
+            if (fwd) {
+                if (decomp == FFT3_SLAB_PENCIL && s.opts.slab_mode == 5 && slab_l2_supported(n0, n1)) {
+                    PassPlan p;
+                    rc = make_slab_blk_pass(&s, n0, n1, n2, &p, err);
+                    if (!rc)
+                        s.passes.push_back(p);
+                } else {
+                    PassGeom gy{}; // as the blocked schedule: y lines from `out` into the workspace
+                    gy.C = 16; gy.A = X / 16; gy.B = Z;
+                    gy.ij = X; gy.ic = 1; gy.ia = 16; gy.ib = X * Y;
+                    gy.ok = 16; gy.oc = 1; gy.oa = Z * Y * 16; gy.ob = Y * 16;
+                    rc = push(0, n0, geom_natural(0, n0, n1, n2, 1), false, BUF_IN, BUF_OUT);
+                    if (!rc)
+                        rc = push(1, n1, gy, false, BUF_OUT, BUF_WS);
+                }
+                if (!rc)
+                    rc = push(2, n2, gb, false, BUF_WS, BUF_OUT);
+            } else {
+                PassGeom gyi{}; // y lines of the blocked workspace into natural order
+                gyi.C = 16; gyi.A = X / 16; gyi.B = Z;
+                gyi.ij = 16; gyi.ic = 1; gyi.ia = Z * Y * 16; gyi.ib = Y * 16;
+                gyi.ok = X; gyi.oc = 1; gyi.oa = 16; gyi.ob = X * Y;
+                rc = push(2, n2, gb, false, BUF_IN, BUF_WS);
+                if (!rc)
+                    rc = push(1, n1, gyi, false, BUF_WS, BUF_OUT);
+                if (!rc)
+                    rc = push(0, n0, geom_natural(0, n0, n1, n2, 1), false, BUF_OUT, BUF_OUT);
+            }
+        }
+        if (rc)
+            return rc;
+        s.need_ws = true;
+    } else if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED && blocked_fits()) {
         rc = emit_blocked();
         if (rc)
             return rc;
@@ -1011,7 +1118,9 @@ std::string Schedule::json() const
     int64_t N = (int64_t)n0 * n1 * n2 * batch;
     o << "{\"dims\":[" << n0 << "," << n1 << "," << n2 << "],\"batch\":" << batch
       << ",\"dtype\":" << dtype << ",\"direction\":" << direction << ",\"decomposition\":\""
-      << decomp_name(decomp) << "\",\"variant\":" << opts.variant
+      << decomp_name(decomp) << "\",\"variant\":" << opts.variant << ",\"layout\":\""
+      << (opts.layout == FFT3_LAYOUT_ROTATED ? "rotated" : opts.layout == FFT3_LAYOUT_PENCILS ? "pencils" : "natural")
+      << "\""
       << ",\"workspace_bytes\":" << (need_ws ? N * 8 : 0) << ",\"hbm_sweeps\":" << passes.size()
       << ",\"twiddle_entries\":" << tw_total << ",\"passes\":[";
     for (size_t i = 0; i < passes.size(); ++i) {

@@ -85,6 +85,9 @@ int factorize(int n, int order, int *rad, int cap);
 int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int direction,
                    const fft3_options *opts, Schedule *out, std::string *err);
 
+// Position of natural flat index idx in a permuted layout (fft3_layout).
+int layout_position(int layout, int64_t n0, int64_t n1, int64_t n2, int64_t batch, int64_t idx, int64_t *pos);
+
 // Runtime radix list for a line of length n (radix order `order`) and its
 // stage-major twiddle exponents.
 int choose_runtime_line(int n, int order, LineChoice *lc, std::string *err);

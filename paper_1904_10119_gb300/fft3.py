@@ -21,6 +21,7 @@ FFT3_C64_SPLITBF16_TC = 1
 FFT3_SLAB_PENCIL, FFT3_PENCIL3, FFT3_VOLUMETRIC, FFT3_AUTO = 0, 1, 2, 3
 FFT3_FORWARD, FFT3_INVERSE = -1, 1
 FFT3_PPP_NATURAL, FFT3_PPP_ROTATE, FFT3_PPP_BLOCKED = 0, 1, 2
+FFT3_LAYOUT_NATURAL, FFT3_LAYOUT_ROTATED, FFT3_LAYOUT_PENCILS = 0, 1, 2
 
 STATUS = {
     0: "FFT3_OK", -1: "FFT3_ERR_INVALID_ARG", -2: "FFT3_ERR_UNSUPPORTED_SIZE", -3: "FFT3_ERR_OOM",
@@ -40,7 +41,8 @@ class Fft3Error(RuntimeError):
 class fft3_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("radix_order", ctypes.c_int), ("tile_lines", ctypes.c_int),
                 ("mesh", ctypes.c_int * 3), ("slab_mode", ctypes.c_int), ("tc_stages", ctypes.c_int),
-                ("slab_chunk", ctypes.c_int), ("slab_lines", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("slab_chunk", ctypes.c_int), ("slab_lines", ctypes.c_int), ("layout", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
 
 
 _lib = None
@@ -72,6 +74,8 @@ def load() -> ctypes.CDLL:
         "fft3_plan_describe": (i, [_P, ctypes.c_char_p, sz]),
         "fft3_plan_schedule": (i, [i, i, i, i, i, i, i, ctypes.POINTER(fft3_options), ctypes.c_char_p, sz]),
         "fft3_factorize": (i, [i, i, pi, i]),
+        "fft3_layout_positions": (i, [i, i, i, i, i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      i64]),
         "fft3_twiddles": (i, [i, i, _P, i64, _P, _P, _P]),
         "fft3_plan_probe_layout": (i, [_P, _P, _P, i, _P]),
         "fft3_plan_execute_pass": (i, [_P, i, _P, _P, _P]),
@@ -120,7 +124,7 @@ def _check(rc: int) -> int:
 
 
 def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mode=0, tc_stages=0,
-                 slab_chunk=0, slab_lines=0) -> fft3_options:
+                 slab_chunk=0, slab_lines=0, layout=0) -> fft3_options:
     o = fft3_options()
     o.variant = int(variant)
     o.radix_order = int(radix_order)
@@ -131,6 +135,7 @@ def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mo
     o.tc_stages = int(tc_stages)
     o.slab_chunk = int(slab_chunk)
     o.slab_lines = int(slab_lines)
+    o.layout = int(layout)
     return o
 
 
@@ -228,6 +233,20 @@ def fft3_plan_schedule(n0, n1, n2, batch=1, dtype=FFT3_C64_FP32, decomposition=F
     buf = ctypes.create_string_buffer(n + 1)
     _check(L.fft3_plan_schedule(n0, n1, n2, batch, dtype, decomposition, direction, po, buf, n + 1))
     return json.loads(buf.value.decode())
+
+
+def fft3_layout_positions(layout: int, n0: int, n1: int, n2: int, batch: int = 1, idx=None):
+    """Positions (int64 numpy array) of natural flat indices `idx` (default:
+    all of them, in order) in the buffer of a permuted layout."""
+    import numpy as np
+    if idx is None:
+        idx = np.arange(n0 * n1 * n2 * batch, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    pos = np.empty_like(idx)
+    p64 = ctypes.POINTER(ctypes.c_int64)
+    _check(load().fft3_layout_positions(layout, n0, n1, n2, batch, idx.ctypes.data_as(p64),
+                                        pos.ctypes.data_as(p64), idx.size))
+    return pos
 
 
 def fft3_factorize(n: int, order: int = 0) -> list[int]:

@@ -257,3 +257,72 @@ def test_tensor_core_schedule():
     assert _kinds(s) == ["line_contig", "line_strided_stream_tc", "line_strided"]
     with pytest.raises(fft3.Fft3Error):
         fft3.fft3_plan_schedule(64, 64, 64, 1, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_SLAB_PENCIL, -1)
+
+
+@pytest.mark.parametrize("layout,name,shape,batch", [
+    (fft3.FFT3_LAYOUT_ROTATED, "rotated", (2, 3, 4), 1), (fft3.FFT3_LAYOUT_ROTATED, "rotated", (30, 25, 18), 3),
+    (fft3.FFT3_LAYOUT_PENCILS, "pencils", (32, 2, 3), 1), (fft3.FFT3_LAYOUT_PENCILS, "pencils", (64, 48, 10), 1)])
+def test_layout_positions_match_oracle(layout, name, shape, batch):
+    """The exported positions of a permuted spectrum (Section 2.4) equal the
+    oracle's, bit for bit, for every element; the natural layout is the identity."""
+    import oracle
+    n0, n1, n2 = shape
+    got = fft3.fft3_layout_positions(layout, n0, n1, n2, batch)
+    assert np.array_equal(got, oracle.layout_positions(name, n0, n1, n2, batch))
+    nat = fft3.fft3_layout_positions(fft3.FFT3_LAYOUT_NATURAL, n0, n1, n2, batch)
+    assert np.array_equal(nat, np.arange(n0 * n1 * n2 * batch))
+    some = np.array([n0 * n1 * n2 * batch - 1, 0, 7], dtype=np.int64)
+    assert np.array_equal(fft3.fft3_layout_positions(layout, n0, n1, n2, batch, some), got[some])
+
+
+def test_layout_positions_errors():
+    with pytest.raises(fft3.Fft3Error):
+        fft3.fft3_layout_positions(fft3.FFT3_LAYOUT_PENCILS, 24, 4, 4)          # n0 % 16
+    with pytest.raises(fft3.Fft3Error):
+        fft3.fft3_layout_positions(fft3.FFT3_LAYOUT_PENCILS, 32, 4, 4, 2)       # batch
+    with pytest.raises(fft3.Fft3Error):
+        fft3.fft3_layout_positions(3, 4, 4, 4)                                  # no such layout
+    with pytest.raises(fft3.Fft3Error):
+        fft3.fft3_layout_positions(fft3.FFT3_LAYOUT_ROTATED, 4, 4, 4, 1, np.array([64], dtype=np.int64))
+
+
+def test_schedule_permuted_layouts():
+    """Forward plans leave out the last redistribution; inverse plans start
+    from the permuted layout and end in natural order."""
+    F, I = fft3.FFT3_FORWARD, fft3.FFT3_INVERSE
+    s = fft3.fft3_plan_schedule(64, 128, 256, 2, 0, fft3.FFT3_PENCIL3, F,
+                                fft3.make_options(layout=fft3.FFT3_LAYOUT_ROTATED))
+    assert s["layout"] == "rotated"
+    assert _kinds(s) == ["line_contig_rotate", "line_contig_rotate", "line_contig"]
+    assert [(p["src"], p["dst"]) for p in s["passes"]] == [("in", "out"), ("out", "workspace"), ("workspace", "out")]
+    g = s["passes"][2]["geom"]
+    assert (g["ij"], g["ic"], g["ia"], g["ok"], g["oc"], g["oa"]) == (1, 256, 256 * 64, 1, 256, 256 * 64)
+    s = fft3.fft3_plan_schedule(64, 128, 256, 2, 0, fft3.FFT3_PENCIL3, I,
+                                fft3.make_options(layout=fft3.FFT3_LAYOUT_ROTATED))
+    assert _kinds(s)[0] == "line_contig_rotate" and s["passes"][0]["line"]["n"] == 256
+    assert [(p["src"], p["dst"]) for p in s["passes"]] == [("in", "workspace"), ("workspace", "out"), ("out", "out")]
+    for decomp in (fft3.FFT3_PENCIL3, fft3.FFT3_SLAB_PENCIL, fft3.FFT3_AUTO):
+        s = fft3.fft3_plan_schedule(1024, 1024, 512, 1, 0, decomp, F,
+                                    fft3.make_options(layout=fft3.FFT3_LAYOUT_PENCILS))
+        assert _kinds(s) == ["line_contig", "line_strided_stream", "line_strided_stream"]
+        gz = s["passes"][2]["geom"]
+        assert (gz["ij"], gz["ia"], gz["ib"]) == (gz["ok"], gz["oa"], gz["ob"]) == (16 * 1024, 16, 16 * 1024 * 512)
+    s = fft3.fft3_plan_schedule(1024, 1024, 512, 1, 0, fft3.FFT3_SLAB_PENCIL, F,
+                                fft3.make_options(layout=fft3.FFT3_LAYOUT_PENCILS, slab_mode=5))
+    assert _kinds(s) == ["slab_l2_blocked", "line_strided_stream"]
+    s = fft3.fft3_plan_schedule(1024, 1024, 512, 1, 0, fft3.FFT3_PENCIL3, I,
+                                fft3.make_options(layout=fft3.FFT3_LAYOUT_PENCILS))
+    assert _kinds(s) == ["line_strided_stream", "line_strided_stream", "line_contig"]
+    assert [(p["src"], p["dst"]) for p in s["passes"]] == [("in", "workspace"), ("workspace", "out"), ("out", "out")]
+    gy = s["passes"][1]["geom"]
+    assert (gy["ij"], gy["ia"], gy["ib"], gy["ok"], gy["oa"], gy["ob"]) == \
+        (16, 16 * 1024 * 512, 16 * 1024, 1024, 16, 1024 * 1024)
+    bad = [((64, 48, 96, 1), fft3.FFT3_VOLUMETRIC, 0, fft3.FFT3_LAYOUT_ROTATED),
+           ((64, 1, 96, 1), fft3.FFT3_PENCIL3, 0, fft3.FFT3_LAYOUT_ROTATED),
+           ((24, 48, 96, 1), fft3.FFT3_PENCIL3, 0, fft3.FFT3_LAYOUT_PENCILS),
+           ((64, 48, 96, 2), fft3.FFT3_PENCIL3, 0, fft3.FFT3_LAYOUT_PENCILS),
+           ((64, 48, 96, 1), fft3.FFT3_PENCIL3, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_LAYOUT_ROTATED),
+           ((64, 48, 96, 1), fft3.FFT3_PENCIL3, 0, 7)]
+    for dims, decomp, dtype, layout in bad:
+        with pytest.raises(fft3.Fft3Error):
+            fft3.fft3_plan_schedule(*dims, dtype, decomp, F, fft3.make_options(layout=layout))

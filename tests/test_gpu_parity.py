@@ -267,3 +267,28 @@ def test_tma_strided_pass(shape, batch, direction):
     kinds = [p["kind"] for p in plan.describe()["passes"]]
     if shape != (40, 40, 40):
         assert "line_strided_tma" in kinds
+
+
+@pytest.mark.parametrize("layout,shape,batch,decomp,extra", [
+    (fft3.FFT3_LAYOUT_ROTATED, (64, 48, 96), 1, P, {}),
+    (fft3.FFT3_LAYOUT_ROTATED, (30, 25, 18), 3, P, {}),
+    (fft3.FFT3_LAYOUT_ROTATED, (1024, 16, 9), 1, fft3.FFT3_AUTO, {}),
+    (fft3.FFT3_LAYOUT_PENCILS, (64, 48, 10), 1, P, {}),
+    (fft3.FFT3_LAYOUT_PENCILS, (256, 256, 6), 1, S, {}),
+    (fft3.FFT3_LAYOUT_PENCILS, (1024, 1024, 4), 1, fft3.FFT3_AUTO, {}),
+    (fft3.FFT3_LAYOUT_PENCILS, (512, 512, 3), 1, S, {"slab_mode": 5})])
+def test_permuted_layouts(layout, shape, batch, decomp, extra):
+    """Permuted spectrum (Section 2.4): a forward plan's output read back through
+    the oracle's positions is the DFT; an inverse plan fed the permuted layout
+    returns the natural-order inverse DFT."""
+    n0, n1, n2 = shape
+    name = {fft3.FFT3_LAYOUT_ROTATED: "rotated", fft3.FFT3_LAYOUT_PENCILS: "pencils"}[layout]
+    pos = oracle.layout_positions(name, n0, n1, n2, batch)
+    x, got, plan = run_plan(shape, batch, decomp, FWD, seed=n2 + batch, layout=layout, **extra)
+    assert plan.describe()["layout"] == name
+    assert_parity(x, got.ravel()[pos].reshape(got.shape), shape, batch, FWD)
+    xs = synth.uniform_c64((batch, n2, n1, n0), n2 + batch + 1)
+    buf = np.empty(xs.size, dtype=np.complex64)
+    buf[pos] = xs.ravel()
+    _, got_i, _ = run_plan(shape, batch, decomp, INV, x=buf.reshape(xs.shape), layout=layout, **extra)
+    assert_parity(xs, got_i, shape, batch, INV)

@@ -277,6 +277,39 @@ def test_rotation_three_times_is_identity_and_explicit():
     assert r1[1] == 12
 
 
+def test_golden_layout_positions():
+    """The permuted spectrum orders (Section 2.4) against hand-worked entries."""
+    rows = open(os.path.join(GOLDEN, "layout_positions_small.txt")).read().split("\n")
+    seen = set()
+    for line in rows:
+        if not line.strip() or line.startswith("#"):
+            continue
+        name, *v = line.split()
+        n0, n1, n2, batch, k0, k1, k2, b, want = map(int, v)
+        pos = oracle.layout_positions(name, n0, n1, n2, batch)
+        N = n0 * n1 * n2
+        assert pos[k0 + n0 * (k1 + n1 * k2) + N * b] == want
+        seen.add(name)
+    assert seen == {"rotated", "pencils"}
+
+
+@pytest.mark.parametrize("layout,shape,batch", [("rotated", (2, 3, 4), 1), ("rotated", (5, 3, 6), 2),
+                                                ("pencils", (32, 2, 3), 1), ("pencils", (48, 5, 7), 1)])
+def test_layout_positions_are_permutations_with_contiguous_lines(layout, shape, batch):
+    """Every layout is a bijection onto the buffer; in the rotated order the z
+    lines are contiguous, in the pencils order a z line steps by 16*n1 and a
+    16-column row of x is contiguous."""
+    n0, n1, n2 = shape
+    pos = oracle.layout_positions(layout, n0, n1, n2, batch)
+    assert np.array_equal(np.sort(pos), np.arange(n0 * n1 * n2 * batch))
+    p = pos.reshape(batch, n2, n1, n0)
+    if layout == "rotated":
+        assert np.all(np.diff(p, axis=1) == 1)
+    else:
+        assert np.all(np.diff(p, axis=1) == 16 * n1)
+        assert np.all(np.diff(p.reshape(batch, n2, n1, n0 // 16, 16), axis=-1) == 1)
+
+
 # --------------------------------------------------------------- roots --- #
 def test_roots_closed_forms():
     n = 8
