@@ -396,8 +396,12 @@ def main():
             extras["forward_plus_inverse_ms"] = {"error": str(e)}
         try:
             extras["batched_4096_uneven"] = bench_batched(fft3, synth, torch, hbm)
-        except Exception as e:
+        except Exception as e:  # noqa: BLE001
             extras["batched_4096_uneven"] = {"error": str(e)}
+        try:
+            extras["complex128_fp64"] = c128_table(fft3, synth, torch)
+        except Exception as e:  # noqa: BLE001
+            extras["complex128_fp64"] = {"error": str(e)}
         if n0 == n1 == n2 == 1024:
             try:
                 extras["smaller_cubes"] = size_table(fft3, synth, torch, (256, 512), decomp_map)
@@ -473,6 +477,34 @@ def size_table(fft3, synth, torch, sizes, decomp_map):
                 p.close()
             row[name] = ent
         table[f"{n}^3"] = row
+        del x, out
+    return table
+
+
+def c128_table(fft3, synth, torch, sizes=(256, 512), reps=5):
+    """complex128 (FP64 butterflies and twiddles) forward ms of n^3, out of
+    place, CUDA events over `reps` back-to-back executions; GFLOP/s in the
+    5 N log2 N convention (the path is bound by FP64 arithmetic)."""
+    import math
+    table = {}
+    st = torch.cuda.current_stream()
+    for n in sizes:
+        x = torch.from_numpy(synth.uniform_c128((n, n, n), 3)).to("cuda")
+        out = torch.empty_like(x)
+        p = fft3.Plan(n, n, n, 1, decomposition=fft3.FFT3_PENCIL3, dtype=fft3.FFT3_C128_FP64)
+        p.execute(x, out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            p.execute(x, out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        assert p.check() == 0, fft3.last_error()
+        ms = e0.elapsed_time(e1) / reps
+        N = n ** 3
+        table[f"{n}^3"] = {"fwd_ms": ms, "gflops": 5 * N * math.log2(N) / ms / 1e6,
+                           "hbm_gbs": 3 * 2 * 16 * N / ms / 1e6}
+        p.close()
         del x, out
     return table
 

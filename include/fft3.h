@@ -42,10 +42,16 @@ extern "C" {
 
 typedef struct fft3_plan_s *fft3_plan; /* opaque; owned by the library */
 
-/* arithmetic of the line transforms; storage is always complex64 */
+/* arithmetic of the line transforms; storage is complex64 except for FFT3_C128_FP64 */
 enum fft3_dtype {
     FFT3_C64_FP32 = 0,         /* FP32 CUDA-core butterflies */
-    FFT3_C64_SPLITBF16_TC = 1  /* radix-16 sub-DFTs as split-BF16 tensor-core GEMMs, FP32 accumulate */
+    FFT3_C64_SPLITBF16_TC = 1, /* radix-16 sub-DFTs as split-BF16 tensor-core GEMMs, FP32 accumulate */
+    FFT3_C128_FP64 = 2         /* complex128 arrays (interleaved FP64 re, im; 16 bytes per element),
+                                  FP64 butterflies and FP64 twiddles: the paper's own precision
+                                  (Section 4).  Natural pencil-pencil-pencil schedule of runtime-radix
+                                  passes (slab-pencil and FFT3_AUTO lower to it; volumetric, rotated,
+                                  blocked and permuted layouts are refused).  Buffers hold
+                                  n0*n1*n2*batch complex128 values */
 };
 
 enum fft3_decomp {

@@ -90,7 +90,7 @@ int fft3_time_plan(int n0, int n1, int n2, int batch, int dtype, int decompositi
     if (rc)
         return rc;
     Scratch s;
-    rc = s.ensure((size_t)n0 * n1 * n2 * batch * 8);
+    rc = s.ensure((size_t)n0 * n1 * n2 * batch * (dtype == FFT3_C128_FP64 ? 16 : 8));
     if (!rc)
         rc = time_plan(p, s.in, s.out, reps, ms);
     fft3_plan_destroy(p);
@@ -103,7 +103,7 @@ int fft3_time_candidates(int n0, int n1, int n2, int batch, int dtype, int direc
     if (count < 1 || !decompositions || !opts || !ms_out || reps < 1)
         return fail(FFT3_ERR_INVALID_ARG, "bad argument to fft3_time_candidates");
     Scratch s;
-    int rc = s.ensure((size_t)n0 * n1 * n2 * batch * 8);
+    int rc = s.ensure((size_t)n0 * n1 * n2 * batch * (dtype == FFT3_C128_FP64 ? 16 : 8));
     if (rc)
         return rc;
     for (int i = 0; i < count; ++i) {
@@ -155,7 +155,7 @@ int fft3_autotune(int n0, int n1, int n2, int batch, int dtype, int direction, i
         add(FFT3_VOLUMETRIC, 0, order, 0, 0, 2, 2, 2);
     }
     Scratch s;
-    int rc = s.ensure((size_t)n0 * n1 * n2 * batch * 8);
+    int rc = s.ensure((size_t)n0 * n1 * n2 * batch * (dtype == FFT3_C128_FP64 ? 16 : 8));
     if (rc)
         return rc;
     float bt = 3.4e38f;

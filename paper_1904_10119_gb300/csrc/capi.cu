@@ -15,6 +15,7 @@
 
 namespace fft3 {
 __global__ void k_pass_g(PassArgs a);
+__global__ void k_pass_g64(PassArgs a);
 __global__ void k_slab(PassArgs a);
 __global__ void k_vol(PassArgs a);
 __global__ void k_probe_pass(PassArgs a);
@@ -228,7 +229,7 @@ static int build_launches(fft3_plan_s *P)
         }
         if (base < 0)
             base = 0;
-        a.tw = P->d_tw + base;
+        a.tw = P->esize == 16 ? (const float2 *)((const double2 *)P->d_tw + base) : P->d_tw + base;
         a.tw_len = (int)(end - base);
         if (p.tw_seg[0] >= 0)
             a.L[0] = to_rt(p.line, (int)(s.tw[p.tw_seg[0]].off - base));
@@ -255,6 +256,7 @@ static int build_launches(fft3_plan_s *P)
             L.tma = true;
             break;
         case PK_G: L.func = (const void *)&k_pass_g; break;
+        case PK_G64: L.func = (const void *)&k_pass_g64; break;
         case PK_SLAB:
             L.func = (const void *)&k_slab;
             L.probe_g = natural_x(s);
@@ -332,7 +334,7 @@ static int build_launches(fft3_plan_s *P)
             int64_t g = std::min<int64_t>(ncl, p.ntiles);
             L.grid = dim3((unsigned)(std::max<int64_t>(1, g) * p.p));
         } else if (p.kind == PK_COPY) {
-            L.grid = dim3((unsigned)std::min<int64_t>(4096, (P->elems + 255) / 256 + 1));
+            L.grid = dim3((unsigned)std::min<int64_t>(4096, (P->elems * (P->esize / 8) + 255) / 256 + 1));
             L.block = dim3(256);
         } else if (p.kind == PK_SLABL2 || p.kind == PK_SLABBLK) {
             rc = occupancy_grid(L.func, L.block.x, L.smem, 0, P->device, &L.grid);
@@ -392,8 +394,9 @@ static int generate_twiddles(fft3_plan_s *P)
 {
     const Schedule &s = P->sched;
     int64_t total = std::max<int64_t>(16, s.tw_total);
-    CUDA_TRY(cudaMalloc(&P->d_tw, total * sizeof(float2)));
-    CUDA_TRY(cudaMemset(P->d_tw, 0, total * sizeof(float2)));
+    const bool fp64 = P->esize == 16; // complex128: the FP64 values are the table
+    CUDA_TRY(cudaMalloc(&P->d_tw, total * P->esize));
+    CUDA_TRY(cudaMemset(P->d_tw, 0, total * P->esize));
     size_t maxm = 1;
     for (const TwSeg &sg : s.tw)
         maxm = std::max(maxm, sg.m.size());
@@ -403,8 +406,9 @@ static int generate_twiddles(fft3_plan_s *P)
         cudaError_t e = cudaMemcpy(d_m, sg.m.data(), sg.m.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) {
             int blocks = (int)std::min<int64_t>(1024, ((int64_t)sg.m.size() + 255) / 256);
-            k_roots<<<std::max(1, blocks), 256>>>(sg.n, FFT3_FORWARD, d_m, (int64_t)sg.m.size(), nullptr,
-                                                  P->d_tw + sg.off);
+            k_roots<<<std::max(1, blocks), 256>>>(sg.n, FFT3_FORWARD, d_m, (int64_t)sg.m.size(),
+                                                  fp64 ? (double *)P->d_tw + 2 * sg.off : nullptr,
+                                                  fp64 ? nullptr : P->d_tw + sg.off);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) {
@@ -502,6 +506,7 @@ int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int d
         return rc;
     }
     P->elems = (int64_t)n0 * n1 * n2 * batch;
+    P->esize = dtype == FFT3_C128_FP64 ? 16 : 8;
     cudaError_t e = cudaMalloc(&P->d_err, sizeof(unsigned));
     if (e == cudaSuccess)
         e = cudaMemset(P->d_err, 0, sizeof(unsigned));
@@ -513,7 +518,7 @@ int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int d
     if (!rc)
         rc = build_launches(P);
     if (!rc && P->sched.need_ws) {
-        P->ws_bytes = (size_t)P->elems * sizeof(float2);
+        P->ws_bytes = (size_t)P->elems * P->esize;
         e = cudaMalloc(&P->d_ws, P->ws_bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -664,7 +669,7 @@ int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream)
         a.in = buf_ptr(p, L.src, in, out);
         a.out = buf_ptr(p, L.dst, in, out);
         if (L.kind == PK_COPY) {
-            k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems);
+            k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems * (p->esize / 8));
             CUDA_TRY(cudaGetLastError());
             continue;
         }
@@ -679,6 +684,8 @@ int fft3_plan_probe_layout(fft3_plan p, const void *in, void *out, int npasses, 
 {
     if (!p || !in || !out || in == out)
         return fail(FFT3_ERR_INVALID_ARG, "null plan or buffer, or in == out");
+    if (p->esize != 8)
+        return fail(FFT3_ERR_INVALID_ARG, "the layout probe moves complex64 elements");
     cudaStream_t st = (cudaStream_t)stream;
     int count = (int)p->launches.size();
     if (npasses >= 0 && npasses < count)
@@ -692,7 +699,7 @@ int fft3_plan_probe_layout(fft3_plan p, const void *in, void *out, int npasses, 
         last_dst = L.dst;
         if (L.kind == PK_COPY || a.in == a.out) {
             if (a.in != a.out) {
-                k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems);
+                k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems * (p->esize / 8));
                 CUDA_TRY(cudaGetLastError());
             }
             continue; // an in-place pass moves nothing
@@ -733,7 +740,7 @@ int fft3_plan_execute_pass(fft3_plan p, int k, const void *in, void *out, void *
     a.in = buf_ptr(p, L.src, in, out);
     a.out = buf_ptr(p, L.dst, in, out);
     if (L.kind == PK_COPY) {
-        k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems);
+        k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems * (p->esize / 8));
         CUDA_TRY(cudaGetLastError());
         return FFT3_OK;
     }
@@ -744,7 +751,7 @@ int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *str
 {
     if (!p || !h_in || !h_out)
         return fail(FFT3_ERR_INVALID_ARG, "null plan or buffer");
-    size_t bytes = (size_t)p->elems * sizeof(float2);
+    size_t bytes = (size_t)p->elems * p->esize;
     if (!p->d_stage_in) {
         CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
         CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
@@ -769,7 +776,7 @@ int fft3_plan_execute_host_pipelined(fft3_plan p, const void *const *h_in, void 
             return fail(FFT3_ERR_INVALID_ARG, "null host buffer in the pointer arrays");
     if (count == 0)
         return FFT3_OK;
-    const size_t bytes = (size_t)p->elems * sizeof(float2);
+    const size_t bytes = (size_t)p->elems * p->esize;
     if (!p->d_stage_in) {
         CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
         CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));

@@ -68,7 +68,8 @@ struct fft3_plan_s {
     fft3::Schedule sched;
     int device = 0;
     int64_t elems = 0; // complex elements per array
-    float2 *d_tw = nullptr;
+    int esize = 8;     // bytes per complex element (16 for complex128)
+    float2 *d_tw = nullptr; // twiddle table (double2 entries for complex128)
     float2 *d_ws = nullptr;
     size_t ws_bytes = 0;
     int *d_counters = nullptr;

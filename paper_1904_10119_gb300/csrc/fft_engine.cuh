@@ -39,6 +39,33 @@ __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.
 __device__ __forceinline__ float2 mul_pi(float2 a) { return make_float2(-a.y, a.x); } // a * (+i)
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
+// The same operations in FP64 (complex128 path).
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 mul_mi(double2 a) { return make_double2(a.y, -a.x); }
+__device__ __forceinline__ double2 mul_pi(double2 a) { return make_double2(-a.y, a.x); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// Scalar type of a complex type, and construction / fused multiply-add in it.
+template <class C>
+struct Cx;
+template <>
+struct Cx<float2> {
+    using S = float;
+    __device__ __forceinline__ static float2 make(float r, float i) { return make_float2(r, i); }
+    __device__ __forceinline__ static float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+};
+template <>
+struct Cx<double2> {
+    using S = double;
+    __device__ __forceinline__ static double2 make(double r, double i) { return make_double2(r, i); }
+    __device__ __forceinline__ static double fma_(double a, double b, double c) { return fma(a, b, c); }
+};
+
 // cos(2 pi m / 16) and sin(2 pi m / 16) from the first-octant values.
 constexpr double kC16 = 0.923879532511286756128183189396788933; // cos(pi/8)
 constexpr double kS16 = 0.382683432365089771728459984030398866; // sin(pi/8)
@@ -54,25 +81,27 @@ __host__ __device__ constexpr double cos16(int m)
 __host__ __device__ constexpr double sin16(int m) { return cos16(m - 4); }
 
 // a * w_R^M with w_R = exp(-2 pi i / R), R in {2, 4, 8, 16}, M known at compile time.
-template <int R, int M>
-__device__ __forceinline__ float2 mul_w(float2 a)
+template <int R, int M, class C>
+__device__ __forceinline__ C mul_w(C a)
 {
+    using X = Cx<C>;
+    using S = typename X::S;
     constexpr int m16 = ((M % R) + R) % R * (16 / R);
     if constexpr (m16 == 0) {
         return a;
     } else if constexpr (m16 == 4) {
         return mul_mi(a);
     } else if constexpr (m16 == 8) {
-        return make_float2(-a.x, -a.y);
+        return X::make(-a.x, -a.y);
     } else if constexpr (m16 == 12) {
         return mul_pi(a);
     } else if constexpr (m16 == 2 || m16 == 6 || m16 == 10 || m16 == 14) {
         // (c - i s) with |c| = |s| = sqrt(1/2)
-        constexpr float c = (float)cos16(m16), s = (float)sin16(m16);
-        return make_float2((a.x * c + a.y * s), (a.y * c - a.x * s));
+        constexpr S c = (S)cos16(m16), s = (S)sin16(m16);
+        return X::make((a.x * c + a.y * s), (a.y * c - a.x * s));
     } else {
-        constexpr float c = (float)cos16(m16), s = (float)sin16(m16);
-        return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+        constexpr S c = (S)cos16(m16), s = (S)sin16(m16);
+        return X::make(X::fma_(a.x, c, a.y * s), X::fma_(a.y, c, -a.x * s));
     }
 }
 
@@ -83,9 +112,10 @@ struct Bfly;
 
 template <>
 struct Bfly<2> {
-    __device__ __forceinline__ static void run(float2 *v)
+    template <class C>
+    __device__ __forceinline__ static void run(C *v)
     {
-        float2 a = v[0], b = v[1];
+        C a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
     }
@@ -93,10 +123,11 @@ struct Bfly<2> {
 
 template <>
 struct Bfly<4> {
-    __device__ __forceinline__ static void run(float2 *v)
+    template <class C>
+    __device__ __forceinline__ static void run(C *v)
     {
-        float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        float2 t2 = cadd(v[1], v[3]), t3 = mul_mi(csub(v[1], v[3]));
+        C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        C t2 = cadd(v[1], v[3]), t3 = mul_mi(csub(v[1], v[3]));
         v[0] = cadd(t0, t2);
         v[2] = csub(t0, t2);
         v[1] = cadd(t1, t3);
@@ -108,10 +139,11 @@ struct Bfly<4> {
 // w_8^{i0 k1}, DFT_2 across i0, output y[k1 + 4 k0].
 template <>
 struct Bfly<8> {
-    __device__ __forceinline__ static void run(float2 *v)
+    template <class C>
+    __device__ __forceinline__ static void run(C *v)
     {
-        float2 e[4] = {v[0], v[2], v[4], v[6]};
-        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
         Bfly<4>::run(e);
         Bfly<4>::run(o);
         o[1] = mul_w<8, 1>(o[1]);
@@ -128,9 +160,10 @@ struct Bfly<8> {
 // 16 = 4 * 4 (Eq. ct with n0 = n1 = 4).
 template <>
 struct Bfly<16> {
-    __device__ __forceinline__ static void run(float2 *v)
+    template <class C>
+    __device__ __forceinline__ static void run(C *v)
     {
-        float2 t[4][4];
+        C t[4][4];
 #pragma unroll
         for (int i0 = 0; i0 < 4; ++i0) {
 #pragma unroll
@@ -149,7 +182,7 @@ struct Bfly<16> {
         t[3][3] = mul_w<16, 9>(t[3][3]);
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
-            float2 c[4] = {t[0][k1], t[1][k1], t[2][k1], t[3][k1]};
+            C c[4] = {t[0][k1], t[1][k1], t[2][k1], t[3][k1]};
             Bfly<4>::run(c);
 #pragma unroll
             for (int k0 = 0; k0 < 4; ++k0)
@@ -158,42 +191,64 @@ struct Bfly<16> {
     }
 };
 
+// A constant in the scalar type: the float literal for FP32 (as written), the
+// double literal for FP64.
+template <class S>
+__host__ __device__ constexpr S kpick(float f, double d)
+{
+    if constexpr (sizeof(S) == 4)
+        return f;
+    else
+        return (S)d;
+}
+
 // DFT_3: w_3 = -1/2 - i sqrt(3)/2.
 template <>
 struct Bfly<3> {
-    __device__ __forceinline__ static void run(float2 *v)
+    template <class C>
+    __device__ __forceinline__ static void run(C *v)
     {
-        constexpr float s3 = 0.866025403784438646763723170752936183f; // sin(2 pi / 3)
-        float2 s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
-        float2 a = make_float2(fmaf(-0.5f, s.x, v[0].x), fmaf(-0.5f, s.y, v[0].y));
-        float2 b = cscale(d, s3);
+        using X = Cx<C>;
+        using S = typename X::S;
+        constexpr S s3 = kpick<S>(0.866025403784438646763723170752936183f,
+                                  0.866025403784438646763723170752936183); // sin(2 pi / 3)
+        C s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        C a = X::make(X::fma_((S)-0.5, s.x, v[0].x), X::fma_((S)-0.5, s.y, v[0].y));
+        C b = X::make(d.x * s3, d.y * s3);
         v[0] = cadd(v[0], s);
-        v[1] = make_float2(a.x + b.y, a.y - b.x); // a - i b
-        v[2] = make_float2(a.x - b.y, a.y + b.x); // a + i b
+        v[1] = X::make(a.x + b.y, a.y - b.x); // a - i b
+        v[2] = X::make(a.x - b.y, a.y + b.x); // a + i b
     }
 };
 
 // DFT_5 with the conjugate-pair form: y_1,4 = a1 -/+ i b1, y_2,3 = a2 -/+ i b2.
 template <>
 struct Bfly<5> {
-    __device__ __forceinline__ static void run(float2 *v)
+    template <class C>
+    __device__ __forceinline__ static void run(C *v)
     {
-        constexpr float c1 = 0.309016994374947424102293417182819059f;  // cos(2 pi/5)
-        constexpr float c2 = -0.809016994374947424102293417182819059f; // cos(4 pi/5)
-        constexpr float s1 = 0.951056516295153572116439333379382143f;  // sin(2 pi/5)
-        constexpr float s2 = 0.587785252292473129168705954639072769f;  // sin(4 pi/5)
-        float2 x0 = v[0];
-        float2 sa = cadd(v[1], v[4]), da = csub(v[1], v[4]);
-        float2 sb = cadd(v[2], v[3]), db = csub(v[2], v[3]);
-        float2 a1 = make_float2(x0.x + c1 * sa.x + c2 * sb.x, x0.y + c1 * sa.y + c2 * sb.y);
-        float2 a2 = make_float2(x0.x + c2 * sa.x + c1 * sb.x, x0.y + c2 * sa.y + c1 * sb.y);
-        float2 b1 = make_float2(s1 * da.x + s2 * db.x, s1 * da.y + s2 * db.y);
-        float2 b2 = make_float2(s2 * da.x - s1 * db.x, s2 * da.y - s1 * db.y);
-        v[0] = make_float2(x0.x + sa.x + sb.x, x0.y + sa.y + sb.y);
-        v[1] = make_float2(a1.x + b1.y, a1.y - b1.x);
-        v[4] = make_float2(a1.x - b1.y, a1.y + b1.x);
-        v[2] = make_float2(a2.x + b2.y, a2.y - b2.x);
-        v[3] = make_float2(a2.x - b2.y, a2.y + b2.x);
+        using X = Cx<C>;
+        using S = typename X::S;
+        constexpr S c1 = kpick<S>(0.309016994374947424102293417182819059f,
+                                  0.309016994374947424102293417182819059);  // cos(2 pi/5)
+        constexpr S c2 = kpick<S>(-0.809016994374947424102293417182819059f,
+                                  -0.809016994374947424102293417182819059); // cos(4 pi/5)
+        constexpr S s1 = kpick<S>(0.951056516295153572116439333379382143f,
+                                  0.951056516295153572116439333379382143);  // sin(2 pi/5)
+        constexpr S s2 = kpick<S>(0.587785252292473129168705954639072769f,
+                                  0.587785252292473129168705954639072769);  // sin(4 pi/5)
+        C x0 = v[0];
+        C sa = cadd(v[1], v[4]), da = csub(v[1], v[4]);
+        C sb = cadd(v[2], v[3]), db = csub(v[2], v[3]);
+        C a1 = X::make(x0.x + c1 * sa.x + c2 * sb.x, x0.y + c1 * sa.y + c2 * sb.y);
+        C a2 = X::make(x0.x + c2 * sa.x + c1 * sb.x, x0.y + c2 * sa.y + c1 * sb.y);
+        C b1 = X::make(s1 * da.x + s2 * db.x, s1 * da.y + s2 * db.y);
+        C b2 = X::make(s2 * da.x - s1 * db.x, s2 * da.y - s1 * db.y);
+        v[0] = X::make(x0.x + sa.x + sb.x, x0.y + sa.y + sb.y);
+        v[1] = X::make(a1.x + b1.y, a1.y - b1.x);
+        v[4] = X::make(a1.x - b1.y, a1.y + b1.x);
+        v[2] = X::make(a2.x + b2.y, a2.y - b2.x);
+        v[3] = X::make(a2.x - b2.y, a2.y + b2.x);
     }
 };
 
@@ -321,15 +376,15 @@ struct EngineSplitFirst<N, T, Radices<R, Rest...>, BAR, NT> {
 // --------------------------------------------------- runtime stage path -- //
 // Same stage with R known at compile time but n, T, NS at run time; used by
 // the generic kernels whose radix list is data (any 2*3*5-smooth length).
-template <int R, class Src, class Dst>
+template <int R, class Src, class Dst, class C>
 __device__ __forceinline__ void stage_rt(int n, int T, int NS, int t, const Src &src, const Dst &dst,
-                                         const float2 *tw, bool active)
+                                         const C *tw, bool active)
 {
     const int NB = n / R;
     if (!active)
         return;
     for (int q = t; q < NB; q += T) {
-        float2 v[R];
+        C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r)
             v[r] = src(q + r * NB);
@@ -347,9 +402,9 @@ __device__ __forceinline__ void stage_rt(int n, int T, int NS, int t, const Src 
     }
 }
 
-template <class Src, class Dst>
+template <class Src, class Dst, class C>
 __device__ __forceinline__ void stage_rt_dispatch(int R, int n, int T, int NS, int t, const Src &src,
-                                                  const Dst &dst, const float2 *tw, bool active)
+                                                  const Dst &dst, const C *tw, bool active)
 {
     switch (R) {
     case 2: stage_rt<2>(n, T, NS, t, src, dst, tw, active); break;

@@ -8,16 +8,23 @@
 namespace fft3 {
 
 // ------------------------------------------------------------ k_pass_g -- //
-__global__ void k_pass_g(PassArgs a)
+// One tile of `lpt` lines staged through shared memory (whichever mapping
+// keeps the global accesses coalesced), the runtime radix stages, the tile
+// stored back.  C = float2 (k_pass_g) or double2 (k_pass_g64: the complex128
+// path, whose arrays and twiddle table hold double2).
+template <class C>
+__device__ __forceinline__ void pass_g_body(const PassArgs &a, const C *in, C *out, const C *twg)
 {
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) unsigned char g_smem_raw[];
+    C *smem = reinterpret_cast<C *>(g_smem_raw);
     const LineRt &L = a.L[0];
     const int n = L.n;
     const int P = line_pitch(n);
-    float2 *tw = smem;
-    float2 *b0 = smem + tw_slots(a.tw_len);
-    float2 *b1 = b0 + a.lpt * P;
-    load_twiddles(tw, a.tw, a.tw_len);
+    C *tw = smem;
+    C *b0 = smem + tw_slots(a.tw_len);
+    C *b1 = b0 + a.lpt * P;
+    for (int i = threadIdx.x; i < a.tw_len; i += blockDim.x)
+        tw[i] = twg[i];
     const bool conj = a.conj != 0;
     const bool in_lines = a.g.ij == 1;  // lines contiguous in the input
     const bool out_lines = a.g.ok == 1; // lines contiguous in the output
@@ -26,29 +33,37 @@ __global__ void k_pass_g(PassArgs a)
         __syncthreads();
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, lpt);
         const int64_t nval = min((int64_t)lpt, a.g.C - id.c0);
-        const float2 *ib = a.in + id.c0 * a.g.ic + id.a * a.g.ia + id.b * a.g.ib;
+        const C *ib = in + id.c0 * a.g.ic + id.a * a.g.ia + id.b * a.g.ib;
         for (int e = threadIdx.x; e < lpt * n; e += blockDim.x) {
             int l, j;
             if (in_lines) { l = e / n; j = e - l * n; }
             else { l = e % lpt; j = e / lpt; }
-            float2 v = make_float2(0.f, 0.f);
+            C v = Cx<C>::make(0, 0);
             if (l < nval)
                 v = ib[l * a.g.ic + (int64_t)j * a.g.ij];
             b0[l * P + padpos(j)] = conj ? cconj(v) : v;
         }
         __syncthreads();
-        const float2 *res = run_stages_lines(L, lpt, P, b0, b1, tw + L.tw_off);
-        float2 *ob = a.out + id.c0 * a.g.oc + id.a * a.g.oa + id.b * a.g.ob;
+        const C *res = run_stages_lines(L, lpt, P, b0, b1, tw + L.tw_off);
+        C *ob = out + id.c0 * a.g.oc + id.a * a.g.oa + id.b * a.g.ob;
         for (int e = threadIdx.x; e < lpt * n; e += blockDim.x) {
             int l, k;
             if (out_lines) { l = e / n; k = e - l * n; }
             else { l = e % lpt; k = e / lpt; }
             if (l < nval) {
-                float2 v = res[l * P + padpos(k)];
+                C v = res[l * P + padpos(k)];
                 ob[l * a.g.oc + (int64_t)k * a.g.ok] = conj ? cconj(v) : v;
             }
         }
     }
+}
+
+__global__ void k_pass_g(PassArgs a) { pass_g_body<float2>(a, a.in, a.out, a.tw); }
+
+__global__ void k_pass_g64(PassArgs a)
+{
+    pass_g_body<double2>(a, reinterpret_cast<const double2 *>(a.in), reinterpret_cast<double2 *>(a.out),
+                         reinterpret_cast<const double2 *>(a.tw));
 }
 
 // -------------------------------------------------------------- k_slab -- //

@@ -183,6 +183,7 @@ struct SmemLineRt {
 __host__ __device__ inline int generic_pitch(int n) { return line_pitch(n); }
 
 __global__ void k_pass_g(PassArgs a);
+__global__ void k_pass_g64(PassArgs a); // the same in FP64 on complex128 arrays
 
 // Identity probe of a pass geometry: out[k*ok...] = in[k*ij...] for every
 // element (used to check the fused redistributions bit-exactly).

@@ -203,18 +203,25 @@ static int line_seg(Schedule *s, const LineChoice &lc)
     return add_seg(s, lc.n, std::move(m));
 }
 
-void generic_launch_shape(int n, int T, bool strided, int tw_len, int *lpt, int *threads, int *smem)
+void generic_launch_shape_elem(int n, int T, bool strided, int tw_len, int esize, int *lpt, int *threads,
+                               int *smem)
 {
     int P = pitch_h(n);
-    int l = strided ? 16 : std::max(1, 256 / T);
+    // strided lines: tiles of 16 (complex64) or 8 (complex128) columns, 128-byte rows
+    int l = strided ? 128 / esize : std::max(1, 256 / T);
     while (l > 1 && T * l > 1024)
         l /= 2;
-    auto bytes = [&](int ll) { return tw_slots_h(tw_len) * 8 + 2 * ll * P * 8; };
+    auto bytes = [&](int ll) { return tw_slots_h(tw_len) * esize + 2 * ll * P * esize; };
     while (l > 1 && bytes(l) > kSmemLimit)
         l /= 2;
     *lpt = l;
     *threads = std::max(32, std::min(1024, (T * l + 31) / 32 * 32));
     *smem = bytes(l);
+}
+
+void generic_launch_shape(int n, int T, bool strided, int tw_len, int *lpt, int *threads, int *smem)
+{
+    generic_launch_shape_elem(n, T, strided, tw_len, 8, lpt, threads, smem);
 }
 
 // --------------------------------------------------------- geometries ---- //
@@ -336,6 +343,23 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
     const bool contig_in = g.ij == 1;
     const bool strided_in = g.ic == 1 && g.oc == 1;
     const int tc_mode = std::min(2, std::max(0, s->opts.tc_stages));
+    if (s->dtype == FFT3_C128_FP64) {
+        // complex128: runtime radix list in FP64 (k_pass_g64), 16-byte elements
+        rc = choose_line(n, order, false, &p.line, err);
+        if (rc)
+            return rc;
+        p.kind = PK_G64;
+        p.tw_seg[0] = line_seg(s, p.line);
+        generic_launch_shape_elem(n, p.line.T, !contig_in, (int)s->tw[p.tw_seg[0]].m.size(), 16, &p.lpt,
+                                  &p.threads, &p.smem_bytes);
+        if (p.smem_bytes > kSmemLimit) {
+            *err = "pass needs more shared memory than a block has";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        set_tiles(&p);
+        *out = p;
+        return FFT3_OK;
+    }
     if (s->dtype == FFT3_C64_SPLITBF16_TC && !rotate && strided_in && n > 1 && s->opts.tile_lines == 0) {
         // streamed strided pass whose 16 x 16 sub-line transforms run on the tensor cores
         int cnt = 0;
@@ -741,7 +765,7 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         *err = "direction must be FFT3_FORWARD (-1) or FFT3_INVERSE (+1)";
         return FFT3_ERR_INVALID_ARG;
     }
-    if (dtype != FFT3_C64_FP32 && dtype != FFT3_C64_SPLITBF16_TC) {
+    if (dtype != FFT3_C64_FP32 && dtype != FFT3_C64_SPLITBF16_TC && dtype != FFT3_C128_FP64) {
         *err = "unknown dtype";
         return FFT3_ERR_INVALID_ARG;
     }
@@ -766,6 +790,17 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
     s.dtype = dtype; s.direction = direction;
     if (opts)
         s.opts = *opts;
+    if (dtype == FFT3_C128_FP64) {
+        // complex128 runs every line transform as one pass of the runtime-radix
+        // FP64 kernel: pencil-pencil-pencil in natural order (the slab-pencil
+        // and automatic choices lower to the same three passes)
+        if (decomp == FFT3_VOLUMETRIC || s.opts.variant != FFT3_PPP_NATURAL ||
+            s.opts.layout != FFT3_LAYOUT_NATURAL) {
+            *err = "complex128 runs the natural pencil-pencil-pencil schedule";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        decomp = FFT3_PENCIL3;
+    }
     if (decomp == FFT3_AUTO && dtype == FFT3_C64_SPLITBF16_TC) {
         decomp = FFT3_PENCIL3;
         if (s.opts.variant == FFT3_PPP_NATURAL && (int64_t)n0 * n1 * 8 >= (4ll << 20))
@@ -1090,8 +1125,9 @@ static const char *kind_name(int k)
     static const char *names[] = {"line_contig", "line_contig_rotate", "line_strided", "line_runtime",
                                   "slab_smem", "slab_l2", "volumetric_split", "copy", "unused",
                                   "line_strided_tma", "line_contig_tc", "line_strided_tc",
-                                  "volumetric_split_fixed", "line_strided_stream", "slab_l2_blocked"};
-    return (k >= 0 && k <= 14) ? names[k] : "?";
+                                  "volumetric_split_fixed", "line_strided_stream", "slab_l2_blocked",
+                                  "line_runtime_fp64"};
+    return (k >= 0 && k <= 15) ? names[k] : "?";
 }
 static const char *buf_name(int b)
 {

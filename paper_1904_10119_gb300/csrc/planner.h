@@ -26,7 +26,8 @@ enum PassKind {
     PK_CTC = 11,   // split-BF16 tensor-core radix-16 stages, strided columns
     PK_VOLC = 12,  // compile-time volumetric split of strided lines (k_volc.cu)
     PK_CSTREAM = 13, // strided lines, decimated sub-lines streamed by TMA (k_cstream.cu)
-    PK_SLABBLK = 14, // 2D slab DFT in one persistent launch, stored as blocked z pencils (k_slab_blk)
+    PK_SLABBLK = 14, // 2D slab DFT in one persistent launch, stored as blocked z pencils (k_slab_tma)
+    PK_G64 = 15,     // complex128: runtime radix list in FP64 (k_pass_g64)
 };
 
 enum BufId { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };
@@ -96,6 +97,9 @@ void line_twiddle_exponents(const LineChoice &lc, std::vector<int64_t> *m);
 // Lines per tile and shared memory of the runtime-radix kernel for a pass.
 void generic_launch_shape(int n, int T, bool strided, int tw_len, int *lpt, int *threads,
                           int *smem);
+// The same for elements of esize bytes (16 for complex128).
+void generic_launch_shape_elem(int n, int T, bool strided, int tw_len, int esize, int *lpt, int *threads,
+                               int *smem);
 
 constexpr int kMaxLine = 4096;
 constexpr int kTileTma = 1; // fft3_options.tile_lines value selecting the TMA strided kernel

@@ -18,6 +18,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "fft3.h")
 
 FFT3_C64_FP32 = 0
 FFT3_C64_SPLITBF16_TC = 1
+FFT3_C128_FP64 = 2
 FFT3_SLAB_PENCIL, FFT3_PENCIL3, FFT3_VOLUMETRIC, FFT3_AUTO = 0, 1, 2, 3
 FFT3_FORWARD, FFT3_INVERSE = -1, 1
 FFT3_PPP_NATURAL, FFT3_PPP_ROTATE, FFT3_PPP_BLOCKED = 0, 1, 2
@@ -359,18 +360,21 @@ class Mlp:
 
 # ------------------------------------------------------ torch convenience -- #
 class Plan:
-    """Owns one fft3 plan; `execute(x, out)` takes contiguous complex64 CUDA tensors."""
+    """Owns one fft3 plan; `execute(x, out)` takes contiguous CUDA tensors of
+    complex64 (complex128 for an FFT3_C128_FP64 plan)."""
 
     def __init__(self, n0, n1, n2, batch=1, decomposition=FFT3_PENCIL3, direction=FFT3_FORWARD,
                  dtype=FFT3_C64_FP32, **opts):
         self.shape = (n0, n1, n2)
         self.batch = batch
+        self.dtype = dtype
         self.handle = fft3_plan_create_ex(n0, n1, n2, batch, dtype, decomposition, direction,
                                           make_options(**opts))
 
     def execute(self, x, out, stream=None) -> None:
         import torch
-        assert x.is_cuda and out.is_cuda and x.dtype == torch.complex64 and out.dtype == torch.complex64
+        want = torch.complex128 if self.dtype == FFT3_C128_FP64 else torch.complex64
+        assert x.is_cuda and out.is_cuda and x.dtype == want and out.dtype == want
         assert x.is_contiguous() and out.is_contiguous()
         s = stream if stream is not None else torch.cuda.current_stream()
         fft3_plan_execute(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)

@@ -41,6 +41,14 @@ def uniform_c64(shape, seed: int, out: np.ndarray | None = None, chunk: int = 1 
     return out.reshape(shape)
 
 
+def uniform_c128(shape, seed: int) -> np.ndarray:
+    """complex128 array of the given shape with re, im i.i.d. uniform[-1, 1)
+    drawn in double precision (53-bit mantissas, for the complex128 path)."""
+    size = int(np.prod(shape))
+    r = _rng(seed).random(2 * size, dtype=np.float64) * 2.0 - 1.0
+    return r.view(np.complex128).reshape(shape)
+
+
 def hdr_c64(shape, seed: int) -> np.ndarray:
     """complex64 with |z| = 10^U(-3,3) (log-uniform in [1e-3, 1e3]) and a
     uniform phase 2*pi*U(0,1); computed in FP64 and rounded once to FP32."""
