@@ -358,6 +358,10 @@ def main():
         variants = dict(decomp_map)
         variants["volumetric_mesh4_compiled"] = (fft3.FFT3_VOLUMETRIC, {"mesh": (1, 4, 4), "tile_lines": 16})
         variants["ppp_plain_strided_kernel"] = (fft3.FFT3_PENCIL3, {"tile_lines": 16})
+        # the cyclic split and the blocked six-step split on the same runtime-radix cluster kernel
+        variants["volumetric_cyclic_runtime_kernel"] = (fft3.FFT3_VOLUMETRIC, {"mesh": (1, 2, 2), "tile_lines": 8})
+        variants["volumetric_blocked_six_step"] = (fft3.FFT3_VOLUMETRIC, {"variant": fft3.FFT3_VOL_BLOCKED_SIX_STEP,
+                                                                          "mesh": (1, 2, 2), "tile_lines": 8})
         variants["permuted_output_pencils"] = (fft3.FFT3_AUTO, {"layout": fft3.FFT3_LAYOUT_PENCILS})
         variants["permuted_output_rotated"] = (fft3.FFT3_PENCIL3, {"layout": fft3.FFT3_LAYOUT_ROTATED})
         tc = fft3.FFT3_C64_SPLITBF16_TC

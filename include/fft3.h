@@ -103,9 +103,19 @@ enum fft3_ppp_variant {
  * or automatic decomposition (FFT3_LAYOUT_PENCILS also with the split-BF16 dtype). */
 enum fft3_layout { FFT3_LAYOUT_NATURAL = 0, FFT3_LAYOUT_ROTATED = 1, FFT3_LAYOUT_PENCILS = 2 };
 
+/* Volumetric variants (options.variant with FFT3_VOLUMETRIC). */
+enum fft3_vol_variant {
+    FFT3_VOL_CYCLIC = 0,           /* elemental-cyclic ownership of every split line: one exchange
+                                      (Section 3.2, needs p | a and p | b) */
+    FFT3_VOL_BLOCKED_SIX_STEP = 1  /* blocked ownership (block r owns elements [r n/p, (r+1) n/p) of a
+                                      line): the six-step algorithm of Section 2.2, Eq. ctparallel,
+                                      with three exchanges; a comparison schedule for what the cyclic
+                                      distribution saves (runtime-radix cluster kernel) */
+};
+
 /* Optional planner controls.  Zero-initialise and set what you need. */
 typedef struct fft3_options {
-    int variant;      /* fft3_ppp_variant for FFT3_PENCIL3 */
+    int variant;      /* fft3_ppp_variant for FFT3_PENCIL3, fft3_vol_variant for FFT3_VOLUMETRIC */
     int radix_order;  /* index into the candidate radix orders of each line length (0 = default) */
     int tile_lines;   /* strided passes: 0 = default (the streamed kernel where one is
                          compiled for the line length, else 16 lines per tile);

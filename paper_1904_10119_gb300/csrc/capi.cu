@@ -238,6 +238,7 @@ static int build_launches(fft3_plan_s *P)
         if (p.tw_seg[2] >= 0)
             a.tw_split_off = (int)(s.tw[p.tw_seg[2]].off - base);
         a.p = p.p;
+        a.six_step = p.six_step ? 1 : 0;
         a.split_a = p.split_a;
         a.split_b = p.split_b;
         L.probe_g = p.g;

@@ -40,6 +40,7 @@ struct PassArgs {
     LineRt L[2];      // runtime line plans: generic L[0]; slab x = L[0], y = L[1];
                       // volumetric rows (DFT_b) = L[0], columns (DFT_a) = L[1]
     int p, split_a, split_b, tw_split_off; // volumetric split n = a*b over p blocks
+    int six_step;     // volumetric split with blocked ownership and three exchanges (k_vol)
     unsigned *err;    // device error flags (persistent kernels)
     int *counters;    // per-slab completion counters + ticket (persistent kernels)
     long long wait_budget; // clock cycles a bounded wait may spin before giving up

@@ -16,6 +16,15 @@
 //         y~[k1, k0] = y[k1 + b*k0], i.e. the outputs k with k mod p = r.
 // Input and output are in the same elemental-cyclic distribution, and one
 // exchange suffices because p | a and p | b (checked by the planner).
+//
+// With a.six_step the line is instead distributed in blocks (block r owns the
+// elements [r n/p, (r+1) n/p) of input and output), the layout of the six-step
+// algorithm of Section 2.2, which needs three exchanges: (0) every block
+// gathers its cyclic rows from the owners of the blocked input (staged in its
+// T1 region), then (I)-(IV) as above, and (V) every block gathers its blocked
+// share of the output from the blocks that computed it (staged in its T0
+// region) and stores it.  This is the comparison schedule for what the
+// elemental-cyclic distribution saves.
 #include <cooperative_groups.h>
 
 #include "pass_kernels.cuh"
@@ -51,17 +60,40 @@ __global__ void k_vol(PassArgs a)
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, lpt);
         const int64_t nval = min((int64_t)lpt, a.g.C - id.c0);
         const float2 *ib = a.in + id.c0 * a.g.ic + id.a * a.g.ia + id.b * a.g.ib;
-        // load this block's cyclic share: rows i0 = r + p*u
         const int cnt0 = lpt * ap * B;
-        for (int e = threadIdx.x; e < cnt0; e += blockDim.x) {
-            int l, u, i1;
-            if (contig) { u = e % ap; int q = e / ap; i1 = q % B; l = q / B; }
-            else { l = e % lpt; int q = e / lpt; i1 = q % B; u = q / B; }
-            const int j = r + p * u + A * i1;
-            float2 v = make_float2(0.f, 0.f);
-            if (l < nval)
-                v = ib[l * a.g.ic + (int64_t)j * a.g.ij];
-            T0[(l * ap + u) * Pb + padpos(i1)] = conj ? cconj(v) : v;
+        const int share = n / p; // elements of a line per block
+        if (!a.six_step) {
+            // load this block's cyclic share: rows i0 = r + p*u
+            for (int e = threadIdx.x; e < cnt0; e += blockDim.x) {
+                int l, u, i1;
+                if (contig) { u = e % ap; int q = e / ap; i1 = q % B; l = q / B; }
+                else { l = e % lpt; int q = e / lpt; i1 = q % B; u = q / B; }
+                const int j = r + p * u + A * i1;
+                float2 v = make_float2(0.f, 0.f);
+                if (l < nval)
+                    v = ib[l * a.g.ic + (int64_t)j * a.g.ij];
+                T0[(l * ap + u) * Pb + padpos(i1)] = conj ? cconj(v) : v;
+            }
+        } else {
+            // load this block's blocked share j = r*share + jj into T1 as [l][jj]
+            for (int e = threadIdx.x; e < lpt * share; e += blockDim.x) {
+                int l, jj;
+                if (contig) { jj = e % share; l = e / share; }
+                else { l = e % lpt; jj = e / lpt; }
+                float2 v = make_float2(0.f, 0.f);
+                if (l < nval)
+                    v = ib[l * a.g.ic + (int64_t)(r * share + jj) * a.g.ij];
+                T1[l * share + jj] = conj ? cconj(v) : v;
+            }
+            cluster.sync();
+            // exchange (0): row i0 = r + p*u gathers x[i0 + A*i1] from block j / share
+            for (int e = threadIdx.x; e < cnt0; e += blockDim.x) {
+                const int i1 = e % B, q = e / B, u = q % ap, l = q / ap;
+                const int j = r + p * u + A * i1;
+                const float2 *src = cluster.map_shared_rank(T1, j / share);
+                T0[(l * ap + u) * Pb + padpos(i1)] = src[l * share + j % share];
+            }
+            cluster.sync(); // every block's staged input is read before T1 is reused
         }
         __syncthreads();
         // (I) DFT_b on every local row
@@ -85,6 +117,28 @@ __global__ void k_vol(PassArgs a)
         // (IV) DFT_a on every local column
         float2 *R1 = run_stages_lines(LA, lpt * bp, Pa, T1, X, tw + LA.tw_off);
         float2 *ob = a.out + id.c0 * a.g.oc + id.a * a.g.oa + id.b * a.g.ob;
+        if (a.six_step) {
+            cluster.sync(); // every block's columns are transformed
+            // exchange (V): output k = r*share + kk, k = k1 + B*k0, computed by
+            // block k1 mod p as its column v = k1 / p; staged in T0 as [l][kk]
+            for (int e = threadIdx.x; e < lpt * share; e += blockDim.x) {
+                const int kk = e % share, l = e / share;
+                const int k = r * share + kk, k1 = k % B, k0 = k / B;
+                const float2 *src = cluster.map_shared_rank(R1, k1 % p);
+                T0[l * share + kk] = src[(l * bp + k1 / p) * Pa + padpos(k0)];
+            }
+            cluster.sync(); // the peers' results are read before the next tile reuses them
+            for (int e = threadIdx.x; e < lpt * share; e += blockDim.x) {
+                int l, kk;
+                if (contig) { kk = e % share; l = e / share; }
+                else { l = e % lpt; kk = e / lpt; }
+                if (l < nval) {
+                    const float2 val = T0[l * share + kk];
+                    ob[l * a.g.oc + (int64_t)(r * share + kk) * a.g.ok] = conj ? cconj(val) : val;
+                }
+            }
+            continue;
+        }
         const int cnt1 = lpt * bp * A;
         for (int e = threadIdx.x; e < cnt1; e += blockDim.x) {
             int l, v, k0;

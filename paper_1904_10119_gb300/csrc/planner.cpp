@@ -566,7 +566,10 @@ static int make_vol_pass(Schedule *s, int d, int n, int p, const PassGeom &g, in
     // a strided line split over a cluster pair whose halves of the decimated
     // sub-lines stream in by TMA (k_cstream.cu), unless tile_lines asks for
     // the compiled splits of k_volc.cu
-    const int ci = p == 2 && s->opts.tile_lines <= kTileStream ? cstream_pick(n, s->opts.radix_order, g, 2) : -1;
+    // the blocked six-step comparison schedule runs on the runtime-radix cluster kernel
+    const bool six = s->opts.variant == FFT3_VOL_BLOCKED_SIX_STEP;
+    const int ci = !six && p == 2 && s->opts.tile_lines <= kTileStream ? cstream_pick(n, s->opts.radix_order, g, 2)
+                                                                       : -1;
     if (ci >= 0) {
         PassPlan q;
         q.dim = d;
@@ -579,10 +582,11 @@ static int make_vol_pass(Schedule *s, int d, int n, int p, const PassGeom &g, in
         *out = q;
         return FFT3_OK;
     }
-    if (make_volc_pass(s, d, n, p, g, src, dst, out))
+    if (!six && make_volc_pass(s, d, n, p, g, src, dst, out))
         return FFT3_OK;
     PassPlan q;
     q.kind = PK_VOL;
+    q.six_step = six;
     q.dim = d;
     q.g = g;
     q.src = src;
@@ -1175,7 +1179,8 @@ std::string Schedule::json() const
         o << ",\"lpt\":" << p.lpt << ",\"threads\":" << p.threads << ",\"smem\":" << p.smem_bytes
           << ",\"tiles\":" << p.ntiles;
         if (p.kind == PK_VOL || p.kind == PK_VOLC)
-            o << ",\"p\":" << p.p << ",\"a\":" << p.split_a << ",\"b\":" << p.split_b;
+            o << ",\"p\":" << p.p << ",\"a\":" << p.split_a << ",\"b\":" << p.split_b
+              << ",\"exchanges\":" << (p.six_step ? 3 : 1);
         if (p.kind == PK_CSTREAM && p.p > 1)
             o << ",\"p\":" << p.p;
         if (p.kind == PK_JTC || p.kind == PK_CTC || (p.kind == PK_CSTREAM && p.tc_mode >= 0))

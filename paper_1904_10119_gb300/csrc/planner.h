@@ -66,6 +66,7 @@ struct PassPlan {
     int cstream = -1;           // PK_CSTREAM: index into the compiled streamed-pass list
     int chunk = 0;              // slabs per chunk of a two-stream pipelined slab stage (0 = one launch)
     bool pair_next = false;     // this pass and the next run chunk-interleaved on two streams
+    bool six_step = false;      // PK_VOL: blocked ownership, three exchanges (Section 2.2)
 };
 
 struct Schedule {

@@ -23,6 +23,7 @@ FFT3_SLAB_PENCIL, FFT3_PENCIL3, FFT3_VOLUMETRIC, FFT3_AUTO = 0, 1, 2, 3
 FFT3_FORWARD, FFT3_INVERSE = -1, 1
 FFT3_PPP_NATURAL, FFT3_PPP_ROTATE, FFT3_PPP_BLOCKED = 0, 1, 2
 FFT3_LAYOUT_NATURAL, FFT3_LAYOUT_ROTATED, FFT3_LAYOUT_PENCILS = 0, 1, 2
+FFT3_VOL_CYCLIC, FFT3_VOL_BLOCKED_SIX_STEP = 0, 1
 
 STATUS = {
     0: "FFT3_OK", -1: "FFT3_ERR_INVALID_ARG", -2: "FFT3_ERR_UNSUPPORTED_SIZE", -3: "FFT3_ERR_OOM",

@@ -326,3 +326,14 @@ def test_schedule_permuted_layouts():
     for dims, decomp, dtype, layout in bad:
         with pytest.raises(fft3.Fft3Error):
             fft3.fft3_plan_schedule(*dims, dtype, decomp, F, fft3.make_options(layout=layout))
+
+
+def test_schedule_volumetric_six_step():
+    """The blocked six-step variant (Section 2.2) splits the same lines over the
+    same meshes on the runtime-radix cluster kernel, with three exchanges."""
+    s = fft3.fft3_plan_schedule(256, 256, 256, 1, 0, fft3.FFT3_VOLUMETRIC, -1,
+                                fft3.make_options(variant=fft3.FFT3_VOL_BLOCKED_SIX_STEP, mesh=(2, 4, 8)))
+    assert _kinds(s) == ["volumetric_split"] * 3
+    assert [(p["p"], p["exchanges"]) for p in s["passes"]] == [(2, 3), (4, 3), (8, 3)]
+    s = fft3.fft3_plan_schedule(256, 256, 256, 1, 0, fft3.FFT3_VOLUMETRIC, -1, fft3.make_options(mesh=(1, 4, 4)))
+    assert all(p.get("exchanges", 1) == 1 for p in s["passes"])

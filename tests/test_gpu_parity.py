@@ -155,6 +155,21 @@ def test_volumetric_meshes(mesh, shape):
             assert p["a"] % p["p"] == 0 and p["b"] % p["p"] == 0
 
 
+@pytest.mark.parametrize("mesh,shape,batch,direction", [((2, 2, 2), (64, 64, 64), 1, FWD),
+                                                        ((4, 4, 4), (64, 64, 64), 1, INV),
+                                                        ((8, 2, 4), (256, 32, 64), 1, FWD),
+                                                        ((1, 4, 2), (30, 64, 36), 2, FWD),
+                                                        ((0, 0, 0), (1024, 1024, 4), 1, INV),
+                                                        ((1, 2, 4), (100, 60, 48), 1, FWD)])
+def test_volumetric_blocked_six_step(mesh, shape, batch, direction):
+    """Blocked ownership of every split line (Section 2.2, Eq. ctparallel): three
+    exchanges instead of one, same result."""
+    x, got, plan = run_plan(shape, batch, V, direction, seed=13, mesh=mesh, variant=fft3.FFT3_VOL_BLOCKED_SIX_STEP)
+    assert_parity(x, got, shape, batch, direction)
+    splits = [p for p in plan.describe()["passes"] if p["kind"] == "volumetric_split"]
+    assert splits and all(p["exchanges"] == 3 for p in splits)
+
+
 @pytest.mark.parametrize("shape,batch", [((1, 64, 16), 1), ((64, 1, 1), 2), ((1, 1, 1), 3), ((1, 1, 96), 1),
                                          ((2, 3, 5), 1), ((5, 1, 3), 4)])
 @pytest.mark.parametrize("decomp", [S, P, V])
