@@ -514,8 +514,10 @@ def c128_table(fft3, synth, torch, sizes=(256, 512), reps=5):
 
 
 def bench_batched(fft3, synth, torch, hbm, count=4096):
-    """`count` independent 3D DFTs with dims drawn from {16..96} (seed 7) in one
-    graph-captured persistent launch: ms per batch, GB/s, roofline fractions."""
+    """`count` independent 3D DFTs with dims drawn from {16..96} (seed 7), one
+    graph-captured execution of the default plan (FFT3_AUTO: the segmented x, y
+    and z passes for a batch this size): ms per batch, GB/s, roofline fractions;
+    the persistent executor (tuning codes 0) timed beside it."""
     import numpy as np
     dims = synth.batched_dims(count, 7)
     vols = dims.prod(axis=1)
@@ -526,24 +528,30 @@ def bench_batched(fft3, synth, torch, hbm, count=4096):
     x.real.uniform_(-1, 1)
     x.imag.uniform_(-1, 1)
     out = torch.empty_like(x)
-    h = fft3.fft3_plan_create_many(dims, offs)
     st = torch.cuda.current_stream()
-    for _ in range(3):
-        fft3.fft3_plan_execute(h, x.data_ptr(), out.data_ptr(), st.cuda_stream)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 10
-    e0.record(st)
-    for _ in range(reps):
-        fft3.fft3_plan_execute(h, x.data_ptr(), out.data_ptr(), st.cuda_stream)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    assert fft3.fft3_plan_check(h) == 0
-    desc = fft3.fft3_plan_describe(h)
-    fft3.fft3_plan_destroy(h)
+
+    def run(tuning):
+        h = fft3.fft3_plan_create_many(dims, offs, tuning=tuning)
+        for _ in range(3):
+            fft3.fft3_plan_execute(h, x.data_ptr(), out.data_ptr(), st.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record(st)
+        for _ in range(reps):
+            fft3.fft3_plan_execute(h, x.data_ptr(), out.data_ptr(), st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        assert fft3.fft3_plan_check(h) == 0
+        desc = fft3.fft3_plan_describe(h)
+        fft3.fft3_plan_destroy(h)
+        return e0.elapsed_time(e1) / reps, desc
+
+    ms, desc = run(None)
+    ms_exec, _ = run([0] * count)
     one_sweep = 2 * 8 * total
-    return {"ms": ms, "elements": total, "problems": count, "items": desc["items"],
+    return {"ms": ms, "mode": desc["mode"], "kernel_launches": desc["kernel_launches"],
+            "executor_ms": ms_exec, "elements": total, "problems": count, "items": desc["items"],
             "GBps_one_sweep": one_sweep / (ms * 1e-3) / 1e9,
             "frac_of_1_sweep": one_sweep / (ms * 1e-3) / 1e9 / hbm,
             "frac_of_3_sweeps": 3 * one_sweep / (ms * 1e-3) / 1e9 / hbm,

@@ -171,15 +171,26 @@ int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int d
 /* Batched uneven transforms: `count` independent 3D DFTs (Section 2.3 for
  * each), problem i of size dims[3i] x dims[3i+1] x dims[3i+2] (first fastest)
  * starting at complex offset offsets[i] of both the input and the output
- * buffer (the problems' extents must not overlap).  One execute is one
- * persistent launch with its counter reset, captured once in a CUDA graph
- * (re-captured when the buffers change).  Dimensions: 2*3*5-smooth, <= 128.
+ * buffer (the problems' extents must not overlap).  Two execution modes, both
+ * captured once in a CUDA graph (re-captured when the buffers change):
+ *   executor:  one persistent launch with its counter reset; work items of
+ *              every problem's phases in waves that keep a problem's
+ *              intermediate in L2;
+ *   segmented: three passes over the whole batch (all x lines, all y lines,
+ *              all z lines of every problem, one compile-time line kernel per
+ *              line length: 8, 16, 24, 32, 40, 48, 64, 80, 96, 128), the
+ *              pencil-pencil-pencil definition of Section 2.3 per problem.
+ * The segmented mode runs when every tuning code has decomposition field 3, or
+ * with FFT3_AUTO, tuning == NULL and at least 4 Mi values in the batch, provided
+ * every line length has a compiled plan; otherwise the executor runs.
+ * Dimensions: 2*3*5-smooth, <= 128.
  * decomposition: FFT3_SLAB_PENCIL, FFT3_PENCIL3 or FFT3_AUTO (per problem).
  * dtype: FFT3_C64_FP32.  `tuning` may be NULL or point to `count` tuning
  * codes built with FFT3_TUNE (0 = defaults); fft3_autotune_many writes them. */
 #define FFT3_TUNE(decomp, radix_order, tile_code, items_code)                        \
     ((decomp) | (((radix_order) + 1) << 2) | ((tile_code) << 5) | ((items_code) << 8))
-/* decomp: 1 = slab-pencil, 2 = pencil-pencil-pencil; tile_code: columns per
+/* decomp: 1 = slab-pencil, 2 = pencil-pencil-pencil, 3 = the segmented passes
+ * (whole batch: every code must ask for it); tile_code: columns per
  * tile of the strided phases, 1 -> 4, 2 -> 8, 3 -> 16, 4 -> 32; items_code:
  * slabs (slab-pencil) or rows (pencil) per first-phase work item, k -> 2^(k-1). */
 int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets,
@@ -337,7 +348,8 @@ int fft3_autotune(int n0, int n1, int n2, int batch, int dtype, int direction, i
  * to every problem whose shared-buffer need stays within the default
  * buffers; then, for three size classes (thirds of the batch by problem
  * volume) in turn, the code that makes the whole batch fastest (kept when it
- * gains at least 1%).  Writes the assignment to tuning_out.  The batch is
+ * gains at least 1%); finally the segmented passes (code 3 for every problem),
+ * taken when faster.  Writes the assignment to tuning_out.  The batch is
  * timed as a whole because the executor's buffers, blocks per SM and item
  * order depend on all its problems (per-shape timings in isolation chose
  * codes that made the mixed batch slower).  `offsets` and `max_per_class`

@@ -268,6 +268,14 @@ int fft3_autotune_many(int count, const int *dims, const int64_t *offsets, int d
             }
         }
     }
+    // 3) the segmented x, y and z passes (decomposition field 3 on every
+    // problem; infeasible when a line length has no compiled plan)
+    std::vector<int> seg(count, 3);
+    float ts = 0.f;
+    if ((rc = time_assignment(seg, &ts)))
+        return rc;
+    if (ts < bt)
+        best = seg;
     for (int i = 0; i < count; ++i)
         tuning_out[i] = best[i];
     return FFT3_OK;

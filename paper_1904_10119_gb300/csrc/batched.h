@@ -44,4 +44,20 @@ struct BatchArgs {
     int prefetch;        // 1: a third buffer stages the next item's first tile (cp.async)
 };
 
+// One launch of the segmented passes (k_segmented.cu): the lines of one
+// length along dimension `dim` of the listed problems, LPT lines per tile.
+struct SegArgs {
+    const float2 *src;     // input of this pass (`in` for the x pass, `out` after)
+    float2 *out;
+    const BatchCube *cubes;
+    const int *list;       // problem index of each listed slot
+    const int64_t *tstart; // first tile of each slot
+    const int *tcube;      // slot of every tile
+    int64_t ntiles;
+    int dim;               // 0: x lines (contiguous), 1: y lines, 2: z lines
+    const float2 *tw;      // the line plan's twiddle table, tw_len entries
+    int tw_len;
+    int conj;
+};
+
 } // namespace fft3

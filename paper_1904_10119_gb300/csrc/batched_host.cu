@@ -17,13 +17,27 @@
 #include <sstream>
 
 #include "capi_internal.h"
+#include "seg_plans.h"
 
 namespace fft3 {
 
 __global__ void k_batched(BatchArgs a);
 __global__ void k_roots(int n, int sign, const int64_t *m, int64_t count, double *o64, float2 *o32);
 
+// One launch of the segmented mode: lines of length n along dimension dim.
+struct SegLaunch {
+    int dim, n, kernel, lpt, threads, smem;
+    int64_t ntiles;
+    int64_t list_off, tstart_off, tcube_off; // offsets into the concatenated device tables
+    int64_t tw_off, tw_len;
+    dim3 grid;
+};
+
 struct BatchState {
+    int seg = 0; // 1: three segmented passes (k_segmented.cu) instead of the persistent executor
+    std::vector<SegLaunch> seg_launches;
+    int *d_seg_list = nullptr, *d_seg_tcube = nullptr;
+    int64_t *d_seg_tstart = nullptr;
     std::vector<BatchCube> cubes;
     std::vector<BatchItem> items;
     std::vector<LineRt> lines;
@@ -74,6 +88,9 @@ void batch_free(BatchState *b)
         cudaGraphDestroy(b->graph);
     if (b->cap_stream)
         cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_seg_list);
+    cudaFree(b->d_seg_tcube);
+    cudaFree(b->d_seg_tstart);
     cudaFree(b->d_cubes);
     cudaFree(b->d_items);
     cudaFree(b->d_lines);
@@ -101,6 +118,10 @@ static int line_index(BatchState *b, std::map<std::pair<int, int>, int> &idx, in
 
 // Elements per shared buffer that keep four blocks of 256 threads on an SM.
 constexpr int kBatchBufTarget = 3072;
+
+// FFT3_AUTO without tuning codes runs the segmented passes from this many
+// values on (every line length compiled in seg_plans.h).
+constexpr int64_t kSegMinElems = 1ll << 22;
 
 // Decodes a tuning code (0 = defaults): items of roughly 2-4 thousand
 // elements, buffers of at most kBatchBufTarget elements unless a slab needs more.
@@ -141,6 +162,8 @@ int batch_buffer_need(int n0, int n1, int n2, int code)
     return std::max(spi * pitch_b(n0), std::max(lpty * pitch_b(n1), lpt * pitch_b(n2)));
 }
 
+int batch_kernel_launches(const BatchState *b) { return b->seg ? (int)b->seg_launches.size() : 1; }
+
 int batch_describe(const BatchState *b, std::string *json)
 {
     std::ostringstream o;
@@ -151,7 +174,8 @@ int batch_describe(const BatchState *b, std::string *json)
         e.first++;
         e.second = b->tuning[i];
     }
-    o << "{\"batched\":true,\"problems\":" << b->cubes.size() << ",\"items\":" << b->items.size()
+    o << "{\"batched\":true,\"mode\":\"" << (b->seg ? "segmented" : "executor") << "\",\"kernel_launches\":"
+      << batch_kernel_launches(b) << ",\"problems\":" << b->cubes.size() << ",\"items\":" << b->items.size()
       << ",\"groups\":" << b->groups << ",\"line_plans\":" << b->lines.size() << ",\"grid\":" << b->grid.x
       << ",\"block\":" << b->threads << ",\"smem\":" << b->smem << ",\"prefetch\":" << b->prefetch << ",\"twiddle_entries\":" << b->tw_total
       << ",\"extent\":" << b->extent << ",\"classes\":[";
@@ -192,10 +216,36 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
     a.buf_elems = b->buf_elems;
     a.prefetch = b->prefetch;
     CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, b->counters_bytes, b->cap_stream);
-    if (e == cudaSuccess) {
-        void *params[1] = {&a};
-        e = cudaLaunchKernel((const void *)&k_batched, b->grid, dim3(b->threads), params, b->smem, b->cap_stream);
+    cudaError_t e = cudaSuccess;
+    if (b->seg) {
+        int cnt = 0;
+        const SegKernel *sk = seg_kernels(&cnt);
+        for (const SegLaunch &L : b->seg_launches) {
+            SegArgs s{};
+            s.src = L.dim == 0 ? (const float2 *)in : (const float2 *)out;
+            s.out = (float2 *)out;
+            s.cubes = b->d_cubes;
+            s.list = b->d_seg_list + L.list_off;
+            s.tstart = b->d_seg_tstart + L.tstart_off;
+            s.tcube = b->d_seg_tcube + L.tcube_off;
+            s.ntiles = L.ntiles;
+            s.dim = L.dim;
+            s.tw = b->d_tw + L.tw_off;
+            s.tw_len = (int)L.tw_len;
+            s.conj = b->conj;
+            void *params[1] = {&s};
+            const void *f = L.dim == 0 ? sk[L.kernel].func_c : sk[L.kernel].func_s;
+            e = cudaLaunchKernel(f, L.grid, dim3(L.threads), params, L.smem, b->cap_stream);
+            if (e != cudaSuccess)
+                break;
+        }
+    } else {
+        e = cudaMemsetAsync(b->d_counters, 0, b->counters_bytes, b->cap_stream);
+        if (e == cudaSuccess) {
+            void *params[1] = {&a};
+            e = cudaLaunchKernel((const void *)&k_batched, b->grid, dim3(b->threads), params, b->smem,
+                                 b->cap_stream);
+        }
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
@@ -302,6 +352,37 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         extent = std::max(extent, offsets[i] + (int64_t)n0 * n1 * n2);
     }
     b->extent = extent;
+    // segmented mode: every line length compiled, and every tuning code asks
+    // for it (decomposition field 3), or FFT3_AUTO without tuning codes (a
+    // null array; an array of zeros keeps the executor) on a large enough batch
+    int scnt = 0;
+    const SegKernel *sk = seg_kernels(&scnt);
+    auto seg_index = [&](int n) {
+        for (int k = 0; k < scnt; ++k)
+            if (sk[k].n == n)
+                return k;
+        return -1;
+    };
+    {
+        bool ok = true, all3 = tuning != nullptr;
+        int64_t values = 0;
+        for (int i = 0; i < count; ++i) {
+            for (int k = 0; k < 3; ++k)
+                ok = ok && seg_index(dims[3 * i + k]) >= 0;
+            if (tuning)
+                all3 = all3 && (tuning[i] & 3) == 3;
+            values += (int64_t)dims[3 * i] * dims[3 * i + 1] * dims[3 * i + 2];
+        }
+        if (all3 && !ok) {
+            batch_free(b);
+            return fail(FFT3_ERR_UNSUPPORTED_SIZE, "the segmented passes have no compiled plan for a line length "
+                                                   "of this batch");
+        }
+        b->seg = ok && (all3 || (decomposition == FFT3_AUTO && !tuning && values >= kSegMinElems)) ? 1 : 0;
+        if (b->seg)
+            for (int i = 0; i < count; ++i)
+                b->tuning[i] = 3;
+    }
     b->buf_elems = (bufmax + 31) / 32 * 32;
     // a third buffer stages the next item's first tile when it still fits
     b->prefetch = 3 * b->buf_elems * (int)sizeof(float2) <= 200 * 1024 ? 1 : 0;
@@ -315,6 +396,7 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
     std::vector<std::pair<int64_t, int64_t>> segs; // (offset, count) per line plan
     int64_t tw_total = 0;
     std::vector<std::vector<int64_t>> exps;
+    std::vector<int> exp_n; // line length of each table
     for (const LineChoice &lc : b->line_choice) {
         std::vector<int64_t> e;
         line_twiddle_exponents(lc, &e);
@@ -331,6 +413,63 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         segs.push_back({tw_total, (int64_t)e.size()});
         tw_total += ((int64_t)e.size() + 15) / 16 * 16;
         exps.push_back(std::move(e));
+        exp_n.push_back(lc.n);
+    }
+    // segmented passes: per dimension and line length, the listed problems,
+    // the first tile of each and the problem slot of every tile
+    std::vector<int> seg_list, seg_tcube;
+    std::vector<int64_t> seg_tstart;
+    if (b->seg) {
+        for (int d = 0; d < 3; ++d) {
+            std::map<int, std::vector<int>> byn;
+            for (int i = 0; i < count; ++i)
+                byn[dims[3 * i + d]].push_back(i);
+            for (auto &kv : byn) {
+                const int kidx = seg_index(kv.first);
+                const SegKernel &K = sk[kidx];
+                SegLaunch L{};
+                L.dim = d;
+                L.n = kv.first;
+                L.kernel = kidx;
+                L.lpt = d == 0 ? K.lpt_c : K.lpt_s;
+                L.threads = K.T * L.lpt;
+                L.list_off = (int64_t)seg_list.size();
+                L.tstart_off = (int64_t)seg_tstart.size();
+                L.tcube_off = (int64_t)seg_tcube.size();
+                int64_t tiles = 0;
+                for (size_t s = 0; s < kv.second.size(); ++s) {
+                    const int i = kv.second[s];
+                    const int64_t n0 = dims[3 * i], n1 = dims[3 * i + 1], n2 = dims[3 * i + 2];
+                    const int64_t lines = d == 0 ? n1 * n2 : d == 1 ? n0 * n2 : n0 * n1;
+                    const int64_t nt = (lines + L.lpt - 1) / L.lpt;
+                    seg_list.push_back(i);
+                    seg_tstart.push_back(tiles);
+                    seg_tcube.insert(seg_tcube.end(), (size_t)nt, (int)s);
+                    tiles += nt;
+                }
+                seg_tstart.push_back(tiles);
+                L.ntiles = tiles;
+                LineChoice lc{};
+                lc.n = K.n;
+                lc.fixed = -1;
+                lc.T = K.T;
+                lc.nst = K.nrad;
+                for (int r = 0; r < K.nrad; ++r)
+                    lc.rad[r] = K.rad[r];
+                std::vector<int64_t> e;
+                line_twiddle_exponents(lc, &e);
+                if (e.empty())
+                    e.push_back(0);
+                L.tw_off = tw_total;
+                L.tw_len = ((int64_t)e.size() + 15) / 16 * 16;
+                segs.push_back({tw_total, (int64_t)e.size()});
+                tw_total += L.tw_len;
+                exps.push_back(std::move(e));
+                exp_n.push_back(K.n);
+                L.smem = (int)(L.tw_len + (d == 0 ? L.lpt * pitch_b(K.n) : L.lpt * K.n)) * (int)sizeof(float2);
+                b->seg_launches.push_back(L);
+            }
+        }
     }
     b->tw_total = tw_total;
     // work items in waves over groups of problems (largest first)
@@ -416,7 +555,7 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         for (size_t i = 0; i < exps.size(); ++i) {
             cudaMemcpy(d_m, exps[i].data(), exps[i].size() * sizeof(int64_t), cudaMemcpyHostToDevice);
             int blocks = (int)std::max<int64_t>(1, ((int64_t)exps[i].size() + 255) / 256);
-            k_roots<<<blocks, 256>>>(b->lines[i].n, FFT3_FORWARD, d_m, (int64_t)exps[i].size(), nullptr,
+            k_roots<<<blocks, 256>>>(exp_n[i], FFT3_FORWARD, d_m, (int64_t)exps[i].size(), nullptr,
                                      b->d_tw + segs[i].first);
         }
         cudaError_t e = cudaDeviceSynchronize();
@@ -429,6 +568,25 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         rc = occupancy_grid((const void *)&k_batched, b->threads, b->smem, 0, dev, &b->grid);
     if (rc)
         return bail(rc);
+    if (b->seg) {
+        if (cudaMalloc(&b->d_seg_list, std::max<size_t>(1, seg_list.size()) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&b->d_seg_tcube, std::max<size_t>(1, seg_tcube.size()) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&b->d_seg_tstart, std::max<size_t>(1, seg_tstart.size()) * sizeof(int64_t)) != cudaSuccess)
+            return bail(fail(FFT3_ERR_OOM, "device allocation for the segmented passes failed"));
+        if (cudaMemcpy(b->d_seg_list, seg_list.data(), seg_list.size() * sizeof(int), cudaMemcpyHostToDevice) ||
+            cudaMemcpy(b->d_seg_tcube, seg_tcube.data(), seg_tcube.size() * sizeof(int), cudaMemcpyHostToDevice) ||
+            cudaMemcpy(b->d_seg_tstart, seg_tstart.data(), seg_tstart.size() * sizeof(int64_t),
+                       cudaMemcpyHostToDevice))
+            return bail(fail(FFT3_ERR_CUDA, "uploading the segmented pass tables failed"));
+        for (SegLaunch &L : b->seg_launches) {
+            const void *f = L.dim == 0 ? sk[L.kernel].func_c : sk[L.kernel].func_s;
+            rc = prepare_func(f, L.smem);
+            if (!rc)
+                rc = occupancy_grid(f, L.threads, L.smem, L.ntiles, dev, &L.grid);
+            if (rc)
+                return bail(rc);
+        }
+    }
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(FFT3_ERR_CUDA, "stream creation failed"));
     *out = P;

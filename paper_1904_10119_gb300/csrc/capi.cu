@@ -861,7 +861,7 @@ int fft3_plan_kernel_launches(fft3_plan p)
     if (!p)
         return fail(FFT3_ERR_INVALID_ARG, "null plan");
     if (p->batch)
-        return 1;
+        return batch_kernel_launches(p->batch);
     int n = 0;
     for (size_t k = 0; k < p->launches.size(); ++k) {
         if (pair_head(p, k)) {

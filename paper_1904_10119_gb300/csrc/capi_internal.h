@@ -60,6 +60,7 @@ int check_device(int *dev);
 int batch_execute(fft3_plan p, const void *in, void *out, cudaStream_t st);
 void batch_free(BatchState *b);
 int batch_describe(const BatchState *b, std::string *json);
+int batch_kernel_launches(const BatchState *b); // kernels in one execution of a batched plan
 int batch_buffer_need(int n0, int n1, int n2, int code);
 
 } // namespace fft3

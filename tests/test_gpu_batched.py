@@ -119,3 +119,51 @@ def test_4096_uneven_cubes_sampled_and_parseval():
         N = int(np.prod(d))
         sx, sg = x2[off:off + N].sum(), g2[off:off + N].sum()
         assert abs(sg - N * sx) <= 1e-5 * N * sx
+
+
+@pytest.mark.parametrize("direction", [fft3.FFT3_FORWARD, fft3.FFT3_INVERSE])
+def test_segmented_passes_every_problem(direction):
+    """Tuning code decomposition field 3: the batch runs as three segmented
+    passes (all x lines, then all y lines, then all z lines, one launch per
+    line length), every problem checked against the oracle."""
+    dims = np.vstack([synth.batched_dims(40, 11), [[8, 128, 16], [128, 8, 96], [24, 40, 8]]])
+    offs, total = _layout(dims, gap=5)
+    x, got, desc = _run(dims, offs, total, direction=direction, tuning=[3] * len(dims), seed=2)
+    assert desc["mode"] == "segmented"
+    classes = sum(len(set(int(v) for v in dims[:, d])) for d in range(3))
+    assert desc["kernel_launches"] == classes
+    for off, d in zip(offs, dims):
+        _check_problem(x, got, int(off), d, direction)
+
+
+def test_segmented_auto_choice_replay_and_refusal():
+    """FFT3_AUTO picks the segmented passes for a large batch of compiled
+    lengths (and the executor for a small one); replay on new buffers; a
+    line length without a compiled plan is refused when the codes ask for it."""
+    dims = synth.batched_dims(200, 4)
+    offs, total = _layout(dims)
+    x = synth.uniform_c64(total, 8)
+    xd = torch.from_numpy(x).cuda()
+    o1, o2 = torch.empty_like(xd), torch.empty_like(xd)
+    h = fft3.fft3_plan_create_many(dims, offs)
+    try:
+        assert fft3.fft3_plan_describe(h)["mode"] == "segmented"
+        fft3.fft3_plan_execute(h, xd.data_ptr(), o1.data_ptr(), 0)
+        fft3.fft3_plan_execute(h, xd.data_ptr(), o2.data_ptr(), 0)
+        torch.cuda.synchronize()
+        assert fft3.fft3_plan_check(h) == 0
+    finally:
+        fft3.fft3_plan_destroy(h)
+    assert torch.equal(o1, o2)
+    g = o1.cpu().numpy()
+    for off, d in list(zip(offs, dims))[::7]:
+        _check_problem(x, g, int(off), d, fft3.FFT3_FORWARD)
+    small = synth.batched_dims(6, 4)
+    so, _ = _layout(small)
+    h = fft3.fft3_plan_create_many(small, so)
+    try:
+        assert fft3.fft3_plan_describe(h)["mode"] == "executor"
+    finally:
+        fft3.fft3_plan_destroy(h)
+    with pytest.raises(fft3.Fft3Error):
+        fft3.fft3_plan_create_many([[30, 16, 16]], [0], tuning=[3])
