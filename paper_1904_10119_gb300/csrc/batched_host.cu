@@ -218,8 +218,8 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
     CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     if (b->seg) {
-        int cnt = 0;
-        const SegKernel *sk = seg_kernels(&cnt);
+        int ccnt = 0, scnt = 0;
+        const SegKernel *skc = seg_kernels(true, &ccnt), *sks = seg_kernels(false, &scnt);
         for (const SegLaunch &L : b->seg_launches) {
             SegArgs s{};
             s.src = L.dim == 0 ? (const float2 *)in : (const float2 *)out;
@@ -234,7 +234,7 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
             s.tw_len = (int)L.tw_len;
             s.conj = b->conj;
             void *params[1] = {&s};
-            const void *f = L.dim == 0 ? sk[L.kernel].func_c : sk[L.kernel].func_s;
+            const void *f = (L.dim == 0 ? skc : sks)[L.kernel].func;
             e = cudaLaunchKernel(f, L.grid, dim3(L.threads), params, L.smem, b->cap_stream);
             if (e != cudaSuccess)
                 break;
@@ -355,14 +355,17 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
     // segmented mode: every line length compiled, and every tuning code asks
     // for it (decomposition field 3), or FFT3_AUTO without tuning codes (a
     // null array; an array of zeros keeps the executor) on a large enough batch
-    int scnt = 0;
-    const SegKernel *sk = seg_kernels(&scnt);
-    auto seg_index = [&](int n) {
-        for (int k = 0; k < scnt; ++k)
-            if (sk[k].n == n)
-                return k;
+    int ccnt = 0, scnt = 0;
+    const SegKernel *skc = seg_kernels(true, &ccnt), *sks = seg_kernels(false, &scnt);
+    auto seg_find = [&](bool contiguous, int n) {
+        const SegKernel *k = contiguous ? skc : sks;
+        const int cnt = contiguous ? ccnt : scnt;
+        for (int i = 0; i < cnt; ++i)
+            if (k[i].n == n)
+                return i;
         return -1;
     };
+    auto seg_index = [&](int n) { return std::min(seg_find(true, n), seg_find(false, n)); };
     {
         bool ok = true, all3 = tuning != nullptr;
         int64_t values = 0;
@@ -425,13 +428,13 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
             for (int i = 0; i < count; ++i)
                 byn[dims[3 * i + d]].push_back(i);
             for (auto &kv : byn) {
-                const int kidx = seg_index(kv.first);
-                const SegKernel &K = sk[kidx];
+                const int kidx = seg_find(d == 0, kv.first);
+                const SegKernel &K = (d == 0 ? skc : sks)[kidx];
                 SegLaunch L{};
                 L.dim = d;
                 L.n = kv.first;
                 L.kernel = kidx;
-                L.lpt = d == 0 ? K.lpt_c : K.lpt_s;
+                L.lpt = K.lpt;
                 L.threads = K.T * L.lpt;
                 L.list_off = (int64_t)seg_list.size();
                 L.tstart_off = (int64_t)seg_tstart.size();
@@ -579,7 +582,7 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
                        cudaMemcpyHostToDevice))
             return bail(fail(FFT3_ERR_CUDA, "uploading the segmented pass tables failed"));
         for (SegLaunch &L : b->seg_launches) {
-            const void *f = L.dim == 0 ? sk[L.kernel].func_c : sk[L.kernel].func_s;
+            const void *f = (L.dim == 0 ? skc : sks)[L.kernel].func;
             rc = prepare_func(f, L.smem);
             if (!rc)
                 rc = occupancy_grid(f, L.threads, L.smem, L.ntiles, dev, &L.grid);

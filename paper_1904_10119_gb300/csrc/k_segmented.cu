@@ -12,8 +12,11 @@
 //   d = 1: c < n0*n2, first element (c / n0)*n0*n1 + c % n0, es = n0
 //   d = 2: c < n0*n1, first element c, es = n0*n1
 // so consecutive lines of a strided tile are adjacent columns (a y tile may
-// run across the end of one slab into the next).  Pass 0 reads `in` and
-// writes `out`; passes 1 and 2 work in place on `out`.
+// run across the end of one slab into the next).  The first stage reads its
+// inputs straight from global memory and the last stage writes its outputs
+// there (threads of a line adjacent for x lines, of a row of columns for y and
+// z lines).  Pass 0 reads `in` and writes `out`; passes 1 and 2 work in place
+// on `out`.
 #include "batched.h"
 #include "pass_kernels.cuh"
 #include "seg_plans.h"
@@ -35,8 +38,8 @@ __global__ void __launch_bounds__(T *LPT) k_seg(SegArgs a)
         __syncthreads();
         const int slot = a.tcube[tile];
         const BatchCube &cb = a.cubes[a.list[slot]];
-        const int64_t c = (tile - a.tstart[slot]) * LPT + l;
         const int64_t n0 = cb.n0, n1 = cb.n1, n2 = cb.n2;
+        const int64_t c = (tile - a.tstart[slot]) * LPT + l;
         int64_t lines, first, es;
         if (a.dim == 0) {
             lines = n1 * n2; first = c * n0; es = 1;
@@ -62,17 +65,22 @@ __global__ void __launch_bounds__(T *LPT) k_seg(SegArgs a)
     }
 }
 
-#define FFT3_SEG_ROW(N, T, LC, LS, ...)                                                                   \
-    {N, T, LC, LS, Radices<__VA_ARGS__>::count, {__VA_ARGS__},                                             \
-     (const void *)&k_seg<N, T, Radices<__VA_ARGS__>, LC, true>,                                          \
-     (const void *)&k_seg<N, T, Radices<__VA_ARGS__>, LS, false>},
+#define FFT3_SEG_ROW_C(N, T, L, ...)                                                                      \
+    {N, T, L, Radices<__VA_ARGS__>::count, {__VA_ARGS__}, (const void *)&k_seg<N, T, Radices<__VA_ARGS__>, L, true>},
+#define FFT3_SEG_ROW_S(N, T, L, ...)                                                                      \
+    {N, T, L, Radices<__VA_ARGS__>::count, {__VA_ARGS__}, (const void *)&k_seg<N, T, Radices<__VA_ARGS__>, L, false>},
 
-static const SegKernel g_seg_kernels[] = {FFT3_SEG_PLANS(FFT3_SEG_ROW)};
+static const SegKernel g_seg_contig[] = {FFT3_SEG_PLANS_CONTIG(FFT3_SEG_ROW_C)};
+static const SegKernel g_seg_strided[] = {FFT3_SEG_PLANS_STRIDED(FFT3_SEG_ROW_S)};
 
-const SegKernel *seg_kernels(int *count)
+const SegKernel *seg_kernels(bool contiguous, int *count)
 {
-    *count = (int)(sizeof(g_seg_kernels) / sizeof(g_seg_kernels[0]));
-    return g_seg_kernels;
+    if (contiguous) {
+        *count = (int)(sizeof(g_seg_contig) / sizeof(g_seg_contig[0]));
+        return g_seg_contig;
+    }
+    *count = (int)(sizeof(g_seg_strided) / sizeof(g_seg_strided[0]));
+    return g_seg_strided;
 }
 
 } // namespace fft3

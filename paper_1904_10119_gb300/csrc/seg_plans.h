@@ -8,27 +8,42 @@
 
 namespace fft3 {
 
-// X(N, T, lines per contiguous tile, columns per strided tile, radices...)
-#define FFT3_SEG_PLANS(X)                  \
-    X(8, 1, 256, 64, 8)                    \
-    X(16, 4, 64, 32, 4, 4)                 \
-    X(24, 4, 64, 32, 8, 3)                 \
-    X(32, 4, 64, 32, 8, 4)                 \
-    X(40, 5, 32, 32, 8, 5)                 \
-    X(48, 4, 64, 32, 16, 3)                \
-    X(64, 8, 32, 32, 8, 8)                 \
-    X(80, 5, 32, 32, 16, 5)                \
-    X(96, 6, 32, 32, 16, 2, 3)             \
-    X(128, 8, 32, 32, 16, 8)
+// X(N, T, lines (x) or columns (y, z) per tile, radices...).  Two stages
+// where the length allows (each stage is a round trip through shared memory;
+// three-stage lists and lists chosen for 32-byte-aligned first-stage runs
+// measured slower on the contiguous x lines).  Strided y and z lines: coalescing
+// is across the tile's columns, so the lists keep registers low and threads busy.
+#define FFT3_SEG_PLANS_CONTIG(X) \
+    X(8, 1, 256, 8)              \
+    X(16, 4, 64, 4, 4)           \
+    X(24, 4, 64, 8, 3)           \
+    X(32, 4, 64, 8, 4)           \
+    X(40, 5, 32, 8, 5)           \
+    X(48, 4, 64, 16, 3)          \
+    X(64, 8, 32, 8, 8)           \
+    X(80, 5, 32, 16, 5)          \
+    X(96, 6, 32, 16, 2, 3)       \
+    X(128, 8, 32, 16, 8)
+
+#define FFT3_SEG_PLANS_STRIDED(X) \
+    X(8, 1, 64, 8)                \
+    X(16, 4, 32, 4, 4)            \
+    X(24, 4, 32, 8, 3)            \
+    X(32, 4, 32, 8, 4)            \
+    X(40, 5, 32, 8, 5)            \
+    X(48, 4, 32, 16, 3)           \
+    X(64, 8, 32, 8, 8)            \
+    X(80, 5, 32, 16, 5)           \
+    X(96, 8, 32, 4, 8, 3)         \
+    X(128, 8, 32, 16, 8)
 
 struct SegKernel {
-    int n, T, lpt_c, lpt_s, nrad;
+    int n, T, lpt, nrad;
     int rad[4];
-    const void *func_c; // contiguous lines (x)
-    const void *func_s; // strided lines (y, z)
+    const void *func;
 };
 
-// The compiled list (device translation unit) and its size.
-const SegKernel *seg_kernels(int *count);
+// The compiled lists (device translation unit) and their sizes.
+const SegKernel *seg_kernels(bool contiguous, int *count);
 
 } // namespace fft3
