@@ -41,18 +41,30 @@ def _peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-# Host-only sources (planning, launching, the C ABI): they do not change what a kernel reads or writes.
-_HOST_SOURCES = ("planner.cpp", "planner.h", "capi.cu", "capi_internal.h", "autotune.cu", "batched_host.cu")
+# Translation units of the kernels whose DRAM traffic profiles/traffic.txt records
+# (the streamed strided pass and the contiguous pass).
+_TRAFFIC_UNITS = ("k_cstream.cu", "k_fixed_a.cu", "k_fixed_b.cu")
 
 
 def _csrc_sha() -> str:
-    """Hash of the device-code sources (kernels, their headers and argument structs)."""
-    h = hashlib.sha256()
+    """Hash of the sources those kernels compile from: their translation units
+    and every header they include, directly or not."""
     d = os.path.join(ROOT, "paper_1904_10119_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")) and name not in _HOST_SOURCES:
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    seen, stack = set(), list(_TRAFFIC_UNITS)
+    while stack:
+        name = stack.pop()
+        path = os.path.join(d, name)
+        if name in seen or not os.path.exists(path):
+            continue
+        seen.add(name)
+        for line in open(path):
+            m = re.match(r'\s*#include\s+"([^"]+)"', line)
+            if m and not m.group(1).startswith(".."):
+                stack.append(os.path.normpath(m.group(1)))
+    h = hashlib.sha256()
+    for name in sorted(seen):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
