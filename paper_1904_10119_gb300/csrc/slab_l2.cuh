@@ -165,27 +165,11 @@ struct GStoreBlk { // element k of an x line at p[(k/16)*s + k%16]
         p[(int64_t)(k >> 4) * s + (k & 15)] = conj ? cconj(v) : v;
     }
 };
-struct GCol16 { // element j of a column of a block at p[16 j]; loads bypass L1,
-                // stores are marked evict-first (the final values leave L2 first)
+struct GCol16 { // element j of a column of a block at p[16 j]; stores are marked
+                // evict-first (the final values leave L2 first)
     float2 *p;
     bool conj;
-    __device__ __forceinline__ float2 operator()(int j) const
-    {
-        const float2 v = __ldcg(p + 16 * j);
-        return conj ? cconj(v) : v;
-    }
     __device__ __forceinline__ void operator()(int k, float2 v) const { __stcs(p + 16 * k, conj ? cconj(v) : v); }
-};
-// Unit-stride line reader marked evict-first: each input value is read once,
-// so the input must not push the slabs' intermediate values out of L2.
-struct GLoadStream {
-    const float2 *p;
-    bool conj;
-    __device__ __forceinline__ float2 operator()(int j) const
-    {
-        const float2 v = __ldcs(p + j);
-        return conj ? cconj(v) : v;
-    }
 };
 
 // Readers of a landing buffer filled by TMA (dense, no padding), with the
