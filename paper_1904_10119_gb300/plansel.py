@@ -141,22 +141,41 @@ def to_xy(table, batch=1):
 
 
 class CostModel:
-    """Feature standardisation + the library perceptron."""
+    """Feature standardisation + the library perceptron; `members` networks
+    with different seeds are trained on the same data and their predictions
+    averaged (an ensemble lowers the variance of the ranking)."""
 
-    def __init__(self, hidden=64, seed=0):
+    def __init__(self, hidden=64, seed=0, members=1):
         self.hidden = hidden
         self.seed = seed
+        self.members = members
         self.mu = self.sd = None
-        self.mlp = None
+        self.mlps = []
+
+    @property
+    def mlp(self):
+        return self.mlps[0] if self.mlps else None
 
     def fit(self, X, y, epochs=200, batch=128, lr=1e-3):
         self.mu = X.mean(0)
         self.sd = X.std(0) + 1e-6
-        self.mlp = fft3.Mlp(X.shape[1], self.hidden, self.seed)
-        return self.mlp.train((X - self.mu) / self.sd, y, epochs=epochs, batch=batch, lr=lr, seed=self.seed + 1)
+        curve = None
+        for m in range(self.members):
+            s = self.seed + 101 * m
+            net = fft3.Mlp(X.shape[1], self.hidden, s)
+            c = net.train((X - self.mu) / self.sd, y, epochs=epochs, batch=batch, lr=lr, seed=s + 1)
+            curve = c if curve is None else curve
+            self.mlps.append(net)
+        return curve
 
     def predict(self, X):
-        return self.mlp.predict((X - self.mu) / self.sd)
+        Z = (X - self.mu) / self.sd
+        return np.mean([net.predict(Z) for net in self.mlps], axis=0)
+
+    def close(self):
+        for net in self.mlps:
+            net.close()
+        self.mlps = []
 
     def ranking(self, shape, batch=1):
         """Candidate indices the planner accepts for this shape, best
@@ -190,6 +209,22 @@ def analytic_ranking(shape, batch=1):
     return [i for _, i in sorted(scored)]
 
 
+def hybrid_ranking(model):
+    """The analytic preference first (fewest HBM sweeps, volumetric penalised by
+    half a sweep), the model's predicted run time among plans that tie on it."""
+    def rank(shape, batch=1):
+        order = model.ranking(shape, batch)
+        pos = {c: k for k, c in enumerate(order)}
+        key = {}
+        for i, (d, o) in enumerate(candidates()):
+            if i not in pos:
+                continue
+            s = fft3.fft3_plan_schedule(*shape, batch, 0, d, -1, fft3.make_options(**o))
+            key[i] = (s["hbm_sweeps"] + (0.5 if s["decomposition"] == "volumetric" else 0.0), pos[i])
+        return sorted(key, key=lambda i: key[i])
+    return rank
+
+
 def regrets(table, ranker):
     """regret = t(chosen) / t(best) - 1 per shape, where the chosen plan is the
     first of the ranking that can be created on the GPU (a proposal whose
@@ -212,7 +247,7 @@ def summarize(r):
             "max": float(np.max(r)), "zero_regret_frac": float(np.mean(r <= 1e-9))}
 
 
-def run(train_shapes=120, test_shapes=200, seed=8, max_volume=1 << 24, reps=3, epochs=400):
+def run(train_shapes=400, test_shapes=200, seed=8, max_volume=1 << 24, reps=3, epochs=400, members=5):
     t0 = time.perf_counter()
     train = sample_shapes(train_shapes, seed, max_volume)
     test = sample_shapes(test_shapes, seed + 1000, max_volume, exclude=train)
@@ -220,31 +255,33 @@ def run(train_shapes=120, test_shapes=200, seed=8, max_volume=1 << 24, reps=3, e
     tab_test = collect(test, reps=reps)
     t_collect = time.perf_counter() - t0
     X, y = to_xy(tab_train)
-    model = CostModel(seed=seed)
+    model = CostModel(seed=seed, members=members)
     curve = model.fit(X, y, epochs=epochs)
     res = {
         "train_shapes": len(train), "test_shapes": len(test), "train_plans": int(X.shape[0]),
-        "candidates": len(candidates()), "collect_seconds": t_collect,
+        "candidates": len(candidates()), "collect_seconds": t_collect, "members": members,
         "loss_first": float(curve[0]), "loss_last": float(curve[-1]),
         "regret_mlp": summarize(regrets(tab_test, lambda s: model.ranking(s))),
+        "regret_hybrid": summarize(regrets(tab_test, hybrid_ranking(model))),
         "regret_fixed_default": summarize(regrets(tab_test, lambda s: [0])),
         "regret_analytic": summarize(regrets(tab_test, analytic_ranking)),
         "exhaustive_ms_per_shape": float(np.mean([ms[ms > 0].sum() for _, ms in tab_test])),
     }
-    model.mlp.close()
+    model.close()
     return res
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train-shapes", type=int, default=120)
+    ap.add_argument("--train-shapes", type=int, default=400)
     ap.add_argument("--test-shapes", type=int, default=200)
     ap.add_argument("--seed", type=int, default=8)
     ap.add_argument("--max-volume", type=int, default=1 << 24)
     ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--members", type=int, default=5, help="networks averaged in the cost model")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    res = run(a.train_shapes, a.test_shapes, a.seed, a.max_volume, epochs=a.epochs)
+    res = run(a.train_shapes, a.test_shapes, a.seed, a.max_volume, epochs=a.epochs, members=a.members)
     s = json.dumps(res, indent=1)
     print(s)
     if a.out:
