@@ -337,3 +337,25 @@ def test_schedule_volumetric_six_step():
     assert [(p["p"], p["exchanges"]) for p in s["passes"]] == [(2, 3), (4, 3), (8, 3)]
     s = fft3.fft3_plan_schedule(256, 256, 256, 1, 0, fft3.FFT3_VOLUMETRIC, -1, fft3.make_options(mesh=(1, 4, 4)))
     assert all(p.get("exchanges", 1) == 1 for p in s["passes"])
+
+
+def test_schedule_complex128():
+    """FFT3_C128_FP64 lowers every decomposition but volumetric to the natural
+    pencil-pencil-pencil passes of the FP64 runtime-radix kernel, with shared
+    memory sized for 16-byte elements; other schedules are refused."""
+    for decomp in (fft3.FFT3_PENCIL3, fft3.FFT3_SLAB_PENCIL, fft3.FFT3_AUTO):
+        s = fft3.fft3_plan_schedule(1024, 48, 30, 2, fft3.FFT3_C128_FP64, decomp, -1)
+        assert s["decomposition"] == "pencil_pencil_pencil"
+        assert _kinds(s) == ["line_runtime_fp64"] * 3
+        for p in s["passes"]:
+            assert p["smem"] <= 227 * 1024
+            n = p["line"]["n"]
+            pitch = ((n - 1) + (n - 1) // 16 + 1) | 1
+            assert p["smem"] >= 16 * 2 * p["lpt"] * pitch  # two 16-byte buffers of lpt padded lines
+        assert s["passes"][0]["geom"]["ij"] == 1 and s["passes"][1]["geom"]["ij"] == 1024
+    s = fft3.fft3_plan_schedule(64, 1, 1, 1, fft3.FFT3_C128_FP64, fft3.FFT3_PENCIL3, 1)
+    assert _kinds(s) == ["line_runtime_fp64"]
+    for decomp, opts in ((fft3.FFT3_VOLUMETRIC, {}), (fft3.FFT3_PENCIL3, {"variant": fft3.FFT3_PPP_BLOCKED}),
+                         (fft3.FFT3_PENCIL3, {"layout": fft3.FFT3_LAYOUT_ROTATED})):
+        with pytest.raises(fft3.Fft3Error):
+            fft3.fft3_plan_schedule(64, 64, 64, 1, fft3.FFT3_C128_FP64, decomp, -1, fft3.make_options(**opts))
