@@ -234,11 +234,14 @@ size_t fft3_plan_workspace_bytes(fft3_plan p);
 
 /* Number of passes of the schedule: the valid indices of fft3_plan_execute_pass.
  * Without pipelined pairs (slab_mode 4) it is also the number of kernel
- * launches one fft3_plan_execute issues; a batched plan counts as one. */
+ * launches one fft3_plan_execute issues; a batched plan counts as one (its
+ * CUDA graph). */
 int fft3_plan_launches(fft3_plan p);
 
 /* Number of kernel launches one fft3_plan_execute issues (a pipelined pair
- * of passes launches each of its two kernels once per chunk). */
+ * of passes launches each of its two kernels once per chunk; a batched plan's
+ * graph holds one launch in executor mode, one per line length and dimension
+ * in segmented mode). */
 int fft3_plan_kernel_launches(fft3_plan p);
 
 /* JSON description of the pass schedule (decomposition, passes, kernels,
