@@ -258,6 +258,12 @@ static int build_launches(fft3_plan_s *P)
             break;
         case PK_G: L.func = (const void *)&k_pass_g; break;
         case PK_G64: L.func = (const void *)&k_pass_g64; break;
+        case PK_J64:
+        case PK_C64: {
+            const Fixed64Kernels *k64 = p.line.fixed >= 0 ? fixed64_kernels(p.line.fixed) : nullptr;
+            L.func = k64 ? (p.kind == PK_J64 ? k64->j : k64->c) : nullptr;
+            break;
+        }
         case PK_SLAB:
             L.func = (const void *)&k_slab;
             L.probe_g = natural_x(s);

@@ -278,13 +278,13 @@ __device__ __forceinline__ void lines_sync()
 // element j of this thread's line, `dst(k, v)` stores element k.  When the
 // source and destination alias, SYNC_MID places a barrier between reading
 // every input and writing any output.
-template <int N, int T, int R, int NS, bool SYNC_MID, int BAR = 0, int NT = 0, class Src, class Dst>
-__device__ __forceinline__ void stage_fixed(int t, const Src &src, const Dst &dst, const float2 *tw)
+template <int N, int T, int R, int NS, bool SYNC_MID, int BAR = 0, int NT = 0, class Src, class Dst, class C>
+__device__ __forceinline__ void stage_fixed(int t, const Src &src, const Dst &dst, const C *tw)
 {
     constexpr int NB = N / R;
     constexpr int BPT = (NB + T - 1) / T;
     constexpr bool FULL = (NB % T) == 0;
-    float2 v[BPT][R];
+    C v[BPT][R];
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         const int q = t + b * T;
@@ -329,9 +329,8 @@ struct EngineFixed;
 // destination is the caller's sink.
 template <int N, int T, int NS, int R, int BAR, int NT>
 struct EngineFixed<N, T, NS, Radices<R>, BAR, NT> {
-    template <bool FIRST, bool SINK_ALIASES, class Src, class Smem, class Dst>
-    __device__ __forceinline__ static void run(int t, const Src &src, const Smem &, const Dst &dst,
-                                               const float2 *tw)
+    template <bool FIRST, bool SINK_ALIASES, class Src, class Smem, class Dst, class C>
+    __device__ __forceinline__ static void run(int t, const Src &src, const Smem &, const Dst &dst, const C *tw)
     {
         stage_fixed<N, T, R, NS, SINK_ALIASES, BAR, NT>(t, src, dst, tw);
     }
@@ -339,9 +338,8 @@ struct EngineFixed<N, T, NS, Radices<R>, BAR, NT> {
 
 template <int N, int T, int NS, int R, int R2, int... Rest, int BAR, int NT>
 struct EngineFixed<N, T, NS, Radices<R, R2, Rest...>, BAR, NT> {
-    template <bool FIRST, bool SINK_ALIASES, class Src, class Smem, class Dst>
-    __device__ __forceinline__ static void run(int t, const Src &src, const Smem &sm, const Dst &dst,
-                                               const float2 *tw)
+    template <bool FIRST, bool SINK_ALIASES, class Src, class Smem, class Dst, class C>
+    __device__ __forceinline__ static void run(int t, const Src &src, const Smem &sm, const Dst &dst, const C *tw)
     {
         // The first stage reads its own source; later stages read the shared
         // buffer they also write, so they need the mid-stage barrier.

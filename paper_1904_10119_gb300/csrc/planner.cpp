@@ -344,7 +344,22 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
     const bool strided_in = g.ic == 1 && g.oc == 1;
     const int tc_mode = std::min(2, std::max(0, s->opts.tc_stages));
     if (s->dtype == FFT3_C128_FP64) {
-        // complex128: runtime radix list in FP64 (k_pass_g64), 16-byte elements
+        // complex128, 16-byte elements: the compile-time FP64 passes (k_pass64.cu)
+        // where the length has a fixed plan, else the runtime radix list (k_pass_g64)
+        const bool contig = contig_in && g.ok == 1;
+        if (p.line.fixed >= 0 && !rotate && (contig || (strided_in && p.line.T * kLpt64Strided <= 1024))) {
+            p.kind = contig ? PK_J64 : PK_C64;
+            p.tw_seg[0] = line_seg(s, p.line);
+            const int twl = tw_slots_h((int)s->tw[p.tw_seg[0]].m.size());
+            p.lpt = contig ? lpt_j(p.line.T) : kLpt64Strided;
+            p.threads = p.line.T * p.lpt;
+            p.smem_bytes = (twl + (contig ? p.lpt * pitch_h(n) : p.lpt * n)) * 16;
+            if (p.smem_bytes <= kSmemLimit) {
+                set_tiles(&p);
+                *out = p;
+                return FFT3_OK;
+            }
+        }
         rc = choose_line(n, order, false, &p.line, err);
         if (rc)
             return rc;
@@ -1130,8 +1145,8 @@ static const char *kind_name(int k)
                                   "slab_smem", "slab_l2", "volumetric_split", "copy", "unused",
                                   "line_strided_tma", "line_contig_tc", "line_strided_tc",
                                   "volumetric_split_fixed", "line_strided_stream", "slab_l2_blocked",
-                                  "line_runtime_fp64"};
-    return (k >= 0 && k <= 15) ? names[k] : "?";
+                                  "line_runtime_fp64", "line_contig_fp64", "line_strided_fp64"};
+    return (k >= 0 && k <= 17) ? names[k] : "?";
 }
 static const char *buf_name(int b)
 {

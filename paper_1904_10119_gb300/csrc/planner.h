@@ -28,6 +28,8 @@ enum PassKind {
     PK_CSTREAM = 13, // strided lines, decimated sub-lines streamed by TMA (k_cstream.cu)
     PK_SLABBLK = 14, // 2D slab DFT in one persistent launch, stored as blocked z pencils (k_slab_tma)
     PK_G64 = 15,     // complex128: runtime radix list in FP64 (k_pass_g64)
+    PK_J64 = 16,     // complex128: fixed plan, contiguous lines (k_pass_j64)
+    PK_C64 = 17,     // complex128: fixed plan, strided columns (k_pass_c64)
 };
 
 enum BufId { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };

@@ -138,6 +138,16 @@ struct FixedKernels {
 };
 const FixedKernels *fixed_kernels(int id);
 
+// complex128 passes of a fixed plan (k_pass64.cu): contiguous lines, lpt_j(T)
+// lines per tile; strided lines, kLpt64Strided columns per tile (0 if not compiled)
+constexpr int kLpt64Strided = 8;
+struct Fixed64Kernels {
+    int id;
+    const void *j;
+    const void *c;
+};
+const Fixed64Kernels *fixed64_kernels(int id);
+
 // Lines per tile of each compiled kernel kind for a plan with T threads per
 // line (0 = not compiled).
 // rows (x tiles) and columns (y tiles) per tile of the L2-resident slab kernel

@@ -341,19 +341,25 @@ def test_schedule_volumetric_six_step():
 
 def test_schedule_complex128():
     """FFT3_C128_FP64 lowers every decomposition but volumetric to the natural
-    pencil-pencil-pencil passes of the FP64 runtime-radix kernel, with shared
-    memory sized for 16-byte elements; other schedules are refused."""
+    pencil-pencil-pencil passes in FP64: the compiled kernels for lengths with
+    a fixed plan (contiguous and strided lines), the runtime-radix kernel for
+    the others, with shared memory sized for 16-byte elements; other schedules
+    are refused."""
     for decomp in (fft3.FFT3_PENCIL3, fft3.FFT3_SLAB_PENCIL, fft3.FFT3_AUTO):
         s = fft3.fft3_plan_schedule(1024, 48, 30, 2, fft3.FFT3_C128_FP64, decomp, -1)
         assert s["decomposition"] == "pencil_pencil_pencil"
-        assert _kinds(s) == ["line_runtime_fp64"] * 3
+        assert _kinds(s) == ["line_contig_fp64", "line_runtime_fp64", "line_runtime_fp64"]
         for p in s["passes"]:
             assert p["smem"] <= 227 * 1024
             n = p["line"]["n"]
             pitch = ((n - 1) + (n - 1) // 16 + 1) | 1
-            assert p["smem"] >= 16 * 2 * p["lpt"] * pitch  # two 16-byte buffers of lpt padded lines
+            buffers = 1 if p["kind"] == "line_contig_fp64" else 2  # the runtime kernel ping-pongs
+            assert p["smem"] >= 16 * buffers * p["lpt"] * pitch
         assert s["passes"][0]["geom"]["ij"] == 1 and s["passes"][1]["geom"]["ij"] == 1024
-    s = fft3.fft3_plan_schedule(64, 1, 1, 1, fft3.FFT3_C128_FP64, fft3.FFT3_PENCIL3, 1)
+    s = fft3.fft3_plan_schedule(1024, 1024, 512, 1, fft3.FFT3_C128_FP64, fft3.FFT3_AUTO, -1)
+    assert _kinds(s) == ["line_contig_fp64", "line_strided_fp64", "line_strided_fp64"]
+    assert [p["lpt"] for p in s["passes"][1:]] == [8, 8]  # 8 columns: 128-byte rows
+    s = fft3.fft3_plan_schedule(60, 1, 1, 1, fft3.FFT3_C128_FP64, fft3.FFT3_PENCIL3, 1)
     assert _kinds(s) == ["line_runtime_fp64"]
     for decomp, opts in ((fft3.FFT3_VOLUMETRIC, {}), (fft3.FFT3_PENCIL3, {"variant": fft3.FFT3_PPP_BLOCKED}),
                          (fft3.FFT3_PENCIL3, {"layout": fft3.FFT3_LAYOUT_ROTATED})):

@@ -25,7 +25,8 @@ def _run(shape, batch, direction, seed, decomposition=fft3.FFT3_PENCIL3, x=None)
     torch.cuda.synchronize()
     assert plan.check() == 0, fft3.last_error()
     assert torch.equal(xt.cpu(), torch.from_numpy(x)), "input was modified"
-    assert all(p["kind"] == "line_runtime_fp64" for p in plan.describe()["passes"])
+    kinds = {p["kind"] for p in plan.describe()["passes"]}
+    assert kinds <= {"line_runtime_fp64", "line_contig_fp64", "line_strided_fp64"}, kinds
     return x, out.cpu().numpy(), plan
 
 
@@ -33,8 +34,11 @@ def _run(shape, batch, direction, seed, decomposition=fft3.FFT3_PENCIL3, x=None)
     ((64, 48, 96), 1, fft3.FFT3_FORWARD), ((30, 25, 18), 3, fft3.FFT3_FORWARD),
     ((100, 60, 9), 1, fft3.FFT3_INVERSE), ((1024, 16, 9), 1, fft3.FFT3_FORWARD),
     ((4096, 2, 3), 1, fft3.FFT3_INVERSE), ((3, 4096, 2), 1, fft3.FFT3_FORWARD),
-    ((256, 256, 8), 1, fft3.FFT3_FORWARD), ((5, 1, 1), 2, fft3.FFT3_FORWARD)])
+    ((256, 256, 8), 1, fft3.FFT3_FORWARD), ((5, 1, 1), 2, fft3.FFT3_FORWARD), ((512, 64, 32), 1, fft3.FFT3_INVERSE),
+    ((64, 1024, 3), 1, fft3.FFT3_FORWARD), ((24, 16, 1024), 1, fft3.FFT3_INVERSE)])
 def test_c128_parity(shape, batch, direction):
+    """FP64 passes: the compiled ones (contiguous and strided lines of a fixed
+    plan's length) and the runtime-radix one, ragged tiles included."""
     x, got, _ = _run(shape, batch, direction, seed=sum(shape) + batch)
     ref = oracle.fft3(x.ravel(), *shape, batch, sign=direction)
     assert np.all(np.isfinite(got))
