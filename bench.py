@@ -68,6 +68,24 @@ def _csrc_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of x over the ranks of the default process group (x itself
+    without one): the job's step time is that of its slowest rank."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized() and \
+            torch.distributed.get_world_size() > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_transform(step_ms: float, world: int) -> float:
+    """Whole-job ms per transform: the path shards by independent transforms
+    (replicas), every rank runs one per step, so `world` transforms finish in
+    one step of the slowest rank."""
+    return step_ms / world
+
+
 def _profiled_traffic(kernel_kind: str):
     """DRAM bytes per launch of `kernel_kind` from the committed ncu summary,
     if it was taken on the current kernel sources."""
@@ -308,11 +326,8 @@ def main():
     clocks = sampler.stop()
     desc = plan.describe()
     mean_ms = sum(step_ms) / len(step_ms)
-    t_local = torch.tensor([mean_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
-    t_step = float(t_local.item())
-    value = t_step / world  # whole-job ms per transform (N replicas each do one per step)
+    t_step = max_over_ranks(mean_ms, "cuda")
+    value = job_ms_per_transform(t_step, world)
 
     # roofline of the dominant pass
     hbm, peak_kind = _peaks()
@@ -358,10 +373,8 @@ def main():
         pipelined_ms = (time.perf_counter() - t0) * 1e3 / 4
         fft3.fft3_plan_destroy(eplan)
         del h_out
-        e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": float(e2e_t.item()) / world, "unit": "ms", "h2d_bytes_per_step": 8 * N,
+        e2e = {"value": job_ms_per_transform(max_over_ranks(e2e_ms, "cuda"), world), "unit": "ms",
+               "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * N, "steps": e2e_steps, "api": "fft3_plan_execute_host",
                "pipelined_ms_per_transform": pipelined_ms}
 

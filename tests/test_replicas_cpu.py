@@ -1,0 +1,51 @@
+"""The N > 1 path of bench.py on CPU: two ranks over gloo (one process per
+rank, rendezvous on 127.0.0.1), the job time is the slowest rank's and the
+whole-job value divides it by the number of replicas."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank: int, world: int, port: int, q):
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+    try:
+        local = 3.0 + 2.5 * rank          # rank 1 is the slow one
+        t = bench.max_over_ranks(local, "cpu")
+        q.put((rank, t, bench.job_ms_per_transform(t, world)))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_replicas_over_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    assert [g[1] for g in got] == [5.5, 5.5]      # both ranks see the slowest rank's time
+    assert [g[2] for g in got] == [2.75, 2.75]    # two transforms per step of 5.5 ms
+
+
+def test_single_process_needs_no_group():
+    import bench
+    assert not dist.is_initialized()
+    assert bench.max_over_ranks(4.0, "cpu") == 4.0
+    assert bench.job_ms_per_transform(4.0, 1) == 4.0
