@@ -196,6 +196,14 @@ int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int d
 int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets,
                           int dtype, int decomposition, int direction, const int *tuning);
 
+/* Host-only planning of a batched plan, no device needed: the JSON description
+ * fft3_plan_create_many's plan would give (mode, kernel launches, problems,
+ * work items, line plans, size classes with their tuning codes), without the
+ * launch grid.  Same arguments as fft3_plan_create_many; returns the length
+ * needed (excluding the terminator) or a negative FFT3_ERR_* code. */
+int fft3_plan_schedule_many(int count, const int *dims, const int64_t *offsets, int dtype, int decomposition,
+                            int direction, const int *tuning, char *buf, size_t len);
+
 /* Execute on `stream` (a cudaStream_t, NULL = legacy default stream).
  * in, out: device pointers to batch*n0*n1*n2 complex64 values (or the
  * extent covered by the offsets of a batched plan).  `in` is not modified.

@@ -36,6 +36,14 @@ struct SegLaunch {
 struct BatchState {
     int seg = 0; // 1: three segmented passes (k_segmented.cu) instead of the persistent executor
     std::vector<SegLaunch> seg_launches;
+    // host tables built by the planning: twiddle segments (offset, count), their
+    // exponents and line lengths; the segmented passes' problem lists, first
+    // tiles and per-tile slots
+    std::vector<std::pair<int64_t, int64_t>> h_segs;
+    std::vector<std::vector<int64_t>> h_exps;
+    std::vector<int> h_exp_n;
+    std::vector<int> h_seg_list, h_seg_tcube;
+    std::vector<int64_t> h_seg_tstart;
     int *d_seg_list = nullptr, *d_seg_tcube = nullptr;
     int64_t *d_seg_tstart = nullptr;
     std::vector<BatchCube> cubes;
@@ -178,7 +186,16 @@ int batch_describe(const BatchState *b, std::string *json)
       << batch_kernel_launches(b) << ",\"problems\":" << b->cubes.size() << ",\"items\":" << b->items.size()
       << ",\"groups\":" << b->groups << ",\"line_plans\":" << b->lines.size() << ",\"grid\":" << b->grid.x
       << ",\"block\":" << b->threads << ",\"smem\":" << b->smem << ",\"prefetch\":" << b->prefetch << ",\"twiddle_entries\":" << b->tw_total
-      << ",\"extent\":" << b->extent << ",\"classes\":[";
+      << ",\"extent\":" << b->extent << ",\"segmented_launches\":[";
+    for (size_t k = 0; k < b->seg_launches.size(); ++k) {
+        const SegLaunch &L = b->seg_launches[k];
+        const int64_t nprob = (k + 1 < b->seg_launches.size() ? b->seg_launches[k + 1].list_off
+                                                              : (int64_t)b->h_seg_list.size()) - L.list_off;
+        o << (k ? "," : "") << "{\"dim\":" << L.dim << ",\"n\":" << L.n << ",\"lines_per_tile\":" << L.lpt
+          << ",\"tiles\":" << L.ntiles << ",\"problems\":" << nprob << ",\"threads\":" << L.threads
+          << ",\"smem\":" << L.smem << "}";
+    }
+    o << "],\"classes\":[";
     bool first = true;
     for (auto &kv : cls) {
         o << (first ? "" : ",") << "{\"dims\":[" << std::get<0>(kv.first) << "," << std::get<1>(kv.first) << ","
@@ -278,12 +295,19 @@ int batch_execute(fft3_plan p, const void *in, void *out, cudaStream_t st)
 
 using namespace fft3;
 
-extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets, int dtype,
-                                     int decomposition, int direction, const int *tuning)
+// Host planning of a batched plan (no device calls): problems, line plans and
+// their twiddle exponents, work items of the executor, and the launches and
+// tables of the segmented passes.  Errors return an FFT3_ERR_* code (message
+// in fft3_last_error); the caller frees `b`.
+static int batch_plan_host(BatchState *b, int count, const int *dims, const int64_t *offsets, int dtype,
+                           int decomposition, int direction, const int *tuning)
 {
-    if (!out)
-        return fail(FFT3_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
+    auto &segs = b->h_segs;
+    auto &exps = b->h_exps;
+    auto &exp_n = b->h_exp_n;
+    auto &seg_list = b->h_seg_list;
+    auto &seg_tcube = b->h_seg_tcube;
+    auto &seg_tstart = b->h_seg_tstart;
     if (count < 1 || !dims || !offsets)
         return fail(FFT3_ERR_INVALID_ARG, "count must be positive and dims/offsets non-null");
     if (direction != FFT3_FORWARD && direction != FFT3_INVERSE)
@@ -292,9 +316,6 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         return fail(FFT3_ERR_UNSUPPORTED_SIZE, "batched plans compute in FP32 only");
     if (decomposition != FFT3_AUTO && decomposition != FFT3_SLAB_PENCIL && decomposition != FFT3_PENCIL3)
         return fail(FFT3_ERR_INVALID_ARG, "batched plans support slab-pencil, pencil-pencil-pencil or auto");
-    auto *b = new (std::nothrow) BatchState();
-    if (!b)
-        return fail(FFT3_ERR_OOM, "host allocation failed");
     std::string err;
     std::map<std::pair<int, int>, int> lidx;
     b->conj = direction == FFT3_INVERSE ? 1 : 0;
@@ -306,7 +327,6 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         const int n0 = dims[3 * i], n1 = dims[3 * i + 1], n2 = dims[3 * i + 2];
         if (n0 < 1 || n1 < 1 || n2 < 1 || n0 > kBatchMaxLine || n1 > kBatchMaxLine || n2 > kBatchMaxLine ||
             !smooth_b(n0) || !smooth_b(n1) || !smooth_b(n2) || offsets[i] < 0) {
-            batch_free(b);
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, "problem " + std::to_string(i) +
                                                        ": dimensions must be 2*3*5-smooth and at most " +
                                                        std::to_string(kBatchMaxLine) + ", offsets non-negative");
@@ -324,10 +344,9 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         c.decomp = decomp;
         c.lpt = lpt;
         c.lpty = lpty;
-        int rc = 0, lx = line_index(b, lidx, n0, order, &err), ly = line_index(b, lidx, n1, order, &err),
+        int lx = line_index(b, lidx, n0, order, &err), ly = line_index(b, lidx, n1, order, &err),
             lz = line_index(b, lidx, n2, order, &err);
         if (lx < 0 || ly < 0 || lz < 0) {
-            batch_free(b);
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, err);
         }
         c.lx = lx; c.ly = ly; c.lz = lz;
@@ -346,7 +365,6 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
             c.items[2] = (n0 * n1 + lpt - 1) / lpt;
             bufmax = std::max(bufmax, std::max(c.spi * pitch_b(n0), std::max(lpty * pitch_b(n1), lpt * pitch_b(n2))));
         }
-        (void)rc;
         b->tuning[i] = (decomp == BD_SLAB ? 1 : 2) | ((order + 1) << 2) |
                        ((lpt == 4 ? 1 : lpt == 8 ? 2 : lpt == 16 ? 3 : 4) << 5);
         extent = std::max(extent, offsets[i] + (int64_t)n0 * n1 * n2);
@@ -377,7 +395,6 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
             values += (int64_t)dims[3 * i] * dims[3 * i + 1] * dims[3 * i + 2];
         }
         if (all3 && !ok) {
-            batch_free(b);
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, "the segmented passes have no compiled plan for a line length "
                                                    "of this batch");
         }
@@ -391,15 +408,11 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
     b->prefetch = 3 * b->buf_elems * (int)sizeof(float2) <= 200 * 1024 ? 1 : 0;
     b->smem = (2 + b->prefetch) * b->buf_elems * (int)sizeof(float2);
     if (b->smem > 227 * 1024) {
-        batch_free(b);
         return fail(FFT3_ERR_UNSUPPORTED_SIZE, "a work item of this batch needs more shared memory than a block has");
     }
     // line plans and their twiddle tables
     std::vector<int64_t> m;
-    std::vector<std::pair<int64_t, int64_t>> segs; // (offset, count) per line plan
     int64_t tw_total = 0;
-    std::vector<std::vector<int64_t>> exps;
-    std::vector<int> exp_n; // line length of each table
     for (const LineChoice &lc : b->line_choice) {
         std::vector<int64_t> e;
         line_twiddle_exponents(lc, &e);
@@ -420,8 +433,6 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
     }
     // segmented passes: per dimension and line length, the listed problems,
     // the first tile of each and the problem slot of every tile
-    std::vector<int> seg_list, seg_tcube;
-    std::vector<int64_t> seg_tstart;
     if (b->seg) {
         for (int d = 0; d < 3; ++d) {
             std::map<int, std::vector<int>> byn;
@@ -511,12 +522,37 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
             }
         }
     if (b->items.size() >= (size_t)0x7fffffff) {
-        batch_free(b);
         return fail(FFT3_ERR_UNSUPPORTED_SIZE, "too many work items");
     }
+    return FFT3_OK;
+}
+
+extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets, int dtype,
+                                     int decomposition, int direction, const int *tuning)
+{
+    if (!out)
+        return fail(FFT3_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    auto *b = new (std::nothrow) BatchState();
+    if (!b)
+        return fail(FFT3_ERR_OOM, "host allocation failed");
+    int rc = batch_plan_host(b, count, dims, offsets, dtype, decomposition, direction, tuning);
+    if (rc) {
+        batch_free(b);
+        return rc;
+    }
+    const auto &segs = b->h_segs;
+    const auto &exps = b->h_exps;
+    const auto &exp_n = b->h_exp_n;
+    const auto &seg_list = b->h_seg_list;
+    const auto &seg_tcube = b->h_seg_tcube;
+    const auto &seg_tstart = b->h_seg_tstart;
+    const int64_t extent = b->extent, tw_total = b->tw_total;
+    int ccnt = 0, scnt = 0;
+    const SegKernel *skc = seg_kernels(true, &ccnt), *sks = seg_kernels(false, &scnt);
     // device state
     int dev = 0;
-    int rc = check_device(&dev);
+    rc = check_device(&dev);
     if (rc) {
         batch_free(b);
         return rc;
@@ -594,4 +630,25 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         return bail(fail(FFT3_ERR_CUDA, "stream creation failed"));
     *out = P;
     return FFT3_OK;
+}
+
+extern "C" int fft3_plan_schedule_many(int count, const int *dims, const int64_t *offsets, int dtype,
+                                       int decomposition, int direction, const int *tuning, char *buf, size_t len)
+{
+    auto *b = new (std::nothrow) BatchState();
+    if (!b)
+        return fail(FFT3_ERR_OOM, "host allocation failed");
+    int rc = batch_plan_host(b, count, dims, offsets, dtype, decomposition, direction, tuning);
+    std::string j;
+    if (!rc)
+        batch_describe(b, &j);
+    batch_free(b);
+    if (rc)
+        return rc;
+    if (buf && len > 0) {
+        const size_t c = std::min(len - 1, j.size());
+        memcpy(buf, j.data(), c);
+        buf[c] = 0;
+    }
+    return (int)j.size();
 }

@@ -75,6 +75,7 @@ def load() -> ctypes.CDLL:
         "fft3_plan_execute_host_pipelined": (i, [_P, _P, _P, ctypes.c_int, _P]),
         "fft3_plan_describe": (i, [_P, ctypes.c_char_p, sz]),
         "fft3_plan_schedule": (i, [i, i, i, i, i, i, i, ctypes.POINTER(fft3_options), ctypes.c_char_p, sz]),
+        "fft3_plan_schedule_many": (i, [i, pi, ctypes.POINTER(ctypes.c_int64), i, i, i, pi, ctypes.c_char_p, sz]),
         "fft3_factorize": (i, [i, i, pi, i]),
         "fft3_layout_positions": (i, [i, i, i, i, i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                       i64]),
@@ -166,6 +167,20 @@ def fft3_plan_create_many(dims, offsets, dtype=FFT3_C64_FP32, decomposition=FFT3
     h = _P()
     _check(load().fft3_plan_create_many(ctypes.byref(h), count, d, o, dtype, decomposition, direction, t))
     return h.value
+
+
+def fft3_plan_schedule_many(dims, offsets, dtype=FFT3_C64_FP32, decomposition=FFT3_AUTO,
+                            direction=FFT3_FORWARD, tuning=None) -> dict:
+    """Host-only description of the batched plan fft3_plan_create_many would build."""
+    count = len(offsets)
+    d = (ctypes.c_int * (3 * count))(*[int(v) for v in list(_flat(dims))])
+    o = (ctypes.c_int64 * count)(*[int(v) for v in offsets])
+    t = (ctypes.c_int * count)(*[int(v) for v in tuning]) if tuning is not None else None
+    L = load()
+    n = _check(L.fft3_plan_schedule_many(count, d, o, dtype, decomposition, direction, t, None, 0))
+    buf = ctypes.create_string_buffer(n + 1)
+    _check(L.fft3_plan_schedule_many(count, d, o, dtype, decomposition, direction, t, buf, n + 1))
+    return json.loads(buf.value.decode())
 
 
 def _flat(dims):

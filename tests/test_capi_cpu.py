@@ -365,3 +365,43 @@ def test_schedule_complex128():
                          (fft3.FFT3_PENCIL3, {"layout": fft3.FFT3_LAYOUT_ROTATED})):
         with pytest.raises(fft3.Fft3Error):
             fft3.fft3_plan_schedule(64, 64, 64, 1, fft3.FFT3_C128_FP64, decomp, -1, fft3.make_options(**opts))
+
+
+def _batch_layout(dims):
+    vols = [int(np.prod(d)) for d in dims]
+    offs = np.zeros(len(dims), np.int64)
+    offs[1:] = np.cumsum(vols[:-1])
+    return offs
+
+
+def test_schedule_many_modes_and_segmented_tables():
+    """Host-only batched planning: FFT3_AUTO without tuning codes takes the
+    segmented passes for a large batch of compiled lengths (one launch per
+    dimension and line length, tiles = sum over its problems of ceil(lines /
+    lines per tile)) and the executor for a small one, for explicit
+    decompositions or for zero codes; codes of 3 ask for the segmented passes."""
+    from paper_1904_10119_gb300 import synth
+    dims = synth.batched_dims(512, 7)
+    offs = _batch_layout(dims)
+    d = fft3.fft3_plan_schedule_many(dims, offs)
+    assert d["mode"] == "segmented" and d["problems"] == 512
+    launches = d["segmented_launches"]
+    assert d["kernel_launches"] == len(launches) == sum(len(set(dims[:, k])) for k in range(3))
+    for L in launches:
+        k, n = L["dim"], L["n"]
+        sel = dims[dims[:, k] == n]
+        lines = {0: sel[:, 1] * sel[:, 2], 1: sel[:, 0] * sel[:, 2], 2: sel[:, 0] * sel[:, 1]}[k]
+        lpt = L["lines_per_tile"]
+        assert L["problems"] == len(sel)
+        assert L["tiles"] == int(sum((int(v) + lpt - 1) // lpt for v in lines))
+    assert [L["dim"] for L in launches] == sorted(L["dim"] for L in launches)  # x, then y, then z
+    assert all(c["tuning"] == 3 for c in d["classes"])
+    small = synth.batched_dims(6, 7)
+    assert fft3.fft3_plan_schedule_many(small, _batch_layout(small))["mode"] == "executor"
+    for kw in ({"decomposition": fft3.FFT3_PENCIL3}, {"tuning": [0] * len(dims)}):
+        assert fft3.fft3_plan_schedule_many(dims, offs, **kw)["mode"] == "executor"
+    d = fft3.fft3_plan_schedule_many(small, _batch_layout(small), tuning=[3] * len(small))
+    assert d["mode"] == "segmented" and d["kernel_launches"] == len(d["segmented_launches"])
+    for bad_dims, tuning in (([[30, 16, 16]], [3]), ([[7, 8, 8]], None), ([[256, 8, 8]], None)):
+        with pytest.raises(fft3.Fft3Error):
+            fft3.fft3_plan_schedule_many(bad_dims, [0], tuning=tuning)
