@@ -511,7 +511,7 @@ static bool volumetric_split(int n, int p, int *a, int *b)
     return true;
 }
 
-static int vol_smem(int n, int p, int a, int b, int lpt, int twlen)
+static int vol_smem(int p, int a, int b, int lpt, int twlen)
 {
     int sub_b = lpt * (a / p) * pitch_h(b); // T0: lpt*(a/p) rows of length b
     int sub_a = lpt * (b / p) * pitch_h(a); // T1: lpt*(b/p) columns of length a
@@ -629,10 +629,10 @@ static int make_vol_pass(Schedule *s, int d, int n, int p, const PassGeom &g, in
         twlen += tw_slots_h((int)s->tw[q.tw_seg[k]].m.size());
     const bool strided = g.ic == 1;
     int lpt = strided ? (s->opts.tile_lines == 8 ? 8 : 16) : std::max(1, 512 / std::max(1, n / p / 4));
-    while (lpt > 1 && vol_smem(n, p, q.split_a, q.split_b, lpt, twlen) > kSmemLimit)
+    while (lpt > 1 && vol_smem(p, q.split_a, q.split_b, lpt, twlen) > kSmemLimit)
         lpt /= 2;
     q.lpt = lpt;
-    q.smem_bytes = vol_smem(n, p, q.split_a, q.split_b, lpt, twlen);
+    q.smem_bytes = vol_smem(p, q.split_a, q.split_b, lpt, twlen);
     if (q.smem_bytes > kSmemLimit) {
         *err = "volumetric pass does not fit in shared memory";
         return FFT3_ERR_UNSUPPORTED_SIZE;
