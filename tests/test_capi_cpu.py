@@ -405,3 +405,23 @@ def test_schedule_many_modes_and_segmented_tables():
     for bad_dims, tuning in (([[30, 16, 16]], [3]), ([[7, 8, 8]], None), ([[256, 8, 8]], None)):
         with pytest.raises(fft3.Fft3Error):
             fft3.fft3_plan_schedule_many(bad_dims, [0], tuning=tuning)
+
+
+def test_headline_plan_is_the_blocked_streamed_schedule():
+    """FFT3_AUTO at 1024^3 (the bench's workload): pencil-pencil-pencil with the
+    blocked intermediate: the x pass from `in` to `out`, the y pass streamed
+    into the workspace as [x/16][z][y][x%16], the z pass streamed back to
+    natural order, both with the k_cstream instance (Q = 4 sub-lines of 256
+    points, two groups, 16 columns) whose DRAM traffic the bench reports; at
+    512^3 (2 MiB between natural z lines) the natural schedule."""
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, 0, fft3.FFT3_AUTO, -1)
+    assert s["decomposition"] == "pencil_pencil_pencil" and s["variant"] == fft3.FFT3_PPP_BLOCKED
+    assert _kinds(s) == ["line_contig", "line_strided_stream", "line_strided_stream"]
+    px, py, pz = s["passes"]
+    assert [(p["src"], p["dst"]) for p in (px, py, pz)] == [("in", "out"), ("out", "workspace"), ("workspace", "out")]
+    for p in (py, pz):
+        assert (p["q"], p["m"], p["groups"], p["cluster"], p["lpt"]) == (4, 256, 2, 1, 16)
+    assert px["line"]["radices"] == [16, 16, 4] and px["line"]["T"] == 64
+    assert (pz["geom"]["ij"], pz["geom"]["ok"]) == (16 * 1024, 1024 * 1024)
+    s = fft3.fft3_plan_schedule(512, 512, 512, 1, 0, fft3.FFT3_AUTO, -1)
+    assert s["variant"] == fft3.FFT3_PPP_NATURAL and _kinds(s)[0] == "line_contig"
