@@ -219,7 +219,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU oracle baseline")
     ap.add_argument("--batched", type=int, default=0, metavar="COUNT",
-                    help="only time the batched executor on COUNT uneven cubes (seed 7) and print its line")
+                    help="only time COUNT uneven cubes (seed 7): the default batched plan and the persistent executor")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -49,3 +49,24 @@ def test_single_process_needs_no_group():
     assert not dist.is_initialized()
     assert bench.max_over_ranks(4.0, "cpu") == 4.0
     assert bench.job_ms_per_transform(4.0, 1) == 4.0
+
+
+def test_reference_arm_runs_on_rank_0_only():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores): one JSON
+    line from rank 0 with the contract's keys; any other rank exits 0 silently."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--n", "16", "--steps", "1",
+           "--warmup", "3", "--cpu-seconds", "0.2"]
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["unit"] == "ms" and line["higher_is_better"] is False
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0 and not out.stdout.strip()
