@@ -425,3 +425,44 @@ def test_headline_plan_is_the_blocked_streamed_schedule():
     assert (pz["geom"]["ij"], pz["geom"]["ok"]) == (16 * 1024, 1024 * 1024)
     s = fft3.fft3_plan_schedule(512, 512, 512, 1, 0, fft3.FFT3_AUTO, -1)
     assert s["variant"] == fft3.FFT3_PPP_NATURAL and _kinds(s)[0] == "line_contig"
+
+
+def _replay_positions(s, total):
+    """Moves labels through the schedule's pass geometries with an identity line
+    transform (element j of an input line -> element j of its output line): the
+    index map the fused redistributions apply, as the GPU layout probe does."""
+    bufs = {"in": np.arange(total, dtype=np.int64), "out": np.full(total, -1, np.int64),
+            "workspace": np.full(total, -1, np.int64)}
+    for p in s["passes"]:
+        g, n = p["geom"], p["line"]["n"]
+        j = np.arange(n)[:, None, None, None]
+        c = np.arange(g["C"])[None, :, None, None]
+        a = np.arange(g["A"])[None, None, :, None]
+        b = np.arange(g["B"])[None, None, None, :]
+        src = (j * g["ij"] + c * g["ic"] + a * g["ia"] + b * g["ib"]).ravel()
+        dst = (j * g["ok"] + c * g["oc"] + a * g["oa"] + b * g["ob"]).ravel()
+        vals = bufs[p["src"]][src].copy()
+        bufs[p["dst"]][dst] = vals
+    return bufs["out"]
+
+
+@pytest.mark.parametrize("layout,name,shape,batch", [
+    (fft3.FFT3_LAYOUT_ROTATED, "rotated", (8, 6, 10), 2), (fft3.FFT3_LAYOUT_ROTATED, "rotated", (4, 5, 3), 1),
+    (fft3.FFT3_LAYOUT_PENCILS, "pencils", (32, 6, 10), 1), (fft3.FFT3_LAYOUT_PENCILS, "pencils", (16, 3, 5), 1)])
+def test_layout_schedules_move_elements_to_exported_positions(layout, name, shape, batch):
+    """Bit-exact on the host: the forward plan's passes put natural element i at
+    fft3_layout_positions(i); the inverse plan's passes bring the element at that
+    position back to natural index i (and the natural layout is the identity)."""
+    n0, n1, n2 = shape
+    total = n0 * n1 * n2 * batch
+    pos = fft3.fft3_layout_positions(layout, n0, n1, n2, batch)
+    fwd = fft3.fft3_plan_schedule(n0, n1, n2, batch, 0, fft3.FFT3_PENCIL3, fft3.FFT3_FORWARD,
+                                  fft3.make_options(layout=layout))
+    out = _replay_positions(fwd, total)
+    assert np.array_equal(out[pos], np.arange(total))  # label i sits at pos[i]
+    inv = fft3.fft3_plan_schedule(n0, n1, n2, batch, 0, fft3.FFT3_PENCIL3, fft3.FFT3_INVERSE,
+                                  fft3.make_options(layout=layout))
+    back = _replay_positions(inv, total)               # label = input position
+    assert np.array_equal(back, pos)                   # natural i comes from pos[i]
+    nat = fft3.fft3_plan_schedule(n0, n1, n2, batch, 0, fft3.FFT3_PENCIL3, fft3.FFT3_FORWARD)
+    assert np.array_equal(_replay_positions(nat, total), np.arange(total))
