@@ -466,3 +466,20 @@ def test_layout_schedules_move_elements_to_exported_positions(layout, name, shap
     assert np.array_equal(back, pos)                   # natural i comes from pos[i]
     nat = fft3.fft3_plan_schedule(n0, n1, n2, batch, 0, fft3.FFT3_PENCIL3, fft3.FFT3_FORWARD)
     assert np.array_equal(_replay_positions(nat, total), np.arange(total))
+
+
+@pytest.mark.parametrize("shape,batch,opts,first_kinds", [
+    ((16, 512, 512), 1, {"variant": fft3.FFT3_PPP_BLOCKED}, ["line_contig", "line_strided_stream"]),
+    ((64, 32, 16), 3, {"variant": fft3.FFT3_PPP_ROTATE}, ["line_contig_rotate"]),
+    ((48, 20, 30), 3, {"variant": fft3.FFT3_PPP_ROTATE}, ["line_runtime"]),
+    ((60, 6, 64), 2, {}, ["line_contig"]),
+    ((32, 512, 8), 1, {"variant": fft3.FFT3_PPP_BLOCKED}, ["line_contig"])])
+def test_natural_schedules_compose_to_the_identity(shape, batch, opts, first_kinds):
+    """The redistributions fused into the passes (the blocked [x/16][z][y][x%16]
+    workspace, the rotations xyz -> yzx -> zxy -> xyz, in-place strided passes)
+    leave every element at its natural index at the end, bit-exactly."""
+    n0, n1, n2 = shape
+    total = n0 * n1 * n2 * batch
+    s = fft3.fft3_plan_schedule(n0, n1, n2, batch, 0, fft3.FFT3_PENCIL3, fft3.FFT3_FORWARD, fft3.make_options(**opts))
+    assert _kinds(s)[:len(first_kinds)] == first_kinds
+    assert np.array_equal(_replay_positions(s, total), np.arange(total))
