@@ -434,7 +434,9 @@ def _replay_positions(s, total):
     bufs = {"in": np.arange(total, dtype=np.int64), "out": np.full(total, -1, np.int64),
             "workspace": np.full(total, -1, np.int64)}
     for p in s["passes"]:
-        g, n = p["geom"], p["line"]["n"]
+        # a cluster split describes its DFT_b sub-line plan; the whole line has a*b points
+        split = p["kind"] in ("volumetric_split", "volumetric_split_fixed")
+        g, n = p["geom"], (p["a"] * p["b"] if split else p["line"]["n"])
         j = np.arange(n)[:, None, None, None]
         c = np.arange(g["C"])[None, :, None, None]
         a = np.arange(g["A"])[None, None, :, None]
@@ -468,18 +470,21 @@ def test_layout_schedules_move_elements_to_exported_positions(layout, name, shap
     assert np.array_equal(_replay_positions(nat, total), np.arange(total))
 
 
-@pytest.mark.parametrize("shape,batch,opts,first_kinds", [
-    ((16, 512, 512), 1, {"variant": fft3.FFT3_PPP_BLOCKED}, ["line_contig", "line_strided_stream"]),
-    ((64, 32, 16), 3, {"variant": fft3.FFT3_PPP_ROTATE}, ["line_contig_rotate"]),
-    ((48, 20, 30), 3, {"variant": fft3.FFT3_PPP_ROTATE}, ["line_runtime"]),
-    ((60, 6, 64), 2, {}, ["line_runtime"]),
-    ((32, 512, 8), 1, {"variant": fft3.FFT3_PPP_BLOCKED}, ["line_contig"])])
-def test_natural_schedules_compose_to_the_identity(shape, batch, opts, first_kinds):
+@pytest.mark.parametrize("shape,batch,decomp,opts,first_kinds", [
+    ((16, 512, 512), 1, fft3.FFT3_PENCIL3, {"variant": fft3.FFT3_PPP_BLOCKED}, ["line_contig", "line_strided_stream"]),
+    ((64, 32, 16), 3, fft3.FFT3_PENCIL3, {"variant": fft3.FFT3_PPP_ROTATE}, ["line_contig_rotate"]),
+    ((48, 20, 30), 3, fft3.FFT3_PENCIL3, {"variant": fft3.FFT3_PPP_ROTATE}, ["line_runtime"]),
+    ((60, 6, 64), 2, fft3.FFT3_PENCIL3, {}, ["line_runtime"]),
+    ((32, 512, 8), 1, fft3.FFT3_PENCIL3, {"variant": fft3.FFT3_PPP_BLOCKED}, ["line_contig"]),
+    ((64, 64, 32), 1, fft3.FFT3_VOLUMETRIC, {"mesh": (2, 2, 2), "tile_lines": 16}, ["volumetric_split"]),
+    ((64, 512, 16), 1, fft3.FFT3_VOLUMETRIC, {}, ["line_contig", "line_strided_stream"])])
+def test_natural_schedules_compose_to_the_identity(shape, batch, decomp, opts, first_kinds):
     """The redistributions fused into the passes (the blocked [x/16][z][y][x%16]
-    workspace, the rotations xyz -> yzx -> zxy -> xyz, in-place strided passes)
-    leave every element at its natural index at the end, bit-exactly."""
+    workspace, the rotations xyz -> yzx -> zxy -> xyz, in-place strided and
+    cluster-split passes) leave every element at its natural index at the end,
+    bit-exactly."""
     n0, n1, n2 = shape
     total = n0 * n1 * n2 * batch
-    s = fft3.fft3_plan_schedule(n0, n1, n2, batch, 0, fft3.FFT3_PENCIL3, fft3.FFT3_FORWARD, fft3.make_options(**opts))
+    s = fft3.fft3_plan_schedule(n0, n1, n2, batch, 0, decomp, fft3.FFT3_FORWARD, fft3.make_options(**opts))
     assert _kinds(s)[:len(first_kinds)] == first_kinds
     assert np.array_equal(_replay_positions(s, total), np.arange(total))
