@@ -70,3 +70,30 @@ def test_reference_arm_runs_on_rank_0_only():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2")
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300, cwd=root)
     assert out.returncode == 0 and not out.stdout.strip()
+
+
+def test_traffic_table_is_keyed_to_the_measured_kernels_sources():
+    """bench.py reads profiles/traffic.txt only while the translation units of
+    the measured kernels and every header they include are unchanged: the hash
+    follows those files (and ignores the others)."""
+    import importlib
+    import shutil
+    import tempfile
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with tempfile.TemporaryDirectory() as tmp:
+        shutil.copytree(os.path.join(root, "paper_1904_10119_gb300", "csrc"),
+                        os.path.join(tmp, "paper_1904_10119_gb300", "csrc"))
+        old = bench.ROOT
+        try:
+            bench.ROOT = tmp
+            h0 = bench._csrc_sha()
+            with open(os.path.join(tmp, "paper_1904_10119_gb300", "csrc", "k_segmented.cu"), "a") as f:
+                f.write("\n// unrelated edit\n")
+            assert bench._csrc_sha() == h0          # not in the closure
+            with open(os.path.join(tmp, "paper_1904_10119_gb300", "csrc", "fft_engine.cuh"), "a") as f:
+                f.write("\n// edit of an included header\n")
+            assert bench._csrc_sha() != h0          # included by the measured kernels
+        finally:
+            bench.ROOT = old
+    importlib.reload(bench)
