@@ -1,5 +1,8 @@
-// k_pass64.cu -- complex128 (FP64) line passes with a compile-time radix list:
-// the Stockham engine of fft_engine.cuh on double2 values, FP64 twiddles.
+// k_pass64.cu -- complex128 (FP64) line passes with a compile-time radix list,
+// the precision of the paper's experiments (Section 4: complex double): the
+// Stockham stages of Section 2.1 (Eq. ct applied repeatedly, fft_engine.cuh)
+// on double2 values with FP64 twiddles, one pass per dimension as in the
+// pencil-pencil-pencil definition of Section 2.3.
 //   k_pass_j64  contiguous lines (ij == 1, ok == 1), T threads per line, LPT
 //               lines per tile, one padded line buffer in shared memory (the
 //               first stage reads global memory, the last writes it).
