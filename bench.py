@@ -7,8 +7,8 @@ already resident in HBM; `value` is ms per transform for the whole job.
 `e2e` times the same transform through fft3_plan_execute_host with pinned
 host buffers (host-to-device copy, transform, device-to-host copy per step).
 `roofline` reports the dominant pass against the measured HBM copy
-bandwidth; `cpu_baseline` the FP64 oracle timed on a bounded sample of the
-same workload on the host cores.
+bandwidth; `cpu_baseline` the FP64 oracle timed on whole transforms of the
+same workload on the host cores (in place on one complex128 array).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -154,45 +154,73 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------- CPU oracle ---- #
-def oracle_sample(n: int, target_s: float, threads: int | None = None):
-    """Times the FP64 oracle's line transforms on a bounded sample of the
-    workload: `lines` lines of length n along each of the three dimensions
-    (x lines contiguous, y and z lines at stride n inside n x n x k blocks),
-    and extrapolates to the 3*n^2 lines of one full transform."""
-    import numpy as np
+def _mem_available() -> int:
+    """Bytes of host memory available to a new allocation (/proc/meminfo)."""
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
 
-    import oracle
-    if threads:
-        oracle.set_num_threads(threads)
-    cores = oracle.num_threads()
 
-    def run(lines: int) -> float:
-        k = max(1, lines // n)
-        buf = np.full((k, n, n), 0.5 - 0.25j, dtype=np.complex128)
+def oracle_cube(n: int, reserve: int = 0) -> int:
+    """Edge of the largest cube, n or n/2^k, whose complex128 array (plus the
+    complex64 input it is widened from and `reserve` bytes) fits host memory."""
+    avail = _mem_available() - reserve
+    m = n
+    while m > 64 and 24 * m ** 3 * 1.1 > avail:
+        m //= 2
+    return m
+
+
+class OracleTransforms:
+    """Whole transforms of the FP64 oracle: the forward 3D DFT of an m^3
+    complex128 array (the seeded complex64 input widened exactly), computed in
+    place by oracle.fft3_inplace: x, y and z lines at their real strides, one
+    array of 16 m^3 bytes.  Each call to step() times one full transform (the
+    array keeps the previous output; the values only grow by m^1.5 per
+    transform, far from overflow)."""
+
+    def __init__(self, n: int, src=None, threads: int | None = None, reserve: int = 0):
+        import numpy as np
+
+        import oracle
+        from paper_1904_10119_gb300 import synth
+        if threads:
+            oracle.set_num_threads(threads)
+        self.oracle = oracle
+        self.cores = oracle.num_threads()
+        self.n = n
+        self.m = m = oracle_cube(n, reserve)
+        self.buf = np.empty((m, m, m), dtype=np.complex128)
+        if src is not None and m == n:
+            np.copyto(self.buf, src.reshape(m, m, m))
+        else:
+            np.copyto(self.buf, synth.uniform_c64((m, m, m), 4))
+
+    def step(self) -> float:
+        """ms of one full in-place m^3 transform."""
         t0 = time.perf_counter()
-        # x lines: contiguous rows
-        oracle.fft1_lines_inplace(buf.reshape(-1), n, k * n, n, 1)
-        # y lines: stride n inside each n x n block (one block at a time)
-        for b in range(k):
-            blk = buf[b].reshape(-1)
-            sub = np.ascontiguousarray(blk)
-            oracle.fft1_lines_inplace(sub, n, n, 1, n)
-            buf[b] = sub.reshape(n, n)
-        # z lines: the same strided access once more (stand-in for stride n*n)
-        for b in range(k):
-            sub = np.ascontiguousarray(buf[b].reshape(-1))
-            oracle.fft1_lines_inplace(sub, n, n, 1, n)
-        return time.perf_counter() - t0, k * n
+        self.oracle.fft3_inplace(self.buf.reshape(-1), self.m, self.m, self.m)
+        return (time.perf_counter() - t0) * 1e3
 
-    t_cal, l_cal = run(n)
-    lines = int(min(n * n, max(n, l_cal * target_s / max(t_cal, 1e-6))))
-    lines = max(n, lines // n * n)
-    t, l = run(lines)
-    ms_full = t * (n * n) / l * 1e3
-    return {"ms": ms_full, "cores": cores, "lines": l, "seconds": t,
-            "sample": f"{l} lines of length {n} along each of the 3 dimensions of the {n}^3 transform "
-                      f"({3 * l} of {3 * n * n} lines; z lines timed at stride {n} instead of {n * n}), "
-                      f"FP64, {cores} OpenMP threads; extrapolated to the full transform"}
+    def to_workload_ms(self, ms: float) -> float:
+        """ms per n^3 transform: the measured value itself when m == n, else
+        scaled by the 5 N log2 N operation count (stated in the sample)."""
+        if self.m == self.n:
+            return ms
+        big, small = self.n ** 3, self.m ** 3
+        return ms * (big * math.log2(big)) / (small * math.log2(small))
+
+    def sample(self, reps: int) -> str:
+        s = (f"{reps} full forward {self.m}^3 transform(s) of the FP64 oracle, in place on one complex128 array "
+             f"(x, y and z lines at their real strides), {self.cores} OpenMP threads")
+        if self.m != self.n:
+            s += (f"; host memory ({_mem_available() >> 30} GiB available) does not hold a {self.n}^3 "
+                  f"complex128 array, so the {self.m}^3 time is scaled to {self.n}^3 by 5 N log2 N")
+        return s
 
 
 # --------------------------------------------------------------- main ---- #
@@ -217,7 +245,8 @@ def main():
     ap.add_argument("--tc-stages", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true", help="skip the per-decomposition and batched tables")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU oracle baseline")
+    ap.add_argument("--cpu-reps", type=int, default=1,
+                    help="whole oracle transforms timed for cpu_baseline (0 skips the CPU oracle baseline)")
     ap.add_argument("--batched", type=int, default=0, metavar="COUNT",
                     help="only time COUNT uneven cubes (seed 7): the default batched plan and the persistent executor")
     args = ap.parse_args()
@@ -234,20 +263,20 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        assert n0 == n1 == n2, "the CPU reference arm samples cubic workloads"
-        vals = []
-        res = None
-        for s in range(args.warmup + args.steps):
-            res = oracle_sample(n0, max(1.0, args.cpu_seconds / max(1, args.steps)))
-            if s >= args.warmup:
-                vals.append(res["ms"])
-        v = sum(vals) / len(vals)
+        assert n0 == n1 == n2, "the CPU reference arm times cubic workloads"
+        ref = OracleTransforms(n0)
+        for _ in range(args.warmup):
+            ref.step()
+        vals = [ref.step() for _ in range(args.steps)]
+        step_ms = sum(vals) / len(vals)
+        v = ref.to_workload_ms(step_ms)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload, "dims": [n0, n1, n2], "batch": 1},
-                "cpu_baseline": {"value": v, "unit": "ms", "cores": res["cores"], "kind": "oracle",
-                                 "sample": res["sample"]},
+                "config": {"workload": workload, "dims": [n0, n1, n2], "batch": 1,
+                           "oracle_cube": [ref.m] * 3},
+                "cpu_baseline": {"value": v, "unit": "ms", "cores": ref.cores, "kind": "oracle",
+                                 "sample": ref.sample(args.steps)},
                 "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -438,11 +467,13 @@ def main():
                 extras["smaller_cubes"] = {"error": str(e)}
 
     cpu = None
-    if rank == 0 and world == 1 and args.cpu_seconds > 0 and n0 == n1 == n2:
+    if rank == 0 and world == 1 and args.cpu_reps > 0 and n0 == n1 == n2:
         try:
-            res = oracle_sample(n0, args.cpu_seconds)
-            cpu = {"value": res["ms"], "unit": "ms", "cores": res["cores"], "kind": "oracle",
-                   "sample": res["sample"]}
+            ref = OracleTransforms(n0, src=h_in.numpy())
+            ms = sum(ref.step() for _ in range(args.cpu_reps)) / args.cpu_reps
+            cpu = {"value": ref.to_workload_ms(ms), "unit": "ms", "cores": ref.cores, "kind": "oracle",
+                   "sample": ref.sample(args.cpu_reps)}
+            del ref
         except Exception as e:
             cpu = {"value": None, "unit": "ms", "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -510,7 +541,7 @@ def size_table(fft3, synth, torch, sizes, decomp_map):
     return table
 
 
-def c128_table(fft3, synth, torch, sizes=(256, 512), reps=5):
+def c128_table(fft3, synth, torch, sizes=(256, 512, 1024), reps=5):
     """complex128 (FP64 butterflies and twiddles) forward ms of n^3, out of
     place, CUDA events over `reps` back-to-back executions; GFLOP/s in the
     5 N log2 N convention (the path is bound by FP64 arithmetic)."""
@@ -518,7 +549,10 @@ def c128_table(fft3, synth, torch, sizes=(256, 512), reps=5):
     table = {}
     st = torch.cuda.current_stream()
     for n in sizes:
-        x = torch.from_numpy(synth.uniform_c128((n, n, n), 3)).to("cuda")
+        # timing only: uniform[-1,1) parts drawn on the device (16 GiB at 1024^3)
+        x = torch.empty((n, n, n), dtype=torch.complex128, device="cuda")
+        x.real.uniform_(-1, 1)
+        x.imag.uniform_(-1, 1)
         out = torch.empty_like(x)
         p = fft3.Plan(n, n, n, 1, decomposition=fft3.FFT3_PENCIL3, dtype=fft3.FFT3_C128_FP64)
         p.execute(x, out)

@@ -204,17 +204,33 @@ int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int6
 int fft3_plan_schedule_many(int count, const int *dims, const int64_t *offsets, int dtype, int decomposition,
                             int direction, const int *tuning, char *buf, size_t len);
 
-/* Execute on `stream` (a cudaStream_t, NULL = legacy default stream).
- * in, out: device pointers to batch*n0*n1*n2 complex64 values (or the
- * extent covered by the offsets of a batched plan).  `in` is not modified.
- * Asynchronous and stream ordered.  in == out returns
- * FFT3_ERR_INPLACE_UNSUPPORTED. */
+/* Computes the plan's transform: for every batch entry b,
+ *   X[k0,k1,k2] = sum_{j0,j1,j2} x[j0,j1,j2] w_n0^{j0 k0} w_n1^{j1 k1} w_n2^{j2 k2}
+ * (Section 2.1: DFT_n = [w_n^{lk}], w_n = exp(-2 pi i / n) forward, read with
+ * the imaginary unit the printed exponent lacks; exp(+2 pi i / n) for the
+ * inverse, unnormalised, so inverse(forward(x)) = n0*n1*n2 * x), as the
+ * plan's passes of batched 1D DFTs (Section 2.3: slab-pencil and
+ * pencil-pencil-pencil; Section 3.2: volumetric).
+ * in, out: device pointers to batch*n0*n1*n2 complex64 values (complex128
+ * for FFT3_C128_FP64), or the extent covered by the offsets of a batched
+ * plan; element (j0, j1, j2) of entry b at j0 + n0*(j1 + n1*(j2 + n2*b))
+ * (Section 2.3: column major, n0 fastest); the output in the same order
+ * unless options.layout asks for a permuted spectrum.  `in` is not modified;
+ * both buffers stay owned by the caller and must be 16-byte aligned.
+ * stream: a cudaStream_t (NULL = legacy default stream); asynchronous and
+ * stream ordered.  Errors: FFT3_ERR_INVALID_ARG (null plan or buffer),
+ * FFT3_ERR_INPLACE_UNSUPPORTED (in == out), FFT3_ERR_CUDA (launch failure,
+ * message in fft3_last_error). */
 int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream);
 
-/* Execute from and to HOST memory: copies `h_in` to plan-owned device
- * buffers, transforms, copies the result to `h_out`, then synchronises
- * `stream`.  Pinned host memory gives full copy bandwidth.  The device
- * staging buffers are allocated on the first call and kept by the plan. */
+/* The transform of fft3_plan_execute (Section 2.1 definition, Section 2.3
+ * layout) from and to HOST memory: copies `h_in` (batch*n0*n1*n2 values,
+ * caller-owned host memory) to plan-owned device buffers, transforms, copies
+ * the result to `h_out`, then synchronises `stream`.  Pinned host memory
+ * gives full copy bandwidth.  The device staging buffers are allocated on
+ * the first call and kept by the plan (FFT3_ERR_OOM if that fails).  The
+ * paper's arrays live in the nodes' memory; this entry point is the
+ * end-to-end form for callers whose data live on the host. */
 int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *stream);
 
 /* `count` transforms from and to HOST memory, pipelined: transform i reads
@@ -235,9 +251,17 @@ int fft3_plan_execute_host_pipelined(fft3_plan p, const void *const *h_in, void 
  * persistent kernel expired).  Synchronises the plan's last stream. */
 int fft3_plan_check(fft3_plan p);
 
+/* Frees a plan and everything it owns (twiddle tables, workspace, staging
+ * buffers, streams, graphs).  The plan must not be executing.  Planning and
+ * plan objects have no counterpart in the paper (its local DFTs are FFTW
+ * plans, Section 4.1).  Returns FFT3_ERR_INVALID_ARG for a null plan. */
 int fft3_plan_destroy(fft3_plan p);
 
-/* Device bytes the plan owns besides its twiddle tables (workspace). */
+/* Device bytes the plan owns besides its twiddle tables: the array-sized
+ * workspace of schedules that redistribute into a second buffer (the blocked
+ * and rotated intermediates of Section 2.4) and the counters of persistent
+ * kernels; 0 for a null plan.  No counterpart in the paper, whose
+ * redistributions go through MPI buffers (Section 4.1). */
 size_t fft3_plan_workspace_bytes(fft3_plan p);
 
 /* Number of passes of the schedule: the valid indices of fft3_plan_execute_pass.
@@ -312,12 +336,18 @@ int fft3_split_bf16(const float *d_x, int64_t count, uint16_t *d_hi, uint16_t *d
  * fragmented.  fft3_execute_noalloc computes the same transform as a
  * pencil-pencil-pencil plan with FFT3_PPP_ROTATE, but its workspace and its
  * twiddle tables live in fixed arrays inside the library (16 MiB + 128 KiB of
- * device memory on every GPU that loads the library, held until the process
- * exits) and it calls no cudaMalloc, cudaFree or other allocating routine.
+ * device memory, reserved on a GPU when the library's device code is first
+ * loaded there -- with CUDA's default lazy loading, at the first use of the
+ * library on that GPU -- and held until the process exits) and it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  *   - in, out: device pointers to batch*n0*n1*n2 complex64 values (n0 fastest);
  *     in is not modified; in == out returns FFT3_ERR_INPLACE_UNSUPPORTED.
  *   - batch*n0*n1*n2 must not exceed FFT3_NOALLOC_MAX_ELEMENTS, otherwise the
- *     call returns FFT3_ERR_UNSUPPORTED_SIZE and does nothing.
+ *     call returns FFT3_ERR_UNSUPPORTED_SIZE and does nothing.  The twiddle
+ *     tables take at most n0 + n1 + n2 + 48 entries, which always fits
+ *     FFT3_NOALLOC_MAX_TWIDDLES because no line may exceed 4096 points (a
+ *     longer line, e.g. 8192 x 2 x 1, is FFT3_ERR_UNSUPPORTED_SIZE as for
+ *     fft3_plan_create).
  *   - The first call on a device looks up the arrays' device addresses on the
  *     current device (cudaGetSymbolAddress); make that first call before any
  *     stream capture.
@@ -401,7 +431,11 @@ int fft3_mlp_train(fft3_mlp m, const float *h_X, const float *h_y, int n, int ep
 /* Predictions for n host samples into h_pred.  Synchronous. */
 int fft3_mlp_predict(fft3_mlp m, const float *h_X, int n, float *h_pred);
 
+/* Message of the last failed call on the calling thread (thread-local,
+ * owned by the library, valid until that thread's next failing call).  No
+ * counterpart in the paper. */
 const char *fft3_last_error(void);
+/* Version number of the library, increased whenever the C ABI changes. */
 int fft3_version(void);
 
 #ifdef __cplusplus

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "capi_internal.h"
+#include "roots.cuh"
 
 namespace fft3 {
 __global__ void k_pass_g(PassArgs a);
@@ -986,41 +987,19 @@ int noalloc_setup(int dev, NoallocDevice **out)
 
 namespace fft3 {
 // Stage-major twiddles of one runtime line plan (fft_engine.cuh) computed on
-// the device from the plan itself, so no exponent list has to be uploaded:
-// entry e of stage s is w_n^{r*k*n/(NS*R)} with r = 1 + e' / NS, k = e' % NS.
-__global__ void k_noalloc_line_roots(LineRt L, float2 *out)
+// the device from the plan itself, so no exponent list has to be uploaded: the
+// exponents and the FP64 roots come from the same helpers (roots.cuh) as the
+// tables of regular plans, so both tables are identical.
+__global__ void k_noalloc_line_roots(LineRt L, int total, float2 *out)
 {
-    int total = 0, NS = 1;
-    for (int s = 0; s < L.nst; ++s) {
-        total += (L.rad[s] - 1) * NS;
-        NS *= L.rad[s];
-    }
     if (L.nst == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0)
             out[0] = make_float2(1.f, 0.f);
         return;
     }
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        int s = 0, off = 0, ns = 1;
-        while ((L.rad[s] - 1) * ns <= e - off) {
-            off += (L.rad[s] - 1) * ns;
-            ns *= L.rad[s];
-            ++s;
-        }
-        const int idx = e - off, R = L.rad[s];
-        const int64_t r = 1 + idx / ns, k = idx % ns;
-        const int64_t m = r * k * (L.n / (ns * R)) % L.n;
-        const int64_t q = (4 * m) / L.n, rem = 4 * m - q * L.n;
-        double sn, cs;
-        sincospi((double)rem / (2.0 * (double)L.n), &sn, &cs);
-        double re, im;
-        switch (q & 3) {
-        case 0: re = cs; im = sn; break;
-        case 1: re = -sn; im = cs; break;
-        case 2: re = -cs; im = -sn; break;
-        default: re = sn; im = -cs; break;
-        }
-        out[e] = make_float2((float)re, (float)-im); // forward roots exp(-2 pi i m / n)
+        const double2 w = root_fp64(stage_twiddle_exponent(L.n, L.rad, L.nst, e), L.n, FFT3_FORWARD);
+        out[e] = make_float2((float)w.x, (float)w.y);
     }
 }
 } // namespace fft3
@@ -1067,8 +1046,8 @@ extern "C" int fft3_execute_noalloc(int n0, int n1, int n2, int batch, int direc
     cudaStream_t st = (cudaStream_t)stream;
     for (const PassPlan &p : P.sched.passes) {
         const TwSeg &sg = P.sched.tw[p.tw_seg[0]];
-        k_noalloc_line_roots<<<std::max(1, ((int)sg.m.size() + 255) / 256), 256, 0, st>>>(to_rt(p.line, 0),
-                                                                                          nd->tw + sg.off);
+        k_noalloc_line_roots<<<std::max(1, ((int)sg.m.size() + 255) / 256), 256, 0, st>>>(
+            to_rt(p.line, 0), (int)sg.m.size(), nd->tw + sg.off);
         CUDA_TRY(cudaGetLastError());
     }
     return fft3_plan_execute(&P, in, out, stream);

@@ -30,6 +30,7 @@
 #include <sstream>
 
 #include "plans.h"
+#include "roots.cuh"
 
 namespace fft3 {
 
@@ -172,15 +173,13 @@ static int choose_line(int n, int order, bool allow_fixed, LineChoice *lc, std::
 // Stage-major twiddle exponents of a line choice (fft_engine.cuh header).
 static void line_twiddles(const LineChoice &lc, std::vector<int64_t> *m)
 {
-    int NS = 1;
+    int64_t total = 0, NS = 1;
     for (int s = 0; s < lc.nst; ++s) {
-        int R = lc.rad[s];
-        int64_t stride = lc.n / (NS * R);
-        for (int r = 1; r < R; ++r)
-            for (int k = 0; k < NS; ++k)
-                m->push_back((int64_t)r * k * stride % lc.n);
-        NS *= R;
+        total += (lc.rad[s] - 1) * NS;
+        NS *= lc.rad[s];
     }
+    for (int64_t e = 0; e < total; ++e)
+        m->push_back(stage_twiddle_exponent(lc.n, lc.rad, lc.nst, e));
 }
 
 static int add_seg(Schedule *s, int n, std::vector<int64_t> m)

@@ -45,12 +45,15 @@ def _sampled_check(x, got, n, direction, seed, parseval_tol=1e-5):
     ref = oracle.dft3_sampled(x.reshape(n, n, n), n, n, n, ks[0], ks[1], ks[2], sign=direction)
     g = got.reshape(n, n, n)[np.ix_(ks[2], ks[1], ks[0])].transpose(2, 1, 0)
     rel = oracle.rel_l2(g, ref)
-    mx = float(np.max(np.abs(g - ref)) / np.max(np.abs(got)))
+    # max-abs relative to the reference's own peak over the sample (at most
+    # max|X| over the whole spectrum, so this is the stricter form of the bar)
+    mx = float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
     assert rel <= REL_L2_TOL and mx <= MAXABS_TOL, (rel, mx)
     # Parseval over the whole array: sum |X|^2 = N sum |x|^2
     N = float(n) ** 3
     sx = float(np.sum(np.abs(x.astype(np.complex128)) ** 2))
     sX = float(np.sum(np.abs(got.astype(np.complex128)) ** 2))
+    print(f"  Parseval relative deviation {abs(sX - N * sx) / (N * sx):.3e}")
     assert abs(sX - N * sx) <= parseval_tol * N * sx
     return rel, mx
 
@@ -90,7 +93,7 @@ def test_fullsize_tensor_cores_sampled(n, inputs):
     assert plan.check() == 0
     plan.close()
     host = out.cpu().numpy()
-    rel, mx = _sampled_check(x, host, n, fft3.FFT3_FORWARD, 31 + n, parseval_tol=5e-5)
+    rel, mx = _sampled_check(x, host, n, fft3.FFT3_FORWARD, 31 + n)
     print(f"TC {n}^3 {inputs}: sampled rel-L2 {rel:.3e} max-abs {mx:.3e}")
     del xd, out
     torch.cuda.empty_cache()

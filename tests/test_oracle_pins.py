@@ -228,6 +228,18 @@ def test_fft1_lines_inplace_matches_fft3_pass():
     assert oracle.rel_l2(buf, ref) < 1e-15
 
 
+@pytest.mark.parametrize("shape,batch,sign", [((8, 6, 10), 1, -1), ((16, 4, 5), 2, 1)])
+def test_fft3_inplace_equals_fft3(shape, batch, sign):
+    """The in-place whole-transform form the CPU baseline times computes the
+    same 3D DFT as the out-of-place oracle (and so inherits its pins)."""
+    n0, n1, n2 = shape
+    x = synth.uniform_c128((batch, n2, n1, n0), 11)
+    buf = np.ascontiguousarray(x.reshape(-1)).copy()
+    oracle.fft3_inplace(buf, n0, n1, n2, batch, sign=sign)
+    ref = oracle.fft3(x.ravel(), n0, n1, n2, batch, sign=sign).ravel()
+    assert np.array_equal(buf, ref)
+
+
 # ------------------------------------------ distributions / simulations --- #
 @pytest.mark.parametrize("n0,n1,p", [(4, 4, 2), (16, 16, 4), (8, 12, 4), (12, 6, 3), (32, 32, 8)])
 def test_rote_parallel_dft1(n0, n1, p):

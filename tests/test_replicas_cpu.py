@@ -58,8 +58,8 @@ def test_reference_arm_runs_on_rank_0_only():
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--n", "16", "--steps", "1",
-           "--warmup", "3", "--cpu-seconds", "0.2"]
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--n", "16", "--steps", "2",
+           "--warmup", "3"]
     env = dict(os.environ, RANK="0", WORLD_SIZE="1")
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300, cwd=root)
     assert out.returncode == 0, out.stderr[-2000:]
@@ -67,6 +67,9 @@ def test_reference_arm_runs_on_rank_0_only():
     assert line["impl"] == "reference" and line["unit"] == "ms" and line["higher_is_better"] is False
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    # every step is one whole transform of the workload, so the value is the measured step time
+    assert "full forward 16^3 transform" in line["cpu_baseline"]["sample"]
+    assert line["ms_per_step"] == line["value"] and line["steps"] == 2
     env = dict(os.environ, RANK="1", WORLD_SIZE="2")
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300, cwd=root)
     assert out.returncode == 0 and not out.stdout.strip()
