@@ -419,9 +419,10 @@ def main():
         variants["permuted_output_pencils"] = (fft3.FFT3_AUTO, {"layout": fft3.FFT3_LAYOUT_PENCILS})
         variants["permuted_output_rotated"] = (fft3.FFT3_PENCIL3, {"layout": fft3.FFT3_LAYOUT_ROTATED})
         tc = fft3.FFT3_C64_SPLITBF16_TC
-        variants["split_bf16_tc_one_stage_per_line"] = (fft3.FFT3_AUTO, {"dtype": tc})
-        variants["split_bf16_tc_shared_memory_stages"] = (fft3.FFT3_AUTO, {"dtype": tc, "tc_stages": 1})
-        variants["split_bf16_tc_every_stage"] = (fft3.FFT3_AUTO, {"dtype": tc, "tc_stages": 2})
+        variants["split_bf16_tc_radix32_tcgen05"] = (fft3.FFT3_AUTO, {"dtype": tc})
+        variants["split_bf16_tc_one_stage_per_line_mma_sync"] = (fft3.FFT3_AUTO, {"dtype": tc, "tc_stages": 3})
+        variants["split_bf16_tc_shared_memory_stages_mma_sync"] = (fft3.FFT3_AUTO, {"dtype": tc, "tc_stages": 1})
+        variants["split_bf16_tc_every_stage_mma_sync"] = (fft3.FFT3_AUTO, {"dtype": tc, "tc_stages": 2})
         for name, (d, o) in variants.items():
             if name == "auto":
                 continue

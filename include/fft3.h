@@ -45,7 +45,8 @@ typedef struct fft3_plan_s *fft3_plan; /* opaque; owned by the library */
 /* arithmetic of the line transforms; storage is complex64 except for FFT3_C128_FP64 */
 enum fft3_dtype {
     FFT3_C64_FP32 = 0,         /* FP32 CUDA-core butterflies */
-    FFT3_C64_SPLITBF16_TC = 1, /* radix-16 sub-DFTs as split-BF16 tensor-core GEMMs, FP32 accumulate */
+    FFT3_C64_SPLITBF16_TC = 1, /* radix-32 / radix-16 sub-DFTs as split-BF16 tensor-core GEMMs (hi + lo
+                                  BF16 parts, three products), FP32 accumulation (options.tc_stages) */
     FFT3_C128_FP64 = 2         /* complex128 arrays (interleaved FP64 re, im; 16 bytes per element),
                                   FP64 butterflies and FP64 twiddles: the paper's own precision
                                   (Section 4).  Natural pencil-pencil-pencil schedule of runtime-radix
@@ -139,11 +140,15 @@ typedef struct fft3_options {
                              sweep for the 2D slab stage; tiles loaded by TMA), then
                              the z pass back to natural order.  Square 256, 512 or
                              1024 slabs, batch 1, n2 > 1; the workspace is array-sized */
-    int tc_stages;    /* FFT3_C64_SPLITBF16_TC: which radix-16 stages run on the tensor cores:
-                         0 = per line, the first radix-16 stage whose operands are both in
-                             shared memory (the fastest; default; lines without one stay FP32),
-                         1 = every radix-16 stage whose operands are both in shared memory,
-                         2 = every radix-16 stage */
+    int tc_stages;    /* FFT3_C64_SPLITBF16_TC: which sub-DFTs run on the tensor cores:
+                         0 = 1024-point lines as two radix-32 stages, both split-BF16 GEMMs on
+                             the tcgen05 tensor cores (M = 128 rows of 4 lines, N = K = 64), other
+                             lengths as mode 3 (the default),
+                         1 = every radix-16 stage whose operands are both in shared memory
+                             (mma.sync m16n8k16),
+                         2 = every radix-16 stage (mma.sync m16n8k16),
+                         3 = per line, the first radix-16 stage whose operands are both in
+                             shared memory (mma.sync m16n8k16; lines without one stay FP32) */
     int slab_chunk;   /* slab_mode 4: slabs per chunk (0 = about 32 MiB of slabs) */
     int slab_lines;   /* slab_mode 5: rows per x tile and columns per y tile, 4 or 8 (0 = 4) */
     int layout;       /* fft3_layout of the forward output / inverse input (0 = natural) */

@@ -306,6 +306,11 @@ static int build_launches(fft3_plan_s *P)
             L.cluster = p.p;
             break;
         }
+        case PK_TCX:
+        case PK_TCS:
+            L.func = tc32_kernel(p.kind == PK_TCX);
+            L.tc32 = p.kind == PK_TCX ? 1 : 2;
+            break;
         case PK_JTC:
             L.func = fk && p.tc_mode >= 0 ? fk->j_tc[p.tc_mode] : nullptr;
             break;
@@ -579,6 +584,20 @@ static int launch_one(fft3_plan_s *P, const Launch &L, const void *func, PassArg
         int rc = encode_stream_map(&tin, a.in, a.g, L.probe_n, L.stream_q, a.lpt);
         if (rc)
             return rc;
+        void *params[2] = {&a, &tin};
+        CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params));
+        return FFT3_OK;
+    }
+    if (L.tc32) {
+        CUtensorMap tin;
+        memset(&tin, 0, sizeof(tin));
+        if ((uintptr_t)a.in & 15)
+            return fail(FFT3_ERR_INVALID_ARG, "this plan moves tiles with TMA: buffers must be 16-byte aligned");
+        if (L.tc32 == 2) {
+            int rc = encode_pass_map(&tin, a.in, a.g, L.probe_n, kTc32Lpt, false);
+            if (rc)
+                return rc;
+        }
         void *params[2] = {&a, &tin};
         CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params));
         return FFT3_OK;

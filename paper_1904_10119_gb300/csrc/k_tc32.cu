@@ -1,0 +1,320 @@
+// k_tc32.cu -- 1024-point line passes whose two 32-point DFT stages run as
+// split-BF16 GEMMs on the fifth-generation tensor cores (tcgen05), with the
+// lines on the MMA's M side.
+//
+// The line is split by Eq. ct (Section 2.1) with n0 = n1 = 32 in
+// decimation-in-time order: for x[j], j = 32 j1 + j2,
+//   (I)   for every j2: X1[j2][k1] = sum_j1 x[32 j1 + j2] w_32^{j1 k1},
+//   (II)  twiddle: X1[j2][k1] *= w_1024^{j2 k1},
+//   (III) transposition (j2, k1) -> (k1, j2),
+//   (IV)  for every k1: X[k1 + 32 k2] = sum_j2 X1[j2][k1] w_32^{j2 k2}.
+// A tile is 4 lines.  Stage (I) is one GEMM D = A B^T with M = 128 rows (4
+// lines x 32 decimated sub-sequences j2), K = 64 (32 complex inputs, re and
+// im interleaved) and N = 64 (32 complex outputs): B is the real-ified DFT_32,
+//   B[2k+0][2j+0] = Re w,  B[2k+0][2j+1] = -Im w,
+//   B[2k+1][2j+0] = Im w,  B[2k+1][2j+1] =  Re w,   w = w_32^{jk},
+// so D[row][2k] and D[row][2k+1] are the real and imaginary parts of output
+// k.  Stage (IV) is the same GEMM with rows (line, k1).  Both operands are
+// split, v = v_hi + v_lo with v_hi = bf16(v), v_lo = bf16(v - v_hi), and
+// three products are accumulated in FP32: A_lo B_hi + A_hi B_lo + A_hi B_hi
+// (A_lo B_lo is dropped).  The twiddles (II) are applied in FP32.
+//
+// One 128-thread block per tile stream; thread t owns GEMM row t in both
+// stages (tensor-memory lane t): it writes its row of A with tcgen05.st
+// (high parts in columns 0-31, low parts in 32-63), one elected thread
+// issues the twelve MMAs (4 K steps x 3 products, M = 128, N = 64, K = 16)
+// into D (columns 64-127) and commits them to an mbarrier, and every thread
+// reads its row of D back with tcgen05.ld.  B (DFT_32 high and low parts)
+// sits in shared memory with the 128-byte swizzle.
+//
+// Tiles arrive by TMA into two landing buffers per block (contiguous lines:
+// one bulk copy of 4 x 8 KB; strided lines: four 4-column x 256-row boxes of
+// a 4D tensor map).  A landing buffer, once its inputs are in registers, holds
+// the tile's transposition (III) in a padded layout, and once stage (IV) has
+// read it back it is refilled with the block's tile after next, so the loads
+// of the next tile overlap this tile's arithmetic.
+//
+// Thread roles (t = threadIdx.x, tile lines/columns l < 4):
+//   contiguous lines (LINES = true):  row t = 32 l + j2 (stage I), 32 l + k1 (IV)
+//   strided columns  (LINES = false): row t = 4 j2 + l (stage I), 4 k1 + l (IV)
+// so every warp's shared-memory accesses cover 32 consecutive complex values
+// or hit distinct banks through the padding.
+#include <cuda_bf16.h>
+
+#include "pass_kernels.cuh"
+#include "plans.h"
+#include "umma.cuh"
+
+namespace fft3 {
+
+namespace {
+
+constexpr int kN = 1024;
+constexpr int kLpt = kTc32Lpt;
+constexpr uint32_t kTileBytes = (uint32_t)kLpt * kN * 8u; // 32 KB
+constexpr int kPitchL = 34;                             // LINES: k1 pitch of the transposition (complex)
+constexpr int kLineT = 32 * kPitchL;                    // LINES: line pitch of the transposition
+constexpr int kPitchC = 132;                            // columns: k1 pitch of the transposition
+constexpr int kLandBytes = kTc32LandBytes;              // 34816 >= 32768
+static_assert(kLandBytes == kLpt * kLineT * 8 && 32 * kPitchC * 8 <= kLandBytes,
+              "both transpositions fit the landing buffer");
+constexpr int kBBytes = 64 * 128;                       // one 64 x 64 BF16 operand
+constexpr int kTwOff = 2 * kBBytes;                     // w_1024^{j2 k1}, [k1][j2]
+constexpr int kLandOff = kTwOff + kN * 8;
+static_assert(kLandOff + 2 * kLandBytes + 1024 == kTc32SmemBytes, "dynamic shared memory (+ alignment slack)");
+
+// w = w_32^m for the DFT_32 operand (FP32 values of the FP64 generator) ->
+// B_hi, B_lo in the 128-byte-swizzled K-major layout.
+__device__ __forceinline__ void build_dft32_operand(uint8_t *bhi, uint8_t *blo, const float2 *w32)
+{
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int n = e >> 6, kk = e & 63;
+        const int kp = n >> 1, cp = n & 1, j = kk >> 1, c = kk & 1;
+        const float2 w = w32[(kp * j) & 31];
+        const float v = (cp == c) ? w.x : (cp == 0 ? -w.y : w.y);
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(h));
+        const int off = (n >> 3) * 1024 + (n & 7) * 128 + (((kk >> 3) ^ (n & 7)) << 4) + (kk & 7) * 2;
+        *(uint16_t *)(bhi + off) = __bfloat16_as_ushort(h);
+        *(uint16_t *)(blo + off) = __bfloat16_as_ushort(lo);
+    }
+}
+
+// The twelve MMAs of one stage: D = A_lo B_hi + A_hi B_lo + A_hi B_hi.
+__device__ __forceinline__ void issue_stage_mmas(uint32_t t_a, uint32_t t_d, uint32_t s_bhi, uint32_t s_blo)
+{
+    constexpr uint32_t idesc = idesc_bf16_f32(128, 64);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        mma_bf16_ta(t_d, t_a + 32 + 8 * s, sdesc_sw128(s_bhi + 32 * s), idesc, s > 0);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        mma_bf16_ta(t_d, t_a + 8 * s, sdesc_sw128(s_blo + 32 * s), idesc, true);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        mma_bf16_ta(t_d, t_a + 8 * s, sdesc_sw128(s_bhi + 32 * s), idesc, true);
+}
+
+// Split 16 complex values into high and low parts and store them to this
+// thread's row of A (columns col .. col+15 and 32+col .. 32+col+15).
+__device__ __forceinline__ void store_a16(uint32_t t_row, int col, const float2 (&v)[16])
+{
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        split_c(v[i].x, v[i].y, hi[i], lo[i]);
+    tmem_st16(t_row + col, hi);
+    tmem_st16(t_row + 32 + col, lo);
+}
+
+// CTA-wide OR of a predicate.
+__device__ __forceinline__ bool cta_any(bool p) { return __syncthreads_or(p ? 1 : 0) != 0; }
+
+} // namespace
+
+template <bool LINES>
+__global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_constant__ CUtensorMap tin)
+{
+    extern __shared__ uint8_t dsm_raw[];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_tmem;
+    uint8_t *dsm = (uint8_t *)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *bhi = dsm, *blo = dsm + kBBytes;
+    float2 *tw = (float2 *)(dsm + kTwOff);
+    uint8_t *land0 = dsm + kLandOff;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool conj = a.conj != 0;
+
+    build_dft32_operand(bhi, blo, a.tw + a.tw_split_off);
+    for (int i = tid; i < kN; i += 128)
+        tw[i] = a.tw[i];
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&mbar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, 128);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem(); // B, written by this thread, is read by the tensor cores
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t t_row = tmem + ((uint32_t)(32 * warp) << 16); // this warp's lanes, column 0
+    const uint32_t t_d = t_row + 64;
+    const uint32_t s_bhi = smem_u32(bhi), s_blo = smem_u32(blo);
+    const uint64_t pol = l2_evict_first_policy();
+
+    // Load of the block's k-th tile into landing buffer k % 2 (thread 0).
+    auto issue = [&](int64_t k) {
+        const int64_t tile = blockIdx.x + k * (int64_t)gridDim.x;
+        if (tile >= a.ntiles)
+            return;
+        const int b = (int)(k & 1);
+        uint8_t *dst = land0 + b * kLandBytes;
+        const TileId id = decode_tile(tile, a.tiles_c, a.g.A, kLpt);
+        if constexpr (LINES) {
+            // lines beyond the array's last one are not loaded (their rows are never stored)
+            const int nval = (int)min((int64_t)kLpt, a.g.C - id.c0);
+            const float2 *src = a.in + id.c0 * a.g.ic + id.a * a.g.ia + id.b * a.g.ib;
+            mbar_expect_tx(&full[b], (uint32_t)nval * kN * 8u);
+            bulk_load(dst, src, (uint32_t)nval * kN * 8u, &full[b], pol);
+        } else {
+            mbar_expect_tx(&full[b], kTileBytes);
+#pragma unroll
+            for (int q = 0; q < kN / 256; ++q)
+                tma_load_4d(dst + q * 256 * kLpt * 8, &tin, (int)id.c0, q * 256, (int)id.a, (int)id.b, &full[b]);
+        }
+    };
+    int64_t issued = -1; // (thread 0) the last tile index k whose load was issued
+    if (tid == 0) {
+        issue(0);
+        issue(1);
+        issued = 1;
+    }
+
+    uint32_t mma_phase = 0;
+    bool failed = false;
+    int64_t k = 0;
+    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
+        const int b = (int)(k & 1);
+        const float2 *land = (const float2 *)(land0 + b * kLandBytes);
+        float2 *tr = (float2 *)(land0 + b * kLandBytes);
+        const bool late = !mbar_wait(&full[b], (uint32_t)((k >> 1) & 1), a.wait_budget);
+        if (cta_any(late)) {
+            failed = true;
+            break;
+        }
+        const TileId id = decode_tile(tile, a.tiles_c, a.g.A, kLpt);
+        // ---- stage (I): row t gathers its decimated sub-sequence x[32 j1 + j2]
+        const int l1 = LINES ? warp : (tid & 3), j2 = LINES ? lane : (tid >> 2);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float2 v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int j = 32 * (16 * h + i) + j2;
+                const float2 e = LINES ? land[l1 * kN + j] : land[j * kLpt + l1];
+                v[i] = conj ? cconj(e) : e;
+            }
+            store_a16(t_row, 16 * h, v);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_stage_mmas(t_row, t_d, s_bhi, s_blo);
+            mma_commit(&mbar);
+        }
+        const bool late1 = !mbar_wait(&mbar, mma_phase, a.wait_budget);
+        mma_phase ^= 1;
+        tc_fence_after();
+        // ---- (II) twiddle and (III) transposition into the landing buffer
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint32_t d[16];
+            tmem_ld16(t_d + 16 * h, d);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k1 = 8 * h + i;
+                const float2 y = cmul(make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1])),
+                                      tw[k1 * 32 + j2]);
+                if constexpr (LINES)
+                    tr[l1 * kLineT + k1 * kPitchL + j2] = y;
+                else
+                    tr[k1 * kPitchC + j2 * kLpt + l1] = y;
+            }
+        }
+        tc_fence_before();
+        if (cta_any(late1)) {
+            failed = true;
+            break;
+        }
+        // ---- stage (IV): row t = (line, k1) reads X1[j2][k1] for every j2
+        const int l2 = LINES ? warp : (tid & 3), k1 = LINES ? lane : (tid >> 2);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float2 v[16];
+            if constexpr (LINES) {
+                const float4 *src = (const float4 *)(tr + l2 * kLineT + k1 * kPitchL + 16 * h);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float4 q = src[i];
+                    v[2 * i] = make_float2(q.x, q.y);
+                    v[2 * i + 1] = make_float2(q.z, q.w);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    v[i] = tr[k1 * kPitchC + (16 * h + i) * kLpt + l2];
+            }
+            store_a16(t_row, 16 * h, v);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        fence_proxy_async_smem(); // this thread's accesses to the landing buffer, before its refill
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_stage_mmas(t_row, t_d, s_bhi, s_blo);
+            mma_commit(&mbar);
+            issue(k + 2); // the landing buffer is read out: the block's tile after next
+            issued = k + 2;
+        }
+        const bool late2 = !mbar_wait(&mbar, mma_phase, a.wait_budget);
+        mma_phase ^= 1;
+        tc_fence_after();
+        // ---- outputs X[k1 + 32 k2] of line l2
+        const int64_t c = id.c0 + l2;
+        const bool valid = !late2 && c < a.g.C;
+        float2 *op = a.out + c * a.g.oc + id.a * a.g.oa + id.b * a.g.ob + (int64_t)k1 * a.g.ok;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            uint32_t d[16];
+            tmem_ld16(t_d + 16 * h, d);
+            tmem_wait_ld();
+            if (valid) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int k2 = 8 * h + i;
+                    const float2 y = make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1]));
+                    op[(int64_t)(32 * k2) * a.g.ok] = conj ? cconj(y) : y;
+                }
+            }
+        }
+        tc_fence_before();
+        if (cta_any(late2)) {
+            failed = true;
+            break;
+        }
+    }
+    if (failed) {
+        // stop: record the timeout and wait (bounded) for the copies still in
+        // flight into this block's landing buffers before the block exits
+        if (tid == 0) {
+            atomicOr(a.err, kErrWaitTimeout);
+            for (int64_t v = k; v <= issued; ++v)
+                if (blockIdx.x + v * (int64_t)gridDim.x < a.ntiles &&
+                    !mbar_wait(&full[v & 1], (uint32_t)((v >> 1) & 1), a.wait_budget))
+                    break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        tmem_dealloc(tmem, 128);
+}
+
+const void *tc32_kernel(bool lines)
+{
+    return lines ? (const void *)&k_tc32<true> : (const void *)&k_tc32<false>;
+}
+
+} // namespace fft3

@@ -341,7 +341,11 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         return rc;
     const bool contig_in = g.ij == 1;
     const bool strided_in = g.ic == 1 && g.oc == 1;
-    const int tc_mode = std::min(2, std::max(0, s->opts.tc_stages));
+    // tc_stages 0: the tcgen05 radix-32 kernels for 1024-point lines, the first
+    // shared-memory radix-16 stage (mma.sync) elsewhere; 1, 2: the mma.sync
+    // radix-16 modes; 3: the first shared-memory radix-16 stage everywhere
+    const int tc_opt = s->opts.tc_stages;
+    const int tc_mode = tc_opt == 3 ? 0 : std::min(2, std::max(0, tc_opt));
     if (s->dtype == FFT3_C128_FP64) {
         // complex128, 16-byte elements: the compile-time FP64 passes (k_pass64.cu)
         // where the length has a fixed plan, else the runtime radix list (k_pass_g64)
@@ -373,6 +377,38 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         set_tiles(&p);
         *out = p;
         return FFT3_OK;
+    }
+    if (s->dtype == FFT3_C64_SPLITBF16_TC && !rotate && n == 1024 && tc_opt == 0 && s->opts.tile_lines == 0) {
+        // both 32-point stages of the line as split-BF16 GEMMs on the tcgen05 tensor cores
+        // (k_tc32.cu): contiguous lines whose 4-line tiles are one bulk copy, or strided
+        // columns the 4D tensor map walks (16-byte multiples for every stride)
+        const bool al = (g.ia * 8) % 16 == 0 && (g.B <= 1 || (g.ib * 8) % 16 == 0);
+        const bool lines = contig_in && g.ic == n && al;
+        const bool cols = strided_in && (g.ij * 8) % 16 == 0 && al && g.C <= 0x7fffffff && g.A <= 0x7fffffff &&
+                          g.B <= 0x7fffffff;
+        if (lines || cols) {
+            p.kind = lines ? PK_TCX : PK_TCS;
+            p.lpt = kTc32Lpt;
+            p.threads = kTc32Threads;
+            p.smem_bytes = kTc32SmemBytes;
+            p.tc_mode = 0;
+            p.line = LineChoice{};
+            p.line.n = n;
+            p.line.fixed = -1;
+            p.line.T = 32;
+            p.line.nst = 2;
+            p.line.rad[0] = p.line.rad[1] = 32;
+            std::vector<int64_t> tw(1024), w32(32);
+            for (int i = 0; i < 1024; ++i)
+                tw[i] = (int64_t)(i % 32) * (i / 32); // [k1][j2]: w_1024^{j2 k1}
+            for (int i = 0; i < 32; ++i)
+                w32[i] = i;                           // w_32^m for the DFT_32 operand
+            p.tw_seg[0] = add_seg(s, n, std::move(tw));
+            p.tw_seg[2] = add_seg(s, 32, std::move(w32));
+            set_tiles(&p);
+            *out = p;
+            return FFT3_OK;
+        }
     }
     if (s->dtype == FFT3_C64_SPLITBF16_TC && !rotate && strided_in && n > 1 && s->opts.tile_lines == 0) {
         // streamed strided pass whose 16 x 16 sub-line transforms run on the tensor cores
@@ -1144,8 +1180,9 @@ static const char *kind_name(int k)
                                   "slab_smem", "slab_l2", "volumetric_split", "copy", "unused",
                                   "line_strided_tma", "line_contig_tc", "line_strided_tc",
                                   "volumetric_split_fixed", "line_strided_stream", "slab_l2_blocked",
-                                  "line_runtime_fp64", "line_contig_fp64", "line_strided_fp64"};
-    return (k >= 0 && k <= 17) ? names[k] : "?";
+                                  "line_runtime_fp64", "line_contig_fp64", "line_strided_fp64",
+                                  "line_contig_r32_tc", "line_strided_r32_tc"};
+    return (k >= 0 && k <= 19) ? names[k] : "?";
 }
 static const char *buf_name(int b)
 {
@@ -1198,7 +1235,9 @@ std::string Schedule::json() const
         if (p.kind == PK_CSTREAM && p.p > 1)
             o << ",\"p\":" << p.p;
         if (p.kind == PK_JTC || p.kind == PK_CTC || (p.kind == PK_CSTREAM && p.tc_mode >= 0))
-            o << ",\"tc_stages\":" << p.tc_mode;
+            o << ",\"tc_stages\":" << p.tc_mode << ",\"mma\":\"mma.sync.m16n8k16\"";
+        if (p.kind == PK_TCX || p.kind == PK_TCS)
+            o << ",\"mma\":\"tcgen05.mma m128n64k16\"";
         if (p.kind == PK_CSTREAM) {
             int cnt = 0;
             const CStreamKernel &m = cstream_meta(&cnt)[p.cstream];

@@ -30,6 +30,8 @@ enum PassKind {
     PK_G64 = 15,     // complex128: runtime radix list in FP64 (k_pass_g64)
     PK_J64 = 16,     // complex128: fixed plan, contiguous lines (k_pass_j64)
     PK_C64 = 17,     // complex128: fixed plan, strided columns (k_pass_c64)
+    PK_TCX = 18,     // split-BF16 radix-32 tcgen05 GEMM stages, contiguous 1024-point lines (k_tc32.cu)
+    PK_TCS = 19,     // split-BF16 radix-32 tcgen05 GEMM stages, strided 1024-point columns (k_tc32.cu)
 };
 
 enum BufId { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };

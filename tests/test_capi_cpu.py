@@ -488,3 +488,30 @@ def test_natural_schedules_compose_to_the_identity(shape, batch, decomp, opts, f
     s = fft3.fft3_plan_schedule(n0, n1, n2, batch, 0, decomp, fft3.FFT3_FORWARD, fft3.make_options(**opts))
     assert _kinds(s)[:len(first_kinds)] == first_kinds
     assert np.array_equal(_replay_positions(s, total), np.arange(total))
+
+
+def test_tcgen05_radix32_schedule():
+    """The split-BF16 dtype lowers 1024-point lines to the tcgen05 radix-32
+    kernels by default (both 32-point stages as GEMMs: tiles of 4 lines, 128
+    threads, twiddles w_1024^{j2 k1} plus w_32^m for the DFT_32 operand) and
+    keeps the mma.sync radix-16 kernels under tc_stages 3."""
+    TC = fft3.FFT3_C64_SPLITBF16_TC
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, TC, fft3.FFT3_AUTO, -1)
+    kinds = [p["kind"] for p in s["passes"]]
+    assert kinds == ["line_contig_r32_tc", "line_strided_r32_tc", "line_strided_r32_tc"]
+    for p in s["passes"]:
+        assert p["lpt"] == 4 and p["threads"] == 128 and p["line"]["radices"] == [32, 32]
+        assert p["mma"].startswith("tcgen05")
+        assert p["tiles"] == 1024 * 1024 // 4
+    assert s["twiddle_entries"] == 3 * (1024 + 32)
+    # the blocked intermediate: the y pass stores into the workspace, the z pass reads it
+    assert [(p["src"], p["dst"]) for p in s["passes"]] == [("in", "out"), ("out", "workspace"), ("workspace", "out")]
+    old = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, TC, fft3.FFT3_AUTO, -1, fft3.make_options(tc_stages=3))
+    assert [p["kind"] for p in old["passes"]] == ["line_contig_tc", "line_strided_stream_tc",
+                                                  "line_strided_stream_tc"]
+    # ragged tiles: 6 lines of 1024 points are two tiles; other lengths keep their kernels
+    s = fft3.fft3_plan_schedule(1024, 6, 5, 2, TC, fft3.FFT3_PENCIL3, -1)
+    assert s["passes"][0]["kind"] == "line_contig_r32_tc" and s["passes"][0]["tiles"] == 2 * 5 * 2
+    assert not s["passes"][1]["kind"].endswith("r32_tc")
+    s = fft3.fft3_plan_schedule(20, 1024, 3, 1, TC, fft3.FFT3_PENCIL3, -1)
+    assert s["passes"][1]["kind"] == "line_strided_r32_tc" and s["passes"][1]["tiles"] == 5 * 3

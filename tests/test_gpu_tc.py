@@ -37,7 +37,7 @@ def _err(x, got, shape, batch, direction):
                                          ((1024, 24, 10), 2), ((40, 1024, 6), 1), ((18, 512, 4), 2),
                                          ((24, 6, 512), 1)])
 @pytest.mark.parametrize("direction", [fft3.FFT3_FORWARD, fft3.FFT3_INVERSE])
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_tc_radix16_stages(shape, batch, direction, mode):
     x, got, plan = run_plan(shape, batch, P, direction, seed=3, dtype=TC, tc_stages=mode)
     kinds = [p["kind"] for p in plan.describe()["passes"]]
@@ -71,6 +71,30 @@ def test_tc_default_mode_meets_fp32_bar(shape):
 
 def _opts_first():
     return fft3.make_options(tc_stages=0)
+
+
+@pytest.mark.parametrize("shape,batch,decomp", [
+    ((1024, 8, 4), 1, P),        # contiguous 1024-point lines: whole 4-line tiles
+    ((1024, 6, 5), 2, P),        # ragged last tile (6 lines = 4 + 2), batch 2
+    ((16, 1024, 8), 1, P),       # strided 1024-point y columns
+    ((20, 1024, 3), 1, P),       # 20 columns = 5 tiles of 4
+    ((8, 16, 1024), 1, P),       # strided z columns (plane stride)
+    ((24, 10, 1024), 1, P),
+    ((1024, 1024, 2), 1, P),     # x and y passes both on tcgen05
+    ((64, 1024, 1024), 1, fft3.FFT3_AUTO),  # blocked intermediate: y stores into it, z reads it
+])
+@pytest.mark.parametrize("direction", [fft3.FFT3_FORWARD, fft3.FFT3_INVERSE])
+def test_tcgen05_radix32_lines(shape, batch, decomp, direction):
+    """1024-point lines as two radix-32 split-BF16 GEMMs on the tcgen05 tensor
+    cores (the default split-BF16 mode): element by element against the oracle."""
+    x, got, plan = run_plan(shape, batch, decomp, direction, seed=9, dtype=TC)
+    kinds = [p["kind"] for p in plan.describe()["passes"]]
+    n_r32 = sum(1 for k in kinds if k.endswith("r32_tc"))
+    assert n_r32 == sum(1 for d in shape if d == 1024), kinds
+    rel, mx = _err(x, got, shape, batch, direction)
+    print(f"tcgen05 r32 {shape} b{batch} dir{direction} {kinds}: rel-L2 {rel:.3e} max-abs {mx:.3e}")
+    assert np.all(np.isfinite(got))
+    assert rel <= REL_L2_TOL and mx <= MAXABS_TOL
 
 
 @pytest.mark.parametrize("mode,label", [(0, "first shared-memory radix-16 stage"), (2, "every radix-16 stage")])
