@@ -71,8 +71,13 @@ int fft3::prepare_func(const void *func, int smem)
         const int cap = optin - (int)fa.sharedSizeBytes; // static shared memory counts against the opt-in
         if (smem > cap)
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, "pass needs more shared memory than the device offers");
-        if (smem + (int)fa.sharedSizeBytes > 48 * 1024)
+        if (smem + (int)fa.sharedSizeBytes > 48 * 1024) {
             CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+            // the largest shared-memory carveout, so that as many blocks as the
+            // shared memory allows are resident (and the occupancy query counts them)
+            CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
+        }
     }
     return FFT3_OK;
 }

@@ -21,11 +21,14 @@
 //
 // One 128-thread block per tile stream; thread t owns GEMM row t in both
 // stages (tensor-memory lane t): it writes its row of A with tcgen05.st
-// (high parts in columns 0-31, low parts in 32-63), one elected thread
-// issues the twelve MMAs (4 K steps x 3 products, M = 128, N = 64, K = 16)
-// into D (columns 64-127) and commits them to an mbarrier, and every thread
-// reads its row of D back with tcgen05.ld.  B (DFT_32 high and low parts)
-// sits in shared memory with the 128-byte swizzle.
+// (high parts in columns 0-31, low parts in 32-63 of the tile's region), one
+// elected thread issues the twelve MMAs (4 K steps x 3 products, M = 128,
+// N = 64, K = 16) into D (columns 64-127 of the region) and commits them to
+// the region's mbarrier, and every thread reads its row of D back with
+// tcgen05.ld.  B (DFT_32 high and low parts) sits in shared memory with the
+// 128-byte swizzle.  Consecutive tiles of a block alternate between two
+// tensor-memory regions of 128 columns, so the block stores the outputs of
+// tile k-1 while the stage-(I) MMAs of tile k run.
 //
 // Tiles arrive by TMA into two landing buffers per block (contiguous lines:
 // one bulk copy of 4 x 8 KB; strided lines: four 4-column x 256-row boxes of
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
 {
     extern __shared__ uint8_t dsm_raw[];
     __shared__ __align__(8) uint64_t full[2];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t s_tmem;
     uint8_t *dsm = (uint8_t *)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *bhi = dsm, *blo = dsm + kBBytes;
@@ -130,22 +133,23 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
     for (int i = tid; i < kN; i += 128)
         tw[i] = a.tw[i];
     if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&mbar, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&mbar[i], 1);
+        }
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(&s_tmem, 128);
+        tmem_alloc(&s_tmem, 256);
         tmem_relinquish();
     }
-    fence_proxy_async_smem(); // B, written by this thread, is read by the tensor cores
+    fence_proxy_async_smem(); // B, written by these threads, is read by the tensor cores
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
+    // region r (tiles k with k % 2 == r): A in columns 128 r .. +63, D in 128 r + 64 .. +127
     const uint32_t t_row = tmem + ((uint32_t)(32 * warp) << 16); // this warp's lanes, column 0
-    const uint32_t t_d = t_row + 64;
     const uint32_t s_bhi = smem_u32(bhi), s_blo = smem_u32(blo);
     const uint64_t pol = l2_evict_first_policy();
 
@@ -177,11 +181,34 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
         issued = 1;
     }
 
-    uint32_t mma_phase = 0;
+    // Stage-(IV) outputs of tile kk (region kk % 2): X[k1 + 32 k2] of line l2.
+    const int l2 = LINES ? warp : (tid & 3), k1 = LINES ? lane : (tid >> 2);
+    auto store_outputs = [&](int64_t kk, bool ok) {
+        const int r = (int)(kk & 1);
+        const TileId id = decode_tile(blockIdx.x + kk * (int64_t)gridDim.x, a.tiles_c, a.g.A, kLpt);
+        uint32_t d[64];
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            tmem_ld16(t_row + 128 * r + 64 + 16 * h, *(uint32_t(*)[16])(d + 16 * h));
+        tmem_wait_ld();
+        tc_fence_before();
+        const int64_t c = id.c0 + l2;
+        if (ok && c < a.g.C) {
+            float2 *op = a.out + c * a.g.oc + id.a * a.g.oa + id.b * a.g.ob + (int64_t)k1 * a.g.ok;
+#pragma unroll
+            for (int k2 = 0; k2 < 32; ++k2) {
+                const float2 y = make_float2(__uint_as_float(d[2 * k2]), __uint_as_float(d[2 * k2 + 1]));
+                op[(int64_t)(32 * k2) * a.g.ok] = conj ? cconj(y) : y;
+            }
+        }
+    };
+
+    uint32_t mph = 0; // bit r: phase of region r's MMA mbarrier
     bool failed = false;
     int64_t k = 0;
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
-        const int b = (int)(k & 1);
+        const int b = (int)(k & 1), r = b;
+        const uint32_t t_a = t_row + 128 * r, t_d = t_a + 64;
         const float2 *land = (const float2 *)(land0 + b * kLandBytes);
         float2 *tr = (float2 *)(land0 + b * kLandBytes);
         const bool late = !mbar_wait(&full[b], (uint32_t)((k >> 1) & 1), a.wait_budget);
@@ -189,7 +216,6 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
             failed = true;
             break;
         }
-        const TileId id = decode_tile(tile, a.tiles_c, a.g.A, kLpt);
         // ---- stage (I): row t gathers its decimated sub-sequence x[32 j1 + j2]
         const int l1 = LINES ? warp : (tid & 3), j2 = LINES ? lane : (tid >> 2);
 #pragma unroll
@@ -201,34 +227,45 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
                 const float2 e = LINES ? land[l1 * kN + j] : land[j * kLpt + l1];
                 v[i] = conj ? cconj(e) : e;
             }
-            store_a16(t_row, 16 * h, v);
+            store_a16(t_a, 16 * h, v);
         }
         tmem_wait_st();
         tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_stage_mmas(t_row, t_d, s_bhi, s_blo);
-            mma_commit(&mbar);
+            issue_stage_mmas(t_a, t_d, s_bhi, s_blo);
+            mma_commit(&mbar[r]);
         }
-        const bool late1 = !mbar_wait(&mbar, mma_phase, a.wait_budget);
-        mma_phase ^= 1;
+        // ---- while those MMAs run: the outputs of the previous tile
+        if (k > 0) {
+            const bool lp = !mbar_wait(&mbar[r ^ 1], (mph >> (r ^ 1)) & 1u, a.wait_budget);
+            mph ^= 1u << (r ^ 1);
+            tc_fence_after();
+            store_outputs(k - 1, !lp);
+            if (cta_any(lp)) {
+                failed = true;
+                break;
+            }
+        }
+        const bool late1 = !mbar_wait(&mbar[r], (mph >> r) & 1u, a.wait_budget);
+        mph ^= 1u << r;
         tc_fence_after();
         // ---- (II) twiddle and (III) transposition into the landing buffer
+        {
+            uint32_t d[64];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            uint32_t d[16];
-            tmem_ld16(t_d + 16 * h, d);
+            for (int h = 0; h < 4; ++h)
+                tmem_ld16(t_d + 16 * h, *(uint32_t(*)[16])(d + 16 * h));
             tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int k1 = 8 * h + i;
-                const float2 y = cmul(make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1])),
-                                      tw[k1 * 32 + j2]);
+            for (int kk1 = 0; kk1 < 32; ++kk1) {
+                const float2 y = cmul(make_float2(__uint_as_float(d[2 * kk1]), __uint_as_float(d[2 * kk1 + 1])),
+                                      tw[kk1 * 32 + j2]);
                 if constexpr (LINES)
-                    tr[l1 * kLineT + k1 * kPitchL + j2] = y;
+                    tr[l1 * kLineT + kk1 * kPitchL + j2] = y;
                 else
-                    tr[k1 * kPitchC + j2 * kLpt + l1] = y;
+                    tr[kk1 * kPitchC + j2 * kLpt + l1] = y;
             }
         }
         tc_fence_before();
@@ -237,7 +274,6 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
             break;
         }
         // ---- stage (IV): row t = (line, k1) reads X1[j2][k1] for every j2
-        const int l2 = LINES ? warp : (tid & 3), k1 = LINES ? lane : (tid >> 2);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float2 v[16];
@@ -254,7 +290,7 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
                 for (int i = 0; i < 16; ++i)
                     v[i] = tr[k1 * kPitchC + (16 * h + i) * kLpt + l2];
             }
-            store_a16(t_row, 16 * h, v);
+            store_a16(t_a, 16 * h, v);
         }
         tmem_wait_st();
         tc_fence_before();
@@ -262,54 +298,34 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_stage_mmas(t_row, t_d, s_bhi, s_blo);
-            mma_commit(&mbar);
+            issue_stage_mmas(t_a, t_d, s_bhi, s_blo);
+            mma_commit(&mbar[r]);
             issue(k + 2); // the landing buffer is read out: the block's tile after next
             issued = k + 2;
         }
-        const bool late2 = !mbar_wait(&mbar, mma_phase, a.wait_budget);
-        mma_phase ^= 1;
-        tc_fence_after();
-        // ---- outputs X[k1 + 32 k2] of line l2
-        const int64_t c = id.c0 + l2;
-        const bool valid = !late2 && c < a.g.C;
-        float2 *op = a.out + c * a.g.oc + id.a * a.g.oa + id.b * a.g.ob + (int64_t)k1 * a.g.ok;
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            uint32_t d[16];
-            tmem_ld16(t_d + 16 * h, d);
-            tmem_wait_ld();
-            if (valid) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int k2 = 8 * h + i;
-                    const float2 y = make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1]));
-                    op[(int64_t)(32 * k2) * a.g.ok] = conj ? cconj(y) : y;
-                }
-            }
-        }
-        tc_fence_before();
-        if (cta_any(late2)) {
-            failed = true;
-            break;
-        }
     }
-    if (failed) {
-        // stop: record the timeout and wait (bounded) for the copies still in
-        // flight into this block's landing buffers before the block exits
-        if (tid == 0) {
-            atomicOr(a.err, kErrWaitTimeout);
-            for (int64_t v = k; v <= issued; ++v)
-                if (blockIdx.x + v * (int64_t)gridDim.x < a.ntiles &&
-                    !mbar_wait(&full[v & 1], (uint32_t)((v >> 1) & 1), a.wait_budget))
-                    break;
-        }
+    if (!failed && k > 0) {
+        // the last tile's outputs
+        const int r = (int)((k - 1) & 1);
+        const bool lp = !mbar_wait(&mbar[r], (mph >> r) & 1u, a.wait_budget);
+        tc_fence_after();
+        store_outputs(k - 1, !lp);
+        failed = cta_any(lp);
+    }
+    if (failed && tid == 0) {
+        // record the timeout and wait (bounded) for the copies still in flight
+        // into this block's landing buffers before the block exits
+        atomicOr(a.err, kErrWaitTimeout);
+        for (int64_t v = k; v <= issued; ++v)
+            if (blockIdx.x + v * (int64_t)gridDim.x < a.ntiles &&
+                !mbar_wait(&full[v & 1], (uint32_t)((v >> 1) & 1), a.wait_budget))
+                break;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        tmem_dealloc(tmem, 128);
+        tmem_dealloc(tmem, 256);
 }
 
 const void *tc32_kernel(bool lines)
