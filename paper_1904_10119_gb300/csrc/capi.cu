@@ -360,6 +360,12 @@ static int build_launches(fft3_plan_s *P)
                 return rc;
             P->counters_bytes = std::max(P->counters_bytes,
                                          (size_t)(1 + p.g.A * p.g.B) * sizeof(int));
+        } else if (L.tc32) {
+            // one block per SM, each running kTc32Groups streams of tiles
+            rc = occupancy_grid(L.func, L.block.x, L.smem, (p.ntiles + kTc32Groups - 1) / kTc32Groups, P->device,
+                                &L.grid);
+            if (rc)
+                return rc;
         } else {
             rc = occupancy_grid(L.func, L.block.x, L.smem, p.ntiles, P->device, &L.grid);
             if (rc)

@@ -19,25 +19,27 @@
 // three products are accumulated in FP32: A_lo B_hi + A_hi B_lo + A_hi B_hi
 // (A_lo B_lo is dropped).  The twiddles (II) are applied in FP32.
 //
-// One 128-thread block per tile stream; thread t owns GEMM row t in both
-// stages (tensor-memory lane t): it writes its row of A with tcgen05.st
-// (high parts in columns 0-31, low parts in 32-63 of the tile's region), one
-// elected thread issues the twelve MMAs (4 K steps x 3 products, M = 128,
-// N = 64, K = 16) into D (columns 64-127 of the region) and commits them to
-// the region's mbarrier, and every thread reads its row of D back with
-// tcgen05.ld.  B (DFT_32 high and low parts) sits in shared memory with the
-// 128-byte swizzle.  Consecutive tiles of a block alternate between two
-// tensor-memory regions of 128 columns, so the block stores the outputs of
-// tile k-1 while the stage-(I) MMAs of tile k run.
+// One persistent 512-thread block per SM (the occupancy of a kernel that
+// allocates tensor memory is one block per SM) made of four independent
+// groups of 128 threads; group g owns tensor-memory columns 128 g .. +127
+// and a landing buffer, and transforms its own stream of tiles, so one
+// group's MMAs and loads overlap the other groups' CUDA-core work.  In a
+// group, thread t owns GEMM row t in both stages (tensor-memory lane t): it
+// writes its row of A with tcgen05.st (high parts in columns 0-31, low parts
+// in 32-63 of the group's region), one elected thread issues the twelve MMAs
+// (4 K steps x 3 products, M = 128, N = 64, K = 16) into D (columns 64-127 of
+// the region) and commits them to the group's mbarrier, and every thread
+// reads its row of D back with tcgen05.ld.  B (DFT_32 high and low parts)
+// sits in shared memory with the 128-byte swizzle, shared by the groups.
 //
-// Tiles arrive by TMA into two landing buffers per block (contiguous lines:
-// one bulk copy of 4 x 8 KB; strided lines: four 4-column x 256-row boxes of
-// a 4D tensor map).  A landing buffer, once its inputs are in registers, holds
-// the tile's transposition (III) in a padded layout, and once stage (IV) has
-// read it back it is refilled with the block's tile after next, so the loads
-// of the next tile overlap this tile's arithmetic.
+// Tiles arrive by TMA into the group's landing buffer (contiguous lines: one
+// bulk copy of 4 x 8 KB; strided lines: four 4-column x 256-row boxes of a 4D
+// tensor map).  Once its inputs are in registers the landing buffer holds the
+// tile's transposition (III) in a padded layout, and once stage (IV) has read
+// that back it is refilled with the group's next tile, whose load overlaps the
+// stage-(IV) MMAs and the output stores.
 //
-// Thread roles (t = threadIdx.x, tile lines/columns l < 4):
+// Thread roles (t = row within the group, tile lines/columns l < 4):
 //   contiguous lines (LINES = true):  row t = 32 l + j2 (stage I), 32 l + k1 (IV)
 //   strided columns  (LINES = false): row t = 4 j2 + l (stage I), 4 k1 + l (IV)
 // so every warp's shared-memory accesses cover 32 consecutive complex values
@@ -64,7 +66,8 @@ static_assert(kLandBytes == kLpt * kLineT * 8 && 32 * kPitchC * 8 <= kLandBytes,
 constexpr int kBBytes = 64 * 128;                       // one 64 x 64 BF16 operand
 constexpr int kTwOff = 2 * kBBytes;                     // w_1024^{j2 k1}, [k1][j2]
 constexpr int kLandOff = kTwOff + kN * 8;
-static_assert(kLandOff + 2 * kLandBytes + 1024 == kTc32SmemBytes, "dynamic shared memory (+ alignment slack)");
+static_assert(kLandOff + kTc32Groups * kLandBytes + 1024 == kTc32SmemBytes,
+              "dynamic shared memory (+ alignment slack)");
 
 // w = w_32^m for the DFT_32 operand (FP32 values of the FP64 generator) ->
 // B_hi, B_lo in the 128-byte-swizzled K-major layout.
@@ -115,152 +118,143 @@ __device__ __forceinline__ bool cta_any(bool p) { return __syncthreads_or(p ? 1 
 
 } // namespace
 
+// Barrier of thread group g (named barrier 1 + g over its 128 threads), with
+// an OR-reduction of a predicate.
+template <int ID>
+__device__ __forceinline__ bool bar_or(bool pred)
+{
+    uint32_t out;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, 128, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(out)
+                 : "r"(pred ? 1u : 0u), "n"(ID)
+                 : "memory");
+    return out != 0;
+}
+__device__ __forceinline__ bool group_or(int g, bool pred)
+{
+    switch (g) {
+    case 0: return bar_or<1>(pred);
+    case 1: return bar_or<2>(pred);
+    case 2: return bar_or<3>(pred);
+    default: return bar_or<4>(pred);
+    }
+}
+
 template <bool LINES>
-__global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_constant__ CUtensorMap tin)
+__global__ void __launch_bounds__(kTc32Threads, 1) k_tc32(PassArgs a, const __grid_constant__ CUtensorMap tin)
 {
     extern __shared__ uint8_t dsm_raw[];
-    __shared__ __align__(8) uint64_t full[2];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t full[kTc32Groups];
+    __shared__ __align__(8) uint64_t mbar[kTc32Groups];
     __shared__ uint32_t s_tmem;
     uint8_t *dsm = (uint8_t *)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *bhi = dsm, *blo = dsm + kBBytes;
     float2 *tw = (float2 *)(dsm + kTwOff);
-    uint8_t *land0 = dsm + kLandOff;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, g = tid >> 7, gt = tid & 127, warp = tid >> 5, lane = tid & 31;
+    const int gw = warp & 3; // warp within the group = its tensor-memory lane quarter
+    uint8_t *land = dsm + kLandOff + g * kLandBytes;
     const bool conj = a.conj != 0;
 
     build_dft32_operand(bhi, blo, a.tw + a.tw_split_off);
-    for (int i = tid; i < kN; i += 128)
+    for (int i = tid; i < kN; i += blockDim.x)
         tw[i] = a.tw[i];
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kTc32Groups; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&mbar[i], 1);
         }
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(&s_tmem, 256);
+        tmem_alloc(&s_tmem, 512);
         tmem_relinquish();
     }
     fence_proxy_async_smem(); // B, written by these threads, is read by the tensor cores
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = s_tmem;
-    // region r (tiles k with k % 2 == r): A in columns 128 r .. +63, D in 128 r + 64 .. +127
-    const uint32_t t_row = tmem + ((uint32_t)(32 * warp) << 16); // this warp's lanes, column 0
+    // group g: A in columns 128 g .. +63, D in 128 g + 64 .. +127; row gt in lane gt
+    const uint32_t t_a = s_tmem + ((uint32_t)(32 * gw) << 16) + 128 * g, t_d = t_a + 64;
     const uint32_t s_bhi = smem_u32(bhi), s_blo = smem_u32(blo);
     const uint64_t pol = l2_evict_first_policy();
+    // the groups of a block take adjacent tiles (the 4-column tiles of one
+    // 128-byte row segment of a strided pass are fetched by one SM together)
+    const int64_t stream = (int64_t)blockIdx.x * kTc32Groups + g, nstreams = (int64_t)gridDim.x * kTc32Groups;
 
-    // Load of the block's k-th tile into landing buffer k % 2 (thread 0).
+    // Load of the group's k-th tile into its landing buffer (the group's thread 0).
     auto issue = [&](int64_t k) {
-        const int64_t tile = blockIdx.x + k * (int64_t)gridDim.x;
+        const int64_t tile = stream + k * nstreams;
         if (tile >= a.ntiles)
             return;
-        const int b = (int)(k & 1);
-        uint8_t *dst = land0 + b * kLandBytes;
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, kLpt);
         if constexpr (LINES) {
             // lines beyond the array's last one are not loaded (their rows are never stored)
             const int nval = (int)min((int64_t)kLpt, a.g.C - id.c0);
             const float2 *src = a.in + id.c0 * a.g.ic + id.a * a.g.ia + id.b * a.g.ib;
-            mbar_expect_tx(&full[b], (uint32_t)nval * kN * 8u);
-            bulk_load(dst, src, (uint32_t)nval * kN * 8u, &full[b], pol);
+            mbar_expect_tx(&full[g], (uint32_t)nval * kN * 8u);
+            bulk_load(land, src, (uint32_t)nval * kN * 8u, &full[g], pol);
         } else {
-            mbar_expect_tx(&full[b], kTileBytes);
+            mbar_expect_tx(&full[g], kTileBytes);
 #pragma unroll
             for (int q = 0; q < kN / 256; ++q)
-                tma_load_4d(dst + q * 256 * kLpt * 8, &tin, (int)id.c0, q * 256, (int)id.a, (int)id.b, &full[b]);
+                tma_load_4d(land + q * 256 * kLpt * 8, &tin, (int)id.c0, q * 256, (int)id.a, (int)id.b, &full[g]);
         }
     };
-    int64_t issued = -1; // (thread 0) the last tile index k whose load was issued
-    if (tid == 0) {
+    int64_t issued = -1; // (the group's thread 0) the last k whose load was issued
+    if (gt == 0) {
         issue(0);
-        issue(1);
-        issued = 1;
+        issued = 0;
     }
 
-    // Stage-(IV) outputs of tile kk (region kk % 2): X[k1 + 32 k2] of line l2.
-    const int l2 = LINES ? warp : (tid & 3), k1 = LINES ? lane : (tid >> 2);
-    auto store_outputs = [&](int64_t kk, bool ok) {
-        const int r = (int)(kk & 1);
-        const TileId id = decode_tile(blockIdx.x + kk * (int64_t)gridDim.x, a.tiles_c, a.g.A, kLpt);
-        uint32_t d[64];
-#pragma unroll
-        for (int h = 0; h < 4; ++h)
-            tmem_ld16(t_row + 128 * r + 64 + 16 * h, *(uint32_t(*)[16])(d + 16 * h));
-        tmem_wait_ld();
-        tc_fence_before();
-        const int64_t c = id.c0 + l2;
-        if (ok && c < a.g.C) {
-            float2 *op = a.out + c * a.g.oc + id.a * a.g.oa + id.b * a.g.ob + (int64_t)k1 * a.g.ok;
-#pragma unroll
-            for (int k2 = 0; k2 < 32; ++k2) {
-                const float2 y = make_float2(__uint_as_float(d[2 * k2]), __uint_as_float(d[2 * k2 + 1]));
-                op[(int64_t)(32 * k2) * a.g.ok] = conj ? cconj(y) : y;
-            }
-        }
-    };
-
-    uint32_t mph = 0; // bit r: phase of region r's MMA mbarrier
+    const float2 *lin = (const float2 *)land;
+    float2 *tr = (float2 *)land;
+    // stage (I) row gt = (line l1, sub-sequence j2); stage (IV) row gt = (line l2, output k1)
+    const int l1 = LINES ? gw : (gt & 3), j2 = LINES ? lane : (gt >> 2);
+    const int l2 = l1, k1 = j2;
+    uint32_t mph = 0;
     bool failed = false;
     int64_t k = 0;
-    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
-        const int b = (int)(k & 1), r = b;
-        const uint32_t t_a = t_row + 128 * r, t_d = t_a + 64;
-        const float2 *land = (const float2 *)(land0 + b * kLandBytes);
-        float2 *tr = (float2 *)(land0 + b * kLandBytes);
-        const bool late = !mbar_wait(&full[b], (uint32_t)((k >> 1) & 1), a.wait_budget);
-        if (cta_any(late)) {
+    for (int64_t tile = stream; tile < a.ntiles; tile += nstreams, ++k) {
+        const bool late = !mbar_wait(&full[g], (uint32_t)(k & 1), a.wait_budget);
+        if (group_or(g, late)) {
             failed = true;
             break;
         }
-        // ---- stage (I): row t gathers its decimated sub-sequence x[32 j1 + j2]
-        const int l1 = LINES ? warp : (tid & 3), j2 = LINES ? lane : (tid >> 2);
+        // ---- stage (I): row gt gathers its decimated sub-sequence x[32 j1 + j2]
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float2 v[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int j = 32 * (16 * h + i) + j2;
-                const float2 e = LINES ? land[l1 * kN + j] : land[j * kLpt + l1];
+                const float2 e = LINES ? lin[l1 * kN + j] : lin[j * kLpt + l1];
                 v[i] = conj ? cconj(e) : e;
             }
             store_a16(t_a, 16 * h, v);
         }
         tmem_wait_st();
         tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
+        group_or(g, false);
+        if (gt == 0) {
             tc_fence_after();
             issue_stage_mmas(t_a, t_d, s_bhi, s_blo);
-            mma_commit(&mbar[r]);
+            mma_commit(&mbar[g]);
         }
-        // ---- while those MMAs run: the outputs of the previous tile
-        if (k > 0) {
-            const bool lp = !mbar_wait(&mbar[r ^ 1], (mph >> (r ^ 1)) & 1u, a.wait_budget);
-            mph ^= 1u << (r ^ 1);
-            tc_fence_after();
-            store_outputs(k - 1, !lp);
-            if (cta_any(lp)) {
-                failed = true;
-                break;
-            }
-        }
-        const bool late1 = !mbar_wait(&mbar[r], (mph >> r) & 1u, a.wait_budget);
-        mph ^= 1u << r;
+        const bool late1 = !mbar_wait(&mbar[g], mph, a.wait_budget);
+        mph ^= 1;
         tc_fence_after();
         // ---- (II) twiddle and (III) transposition into the landing buffer
-        {
-            uint32_t d[64];
 #pragma unroll
-            for (int h = 0; h < 4; ++h)
-                tmem_ld16(t_d + 16 * h, *(uint32_t(*)[16])(d + 16 * h));
+        for (int h = 0; h < 2; ++h) {
+            uint32_t d[32];
+            tmem_ld16(t_d + 32 * h, *(uint32_t(*)[16])(d));
+            tmem_ld16(t_d + 32 * h + 16, *(uint32_t(*)[16])(d + 16));
             tmem_wait_ld();
 #pragma unroll
-            for (int kk1 = 0; kk1 < 32; ++kk1) {
-                const float2 y = cmul(make_float2(__uint_as_float(d[2 * kk1]), __uint_as_float(d[2 * kk1 + 1])),
+            for (int i = 0; i < 16; ++i) {
+                const int kk1 = 16 * h + i;
+                const float2 y = cmul(make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1])),
                                       tw[kk1 * 32 + j2]);
                 if constexpr (LINES)
                     tr[l1 * kLineT + kk1 * kPitchL + j2] = y;
@@ -269,11 +263,11 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
             }
         }
         tc_fence_before();
-        if (cta_any(late1)) {
+        if (group_or(g, late1)) {
             failed = true;
             break;
         }
-        // ---- stage (IV): row t = (line, k1) reads X1[j2][k1] for every j2
+        // ---- stage (IV): row gt = (line, k1) reads X1[j2][k1] for every j2
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float2 v[16];
@@ -295,37 +289,56 @@ __global__ void __launch_bounds__(128, 2) k_tc32(PassArgs a, const __grid_consta
         tmem_wait_st();
         tc_fence_before();
         fence_proxy_async_smem(); // this thread's accesses to the landing buffer, before its refill
-        __syncthreads();
-        if (tid == 0) {
+        group_or(g, false);
+        if (gt == 0) {
             tc_fence_after();
             issue_stage_mmas(t_a, t_d, s_bhi, s_blo);
-            mma_commit(&mbar[r]);
-            issue(k + 2); // the landing buffer is read out: the block's tile after next
-            issued = k + 2;
+            mma_commit(&mbar[g]);
+            issue(k + 1); // the landing buffer is read out: the group's next tile
+            issued = k + 1;
+        }
+        const bool late2 = !mbar_wait(&mbar[g], mph, a.wait_budget);
+        mph ^= 1;
+        tc_fence_after();
+        // ---- outputs X[k1 + 32 k2] of line l2
+        const TileId id = decode_tile(tile, a.tiles_c, a.g.A, kLpt);
+        const int64_t c = id.c0 + l2;
+        const bool valid = !late2 && c < a.g.C;
+        float2 *op = a.out + c * a.g.oc + id.a * a.g.oa + id.b * a.g.ob + (int64_t)k1 * a.g.ok;
+        const int64_t ostep = 32 * a.g.ok;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t d[32];
+            tmem_ld16(t_d + 32 * h, *(uint32_t(*)[16])(d));
+            tmem_ld16(t_d + 32 * h + 16, *(uint32_t(*)[16])(d + 16));
+            tmem_wait_ld();
+            if (valid) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float2 y = make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1]));
+                    op[(16 * h + i) * ostep] = conj ? cconj(y) : y;
+                }
+            }
+        }
+        tc_fence_before();
+        if (group_or(g, late2)) {
+            failed = true;
+            break;
         }
     }
-    if (!failed && k > 0) {
-        // the last tile's outputs
-        const int r = (int)((k - 1) & 1);
-        const bool lp = !mbar_wait(&mbar[r], (mph >> r) & 1u, a.wait_budget);
-        tc_fence_after();
-        store_outputs(k - 1, !lp);
-        failed = cta_any(lp);
-    }
-    if (failed && tid == 0) {
-        // record the timeout and wait (bounded) for the copies still in flight
-        // into this block's landing buffers before the block exits
+    if (failed && gt == 0) {
+        // record the timeout and wait (bounded) for the copy still in flight
+        // into this group's landing buffer before the block exits
         atomicOr(a.err, kErrWaitTimeout);
         for (int64_t v = k; v <= issued; ++v)
-            if (blockIdx.x + v * (int64_t)gridDim.x < a.ntiles &&
-                !mbar_wait(&full[v & 1], (uint32_t)((v >> 1) & 1), a.wait_budget))
+            if (stream + v * nstreams < a.ntiles && !mbar_wait(&full[g], (uint32_t)(v & 1), a.wait_budget))
                 break;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(s_tmem, 512);
 }
 
 const void *tc32_kernel(bool lines)

@@ -102,14 +102,15 @@ constexpr int cstream_min_blocks(int smem_bytes, int threads)
     return (2 * (smem_bytes + 1024) <= 228 * 1024 && threads <= 512) ? 2 : 1;
 }
 
-// Split-BF16 tcgen05 passes of 1024-point lines (k_tc32.cu): 128 threads,
-// tiles of 4 lines, two landing buffers of 34816 bytes (the 32 KB tile, then
-// its padded transposition), the DFT_32 operand (16 KB), the w_1024 twiddle
-// table (8 KB) and 1 KB of alignment slack.
-constexpr int kTc32Threads = 128;
+// Split-BF16 tcgen05 passes of 1024-point lines (k_tc32.cu): one block of
+// four 128-thread groups per SM, tiles of 4 lines, one landing buffer of 34816
+// bytes per group (the 32 KB tile, then its padded transposition), the DFT_32
+// operand (16 KB), the w_1024 twiddle table (8 KB) and 1 KB of alignment slack.
+constexpr int kTc32Groups = 4;
+constexpr int kTc32Threads = 128 * kTc32Groups;
 constexpr int kTc32Lpt = 4;
 constexpr int kTc32LandBytes = kTc32Lpt * 32 * 34 * 8;
-constexpr int kTc32SmemBytes = 2 * 64 * 128 + 1024 * 8 + 2 * kTc32LandBytes + 1024;
+constexpr int kTc32SmemBytes = 2 * 64 * 128 + 1024 * 8 + kTc32Groups * kTc32LandBytes + 1024;
 // lines = true: contiguous lines (x pass), false: strided columns
 const void *tc32_kernel(bool lines);
 

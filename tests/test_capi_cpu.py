@@ -500,7 +500,7 @@ def test_tcgen05_radix32_schedule():
     kinds = [p["kind"] for p in s["passes"]]
     assert kinds == ["line_contig_r32_tc", "line_strided_r32_tc", "line_strided_r32_tc"]
     for p in s["passes"]:
-        assert p["lpt"] == 4 and p["threads"] == 128 and p["line"]["radices"] == [32, 32]
+        assert p["lpt"] == 4 and p["threads"] == 512 and p["line"]["radices"] == [32, 32]
         assert p["mma"].startswith("tcgen05")
         assert p["tiles"] == 1024 * 1024 // 4
     assert s["twiddle_entries"] == 3 * (1024 + 32)
