@@ -239,8 +239,10 @@ def test_volumetric_automatic_mesh_and_compiled_splits():
 
 
 def test_tensor_core_schedule():
-    # the strided 1024-point lines stream their 16 x 16 sub-line transforms through the tensor cores
-    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_AUTO, -1)
+    # tc_stages 3: the strided 1024-point lines stream their 16 x 16 sub-line transforms
+    # through the mma.sync tensor-core stage
+    s = fft3.fft3_plan_schedule(1024, 1024, 1024, 1, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_AUTO, -1,
+                                fft3.make_options(tc_stages=3))
     assert _kinds(s) == ["line_contig_tc", "line_strided_stream_tc", "line_strided_stream_tc"]
     assert all(16 in p["line"]["radices"] for p in s["passes"])
     assert all(p["tc_stages"] == 0 for p in s["passes"])
@@ -253,7 +255,8 @@ def test_tensor_core_schedule():
                                 fft3.make_options(tile_lines=8, tc_stages=2))
     assert _kinds(s) == ["line_contig_tc", "line_strided_tc", "line_strided_tc"]
     # short lines fall back to the FP32 kernels; other decompositions are FP32 only
-    s = fft3.fft3_plan_schedule(64, 1024, 32, 1, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_PENCIL3, -1)
+    s = fft3.fft3_plan_schedule(64, 1024, 32, 1, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_PENCIL3, -1,
+                                fft3.make_options(tc_stages=3))
     assert _kinds(s) == ["line_contig", "line_strided_stream_tc", "line_strided"]
     with pytest.raises(fft3.Fft3Error):
         fft3.fft3_plan_schedule(64, 64, 64, 1, fft3.FFT3_C64_SPLITBF16_TC, fft3.FFT3_SLAB_PENCIL, -1)
