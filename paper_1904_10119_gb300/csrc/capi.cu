@@ -313,8 +313,9 @@ static int build_launches(fft3_plan_s *P)
         }
         case PK_TCX:
         case PK_TCS:
-            L.func = tc32_kernel(p.kind == PK_TCX);
-            L.tc32 = p.kind == PK_TCX ? 1 : 2;
+        case PK_TCB:
+            L.func = tc32_kernel(p.kind == PK_TCX ? 0 : p.kind == PK_TCS ? 1 : 2);
+            L.tc32 = p.kind == PK_TCS ? 2 : 1;
             break;
         case PK_JTC:
             L.func = fk && p.tc_mode >= 0 ? fk->j_tc[p.tc_mode] : nullptr;

@@ -39,7 +39,7 @@ struct Launch {
     bool slab_map = false; // k_slab_tma: 2D tensor map of the blocked workspace
     bool tma = false; // kernel takes two tensor maps after its PassArgs
     int stream_q = 0; // > 0: streamed strided pass, one 5D input map of Q decimated sub-lines
-    int tc32 = 0;     // k_tc32: 1 = contiguous lines (unused map), 2 = strided columns (4D input map)
+    int tc32 = 0;     // k_tc32: 1 = tiles by bulk copies (unused map), 2 = strided columns (4D input map)
     // two-stream pipelined pair: this pass (on the caller's stream) and the
     // next one (on the plan's side stream) run over chunks of `chunk` values
     // of a, the next pass's chunk c after this pass's chunk c

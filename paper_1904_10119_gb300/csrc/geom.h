@@ -11,6 +11,9 @@ struct PassGeom {
     int64_t C, A, B;
     int64_t ij, ic, ia, ib;
     int64_t ok, oc, oa, ob;
+    // 0: output element k of a line at k*ok; > 0: at (k/4)*oblk + (k%4)*ok
+    // (a line stored in blocks of 4, as the 4-column blocked layouts need)
+    int64_t oblk;
 };
 
 // Error flag bits written by device code (read back by fft3_plan_check).

@@ -326,6 +326,32 @@ static void set_cstream(PassPlan *p, int ci)
     p->smem_bytes = cstream_smem_p(m.n, m.q, m.q / m.pair, m.lpt, m.groups * m.stages);
 }
 
+// Kind, tile, line, twiddles and launch shape of a tcgen05 radix-32 pass of
+// 1024-point lines (k_tc32.cu): twiddles w_1024^{j2 k1} stored [k1][j2], then
+// w_32^m for the DFT_32 operand.
+static void set_tc32(Schedule *s, PassPlan *p, int kind)
+{
+    p->kind = kind;
+    p->lpt = kTc32Lpt;
+    p->threads = kTc32Threads;
+    p->smem_bytes = kTc32SmemBytes;
+    p->tc_mode = 0;
+    p->line = LineChoice{};
+    p->line.n = 1024;
+    p->line.fixed = -1;
+    p->line.T = 32;
+    p->line.nst = 2;
+    p->line.rad[0] = p->line.rad[1] = 32;
+    std::vector<int64_t> tw(1024), w32(32);
+    for (int i = 0; i < 1024; ++i)
+        tw[i] = (int64_t)(i % 32) * (i / 32);
+    for (int i = 0; i < 32; ++i)
+        w32[i] = i;
+    p->tw_seg[0] = add_seg(s, 1024, std::move(tw));
+    p->tw_seg[2] = add_seg(s, 32, std::move(w32));
+    set_tiles(p);
+}
+
 // A single 1D pass on dimension d with geometry g.
 static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rotate, int src, int dst,
                           PassPlan *out, std::string *err)
@@ -387,25 +413,7 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         const bool cols = strided_in && (g.ij * 8) % 16 == 0 && al && g.C <= 0x7fffffff && g.A <= 0x7fffffff &&
                           g.B <= 0x7fffffff;
         if (lines || cols) {
-            p.kind = lines ? PK_TCX : PK_TCS;
-            p.lpt = kTc32Lpt;
-            p.threads = kTc32Threads;
-            p.smem_bytes = kTc32SmemBytes;
-            p.tc_mode = 0;
-            p.line = LineChoice{};
-            p.line.n = n;
-            p.line.fixed = -1;
-            p.line.T = 32;
-            p.line.nst = 2;
-            p.line.rad[0] = p.line.rad[1] = 32;
-            std::vector<int64_t> tw(1024), w32(32);
-            for (int i = 0; i < 1024; ++i)
-                tw[i] = (int64_t)(i % 32) * (i / 32); // [k1][j2]: w_1024^{j2 k1}
-            for (int i = 0; i < 32; ++i)
-                w32[i] = i;                           // w_32^m for the DFT_32 operand
-            p.tw_seg[0] = add_seg(s, n, std::move(tw));
-            p.tw_seg[2] = add_seg(s, 32, std::move(w32));
-            set_tiles(&p);
+            set_tc32(s, &p, lines ? PK_TCX : PK_TCS);
             *out = p;
             return FFT3_OK;
         }
@@ -1030,6 +1038,40 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         if (rc)
             return rc;
         s.need_ws = true;
+    } else if (dtype == FFT3_C64_SPLITBF16_TC && decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED &&
+               s.opts.tc_stages == 0 && s.opts.tile_lines == 0 && n0 == 1024 && n1 == 1024 && n2 == 1024 &&
+               batch == 1) {
+        // tcgen05 radix-32 passes with 4-column blocked intermediates, so that every
+        // pass loads contiguous 32 KB tiles (4 lines or 4 columns of 1024 points):
+        //   x: natural -> [z][x/4][y][x%4]  (out),
+        //   y: [z][x/4][y][x%4] -> [x/4][y][z][x%4]  (workspace),
+        //   z: [x/4][y][z][x%4] -> natural  (out).
+        // Each store writes 32-byte pieces; the four groups of a block take adjacent
+        // tiles, so the pieces of one 128-byte row are written together.
+        const int64_t X = n0, Y = n1, Z = n2;
+        PassGeom gx{}, gy{}, gz{};
+        gx.C = Y; gx.A = Z; gx.B = 1;
+        gx.ij = 1; gx.ic = X; gx.ia = X * Y; gx.ib = X * Y * Z;
+        gx.ok = 1; gx.oblk = 4 * Y; gx.oc = 4; gx.oa = X * Y; gx.ob = X * Y * Z;
+        gy.C = 4; gy.A = X / 4; gy.B = Z;
+        gy.ij = 4; gy.ic = 1; gy.ia = 4 * Y; gy.ib = X * Y;
+        gy.ok = 4 * Z; gy.oc = 1; gy.oa = 4 * Y * Z; gy.ob = 4;
+        gz.C = 4; gz.A = X / 4; gz.B = Y;
+        gz.ij = 4; gz.ic = 1; gz.ia = 4 * Y * Z; gz.ib = 4 * Z;
+        gz.ok = X * Y; gz.oc = 1; gz.oa = 4; gz.ob = X;
+        const PassGeom gs[3] = {gx, gy, gz};
+        const int kinds[3] = {PK_TCX, PK_TCB, PK_TCB};
+        const int bufs[3][2] = {{BUF_IN, BUF_OUT}, {BUF_OUT, BUF_WS}, {BUF_WS, BUF_OUT}};
+        for (int d = 0; d < 3; ++d) {
+            PassPlan p;
+            p.dim = d;
+            p.g = gs[d];
+            p.src = bufs[d][0];
+            p.dst = bufs[d][1];
+            set_tc32(&s, &p, kinds[d]);
+            s.passes.push_back(p);
+        }
+        s.need_ws = true;
     } else if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED && blocked_fits()) {
         rc = emit_blocked();
         if (rc)
@@ -1181,8 +1223,8 @@ static const char *kind_name(int k)
                                   "line_strided_tma", "line_contig_tc", "line_strided_tc",
                                   "volumetric_split_fixed", "line_strided_stream", "slab_l2_blocked",
                                   "line_runtime_fp64", "line_contig_fp64", "line_strided_fp64",
-                                  "line_contig_r32_tc", "line_strided_r32_tc"};
-    return (k >= 0 && k <= 19) ? names[k] : "?";
+                                  "line_contig_r32_tc", "line_strided_r32_tc", "line_blocked4_r32_tc"};
+    return (k >= 0 && k <= 20) ? names[k] : "?";
 }
 static const char *buf_name(int b)
 {
@@ -1236,7 +1278,7 @@ std::string Schedule::json() const
             o << ",\"p\":" << p.p;
         if (p.kind == PK_JTC || p.kind == PK_CTC || (p.kind == PK_CSTREAM && p.tc_mode >= 0))
             o << ",\"tc_stages\":" << p.tc_mode << ",\"mma\":\"mma.sync.m16n8k16\"";
-        if (p.kind == PK_TCX || p.kind == PK_TCS)
+        if (p.kind == PK_TCX || p.kind == PK_TCS || p.kind == PK_TCB)
             o << ",\"mma\":\"tcgen05.mma m128n64k16\"";
         if (p.kind == PK_CSTREAM) {
             int cnt = 0;
@@ -1250,7 +1292,10 @@ std::string Schedule::json() const
         const PassGeom &g = p.g;
         o << ",\"geom\":{\"C\":" << g.C << ",\"A\":" << g.A << ",\"B\":" << g.B << ",\"ij\":" << g.ij
           << ",\"ic\":" << g.ic << ",\"ia\":" << g.ia << ",\"ib\":" << g.ib << ",\"ok\":" << g.ok
-          << ",\"oc\":" << g.oc << ",\"oa\":" << g.oa << ",\"ob\":" << g.ob << "}}";
+          << ",\"oc\":" << g.oc << ",\"oa\":" << g.oa << ",\"ob\":" << g.ob;
+        if (g.oblk)
+            o << ",\"oblk\":" << g.oblk;
+        o << "}}";
     }
     o << "]}";
     return o.str();

@@ -132,3 +132,29 @@ def test_bounded_wait_expires_and_reports_timeout(mode):
     from tests.gpu_util import assert_parity, run_plan
     x, got, _ = run_plan(shape, 1, fft3.FFT3_SLAB_PENCIL, -1, x=x, slab_mode=mode)
     assert_parity(x, got, shape)
+
+
+def test_tcgen05_blocked4_probe_is_identity_at_1024cubed():
+    """The 1024^3 split-BF16 schedule (4-column blocked intermediates, line
+    transforms replaced by the identity): after all three passes every element
+    is back at its natural position, bit-exact; after the x pass element
+    (x, y, z) sits at z*X*Y + (x/4)*4Y + 4y + x%4."""
+    n = 1024
+    plan = fft3.Plan(n, n, n, 1, decomposition=fft3.FFT3_AUTO, dtype=fft3.FFT3_C64_SPLITBF16_TC)
+    assert [p["kind"] for p in plan.describe()["passes"]][1:] == ["line_blocked4_r32_tc"] * 2
+    N = n ** 3
+    i = torch.arange(N, device="cuda", dtype=torch.int64)
+    x = torch.complex((i % 4096).float(), (i // 4096).float())
+    out = torch.full_like(x, complex(-1.0, -1.0))
+    for npasses in (1, -1):
+        fft3.fft3_plan_probe_layout(plan.handle, x.data_ptr(), out.data_ptr(), npasses, 0)
+        torch.cuda.synchronize()
+        got = out.real.long() + 4096 * out.imag.long()  # got[position] = natural index
+        if npasses == -1:
+            assert torch.equal(got, i)
+        else:
+            xx, yy, zz = i % n, (i // n) % n, i // (n * n)
+            pos = zz * n * n + (xx // 4) * 4 * n + 4 * yy + xx % 4
+            assert torch.equal(got[pos], i)
+        del got
+    plan.close()
