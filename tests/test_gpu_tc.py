@@ -41,8 +41,8 @@ def _err(x, got, shape, batch, direction):
 def test_tc_radix16_stages(shape, batch, direction, mode):
     x, got, plan = run_plan(shape, batch, P, direction, seed=3, dtype=TC, tc_stages=mode)
     kinds = [p["kind"] for p in plan.describe()["passes"]]
-    # mode 1 leaves lines without a radix-16 stage in shared memory on the FP32 kernels
-    assert any(k.endswith("_tc") for k in kinds) or mode == 1
+    # modes 1 and 3 leave lines without a radix-16 stage in shared memory on the FP32 kernels
+    assert any(k.endswith("_tc") for k in kinds) or mode in (1, 3)
     if 1024 in shape[1:] or 512 in shape[1:]:
         assert "line_strided_stream_tc" in kinds
     rel, mx = _err(x, got, shape, batch, direction)
