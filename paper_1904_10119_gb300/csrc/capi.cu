@@ -313,8 +313,7 @@ static int build_launches(fft3_plan_s *P)
         }
         case PK_TCX:
         case PK_TCS:
-        case PK_TCB:
-            L.func = tc32_kernel(p.kind == PK_TCX ? 0 : p.kind == PK_TCS ? 1 : 2);
+            L.func = tc32_kernel(p.kind == PK_TCX ? 0 : 1);
             L.tc32 = p.kind == PK_TCS ? 2 : 1;
             break;
         case PK_JTC:

@@ -11,8 +11,8 @@ struct PassGeom {
     int64_t C, A, B;
     int64_t ij, ic, ia, ib;
     int64_t ok, oc, oa, ob;
-    // 0: output element k of a line at k*ok; > 0: at (k/4)*oblk + (k%4)*ok
-    // (a line stored in blocks of 4, as the 4-column blocked layouts need)
+    // 0: output element k of a line at k*ok; > 0: at (k/16)*oblk + (k%16)*ok
+    // (a line stored in blocks of 16, as the 16-column blocked layouts need)
     int64_t oblk;
 };
 

@@ -117,7 +117,7 @@ __global__ void k_probe_pass(PassArgs a)
         const int64_t c = r % a.g.C;
         r /= a.g.C;
         const int64_t aa = r % a.g.A, b = r / a.g.A;
-        const int64_t jo = a.g.oblk ? (j >> 2) * a.g.oblk + (j & 3) * a.g.ok : j * a.g.ok;
+        const int64_t jo = a.g.oblk ? (j >> 4) * a.g.oblk + (j & 15) * a.g.ok : j * a.g.ok;
         a.out[jo + c * a.g.oc + aa * a.g.oa + b * a.g.ob] = a.in[j * a.g.ij + c * a.g.ic + aa * a.g.ia + b * a.g.ib];
     }
 }

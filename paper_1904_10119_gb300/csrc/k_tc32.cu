@@ -32,16 +32,18 @@
 // reads its row of D back with tcgen05.ld.  B (DFT_32 high and low parts)
 // sits in shared memory with the 128-byte swizzle, shared by the groups.
 //
-// Tiles arrive by TMA into the group's landing buffer (contiguous lines, and
-// the columns of a 4-column blocked layout: one bulk copy of 32 KB; strided
-// columns: four 4-column x 256-row boxes of a 4D tensor map).  Once its inputs are in registers the landing buffer holds the
+// Tiles arrive by TMA into the group's landing buffer (contiguous lines: one
+// bulk copy of 32 KB; strided columns: four 4-column x 256-row boxes of a 4D
+// tensor map).  The four groups of a block take the four adjacent 4-column
+// tiles of a 16-column block, so between them they read and write whole
+// 128-byte rows.  Once its inputs are in registers the landing buffer holds the
 // tile's transposition (III) in a padded layout, and once stage (IV) has read
 // that back it is refilled with the group's next tile, whose load overlaps the
 // stage-(IV) MMAs and the output stores.
 //
 // Thread roles (t = row within the group, tile lines/columns l < 4):
 //   contiguous lines (MODE 0): row t = 32 l + j2 (stage I), 32 l + k1 (IV)
-//   columns (MODES 1, 2):      row t = 4 j2 + l (stage I), 4 k1 + l (IV)
+//   strided columns (MODE 1):  row t = 4 j2 + l (stage I), 4 k1 + l (IV)
 // so every warp's shared-memory accesses cover 32 consecutive complex values
 // or hit distinct banks through the padding.
 #include <cuda_bf16.h>
@@ -142,8 +144,7 @@ __device__ __forceinline__ bool group_or(int g, bool pred)
 }
 
 // MODE 0: contiguous lines, tiles loaded as one bulk copy; 1: strided columns,
-// tiles loaded through the 4D tensor map; 2: columns of a 4-column blocked
-// layout (element j of column c at 4 j + c), tiles loaded as one bulk copy.
+// tiles loaded through the 4D tensor map.
 template <int MODE>
 __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32(PassArgs a, const __grid_constant__ CUtensorMap tin)
 {
@@ -198,11 +199,6 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32(PassArgs a, const __gr
             const float2 *src = a.in + id.c0 * a.g.ic + id.a * a.g.ia + id.b * a.g.ib;
             mbar_expect_tx(&full[g], (uint32_t)nval * kN * 8u);
             bulk_load(land, src, (uint32_t)nval * kN * 8u, &full[g], pol);
-        } else if constexpr (MODE == 2) {
-            // the tile's 4 columns x 1024 rows are one contiguous block
-            const float2 *src = a.in + id.a * a.g.ia + id.b * a.g.ib;
-            mbar_expect_tx(&full[g], kTileBytes);
-            bulk_load(land, src, kTileBytes, &full[g], pol);
         } else {
             mbar_expect_tx(&full[g], kTileBytes);
 #pragma unroll
@@ -313,10 +309,10 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32(PassArgs a, const __gr
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, kLpt);
         const int64_t c = id.c0 + l2;
         const bool valid = !late2 && c < a.g.C;
-        // element k = k1 + 32 k2 at k*ok, or blocked by 4 at (k/4)*oblk + (k%4)*ok
+        // element k = k1 + 32 k2 at k*ok, or blocked by 16 at (k/16)*oblk + (k%16)*ok
         float2 *op = a.out + c * a.g.oc + id.a * a.g.oa + id.b * a.g.ob +
-                     (a.g.oblk ? (int64_t)(k1 >> 2) * a.g.oblk + (k1 & 3) * a.g.ok : (int64_t)k1 * a.g.ok);
-        const int64_t ostep = a.g.oblk ? 8 * a.g.oblk : 32 * a.g.ok;
+                     (a.g.oblk ? (int64_t)(k1 >> 4) * a.g.oblk + (k1 & 15) * a.g.ok : (int64_t)k1 * a.g.ok);
+        const int64_t ostep = a.g.oblk ? 2 * a.g.oblk : 32 * a.g.ok;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             uint32_t d[32];
@@ -352,9 +348,6 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32(PassArgs a, const __gr
         tmem_dealloc(s_tmem, 512);
 }
 
-const void *tc32_kernel(int mode)
-{
-    return mode == 0 ? (const void *)&k_tc32<0> : mode == 1 ? (const void *)&k_tc32<1> : (const void *)&k_tc32<2>;
-}
+const void *tc32_kernel(int mode) { return mode == 0 ? (const void *)&k_tc32<0> : (const void *)&k_tc32<1>; }
 
 } // namespace fft3

@@ -1041,26 +1041,25 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
     } else if (dtype == FFT3_C64_SPLITBF16_TC && decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED &&
                s.opts.tc_stages == 0 && s.opts.tile_lines == 0 && n0 == 1024 && n1 == 1024 && n2 == 1024 &&
                batch == 1) {
-        // tcgen05 radix-32 passes with 4-column blocked intermediates, so that every
-        // pass loads contiguous 32 KB tiles (4 lines or 4 columns of 1024 points):
-        //   x: natural -> [z][x/4][y][x%4]  (out),
-        //   y: [z][x/4][y][x%4] -> [x/4][y][z][x%4]  (workspace),
-        //   z: [x/4][y][z][x%4] -> natural  (out).
-        // Each store writes 32-byte pieces; the four groups of a block take adjacent
-        // tiles, so the pieces of one 128-byte row are written together.
+        // tcgen05 radix-32 passes (tiles of 4 lines or 4 columns; the four groups of a
+        // block take the four 4-column tiles of one 16-column block) with 16-column
+        // blocked intermediates, so that every load and store moves whole 128-byte rows:
+        //   x: natural -> [z][x/16][y][x%16]  (out; 4 lines write 512 contiguous bytes per block),
+        //   y: [z][x/16][y][x%16] -> [x/16][z][y][x%16]  (workspace; contiguous 128 KB blocks in and out),
+        //   z: [x/16][z][y][x%16] -> natural  (out; 128-byte rows as the FP32 blocked z pass).
         const int64_t X = n0, Y = n1, Z = n2;
         PassGeom gx{}, gy{}, gz{};
         gx.C = Y; gx.A = Z; gx.B = 1;
         gx.ij = 1; gx.ic = X; gx.ia = X * Y; gx.ib = X * Y * Z;
-        gx.ok = 1; gx.oblk = 4 * Y; gx.oc = 4; gx.oa = X * Y; gx.ob = X * Y * Z;
-        gy.C = 4; gy.A = X / 4; gy.B = Z;
-        gy.ij = 4; gy.ic = 1; gy.ia = 4 * Y; gy.ib = X * Y;
-        gy.ok = 4 * Z; gy.oc = 1; gy.oa = 4 * Y * Z; gy.ob = 4;
-        gz.C = 4; gz.A = X / 4; gz.B = Y;
-        gz.ij = 4; gz.ic = 1; gz.ia = 4 * Y * Z; gz.ib = 4 * Z;
-        gz.ok = X * Y; gz.oc = 1; gz.oa = 4; gz.ob = X;
+        gx.ok = 1; gx.oblk = 16 * Y; gx.oc = 16; gx.oa = X * Y; gx.ob = X * Y * Z;
+        gy.C = 16; gy.A = X / 16; gy.B = Z;
+        gy.ij = 16; gy.ic = 1; gy.ia = 16 * Y; gy.ib = X * Y;
+        gy.ok = 16; gy.oc = 1; gy.oa = 16 * Y * Z; gy.ob = 16 * Y;
+        gz.C = 16; gz.A = Y; gz.B = X / 16;
+        gz.ij = 16 * Y; gz.ic = 1; gz.ia = 16; gz.ib = 16 * Y * Z;
+        gz.ok = X * Y; gz.oc = 1; gz.oa = X; gz.ob = 16;
         const PassGeom gs[3] = {gx, gy, gz};
-        const int kinds[3] = {PK_TCX, PK_TCB, PK_TCB};
+        const int kinds[3] = {PK_TCX, PK_TCS, PK_TCS};
         const int bufs[3][2] = {{BUF_IN, BUF_OUT}, {BUF_OUT, BUF_WS}, {BUF_WS, BUF_OUT}};
         for (int d = 0; d < 3; ++d) {
             PassPlan p;
@@ -1223,8 +1222,8 @@ static const char *kind_name(int k)
                                   "line_strided_tma", "line_contig_tc", "line_strided_tc",
                                   "volumetric_split_fixed", "line_strided_stream", "slab_l2_blocked",
                                   "line_runtime_fp64", "line_contig_fp64", "line_strided_fp64",
-                                  "line_contig_r32_tc", "line_strided_r32_tc", "line_blocked4_r32_tc"};
-    return (k >= 0 && k <= 20) ? names[k] : "?";
+                                  "line_contig_r32_tc", "line_strided_r32_tc"};
+    return (k >= 0 && k <= 19) ? names[k] : "?";
 }
 static const char *buf_name(int b)
 {
@@ -1278,7 +1277,7 @@ std::string Schedule::json() const
             o << ",\"p\":" << p.p;
         if (p.kind == PK_JTC || p.kind == PK_CTC || (p.kind == PK_CSTREAM && p.tc_mode >= 0))
             o << ",\"tc_stages\":" << p.tc_mode << ",\"mma\":\"mma.sync.m16n8k16\"";
-        if (p.kind == PK_TCX || p.kind == PK_TCS || p.kind == PK_TCB)
+        if (p.kind == PK_TCX || p.kind == PK_TCS)
             o << ",\"mma\":\"tcgen05.mma m128n64k16\"";
         if (p.kind == PK_CSTREAM) {
             int cnt = 0;

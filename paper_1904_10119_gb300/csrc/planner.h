@@ -32,7 +32,6 @@ enum PassKind {
     PK_C64 = 17,     // complex128: fixed plan, strided columns (k_pass_c64)
     PK_TCX = 18,     // split-BF16 radix-32 tcgen05 GEMM stages, contiguous 1024-point lines (k_tc32.cu)
     PK_TCS = 19,     // split-BF16 radix-32 tcgen05 GEMM stages, strided 1024-point columns (k_tc32.cu)
-    PK_TCB = 20,     // the same on the columns of a 4-column blocked layout, contiguous tiles (k_tc32.cu)
 };
 
 enum BufId { BUF_IN = 0, BUF_OUT = 1, BUF_WS = 2 };

@@ -111,8 +111,7 @@ constexpr int kTc32Threads = 128 * kTc32Groups;
 constexpr int kTc32Lpt = 4;
 constexpr int kTc32LandBytes = kTc32Lpt * 32 * 34 * 8;
 constexpr int kTc32SmemBytes = 2 * 64 * 128 + 1024 * 8 + kTc32Groups * kTc32LandBytes + 1024;
-// mode 0: contiguous lines (bulk copies), 1: strided columns (4D tensor map),
-// 2: columns of a 4-column blocked layout (bulk copies)
+// mode 0: contiguous lines (bulk copies), 1: strided columns (4D tensor map)
 const void *tc32_kernel(int mode);
 
 struct VolcKernel {

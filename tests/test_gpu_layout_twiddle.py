@@ -134,14 +134,14 @@ def test_bounded_wait_expires_and_reports_timeout(mode):
     assert_parity(x, got, shape)
 
 
-def test_tcgen05_blocked4_probe_is_identity_at_1024cubed():
-    """The 1024^3 split-BF16 schedule (4-column blocked intermediates, line
+def test_tcgen05_blocked_probe_is_identity_at_1024cubed():
+    """The 1024^3 split-BF16 schedule (16-column blocked intermediates, line
     transforms replaced by the identity): after all three passes every element
     is back at its natural position, bit-exact; after the x pass element
-    (x, y, z) sits at z*X*Y + (x/4)*4Y + 4y + x%4."""
+    (x, y, z) sits at z*X*Y + (x/16)*16Y + 16y + x%16."""
     n = 1024
     plan = fft3.Plan(n, n, n, 1, decomposition=fft3.FFT3_AUTO, dtype=fft3.FFT3_C64_SPLITBF16_TC)
-    assert [p["kind"] for p in plan.describe()["passes"]][1:] == ["line_blocked4_r32_tc"] * 2
+    assert [p["kind"] for p in plan.describe()["passes"]][1:] == ["line_strided_r32_tc"] * 2
     N = n ** 3
     i = torch.arange(N, device="cuda", dtype=torch.int64)
     x = torch.complex((i % 4096).float(), (i // 4096).float())
@@ -154,7 +154,7 @@ def test_tcgen05_blocked4_probe_is_identity_at_1024cubed():
             assert torch.equal(got, i)
         else:
             xx, yy, zz = i % n, (i // n) % n, i // (n * n)
-            pos = zz * n * n + (xx // 4) * 4 * n + 4 * yy + xx % 4
+            pos = zz * n * n + (xx // 16) * 16 * n + 16 * yy + xx % 16
             assert torch.equal(got[pos], i)
         del got
     plan.close()
