@@ -145,9 +145,10 @@ static int encode_blocked_map(CUtensorMap *m, const void *base, int64_t elems, i
 }
 
 // Input map of a streamed strided pass: the array as {C, Q, M, A, B} with
-// line element j = Q*j' + q, so one box {LPT, 1, M, 1, 1} is the decimated
-// sub-line q of a tile.
-static int encode_stream_map(CUtensorMap *m, const void *base, const PassGeom &g, int n, int q, int lpt)
+// line element j = Q*j' + q, so one box {LPT, QBOX, M, 1, 1} holds QBOX
+// consecutive decimated sub-lines q of a tile.
+static int encode_stream_map(CUtensorMap *m, const void *base, const PassGeom &g, int n, int q, int lpt,
+                             int qbox = 1)
 {
     auto fn = encode_fn();
     if (!fn)
@@ -158,7 +159,7 @@ static int encode_stream_map(CUtensorMap *m, const void *base, const PassGeom &g
     cuuint64_t dims[5] = {(cuuint64_t)g.C, (cuuint64_t)q, (cuuint64_t)mm, (cuuint64_t)g.A, (cuuint64_t)g.B};
     cuuint64_t strides[4] = {(cuuint64_t)g.ij * 8, (cuuint64_t)g.ij * q * 8, (cuuint64_t)g.ia * 8,
                              (cuuint64_t)(g.B > 1 ? g.ib : g.ia * g.A) * 8};
-    cuuint32_t box[5] = {(cuuint32_t)lpt, 1, (cuuint32_t)mm, 1, 1};
+    cuuint32_t box[5] = {(cuuint32_t)lpt, (cuuint32_t)qbox, (cuuint32_t)mm, 1, 1};
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, const_cast<void *>(base), dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -361,9 +362,10 @@ static int build_launches(fft3_plan_s *P)
             P->counters_bytes = std::max(P->counters_bytes,
                                          (size_t)(1 + p.g.A * p.g.B) * sizeof(int));
         } else if (L.tc32) {
-            // one block per SM, each running kTc32Groups streams of tiles
-            rc = occupancy_grid(L.func, L.block.x, L.smem, (p.ntiles + kTc32Groups - 1) / kTc32Groups, P->device,
-                                &L.grid);
+            // one block per SM (contiguous lines: each running kTc32Groups streams of tiles)
+            rc = occupancy_grid(L.func, L.block.x, L.smem,
+                                p.kind == PK_TCX ? (p.ntiles + kTc32Groups - 1) / kTc32Groups : p.ntiles,
+                                P->device, &L.grid);
             if (rc)
                 return rc;
         } else {
@@ -600,17 +602,16 @@ static int launch_one(fft3_plan_s *P, const Launch &L, const void *func, PassArg
         return FFT3_OK;
     }
     if (L.tc32) {
-        CUtensorMap tin;
-        memset(&tin, 0, sizeof(tin));
         if ((uintptr_t)a.in & 15)
             return fail(FFT3_ERR_INVALID_ARG, "this plan moves tiles with TMA: buffers must be 16-byte aligned");
-        if (L.tc32 == 2) {
-            int rc = encode_pass_map(&tin, a.in, a.g, L.probe_n, kTc32Lpt, false);
+        CUtensorMap tin;
+        void *params[2] = {&a, &tin};
+        if (L.tc32 == 2) { // 16 columns x 8 decimated sub-sequences x 32 values per box
+            int rc = encode_stream_map(&tin, a.in, a.g, L.probe_n, 32, kTcsLpt, 8);
             if (rc)
                 return rc;
         }
-        void *params[2] = {&a, &tin};
-        CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params));
+        CUDA_TRY(cudaLaunchKernelExC(&cfg, func, params)); // the contiguous-line kernel takes only `a`
         return FFT3_OK;
     }
     if (L.slab_map) {

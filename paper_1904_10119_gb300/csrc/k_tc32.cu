@@ -70,6 +70,8 @@ constexpr int kTwOff = 2 * kBBytes;                     // w_1024^{j2 k1}, [k1][
 constexpr int kLandOff = kTwOff + kN * 8;
 static_assert(kLandOff + kTc32Groups * kLandBytes + 1024 == kTc32SmemBytes,
               "dynamic shared memory (+ alignment slack)");
+static_assert(kLandOff + kTcsQuarters * kTcsQuarterBytes + 1024 == kTcsSmemBytes && kTcsSmemBytes <= 227 * 1024,
+              "dynamic shared memory of the strided kernel (+ alignment slack)");
 
 // w = w_32^m for the DFT_32 operand (FP32 values of the FP64 generator) ->
 // B_hi, B_lo in the 128-byte-swizzled K-major layout.
@@ -143,12 +145,11 @@ __device__ __forceinline__ bool group_or(int g, bool pred)
     }
 }
 
-// MODE 0: contiguous lines, tiles loaded as one bulk copy; 1: strided columns,
-// tiles loaded through the 4D tensor map.
-template <int MODE>
-__global__ void __launch_bounds__(kTc32Threads, 1) k_tc32(PassArgs a, const __grid_constant__ CUtensorMap tin)
+// Contiguous lines: four independent groups, tiles of 4 lines loaded as one
+// bulk copy each.
+__global__ void __launch_bounds__(kTc32Threads, 1) k_tc32x(PassArgs a)
 {
-    constexpr bool LINES = MODE == 0;
+    constexpr bool LINES = true;
     extern __shared__ uint8_t dsm_raw[];
     __shared__ __align__(8) uint64_t full[kTc32Groups];
     __shared__ __align__(8) uint64_t mbar[kTc32Groups];
@@ -183,8 +184,6 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32(PassArgs a, const __gr
     const uint32_t t_a = s_tmem + ((uint32_t)(32 * gw) << 16) + 128 * g, t_d = t_a + 64;
     const uint32_t s_bhi = smem_u32(bhi), s_blo = smem_u32(blo);
     const uint64_t pol = l2_evict_first_policy();
-    // the groups of a block take adjacent tiles (the 4-column tiles of one
-    // 128-byte row segment of a strided pass are fetched by one SM together)
     const int64_t stream = (int64_t)blockIdx.x * kTc32Groups + g, nstreams = (int64_t)gridDim.x * kTc32Groups;
 
     // Load of the group's k-th tile into its landing buffer (the group's thread 0).
@@ -193,18 +192,11 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32(PassArgs a, const __gr
         if (tile >= a.ntiles)
             return;
         const TileId id = decode_tile(tile, a.tiles_c, a.g.A, kLpt);
-        if constexpr (MODE == 0) {
-            // lines beyond the array's last one are not loaded (their rows are never stored)
-            const int nval = (int)min((int64_t)kLpt, a.g.C - id.c0);
-            const float2 *src = a.in + id.c0 * a.g.ic + id.a * a.g.ia + id.b * a.g.ib;
-            mbar_expect_tx(&full[g], (uint32_t)nval * kN * 8u);
-            bulk_load(land, src, (uint32_t)nval * kN * 8u, &full[g], pol);
-        } else {
-            mbar_expect_tx(&full[g], kTileBytes);
-#pragma unroll
-            for (int q = 0; q < kN / 256; ++q)
-                tma_load_4d(land + q * 256 * kLpt * 8, &tin, (int)id.c0, q * 256, (int)id.a, (int)id.b, &full[g]);
-        }
+        // lines beyond the array's last one are not loaded (their rows are never stored)
+        const int nval = (int)min((int64_t)kLpt, a.g.C - id.c0);
+        const float2 *src = a.in + id.c0 * a.g.ic + id.a * a.g.ia + id.b * a.g.ib;
+        mbar_expect_tx(&full[g], (uint32_t)nval * kN * 8u);
+        bulk_load(land, src, (uint32_t)nval * kN * 8u, &full[g], pol);
     };
     int64_t issued = -1; // (the group's thread 0) the last k whose load was issued
     if (gt == 0) {
@@ -348,6 +340,198 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32(PassArgs a, const __gr
         tmem_dealloc(s_tmem, 512);
 }
 
-const void *tc32_kernel(int mode) { return mode == 0 ? (const void *)&k_tc32<0> : (const void *)&k_tc32<1>; }
+// ---------------------------------------------------------------------------
+// Strided columns (y and z lines): one block transforms one tile of 16
+// adjacent columns at a time, loaded as four 32 KB quarters through a 5D
+// tensor map {C, 32, 32, A, B} of the decimated sub-sequences x[32 j1 + j2]
+// (box: 16 columns x 8 values of j2 x 32 values of j1, whole 128-byte rows).
+//   stage (I):  group g transforms the sub-sequences j2 in [8g, 8g + 8) of the
+//               16 columns (row t = (q, c), j2 = 8g + q, q = t / 16, c = t % 16)
+//               and writes its twiddled outputs X1[c][j2][k1] back into its
+//               own quarter, in place (slot of j1 := k1);
+//   block barrier;
+//   stage (IV): group g transforms the outputs k1 in [8g, 8g + 8) (row t =
+//               (kk, c), k1 = 8g + kk), reading X1[c][j2][k1] for every j2
+//               from the four quarters, and stores rows k1 + 32 k2: each warp
+//               writes two whole 128-byte rows per instruction.
+// Six quarter buffers rotate: quarter e of the block's i-th tile sits in
+// buffer (4i + e) % 6, so the first two quarters of the next tile load while
+// this tile is transformed, and the four buffers of a tile are refilled once
+// every group has read them in stage (IV).
+__global__ void __launch_bounds__(kTc32Threads, 1) k_tc32s(PassArgs a, const __grid_constant__ CUtensorMap tin)
+{
+    constexpr int NQ = kTcsQuarters;
+    constexpr uint32_t QBYTES = kTcsQuarterBytes;
+    extern __shared__ uint8_t dsm_raw[];
+    __shared__ __align__(8) uint64_t full[NQ];
+    __shared__ __align__(8) uint64_t mbar[kTc32Groups];
+    __shared__ uint32_t s_tmem;
+    uint8_t *dsm = (uint8_t *)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *bhi = dsm, *blo = dsm + kBBytes;
+    float2 *tw = (float2 *)(dsm + kTwOff);
+    float2 *qbuf = (float2 *)(dsm + kLandOff); // NQ quarters of 4096 values
+    const int tid = threadIdx.x, g = tid >> 7, gt = tid & 127, warp = tid >> 5;
+    const int gw = warp & 3;
+    const bool conj = a.conj != 0;
+
+    build_dft32_operand(bhi, blo, a.tw + a.tw_split_off);
+    for (int i = tid; i < kN; i += blockDim.x)
+        tw[i] = a.tw[i];
+    if (tid == 0) {
+        for (int i = 0; i < NQ; ++i)
+            mbar_init(&full[i], 1);
+        for (int i = 0; i < kTc32Groups; ++i)
+            mbar_init(&mbar[i], 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, 512);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t t_a = s_tmem + ((uint32_t)(32 * gw) << 16) + 128 * g, t_d = t_a + 64;
+    const uint32_t s_bhi = smem_u32(bhi), s_blo = smem_u32(blo);
+
+    // Quarter L = 4 i + e of the block's tile sequence (thread 0 only).
+    auto issue = [&](int64_t L) {
+        const int64_t tile = blockIdx.x + (L >> 2) * (int64_t)gridDim.x;
+        if (tile >= a.ntiles)
+            return;
+        const int b = (int)(L % NQ);
+        const TileId id = decode_tile(tile, a.tiles_c, a.g.A, kTcsLpt);
+        mbar_expect_tx(&full[b], QBYTES);
+        tma_load_5d(qbuf + b * 4096, &tin, (int)id.c0, 8 * (int)(L & 3), 0, (int)id.a, (int)id.b, &full[b]);
+    };
+    int64_t issued = -1; // (thread 0) the last quarter issued
+    if (tid == 0) {
+        for (int64_t L = 0; L < NQ; ++L)
+            issue(L);
+        issued = NQ - 1;
+    }
+    const int q = gt >> 4, c = gt & 15;
+    const int j2 = 8 * g + q, k1 = 8 * g + q; // stage (I) / stage (IV) index of this row
+    uint32_t mph = 0;
+    bool failed = false;
+    int64_t i = 0;
+    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++i) {
+        const int64_t L = 4 * i + g;
+        const int b = (int)(L % NQ);
+        float2 *mine = qbuf + b * 4096;
+        const bool late = !mbar_wait(&full[b], (uint32_t)((L / NQ) & 1), a.wait_budget);
+        // ---- stage (I): element (c, q, j1) of the quarter at (j1 * 8 + q) * 16 + c
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float2 v[16];
+#pragma unroll
+            for (int ii = 0; ii < 16; ++ii) {
+                const float2 e = mine[((16 * h + ii) * 8 + q) * 16 + c];
+                v[ii] = conj ? cconj(e) : e;
+            }
+            store_a16(t_a, 16 * h, v);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        group_or(g, false);
+        if (gt == 0) {
+            tc_fence_after();
+            issue_stage_mmas(t_a, t_d, s_bhi, s_blo);
+            mma_commit(&mbar[g]);
+        }
+        const bool late1 = !mbar_wait(&mbar[g], mph, a.wait_budget);
+        mph ^= 1;
+        tc_fence_after();
+        // ---- (II) twiddle w_1024^{j2 k1}, (III) in place: X1[c][j2][k1] at (k1 * 8 + q) * 16 + c
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t d[32];
+            tmem_ld16(t_d + 32 * h, *(uint32_t(*)[16])(d));
+            tmem_ld16(t_d + 32 * h + 16, *(uint32_t(*)[16])(d + 16));
+            tmem_wait_ld();
+#pragma unroll
+            for (int ii = 0; ii < 16; ++ii) {
+                const int kk1 = 16 * h + ii;
+                mine[(kk1 * 8 + q) * 16 + c] =
+                    cmul(make_float2(__uint_as_float(d[2 * ii]), __uint_as_float(d[2 * ii + 1])), tw[kk1 * 32 + j2]);
+            }
+        }
+        tc_fence_before();
+        if (cta_any(late || late1)) { // every quarter of the tile is transposed
+            failed = true;
+            break;
+        }
+        // ---- stage (IV): X1[c][j2][k1] for every j2, from quarter j2 / 8 of this tile
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float2 v[16];
+#pragma unroll
+            for (int ii = 0; ii < 16; ++ii) {
+                const int jj = 16 * h + ii;
+                const float2 *src = qbuf + (int)((4 * i + (jj >> 3)) % NQ) * 4096;
+                v[ii] = src[(k1 * 8 + (jj & 7)) * 16 + c];
+            }
+            store_a16(t_a, 16 * h, v);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        fence_proxy_async_smem(); // this thread's accesses to the quarters, before their refill
+        __syncthreads();          // every quarter of the tile is read out
+        if (tid == 0) {
+            for (int64_t Ln = 4 * i + NQ; Ln < 4 * i + NQ + 4; ++Ln)
+                issue(Ln);
+            issued = 4 * i + NQ + 3;
+        }
+        if (gt == 0) {
+            tc_fence_after();
+            issue_stage_mmas(t_a, t_d, s_bhi, s_blo);
+            mma_commit(&mbar[g]);
+        }
+        const bool late2 = !mbar_wait(&mbar[g], mph, a.wait_budget);
+        mph ^= 1;
+        tc_fence_after();
+        // ---- outputs X[k1 + 32 k2] of column c
+        const TileId id = decode_tile(tile, a.tiles_c, a.g.A, kTcsLpt);
+        const int64_t col = id.c0 + c;
+        const bool valid = !late2 && col < a.g.C;
+        float2 *op = a.out + col * a.g.oc + id.a * a.g.oa + id.b * a.g.ob + (int64_t)k1 * a.g.ok;
+        const int64_t ostep = 32 * a.g.ok;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t d[32];
+            tmem_ld16(t_d + 32 * h, *(uint32_t(*)[16])(d));
+            tmem_ld16(t_d + 32 * h + 16, *(uint32_t(*)[16])(d + 16));
+            tmem_wait_ld();
+            if (valid) {
+#pragma unroll
+                for (int ii = 0; ii < 16; ++ii) {
+                    const float2 y = make_float2(__uint_as_float(d[2 * ii]), __uint_as_float(d[2 * ii + 1]));
+                    op[(16 * h + ii) * ostep] = conj ? cconj(y) : y;
+                }
+            }
+        }
+        tc_fence_before();
+        if (cta_any(late2)) {
+            failed = true;
+            break;
+        }
+    }
+    if (failed && tid == 0) {
+        // record the timeout and wait (bounded) for the quarters still in flight
+        atomicOr(a.err, kErrWaitTimeout);
+        for (int64_t L = 4 * i; L <= issued; ++L)
+            if (blockIdx.x + (L >> 2) * (int64_t)gridDim.x < a.ntiles &&
+                !mbar_wait(&full[L % NQ], (uint32_t)((L / NQ) & 1), a.wait_budget))
+                break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        tmem_dealloc(s_tmem, 512);
+}
+
+const void *tc32_kernel(int mode) { return mode == 0 ? (const void *)&k_tc32x : (const void *)&k_tc32s; }
 
 } // namespace fft3

@@ -332,9 +332,9 @@ static void set_cstream(PassPlan *p, int ci)
 static void set_tc32(Schedule *s, PassPlan *p, int kind)
 {
     p->kind = kind;
-    p->lpt = kTc32Lpt;
+    p->lpt = kind == PK_TCX ? kTc32Lpt : kTcsLpt;
     p->threads = kTc32Threads;
-    p->smem_bytes = kTc32SmemBytes;
+    p->smem_bytes = kind == PK_TCX ? kTc32SmemBytes : kTcsSmemBytes;
     p->tc_mode = 0;
     p->line = LineChoice{};
     p->line.n = 1024;
@@ -407,7 +407,8 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
     if (s->dtype == FFT3_C64_SPLITBF16_TC && !rotate && n == 1024 && tc_opt == 0 && s->opts.tile_lines == 0) {
         // both 32-point stages of the line as split-BF16 GEMMs on the tcgen05 tensor cores
         // (k_tc32.cu): contiguous lines whose 4-line tiles are one bulk copy, or strided
-        // columns the 4D tensor map walks (16-byte multiples for every stride)
+        // columns in 16-column tiles the 5D tensor map walks (16-byte multiples for
+        // every stride)
         const bool al = (g.ia * 8) % 16 == 0 && (g.B <= 1 || (g.ib * 8) % 16 == 0);
         const bool lines = contig_in && g.ic == n && al;
         const bool cols = strided_in && (g.ij * 8) % 16 == 0 && al && g.C <= 0x7fffffff && g.A <= 0x7fffffff &&
@@ -1037,39 +1038,6 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
         }
         if (rc)
             return rc;
-        s.need_ws = true;
-    } else if (dtype == FFT3_C64_SPLITBF16_TC && decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED &&
-               s.opts.tc_stages == 0 && s.opts.tile_lines == 0 && n0 == 1024 && n1 == 1024 && n2 == 1024 &&
-               batch == 1) {
-        // tcgen05 radix-32 passes (tiles of 4 lines or 4 columns; the four groups of a
-        // block take the four 4-column tiles of one 16-column block) with 16-column
-        // blocked intermediates, so that every load and store moves whole 128-byte rows:
-        //   x: natural -> [z][x/16][y][x%16]  (out; 4 lines write 512 contiguous bytes per block),
-        //   y: [z][x/16][y][x%16] -> [x/16][z][y][x%16]  (workspace; contiguous 128 KB blocks in and out),
-        //   z: [x/16][z][y][x%16] -> natural  (out; 128-byte rows as the FP32 blocked z pass).
-        const int64_t X = n0, Y = n1, Z = n2;
-        PassGeom gx{}, gy{}, gz{};
-        gx.C = Y; gx.A = Z; gx.B = 1;
-        gx.ij = 1; gx.ic = X; gx.ia = X * Y; gx.ib = X * Y * Z;
-        gx.ok = 1; gx.oblk = 16 * Y; gx.oc = 16; gx.oa = X * Y; gx.ob = X * Y * Z;
-        gy.C = 16; gy.A = X / 16; gy.B = Z;
-        gy.ij = 16; gy.ic = 1; gy.ia = 16 * Y; gy.ib = X * Y;
-        gy.ok = 16; gy.oc = 1; gy.oa = 16 * Y * Z; gy.ob = 16 * Y;
-        gz.C = 16; gz.A = Y; gz.B = X / 16;
-        gz.ij = 16 * Y; gz.ic = 1; gz.ia = 16; gz.ib = 16 * Y * Z;
-        gz.ok = X * Y; gz.oc = 1; gz.oa = X; gz.ob = 16;
-        const PassGeom gs[3] = {gx, gy, gz};
-        const int kinds[3] = {PK_TCX, PK_TCS, PK_TCS};
-        const int bufs[3][2] = {{BUF_IN, BUF_OUT}, {BUF_OUT, BUF_WS}, {BUF_WS, BUF_OUT}};
-        for (int d = 0; d < 3; ++d) {
-            PassPlan p;
-            p.dim = d;
-            p.g = gs[d];
-            p.src = bufs[d][0];
-            p.dst = bufs[d][1];
-            set_tc32(&s, &p, kinds[d]);
-            s.passes.push_back(p);
-        }
         s.need_ws = true;
     } else if (decomp == FFT3_PENCIL3 && s.opts.variant == FFT3_PPP_BLOCKED && blocked_fits()) {
         rc = emit_blocked();

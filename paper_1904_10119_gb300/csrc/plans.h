@@ -111,6 +111,12 @@ constexpr int kTc32Threads = 128 * kTc32Groups;
 constexpr int kTc32Lpt = 4;
 constexpr int kTc32LandBytes = kTc32Lpt * 32 * 34 * 8;
 constexpr int kTc32SmemBytes = 2 * 64 * 128 + 1024 * 8 + kTc32Groups * kTc32LandBytes + 1024;
+// Strided columns (k_tc32s): tiles of 16 columns, six rotating quarter
+// buffers of 4096 values (16 columns x 8 x 32 decimated values).
+constexpr int kTcsLpt = 16;
+constexpr int kTcsQuarters = 6;
+constexpr int kTcsQuarterBytes = 4096 * 8;
+constexpr int kTcsSmemBytes = 2 * 64 * 128 + 1024 * 8 + kTcsQuarters * kTcsQuarterBytes + 1024;
 // mode 0: contiguous lines (bulk copies), 1: strided columns (4D tensor map)
 const void *tc32_kernel(int mode);
 

@@ -134,19 +134,20 @@ def test_bounded_wait_expires_and_reports_timeout(mode):
     assert_parity(x, got, shape)
 
 
-def test_tcgen05_blocked_probe_is_identity_at_1024cubed():
-    """The 1024^3 split-BF16 schedule (16-column blocked intermediates, line
-    transforms replaced by the identity): after all three passes every element
-    is back at its natural position, bit-exact; after the x pass element
-    (x, y, z) sits at z*X*Y + (x/16)*16Y + 16y + x%16."""
+def test_tcgen05_schedule_probe_is_identity_at_1024cubed():
+    """The 1024^3 split-BF16 schedule (tcgen05 passes on the blocked
+    intermediate [x/16][z][y][x%16], line transforms replaced by the identity):
+    after all three passes every element is back at its natural position,
+    bit-exact; after the y pass element (x, y, z) sits in the workspace at
+    (x/16)*16*Y*Z + z*16*Y + 16*y + x%16 (the probe copies it to `out`)."""
     n = 1024
     plan = fft3.Plan(n, n, n, 1, decomposition=fft3.FFT3_AUTO, dtype=fft3.FFT3_C64_SPLITBF16_TC)
-    assert [p["kind"] for p in plan.describe()["passes"]][1:] == ["line_strided_r32_tc"] * 2
+    assert [p["kind"] for p in plan.describe()["passes"]] == ["line_contig_r32_tc"] + ["line_strided_r32_tc"] * 2
     N = n ** 3
     i = torch.arange(N, device="cuda", dtype=torch.int64)
     x = torch.complex((i % 4096).float(), (i // 4096).float())
     out = torch.full_like(x, complex(-1.0, -1.0))
-    for npasses in (1, -1):
+    for npasses in (2, -1):
         fft3.fft3_plan_probe_layout(plan.handle, x.data_ptr(), out.data_ptr(), npasses, 0)
         torch.cuda.synchronize()
         got = out.real.long() + 4096 * out.imag.long()  # got[position] = natural index
@@ -154,7 +155,7 @@ def test_tcgen05_blocked_probe_is_identity_at_1024cubed():
             assert torch.equal(got, i)
         else:
             xx, yy, zz = i % n, (i // n) % n, i // (n * n)
-            pos = zz * n * n + (xx // 16) * 16 * n + 16 * yy + xx % 16
+            pos = (xx // 16) * 16 * n * n + zz * 16 * n + 16 * yy + xx % 16
             assert torch.equal(got[pos], i)
         del got
     plan.close()
