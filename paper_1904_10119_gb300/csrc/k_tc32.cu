@@ -41,11 +41,10 @@
 // that back it is refilled with the group's next tile, whose load overlaps the
 // stage-(IV) MMAs and the output stores.
 //
-// Thread roles (t = row within the group, tile lines/columns l < 4):
-//   contiguous lines (MODE 0): row t = 32 l + j2 (stage I), 32 l + k1 (IV)
-//   strided columns (MODE 1):  row t = 4 j2 + l (stage I), 4 k1 + l (IV)
-// so every warp's shared-memory accesses cover 32 consecutive complex values
-// or hit distinct banks through the padding.
+// Thread roles of the contiguous-line kernel (t = row within the group, tile
+// lines l < 4): row t = 32 l + j2 (stage I), 32 l + k1 (IV), so every warp's
+// shared-memory accesses cover 32 consecutive complex values or hit distinct
+// banks through the padding.
 #include <cuda_bf16.h>
 
 #include "pass_kernels.cuh"
@@ -59,12 +58,10 @@ namespace {
 constexpr int kN = 1024;
 constexpr int kLpt = kTc32Lpt;
 constexpr uint32_t kTileBytes = (uint32_t)kLpt * kN * 8u; // 32 KB
-constexpr int kPitchL = 34;                             // LINES: k1 pitch of the transposition (complex)
-constexpr int kLineT = 32 * kPitchL;                    // LINES: line pitch of the transposition
-constexpr int kPitchC = 132;                            // columns: k1 pitch of the transposition
+constexpr int kPitchL = 34;                             // k1 pitch of the transposition (complex)
+constexpr int kLineT = 32 * kPitchL;                    // line pitch of the transposition
 constexpr int kLandBytes = kTc32LandBytes;              // 34816 >= 32768
-static_assert(kLandBytes == kLpt * kLineT * 8 && 32 * kPitchC * 8 <= kLandBytes,
-              "both transpositions fit the landing buffer");
+static_assert(kLandBytes == kLpt * kLineT * 8, "the transposition fits the landing buffer");
 constexpr int kBBytes = 64 * 128;                       // one 64 x 64 BF16 operand
 constexpr int kTwOff = 2 * kBBytes;                     // w_1024^{j2 k1}, [k1][j2]
 constexpr int kLandOff = kTwOff + kN * 8;
@@ -74,13 +71,14 @@ static_assert(kLandOff + kTcsQuarters * kTcsQuarterBytes + 1024 == kTcsSmemBytes
               "dynamic shared memory of the strided kernel (+ alignment slack)");
 
 // w = w_32^m for the DFT_32 operand (FP32 values of the FP64 generator) ->
-// B_hi, B_lo in the 128-byte-swizzled K-major layout.
-__device__ __forceinline__ void build_dft32_operand(uint8_t *bhi, uint8_t *blo, const float2 *w32)
+// B_hi, B_lo in the 128-byte-swizzled K-major layout; the inverse transform
+// uses the conjugate roots (the same factorisation with w_n^-1).
+__device__ __forceinline__ void build_dft32_operand(uint8_t *bhi, uint8_t *blo, const float2 *w32, bool conj)
 {
     for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
         const int n = e >> 6, kk = e & 63;
         const int kp = n >> 1, cp = n & 1, j = kk >> 1, c = kk & 1;
-        const float2 w = w32[(kp * j) & 31];
+        const float2 w = conj ? cconj(w32[(kp * j) & 31]) : w32[(kp * j) & 31];
         const float v = (cp == c) ? w.x : (cp == 0 ? -w.y : w.y);
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -149,7 +147,6 @@ __device__ __forceinline__ bool group_or(int g, bool pred)
 // bulk copy each.
 __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32x(PassArgs a)
 {
-    constexpr bool LINES = true;
     extern __shared__ uint8_t dsm_raw[];
     __shared__ __align__(8) uint64_t full[kTc32Groups];
     __shared__ __align__(8) uint64_t mbar[kTc32Groups];
@@ -162,9 +159,9 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32x(PassArgs a)
     uint8_t *land = dsm + kLandOff + g * kLandBytes;
     const bool conj = a.conj != 0;
 
-    build_dft32_operand(bhi, blo, a.tw + a.tw_split_off);
+    build_dft32_operand(bhi, blo, a.tw + a.tw_split_off, conj);
     for (int i = tid; i < kN; i += blockDim.x)
-        tw[i] = a.tw[i];
+        tw[i] = conj ? cconj(a.tw[i]) : a.tw[i];
     if (tid == 0) {
         for (int i = 0; i < kTc32Groups; ++i) {
             mbar_init(&full[i], 1);
@@ -207,7 +204,7 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32x(PassArgs a)
     const float2 *lin = (const float2 *)land;
     float2 *tr = (float2 *)land;
     // stage (I) row gt = (line l1, sub-sequence j2); stage (IV) row gt = (line l2, output k1)
-    const int l1 = LINES ? gw : (gt & 3), j2 = LINES ? lane : (gt >> 2);
+    const int l1 = gw, j2 = lane;
     const int l2 = l1, k1 = j2;
     uint32_t mph = 0;
     bool failed = false;
@@ -225,8 +222,7 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32x(PassArgs a)
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int j = 32 * (16 * h + i) + j2;
-                const float2 e = LINES ? lin[l1 * kN + j] : lin[j * kLpt + l1];
-                v[i] = conj ? cconj(e) : e;
+                v[i] = lin[l1 * kN + j];
             }
             store_a16(t_a, 16 * h, v);
         }
@@ -242,22 +238,16 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32x(PassArgs a)
         mph ^= 1;
         tc_fence_after();
         // ---- (II) twiddle and (III) transposition into the landing buffer
+        {
+            uint32_t d[64];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t d[32];
-            tmem_ld16(t_d + 32 * h, *(uint32_t(*)[16])(d));
-            tmem_ld16(t_d + 32 * h + 16, *(uint32_t(*)[16])(d + 16));
+            for (int h = 0; h < 4; ++h)
+                tmem_ld16(t_d + 16 * h, *(uint32_t(*)[16])(d + 16 * h));
             tmem_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int kk1 = 16 * h + i;
-                const float2 y = cmul(make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1])),
-                                      tw[kk1 * 32 + j2]);
-                if constexpr (LINES)
-                    tr[l1 * kLineT + kk1 * kPitchL + j2] = y;
-                else
-                    tr[kk1 * kPitchC + j2 * kLpt + l1] = y;
-            }
+            for (int kk1 = 0; kk1 < 32; ++kk1)
+                tr[l1 * kLineT + kk1 * kPitchL + j2] =
+                    cmul(make_float2(__uint_as_float(d[2 * kk1]), __uint_as_float(d[2 * kk1 + 1])), tw[kk1 * 32 + j2]);
         }
         tc_fence_before();
         if (group_or(g, late1)) {
@@ -268,18 +258,12 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32x(PassArgs a)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float2 v[16];
-            if constexpr (LINES) {
-                const float4 *src = (const float4 *)(tr + l2 * kLineT + k1 * kPitchL + 16 * h);
+            const float4 *src = (const float4 *)(tr + l2 * kLineT + k1 * kPitchL + 16 * h);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float4 q = src[i];
-                    v[2 * i] = make_float2(q.x, q.y);
-                    v[2 * i + 1] = make_float2(q.z, q.w);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    v[i] = tr[k1 * kPitchC + (16 * h + i) * kLpt + l2];
+            for (int i = 0; i < 8; ++i) {
+                const float4 q = src[i];
+                v[2 * i] = make_float2(q.x, q.y);
+                v[2 * i + 1] = make_float2(q.z, q.w);
             }
             store_a16(t_a, 16 * h, v);
         }
@@ -305,18 +289,16 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32x(PassArgs a)
         float2 *op = a.out + c * a.g.oc + id.a * a.g.oa + id.b * a.g.ob +
                      (a.g.oblk ? (int64_t)(k1 >> 4) * a.g.oblk + (k1 & 15) * a.g.ok : (int64_t)k1 * a.g.ok);
         const int64_t ostep = a.g.oblk ? 2 * a.g.oblk : 32 * a.g.ok;
+        {
+            uint32_t d[64];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t d[32];
-            tmem_ld16(t_d + 32 * h, *(uint32_t(*)[16])(d));
-            tmem_ld16(t_d + 32 * h + 16, *(uint32_t(*)[16])(d + 16));
+            for (int h = 0; h < 4; ++h)
+                tmem_ld16(t_d + 16 * h, *(uint32_t(*)[16])(d + 16 * h));
             tmem_wait_ld();
             if (valid) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float2 y = make_float2(__uint_as_float(d[2 * i]), __uint_as_float(d[2 * i + 1]));
-                    op[(16 * h + i) * ostep] = conj ? cconj(y) : y;
-                }
+                for (int k2 = 0; k2 < 32; ++k2)
+                    op[k2 * ostep] = make_float2(__uint_as_float(d[2 * k2]), __uint_as_float(d[2 * k2 + 1]));
             }
         }
         tc_fence_before();
@@ -374,9 +356,9 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32s(PassArgs a, const __g
     const int gw = warp & 3;
     const bool conj = a.conj != 0;
 
-    build_dft32_operand(bhi, blo, a.tw + a.tw_split_off);
+    build_dft32_operand(bhi, blo, a.tw + a.tw_split_off, conj);
     for (int i = tid; i < kN; i += blockDim.x)
-        tw[i] = a.tw[i];
+        tw[i] = conj ? cconj(a.tw[i]) : a.tw[i];
     if (tid == 0) {
         for (int i = 0; i < NQ; ++i)
             mbar_init(&full[i], 1);
@@ -427,8 +409,7 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32s(PassArgs a, const __g
             float2 v[16];
 #pragma unroll
             for (int ii = 0; ii < 16; ++ii) {
-                const float2 e = mine[((16 * h + ii) * 8 + q) * 16 + c];
-                v[ii] = conj ? cconj(e) : e;
+                v[ii] = mine[((16 * h + ii) * 8 + q) * 16 + c];
             }
             store_a16(t_a, 16 * h, v);
         }
@@ -444,18 +425,16 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32s(PassArgs a, const __g
         mph ^= 1;
         tc_fence_after();
         // ---- (II) twiddle w_1024^{j2 k1}, (III) in place: X1[c][j2][k1] at (k1 * 8 + q) * 16 + c
+        {
+            uint32_t d[64];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t d[32];
-            tmem_ld16(t_d + 32 * h, *(uint32_t(*)[16])(d));
-            tmem_ld16(t_d + 32 * h + 16, *(uint32_t(*)[16])(d + 16));
+            for (int h = 0; h < 4; ++h)
+                tmem_ld16(t_d + 16 * h, *(uint32_t(*)[16])(d + 16 * h));
             tmem_wait_ld();
 #pragma unroll
-            for (int ii = 0; ii < 16; ++ii) {
-                const int kk1 = 16 * h + ii;
+            for (int kk1 = 0; kk1 < 32; ++kk1)
                 mine[(kk1 * 8 + q) * 16 + c] =
-                    cmul(make_float2(__uint_as_float(d[2 * ii]), __uint_as_float(d[2 * ii + 1])), tw[kk1 * 32 + j2]);
-            }
+                    cmul(make_float2(__uint_as_float(d[2 * kk1]), __uint_as_float(d[2 * kk1 + 1])), tw[kk1 * 32 + j2]);
         }
         tc_fence_before();
         if (cta_any(late || late1)) { // every quarter of the tile is transposed
@@ -497,18 +476,16 @@ __global__ void __launch_bounds__(kTc32Threads, 1) k_tc32s(PassArgs a, const __g
         const bool valid = !late2 && col < a.g.C;
         float2 *op = a.out + col * a.g.oc + id.a * a.g.oa + id.b * a.g.ob + (int64_t)k1 * a.g.ok;
         const int64_t ostep = 32 * a.g.ok;
+        {
+            uint32_t d[64];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint32_t d[32];
-            tmem_ld16(t_d + 32 * h, *(uint32_t(*)[16])(d));
-            tmem_ld16(t_d + 32 * h + 16, *(uint32_t(*)[16])(d + 16));
+            for (int h = 0; h < 4; ++h)
+                tmem_ld16(t_d + 16 * h, *(uint32_t(*)[16])(d + 16 * h));
             tmem_wait_ld();
             if (valid) {
 #pragma unroll
-                for (int ii = 0; ii < 16; ++ii) {
-                    const float2 y = make_float2(__uint_as_float(d[2 * ii]), __uint_as_float(d[2 * ii + 1]));
-                    op[(16 * h + ii) * ostep] = conj ? cconj(y) : y;
-                }
+                for (int k2 = 0; k2 < 32; ++k2)
+                    op[k2 * ostep] = make_float2(__uint_as_float(d[2 * k2]), __uint_as_float(d[2 * k2 + 1]));
             }
         }
         tc_fence_before();
