@@ -60,4 +60,38 @@ struct SegArgs {
     int conj;
 };
 
+// One segment of the one-launch segmented executor (k_seg_all): the tiles of
+// one line length along one dimension of the problems of one wave.
+struct SegAllSeg {
+    int64_t tile0;      // first tile of the segment within its step
+    int64_t list_off, tstart_off, tcube_off; // offsets into the problem list, first-tile and slot tables
+    int kidx;           // line kernel: 0 .. kSegLens-1 contiguous (x), kSegLens .. 2 kSegLens-1 strided (y, z)
+    int dim;
+    int tw_off;         // offset of the line's twiddle table in the block's shared copy
+    int pad;
+};
+
+// The whole batch in one cooperative launch: steps separated by grid
+// barriers; step s holds segments seg0[s] .. seg0[s+1]-1 and ntiles[s] tiles.
+struct SegAllArgs {
+    const float2 *in;
+    float2 *out;
+    const BatchCube *cubes;
+    const int *list;
+    const int64_t *tstart;
+    const int *tcube;
+    const SegAllSeg *segs;
+    const int *seg0;
+    const int64_t *ntiles;
+    int nsteps;
+    const float2 *tw;   // every line kernel's twiddle table, tw_len entries (copied to shared memory)
+    int tw_len;
+    int *barrier;       // grid-barrier arrivals (zero at launch)
+    unsigned *err;
+    long long wait_budget;
+    int conj;
+};
+
+constexpr int kSegAllThreads = 256;
+
 } // namespace fft3

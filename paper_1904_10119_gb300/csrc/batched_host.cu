@@ -19,6 +19,8 @@
 #include "capi_internal.h"
 #include "seg_plans.h"
 
+#include <type_traits>
+
 namespace fft3 {
 
 __global__ void k_batched(BatchArgs a);
@@ -36,6 +38,20 @@ struct SegLaunch {
 struct BatchState {
     int seg = 0; // 1: three segmented passes (k_segmented.cu) instead of the persistent executor
     std::vector<SegLaunch> seg_launches;
+    // the segmented passes as one cooperative launch (k_seg_all): waves of
+    // problems, steps of segments, and their tables
+    int seg1 = 0;
+    int waves = 1;
+    std::vector<SegAllSeg> sa_segs;
+    std::vector<int> sa_seg0, sa_list, sa_tcube;
+    std::vector<int64_t> sa_ntiles, sa_tstart;
+    int64_t sa_tw_off = 0;
+    int sa_tw_len = 0;
+    SegAllSeg *d_sa_segs = nullptr;
+    int *d_sa_seg0 = nullptr, *d_sa_list = nullptr, *d_sa_tcube = nullptr, *d_sa_barrier = nullptr;
+    int64_t *d_sa_ntiles = nullptr, *d_sa_tstart = nullptr;
+    int sa_smem = 0;
+    dim3 sa_grid;
     // host tables built by the planning: twiddle segments (offset, count), their
     // exponents and line lengths; the segmented passes' problem lists, first
     // tiles and per-tile slots
@@ -99,6 +115,13 @@ void batch_free(BatchState *b)
     cudaFree(b->d_seg_list);
     cudaFree(b->d_seg_tcube);
     cudaFree(b->d_seg_tstart);
+    cudaFree(b->d_sa_segs);
+    cudaFree(b->d_sa_seg0);
+    cudaFree(b->d_sa_list);
+    cudaFree(b->d_sa_tcube);
+    cudaFree(b->d_sa_barrier);
+    cudaFree(b->d_sa_ntiles);
+    cudaFree(b->d_sa_tstart);
     cudaFree(b->d_cubes);
     cudaFree(b->d_items);
     cudaFree(b->d_lines);
@@ -170,7 +193,7 @@ int batch_buffer_need(int n0, int n1, int n2, int code)
     return std::max(spi * pitch_b(n0), std::max(lpty * pitch_b(n1), lpt * pitch_b(n2)));
 }
 
-int batch_kernel_launches(const BatchState *b) { return b->seg ? (int)b->seg_launches.size() : 1; }
+int batch_kernel_launches(const BatchState *b) { return b->seg && !b->seg1 ? (int)b->seg_launches.size() : 1; }
 
 int batch_describe(const BatchState *b, std::string *json)
 {
@@ -182,11 +205,16 @@ int batch_describe(const BatchState *b, std::string *json)
         e.first++;
         e.second = b->tuning[i];
     }
-    o << "{\"batched\":true,\"mode\":\"" << (b->seg ? "segmented" : "executor") << "\",\"kernel_launches\":"
+    o << "{\"batched\":true,\"mode\":\""
+      << (b->seg1 ? "segmented_one_launch" : b->seg ? "segmented" : "executor") << "\",\"kernel_launches\":"
       << batch_kernel_launches(b) << ",\"problems\":" << b->cubes.size() << ",\"items\":" << b->items.size()
       << ",\"groups\":" << b->groups << ",\"line_plans\":" << b->lines.size() << ",\"grid\":" << b->grid.x
       << ",\"block\":" << b->threads << ",\"smem\":" << b->smem << ",\"prefetch\":" << b->prefetch << ",\"twiddle_entries\":" << b->tw_total
-      << ",\"extent\":" << b->extent << ",\"segmented_launches\":[";
+      << ",\"extent\":" << b->extent;
+    if (b->seg1)
+        o << ",\"waves\":" << b->waves << ",\"steps\":" << b->sa_ntiles.size() << ",\"segments\":" << b->sa_segs.size()
+          << ",\"one_launch_grid\":" << b->sa_grid.x << ",\"one_launch_smem\":" << b->sa_smem;
+    o << ",\"segmented_launches\":[";
     for (size_t k = 0; k < b->seg_launches.size(); ++k) {
         const SegLaunch &L = b->seg_launches[k];
         const int64_t nprob = (k + 1 < b->seg_launches.size() ? b->seg_launches[k + 1].list_off
@@ -234,7 +262,41 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
     a.prefetch = b->prefetch;
     CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    if (b->seg) {
+    if (b->seg1) {
+        SegAllArgs s{};
+        s.in = (const float2 *)in;
+        s.out = (float2 *)out;
+        s.cubes = b->d_cubes;
+        s.list = b->d_sa_list;
+        s.tstart = b->d_sa_tstart;
+        s.tcube = b->d_sa_tcube;
+        s.segs = b->d_sa_segs;
+        s.seg0 = b->d_sa_seg0;
+        s.ntiles = b->d_sa_ntiles;
+        s.nsteps = (int)b->sa_ntiles.size();
+        s.tw = b->d_tw + b->sa_tw_off;
+        s.tw_len = b->sa_tw_len;
+        s.barrier = b->d_sa_barrier;
+        s.err = b->d_err;
+        s.wait_budget = 4000000000LL;
+        s.conj = b->conj;
+        e = cudaMemsetAsync(b->d_sa_barrier, 0, sizeof(int), b->cap_stream);
+        if (e == cudaSuccess) {
+            // cooperative: every block resident at once, so the grid barriers end
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.gridDim = b->sa_grid;
+            cfg.blockDim = dim3(kSegAllThreads);
+            cfg.dynamicSmemBytes = b->sa_smem;
+            cfg.stream = b->cap_stream;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            void *params[1] = {&s};
+            e = cudaLaunchKernelExC(&cfg, (const void *)&k_seg_all, params);
+        }
+    } else if (b->seg) {
         int ccnt = 0, scnt = 0;
         const SegKernel *skc = seg_kernels(true, &ccnt), *sks = seg_kernels(false, &scnt);
         for (const SegLaunch &L : b->seg_launches) {
@@ -399,9 +461,20 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
                                                    "of this batch");
         }
         b->seg = ok && (all3 || (decomposition == FFT3_AUTO && !tuning && values >= kSegMinElems)) ? 1 : 0;
+        // decomposition field 3 with the items field k >= 1 on every code: the
+        // segmented passes in one cooperative launch, in 2^(k-1) waves
+        int items = all3 ? (tuning[0] >> 8) : 0;
+        for (int i = 0; all3 && i < count; ++i)
+            items = (tuning[i] >> 8) == items ? items : -1;
+        if (b->seg && items > 0) {
+            if (items > 11)
+                return fail(FFT3_ERR_INVALID_ARG, "at most 1024 waves");
+            b->seg1 = 1;
+            b->waves = std::min(count, 1 << (items - 1));
+        }
         if (b->seg)
             for (int i = 0; i < count; ++i)
-                b->tuning[i] = 3;
+                b->tuning[i] = 3 | (b->seg1 ? items << 8 : 0);
     }
     b->buf_elems = (bufmax + 31) / 32 * 32;
     // a third buffer stages the next item's first tile when it still fits
@@ -484,6 +557,92 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
                 b->seg_launches.push_back(L);
             }
         }
+    }
+    if (b->seg1) {
+        // every line kernel's twiddle table, one after the other (copied to
+        // shared memory by every block of the one-launch executor)
+        std::vector<int> kt(ccnt + scnt);
+        b->sa_tw_off = tw_total;
+        int64_t local = 0;
+        for (int k = 0; k < ccnt + scnt; ++k) {
+            const SegKernel &K = k < ccnt ? skc[k] : sks[k - ccnt];
+            LineChoice lc{};
+            lc.n = K.n;
+            lc.fixed = -1;
+            lc.T = K.T;
+            lc.nst = K.nrad;
+            for (int r = 0; r < K.nrad; ++r)
+                lc.rad[r] = K.rad[r];
+            std::vector<int64_t> e;
+            line_twiddle_exponents(lc, &e);
+            if (e.empty())
+                e.push_back(0);
+            kt[k] = (int)local;
+            segs.push_back({tw_total + local, (int64_t)e.size()});
+            local += ((int64_t)e.size() + 15) / 16 * 16;
+            exps.push_back(std::move(e));
+            exp_n.push_back(K.n);
+        }
+        b->sa_tw_len = (int)local;
+        tw_total += local;
+        // waves: consecutive problems of about equal volume
+        std::vector<int> wave_of(count);
+        {
+            int64_t total = 0, acc = 0;
+            for (int i = 0; i < count; ++i)
+                total += (int64_t)dims[3 * i] * dims[3 * i + 1] * dims[3 * i + 2];
+            for (int i = 0; i < count; ++i) {
+                wave_of[i] = (int)std::min<int64_t>(b->waves - 1, acc * b->waves / std::max<int64_t>(1, total));
+                acc += (int64_t)dims[3 * i] * dims[3 * i + 1] * dims[3 * i + 2];
+            }
+        }
+        // steps: with one wave the x, y and z lines; with W waves, step k holds the
+        // x lines of wave k, the y lines of wave k-1 and the z lines of wave k-2
+        const int W = b->waves;
+        const int nsteps = W == 1 ? 3 : W + 2;
+        for (int st = 0; st < nsteps; ++st) {
+            b->sa_seg0.push_back((int)b->sa_segs.size());
+            int64_t tiles = 0;
+            for (int d = 0; d < 3; ++d) {
+                const int w = W == 1 ? (st == d ? 0 : -1) : st - d;
+                if (w < 0 || w >= W)
+                    continue;
+                std::map<int, std::vector<int>> byn;
+                for (int i = 0; i < count; ++i)
+                    if (wave_of[i] == w)
+                        byn[dims[3 * i + d]].push_back(i);
+                for (auto &kv : byn) {
+                    const int kidx = d == 0 ? seg_find(true, kv.first) : ccnt + seg_find(false, kv.first);
+                    const int T = kidx < ccnt ? skc[kidx].T : sks[kidx - ccnt].T;
+                    const int L = kSegAllThreads / T;
+                    SegAllSeg sg{};
+                    sg.tile0 = tiles;
+                    sg.list_off = (int64_t)b->sa_list.size();
+                    sg.tstart_off = (int64_t)b->sa_tstart.size();
+                    sg.tcube_off = (int64_t)b->sa_tcube.size();
+                    sg.kidx = kidx;
+                    sg.dim = d;
+                    sg.tw_off = kt[kidx];
+                    int64_t t = 0;
+                    for (size_t q = 0; q < kv.second.size(); ++q) {
+                        const int i = kv.second[q];
+                        const int64_t n0 = dims[3 * i], n1 = dims[3 * i + 1], n2 = dims[3 * i + 2];
+                        const int64_t lines = d == 0 ? n1 * n2 : d == 1 ? n0 * n2 : n0 * n1;
+                        const int64_t nt = (lines + L - 1) / L;
+                        b->sa_list.push_back(i);
+                        b->sa_tstart.push_back(t);
+                        b->sa_tcube.insert(b->sa_tcube.end(), (size_t)nt, (int)q);
+                        t += nt;
+                    }
+                    b->sa_tstart.push_back(t);
+                    tiles += t;
+                    b->sa_segs.push_back(sg);
+                }
+            }
+            b->sa_ntiles.push_back(tiles);
+        }
+        b->sa_seg0.push_back((int)b->sa_segs.size());
+        b->sa_smem = seg_all_smem_bytes(b->sa_tw_len);
     }
     b->tw_total = tw_total;
     // work items in waves over groups of problems (largest first)
@@ -625,6 +784,23 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
             if (rc)
                 return bail(rc);
         }
+    }
+    if (b->seg1) {
+        auto up = [&](auto **d, const auto &v) -> bool {
+            using T = typename std::remove_reference<decltype(v)>::type::value_type;
+            if (cudaMalloc((void **)d, std::max<size_t>(1, v.size()) * sizeof(T)) != cudaSuccess)
+                return false;
+            return v.empty() || cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+        };
+        if (!up(&b->d_sa_segs, b->sa_segs) || !up(&b->d_sa_seg0, b->sa_seg0) || !up(&b->d_sa_list, b->sa_list) ||
+            !up(&b->d_sa_tcube, b->sa_tcube) || !up(&b->d_sa_ntiles, b->sa_ntiles) ||
+            !up(&b->d_sa_tstart, b->sa_tstart) || cudaMalloc(&b->d_sa_barrier, sizeof(int)) != cudaSuccess)
+            return bail(fail(FFT3_ERR_OOM, "device tables of the one-launch executor"));
+        rc = prepare_func((const void *)&k_seg_all, b->sa_smem);
+        if (!rc)
+            rc = occupancy_grid((const void *)&k_seg_all, kSegAllThreads, b->sa_smem, 0, dev, &b->sa_grid);
+        if (rc)
+            return bail(rc);
     }
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(FFT3_ERR_CUDA, "stream creation failed"));

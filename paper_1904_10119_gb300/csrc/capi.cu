@@ -60,7 +60,7 @@ int fft3::device_sms(int dev)
 
 // Raise the dynamic shared-memory cap of a kernel to the device's opt-in
 // maximum (the cap is per function, so it is never lowered by a later plan).
-int fft3::prepare_func(const void *func, int smem)
+int fft3::prepare_func(const void *func, int smem, bool max_shared)
 {
     if (smem > 0) {
         int dev = 0, optin = 0;
@@ -71,13 +71,12 @@ int fft3::prepare_func(const void *func, int smem)
         const int cap = optin - (int)fa.sharedSizeBytes; // static shared memory counts against the opt-in
         if (smem > cap)
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, "pass needs more shared memory than the device offers");
-        if (smem + (int)fa.sharedSizeBytes > 48 * 1024) {
+        if (smem + (int)fa.sharedSizeBytes > 48 * 1024)
             CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-            // the largest shared-memory carveout, so that as many blocks as the
-            // shared memory allows are resident (and the occupancy query counts them)
+        // the largest shared-memory carveout (least L1), on request
+        if (max_shared)
             CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           cudaSharedmemCarveoutMaxShared));
-        }
     }
     return FFT3_OK;
 }
@@ -331,7 +330,7 @@ static int build_launches(fft3_plan_s *P)
         }
         if (!L.func)
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, "no compiled kernel for this pass");
-        int rc = prepare_func(L.func, L.smem);
+        int rc = prepare_func(L.func, L.smem, L.tc32 != 0);
         if (rc)
             return rc;
         if (p.kind == PK_VOL || p.kind == PK_VOLC || (p.kind == PK_CSTREAM && p.p > 1)) {

@@ -53,7 +53,11 @@ struct Launch {
 struct BatchState; // batched uneven plans (batched_host.cu)
 
 int device_sms(int dev);
-int prepare_func(const void *func, int smem);
+// Opts a kernel in to `smem` bytes of dynamic shared memory; max_shared also
+// asks for the largest shared-memory carveout (the tensor-memory kernels,
+// whose blocks fill an SM's shared memory; kernels that lean on L1 keep the
+// driver's choice).
+int prepare_func(const void *func, int smem, bool max_shared = false);
 int occupancy_grid(const void *func, int threads, int smem, int64_t ntiles, int dev, dim3 *grid);
 int check_device(int *dev);
 

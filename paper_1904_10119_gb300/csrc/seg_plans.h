@@ -46,4 +46,10 @@ struct SegKernel {
 // The compiled lists (device translation unit) and their sizes.
 const SegKernel *seg_kernels(bool contiguous, int *count);
 
+// The one-launch executor (k_seg_all): its line kernel kidx is the index in
+// the contiguous list, or the count of that list plus the index in the
+// strided list; dynamic shared memory for a twiddle table of tw_len entries.
+__global__ void k_seg_all(struct SegAllArgs a);
+int seg_all_smem_bytes(int tw_len);
+
 } // namespace fft3

@@ -524,3 +524,29 @@ def test_tcgen05_radix32_schedule():
     assert not s["passes"][1]["kind"].endswith("r32_tc")
     s = fft3.fft3_plan_schedule(20, 1024, 3, 1, TC, fft3.FFT3_PENCIL3, -1)
     assert s["passes"][1]["kind"] == "line_strided_r32_tc" and s["passes"][1]["tiles"] == 2 * 3
+
+
+def test_schedule_many_one_launch_segmented_steps():
+    """Tuning codes 3 | (k << 8): the segmented passes in one cooperative launch
+    in 2^(k-1) waves of problems.  One wave: three steps (x, y, z lines); W
+    waves: W + 2 steps, step s holding the x lines of wave s, the y lines of
+    wave s-1 and the z lines of wave s-2.  The tiles of every dimension add up
+    to the sum over problems of ceil(lines / (256 / T)) whatever the waves."""
+    from paper_1904_10119_gb300 import synth
+    dims = synth.batched_dims(300, 7)
+    offs = _batch_layout(dims)
+    per_dim = {}
+    for k in (1, 3, 5):
+        d = fft3.fft3_plan_schedule_many(dims, offs, tuning=[3 | (k << 8)] * len(dims))
+        W = 1 << (k - 1)
+        assert d["mode"] == "segmented_one_launch" and d["kernel_launches"] == 1
+        assert d["waves"] == W and d["steps"] == (3 if W == 1 else W + 2)
+        assert all(c["tuning"] == 3 | (k << 8) for c in d["classes"])
+        per_dim[k] = d["segments"]
+    assert per_dim[1] == sum(len(set(dims[:, j])) for j in range(3))  # one segment per dimension and length
+    assert per_dim[5] >= per_dim[3] >= per_dim[1]
+    # mixed items fields fall back to the launch per line length
+    mixed = [3 | (1 << 8)] * (len(dims) - 1) + [3]
+    assert fft3.fft3_plan_schedule_many(dims, offs, tuning=mixed)["mode"] == "segmented"
+    with pytest.raises(fft3.Fft3Error):
+        fft3.fft3_plan_schedule_many(dims, offs, tuning=[3 | (12 << 8)] * len(dims))

@@ -167,3 +167,44 @@ def test_segmented_auto_choice_replay_and_refusal():
         fft3.fft3_plan_destroy(h)
     with pytest.raises(fft3.Fft3Error):
         fft3.fft3_plan_create_many([[30, 16, 16]], [0], tuning=[3])
+
+
+@pytest.mark.parametrize("waves_code", [1, 3])
+@pytest.mark.parametrize("direction", [fft3.FFT3_FORWARD, fft3.FFT3_INVERSE])
+def test_one_launch_segmented_every_problem(waves_code, direction):
+    """Tuning codes 3 | (k << 8): all x, y and z lines of the batch in one
+    cooperative launch (grid barriers between steps, 2^(k-1) waves), every
+    problem checked against the oracle; replayed on the same buffers it gives
+    the same bits."""
+    dims = np.vstack([synth.batched_dims(40, 11), [[8, 128, 16], [128, 8, 96], [24, 40, 8]]])
+    offs, total = _layout(dims, gap=5)
+    code = 3 | (waves_code << 8)
+    x, got, desc = _run(dims, offs, total, direction=direction, tuning=[code] * len(dims), seed=2)
+    assert desc["mode"] == "segmented_one_launch" and desc["kernel_launches"] == 1
+    assert desc["waves"] == 1 << (waves_code - 1)
+    for off, d in zip(offs, dims):
+        _check_problem(x, got, int(off), d, direction)
+    _, again, _ = _run(dims, offs, total, direction=direction, tuning=[code] * len(dims), seed=2)
+    assert np.array_equal(got, again)
+
+
+def test_one_launch_segmented_4096_cubes_sampled_and_parseval():
+    """The 4096-cube workload in one cooperative launch: a sample covering
+    every size class element by element, Parseval for every problem."""
+    dims = synth.batched_dims(4096, 7)
+    offs, total = _layout(dims)
+    x, got, desc = _run(dims, offs, total, seed=7, tuning=[3 | (1 << 8)] * len(dims))
+    assert desc["mode"] == "segmented_one_launch"
+    seen, sample = set(), []
+    for i, d in enumerate(map(tuple, dims)):
+        if d not in seen:
+            seen.add(d)
+            sample.append(i)
+    for i in sample[:120]:
+        _check_problem(x, got, int(offs[i]), dims[i], fft3.FFT3_FORWARD)
+    x2 = np.abs(x.astype(np.complex128)) ** 2
+    g2 = np.abs(got.astype(np.complex128)) ** 2
+    for off, d in zip(offs, dims):
+        N = int(np.prod(d))
+        sx, sg = x2[off:off + N].sum(), g2[off:off + N].sum()
+        assert abs(sg - N * sx) <= 1e-5 * N * sx
