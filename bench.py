@@ -609,8 +609,14 @@ def bench_batched(fft3, synth, torch, hbm, count=4096):
 
     ms, desc = run(None)
     ms_exec, _ = run([0] * count)
+    # the segmented passes in one cooperative launch, 2^(k-1) waves of problems
+    one_launch = {}
+    for k in (1, 3, 5, 7):
+        t, d = run([3 | (k << 8)] * count)
+        one_launch[f"waves_{d['waves']}"] = t
     one_sweep = 2 * 8 * total
     return {"ms": ms, "mode": desc["mode"], "kernel_launches": desc["kernel_launches"],
+            "one_launch_ms": one_launch,
             "executor_ms": ms_exec, "elements": total, "problems": count, "items": desc["items"],
             "GBps_one_sweep": one_sweep / (ms * 1e-3) / 1e9,
             "frac_of_1_sweep": one_sweep / (ms * 1e-3) / 1e9 / hbm,

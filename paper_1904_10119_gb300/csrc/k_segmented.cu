@@ -168,7 +168,7 @@ __device__ __forceinline__ int ld_acquire_seg(const int *p)
     return v;
 }
 
-__global__ void __launch_bounds__(kSegAllThreads, 2) k_seg_all(SegAllArgs a)
+__global__ void __launch_bounds__(kSegAllThreads, 4) k_seg_all(SegAllArgs a)
 {
     extern __shared__ float2 smem[];
     float2 *tw = smem;

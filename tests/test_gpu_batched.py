@@ -185,7 +185,7 @@ def test_one_launch_segmented_every_problem(waves_code, direction):
     for off, d in zip(offs, dims):
         _check_problem(x, got, int(off), d, direction)
     _, again, _ = _run(dims, offs, total, direction=direction, tuning=[code] * len(dims), seed=2)
-    assert np.array_equal(got, again)
+    assert np.array_equal(got, again, equal_nan=True)  # the gaps between problems stay NaN
 
 
 def test_one_launch_segmented_4096_cubes_sampled_and_parseval():
