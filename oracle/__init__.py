@@ -474,3 +474,28 @@ def dft3_sampled(x, n0: int, n1: int, n2: int, k0s, k1s, k2s, sign: int = FORWAR
     A = A.reshape(n2, n1, k0s.size)
     B = np.einsum("zyk,yl->zkl", A, F1)
     return np.einsum("zkl,zm->klm", B, F2)
+
+
+def dft3_line(x, n0: int, n1: int, n2: int, dim: int, ka: int, kb: int, sign: int = FORWARD,
+              chunk: int = 16) -> np.ndarray:
+    """One whole output line of the 3D DFT of a (n2, n1, n0) array (Section 2.3,
+    separable definition): every frequency along dimension `dim`, the other two
+    fixed (ka, kb in increasing dimension order).  The two fixed dimensions are
+    summed out first with their roots w^{j k} (one sweep over x, FP64), then
+    the remaining vector gets the direct O(n^2) DFT along `dim`."""
+    n = (n0, n1, n2)
+    other = [d for d in range(3) if d != dim]
+    k = {other[0]: ka, other[1]: kb}
+    w = {d: roots(n[d], np.arange(n[d]) * k[d] % n[d], sign) for d in other}
+    v = np.asarray(x).reshape(n2, n1, n0)
+    acc = np.zeros(n[dim], dtype=np.complex128)
+    for z0 in range(0, n2, chunk):
+        blk = v[z0:z0 + chunk].astype(np.complex128)           # (z, y, x)
+        if dim == 0:
+            acc += w[1] @ np.tensordot(w[2][z0:z0 + chunk], blk, axes=(0, 0))
+        elif dim == 1:
+            acc += np.tensordot(w[2][z0:z0 + chunk], blk, axes=(0, 0)) @ w[0]
+        else:
+            acc[z0:z0 + chunk] = np.tensordot(blk, w[0], axes=(2, 0)) @ w[1]
+    return dft1_direct(acc, sign)
+

@@ -422,3 +422,18 @@ def test_sampled_outputs_equal_full_transform():
     gi = oracle.dft3_sampled(x, n0, n1, n2, k0s, k1s, k2s, sign=oracle.INVERSE)
     fi = oracle.fft3(x.ravel(), n0, n1, n2, sign=oracle.INVERSE)
     assert oracle.rel_l2(gi, fi[np.ix_(k2s, k1s, k0s)].transpose(2, 1, 0)) < 1e-14
+
+
+@pytest.mark.parametrize("shape,sign", [((8, 6, 10), -1), ((12, 5, 9), 1)])
+def test_dft3_line_equals_fft3_lines(shape, sign):
+    """A whole output line along each dimension, by the separable definition
+    with the other two frequencies fixed, equals the corresponding line of
+    the full oracle transform."""
+    n0, n1, n2 = shape
+    x = synth.uniform_c128((n2, n1, n0), 21)
+    ref = oracle.fft3(x.ravel(), n0, n1, n2, sign=sign).reshape(n2, n1, n0)
+    for dim, ka, kb in ((0, 2, 3), (1, 5, 7), (2, 1, 4)):
+        line = oracle.dft3_line(x, n0, n1, n2, dim, ka, kb, sign=sign, chunk=3)
+        want = ref[kb, ka, :] if dim == 0 else ref[kb, :, ka] if dim == 1 else ref[:, kb, ka]
+        assert np.max(np.abs(line - want)) <= 1e-12 * np.max(np.abs(want))
+
