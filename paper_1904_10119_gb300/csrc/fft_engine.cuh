@@ -191,6 +191,38 @@ struct Bfly<16> {
     }
 };
 
+// cos(pi m / 16) and sin(pi m / 16) for m in 0..7, from which every power of
+// w_32 follows by symmetry.
+constexpr double kC32[8] = {1.0,
+                            0.980785280403230449126182236134239037,
+                            0.923879532511286756128183189396788933,
+                            0.831469612302545237078788377617905756,
+                            0.707106781186547524400844362104849039,
+                            0.555570233019602224742830813948532874,
+                            0.382683432365089771728459984030398866,
+                            0.195090322016128267848284868477022240};
+__host__ __device__ constexpr double cos32(int m)
+{
+    m &= 31;
+    return m <= 8 ? (m == 8 ? 0.0 : kC32[m]) : m < 16 ? -cos32(16 - m) : m < 24 ? -cos32(m - 16) : cos32(32 - m);
+}
+__host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
+
+// a * w_32^M, M known at compile time (the exact cases of mul_w where M is a
+// multiple of 2, the general complex product otherwise).
+template <int M, class C>
+__device__ __forceinline__ C mul_w32(C a)
+{
+    if constexpr ((M & 1) == 0) {
+        return mul_w<16, M / 2>(a);
+    } else {
+        using X = Cx<C>;
+        using S = typename X::S;
+        constexpr S c = (S)cos32(M), s = (S)sin32(M);
+        return X::make(X::fma_(a.x, c, a.y * s), X::fma_(a.y, c, -a.x * s));
+    }
+}
+
 // A constant in the scalar type: the float literal for FP32 (as written), the
 // double literal for FP64.
 template <class S>
@@ -201,6 +233,42 @@ __host__ __device__ constexpr S kpick(float f, double d)
     else
         return (S)d;
 }
+
+// 32 = 2 * 16 (Eq. ct with n0 = 2, n1 = 16): DFT_16 on x[i0 + 2 i1], twiddle
+// w_32^{i0 k1}, DFT_2 across i0, output y[k1 + 16 k0].  Every value stays in
+// registers: one thread transforms a whole 32-point sub-line.
+template <int K>
+struct Tw32Step {
+    template <class C>
+    __device__ __forceinline__ static void run(C *o)
+    {
+        o[K] = mul_w32<K>(o[K]);
+        if constexpr (K + 1 < 16)
+            Tw32Step<K + 1>::run(o);
+    }
+};
+
+template <>
+struct Bfly<32> {
+    template <class C>
+    __device__ __forceinline__ static void run(C *v)
+    {
+        C e[16], o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        Bfly<16>::run(e);
+        Bfly<16>::run(o);
+        Tw32Step<1>::run(o);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + 16] = csub(e[k], o[k]);
+        }
+    }
+};
 
 // DFT_3: w_3 = -1/2 - i sqrt(3)/2.
 template <>

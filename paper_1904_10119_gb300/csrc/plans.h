@@ -7,7 +7,8 @@
 // runtime-radix kernel (any 2*3*5-smooth length up to 4096).
 //
 // Candidates for one length are listed best-first by default; the planner's
-// `radix_order` option (and the autotuner) picks among them.
+// `radix_order` option (and the autotuner) picks among them (ids follow the
+// table order: a new candidate goes to the end, after the existing ids).
 #pragma once
 
 #define FFT3_FIXED_PLANS_A(X)          \
@@ -34,7 +35,8 @@
     X(18, 16, 4, 4, 4)                 \
     X(19, 8, 1, 8)                     \
     X(20, 4, 1, 4)                     \
-    X(21, 2, 1, 2)
+    X(21, 2, 1, 2)                     \
+    X(22, 1024, 32, 32, 32)
 
 #define FFT3_FIXED_PLANS(X) FFT3_FIXED_PLANS_A(X) FFT3_FIXED_PLANS_B(X)
 

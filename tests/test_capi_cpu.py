@@ -550,3 +550,16 @@ def test_schedule_many_one_launch_segmented_steps():
     assert fft3.fft3_plan_schedule_many(dims, offs, tuning=mixed)["mode"] == "segmented"
     with pytest.raises(fft3.Fft3Error):
         fft3.fft3_plan_schedule_many(dims, offs, tuning=[3 | (12 << 8)] * len(dims))
+
+
+def test_radix32_plan_is_a_1024_candidate():
+    """The 32 x 32 plan for 1024-point lines (32 threads per line, one whole
+    32-point butterfly per thread and stage) is the fifth 1024-point candidate:
+    radix_order 4 selects it for the contiguous pass; its stage-major twiddle
+    table holds (32 - 1) * 32 entries (the first stage has none)."""
+    s = fft3.fft3_plan_schedule(1024, 8, 8, 1, 0, fft3.FFT3_PENCIL3, -1, fft3.make_options(radix_order=4))
+    p = s["passes"][0]
+    assert p["kind"] == "line_contig" and p["line"]["radices"] == [32, 32] and p["line"]["T"] == 32
+    assert fft3.fft3_factorize(1024, 0) != [32, 32]
+    s0 = fft3.fft3_plan_schedule(1024, 1, 1, 1, 0, fft3.FFT3_PENCIL3, -1, fft3.make_options(radix_order=4))
+    assert s0["twiddle_entries"] >= 31 * 32

@@ -62,6 +62,22 @@ def test_radix_orders(shape, order):
     assert_parity(x, got, shape)
 
 
+@pytest.mark.parametrize("kw,shape,direction", [
+    ({}, (1024, 12, 10), FWD),                                  # contiguous pass
+    ({"tile_lines": 16}, (24, 1024, 6), INV),                   # plain strided pass
+    ({"tile_lines": 8}, (8, 6, 1024), FWD),
+    ({"slab_mode": 5, "slab_lines": 4}, (1024, 1024, 3), FWD),  # fused slab stage
+    ({"slab_mode": 5, "slab_lines": 8}, (1024, 1024, 2), INV)])
+def test_radix32_register_plan(kw, shape, direction):
+    """The 1024-point plan with two radix-32 stages (one whole 32-point
+    butterfly per thread in registers; radix_order 4 among the 1024-point
+    candidates) in the kernels that run compile-time plans."""
+    decomp = S if "slab_mode" in kw else P
+    x, got, plan = run_plan(shape, 1, decomp, direction, seed=11, radix_order=4, **kw)
+    assert_parity(x, got, shape, 1, direction)
+    assert any(p["line"]["radices"] == [32, 32] for p in plan.describe()["passes"])
+
+
 @pytest.mark.parametrize("mode,shape", [(1, (64, 64, 20)), (1, (96, 96, 8)), (2, (256, 256, 6)),
                                         (2, (512, 512, 3)), (3, (256, 256, 6)), (3, (100, 60, 12))])
 def test_slab_modes(mode, shape):
