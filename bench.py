@@ -463,6 +463,10 @@ def main():
             extras["complex128_fp64"] = {"error": str(e)}
         if n0 == n1 == n2 == 1024:
             try:
+                extras["slab_pencil_rank_local"] = dist_table(fft3, torch, n0, hbm)
+            except Exception as e:  # noqa: BLE001
+                extras["slab_pencil_rank_local"] = {"error": str(e)}
+            try:
                 extras["smaller_cubes"] = size_table(fft3, synth, torch, (256, 512), decomp_map)
             except Exception as e:
                 extras["smaller_cubes"] = {"error": str(e)}
@@ -539,6 +543,47 @@ def size_table(fft3, synth, torch, sizes, decomp_map):
             row[name] = ent
         table[f"{n}^3"] = row
         del x, out
+    return table
+
+
+def dist_table(fft3, torch, n, hbm, ranks=(2, 4, 8), reps=10):
+    """Local work of one rank of the slab-pencil decomposition on a 1D grid of
+    P processes (n^3 forward): the slab stage on n/P slabs (x pass, y pass
+    storing the blocks packed for the all-to-all) and the pencil stage on the
+    n/P-wide x range (z pass), each timed with CUDA events over `reps`
+    back-to-back executions on this GPU.  The all-to-all between them (one
+    exchange of (P-1)/P of the rank's data) runs over the interconnect and is
+    not part of these numbers."""
+    table = {}
+    st = torch.cuda.current_stream()
+    for P in ranks:
+        loc = n * n * n // P
+        a = torch.empty(loc, dtype=torch.complex64, device="cuda")
+        a.real.uniform_(-1, 1)
+        a.imag.uniform_(-1, 1)
+        b = torch.empty_like(a)
+        row = {}
+        for name, dims, stage in (("slab_stage_ms", (n, n, n // P), 1), ("pencil_stage_ms", (n // P, n, n), 2)):
+            p = fft3.Plan(*dims, 1, fft3.FFT3_SLAB_PENCIL, fft3.FFT3_FORWARD, dist_ranks=P, dist_stage=stage)
+            for _ in range(3):
+                p.execute(a, b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                p.execute(a, b)
+            e1.record(st)
+            torch.cuda.synchronize()
+            assert p.check() == 0, fft3.last_error()
+            row[name] = e0.elapsed_time(e1) / reps
+            row[name.replace("_ms", "_kinds")] = [q["kind"] for q in p.describe()["passes"]]
+            p.close()
+        ms = row["slab_stage_ms"] + row["pencil_stage_ms"]
+        row["local_ms"] = ms
+        # three sweeps of the rank's data, each read and written once
+        row["local_hbm_frac_of_measured"] = 3 * 2 * 8 * loc / (ms * 1e-3) / 1e9 / hbm
+        row["exchange_bytes_per_rank"] = 8 * loc * (P - 1) // P
+        table[f"P{P}"] = row
+        del a, b
     return table
 
 

@@ -152,6 +152,33 @@ typedef struct fft3_options {
     int slab_chunk;   /* slab_mode 4: slabs per chunk (0 = about 32 MiB of slabs) */
     int slab_lines;   /* slab_mode 5: rows per x tile and columns per y tile, 4 or 8 (0 = 4) */
     int layout;       /* fft3_layout of the forward output / inverse input (0 = natural) */
+    int dist_ranks;   /* > 1: a rank-local plan of the slab-pencil decomposition distributed over
+                         dist_ranks processes (Section 2.4, a 1D grid of P processes; FFT3_SLAB_PENCIL,
+                         batch 1, complex64 or complex128).  Rank r owns the slabs z in
+                         [r n2/P, (r+1) n2/P) of the input and the x range [r n0/P, (r+1) n0/P) of
+                         the spectrum.  dist_stage selects the plan:
+                         1 = the 2D DFT of the rank's slabs: create with (n0, n1, n2/P); `in` holds the
+                             rank's slabs [z_local][y][x]; `out` receives them packed for the all-to-all
+                             as [dest][z_local][y][x_local] (the y pass stores there directly), so block
+                             `dest` of n0 n1 n2 / P^2 values goes to rank dest (needs P | n0);
+                         2 = the DFTs along z of the rank's pencils: create with (n0/P, n1, n2); `in` is
+                             the all-to-all's receive buffer, [src][z_local][y][x_local] = the natural
+                             layout [z][y][x_local] of the rank's x range; `out` the same layout.
+                         3 = the local side of the second exchange, which returns the spectrum to
+                             slabs (Fig. 3dslabpencil; optional, as the paper allows leaving the
+                             spectrum in pencils): create with (n0, n1, n2/P); forward: `in` is that
+                             exchange's receive buffer [src][z_local][y][x_local], `out` the natural
+                             slabs [z_local][y][x]; inverse: the reverse, packing natural spectrum
+                             slabs for the first exchange.
+                         Forward: stage 1, exchange, stage 2 (then exchange, stage 3); inverse: (stage 3,
+                         exchange,) stage 2, exchange, stage 1.  The exchanges (all-to-alls of P equal
+                         blocks of n0 n1 n2 / P^2 values) belong to the caller's communication library.
+                         Rejected with FFT3_ERR_INVALID_ARG: dist_ranks < 0, a stage outside 0..3, a
+                         stage without dist_ranks > 1 or dist_ranks > 1 without a stage;
+                         FFT3_ERR_UNSUPPORTED_SIZE: another decomposition than FFT3_SLAB_PENCIL or
+                         FFT3_AUTO, the split-BF16 dtype, batch > 1, a permuted layout, and for
+                         stages 1 and 3 a rank count that does not divide n0 */
+    int dist_stage;   /* see dist_ranks */
     int reserved[8];  /* test hooks of the failure-detection tests, 0 in normal use:
                          [0] = s + 1 makes the x tiles of slab s never signal their
                          completion, so the waits of its y tiles expire;

@@ -21,6 +21,10 @@ Multi-Dimensional DFTs"):
   explicit local buffers: ``rote_parallel_dft1``; applied along each
   dimension of a cube distributed cyclically on a 3D mesh (the volumetric
   decomposition of Fig. cuboid): ``volumetric3_sim``.
+* Section 2.4 -- the slab-pencil algorithm on a 1D grid of p processes
+  (Fig. 3dslabpencil): 2D DFTs of each rank's slabs, an all-to-all, the 1D
+  DFTs of each rank's z pencils, and the optional second exchange back to
+  slabs, simulated with p explicit local arrays: ``slab_pencil_sim``.
 * Section 2.4 -- the data rotations xyz -> yzx -> zxy of the
   pencil-pencil-pencil algorithm: ``rotation_dst_index``; the shuffled
   spectrum left when the last redistribution is dropped, and the blocked
@@ -316,6 +320,49 @@ def volumetric3_sim(x, n0: int, n1: int, n2: int, mesh=(2, 2, 2), splits=None,
             res[l], _, _ = rote_parallel_dft1(flat[l], a, b, p, sign)
         out = np.moveaxis(res.reshape(moved.shape), -1, axis)
     return np.ascontiguousarray(out)
+
+
+def slab_pencil_sim(local_in, n0: int, n1: int, n2: int, p: int, sign: int = FORWARD,
+                    natural: bool = False):
+    """Slab-pencil 3D DFT on a 1D grid of p processes (Section 2.4,
+    Fig. 3dslabpencil), each rank's data an explicit array (n0 fastest):
+
+    * slabs: rank r holds z in [r n2/p, (r+1) n2/p) as a (n2/p, n1, n0) array;
+    * pencils: rank r holds x in [r n0/p, (r+1) n0/p) as a (n2, n1, n0/p) array.
+
+    Forward (sign -1): ``local_in`` are the slabs; every rank applies the 2D
+    DFT to its slabs, an all-to-all gives rank r the columns of its x range
+    from every rank, every rank applies the 1D DFTs along z, and with
+    ``natural`` a second all-to-all returns the spectrum to slabs (otherwise
+    the spectrum stays in pencils, the last redistribution dropped).  Inverse
+    (sign +1): the same steps in reverse order, from pencils (or slabs with
+    ``natural``) to slabs.  Returns the list of the p output arrays."""
+    assert n0 % p == 0 and n2 % p == 0
+    xl, zl = n0 // p, n2 // p
+
+    def to_pencils(slabs):       # all-to-all: x range r of every rank's slabs to rank r
+        return [np.concatenate([slabs[s][:, :, r * xl:(r + 1) * xl] for s in range(p)], axis=0)
+                for r in range(p)]
+
+    def to_slabs(pencils):       # all-to-all: z range r of every rank's pencils to rank r
+        return [np.concatenate([pencils[s][r * zl:(r + 1) * zl] for s in range(p)], axis=2)
+                for r in range(p)]
+
+    def slab_dft(slabs):
+        return [fft3_dims(a, n0, n1, zl, 1, sign, (0, 1)).reshape(zl, n1, n0) for a in slabs]
+
+    def pencil_dft(pencils):
+        return [fft3_dims(a, xl, n1, n2, 1, sign, (2,)).reshape(n2, n1, xl) for a in pencils]
+
+    if sign == FORWARD:
+        data = [_c128(a).reshape(zl, n1, n0) for a in local_in]
+        data = pencil_dft(to_pencils(slab_dft(data)))
+        return to_slabs(data) if natural else data
+    if natural:
+        data = to_pencils([_c128(a).reshape(zl, n1, n0) for a in local_in])
+    else:
+        data = [_c128(a).reshape(n2, n1, xl) for a in local_in]
+    return slab_dft(to_slabs(pencil_dft(data)))
 
 
 # --------------------------------------------------------------------------- #

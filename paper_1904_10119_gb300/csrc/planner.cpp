@@ -816,6 +816,85 @@ int layout_position(int layout, int64_t n0, int64_t n1, int64_t n2, int64_t batc
     }
 }
 
+// Rank-local stages of the slab-pencil decomposition over a 1D grid of P
+// processes (Section 2.4): the slab stage (the rank's n2/P slabs, 2D DFT) and
+// the pencil stage (the z lines of the rank's n0/P x columns), with the
+// all-to-all between them left to the caller.  The packing for the exchange
+// is the slab stage's y-pass store: x = d*Xl + xl goes to block d as
+// [d][z_local][y][x_local], and the receiving rank's blocks [src][z_local][y][x_local]
+// are its natural [z][y][x_local] pencils, so no stage has a separate pack
+// or unpack.  The inverse runs the pencil stage first (its natural output is
+// already split by z into the blocks for each rank) and the slab stage last,
+// reading the packed blocks.
+static int build_dist_stage(Schedule *s, std::string *err)
+{
+    const int P = s->opts.dist_ranks, stage = s->opts.dist_stage;
+    const int64_t n0 = s->n0, n1 = s->n1, n2 = s->n2;
+    if (s->dtype != FFT3_C64_FP32 && s->dtype != FFT3_C128_FP64) {
+        *err = "the distributed slab-pencil stages run in complex64 or complex128";
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    }
+    if (s->batch != 1 || s->opts.layout != FFT3_LAYOUT_NATURAL) {
+        *err = "the distributed slab-pencil stages need batch 1 and the natural layout";
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    }
+    s->decomp = FFT3_SLAB_PENCIL;
+    const bool fwd = s->direction == FFT3_FORWARD;
+    PassPlan p;
+    int rc = FFT3_OK;
+    auto push = [&](int d, int n, const PassGeom &g, int src, int dst) {
+        if (!rc)
+            rc = make_line_pass(s, d, n, g, false, src, dst, &p, err);
+        if (!rc)
+            s->passes.push_back(p);
+    };
+    if (stage == 2) {
+        // z lines of the rank's (n0/P) x n1 x n2 pencils, natural on both sides
+        if (n2 > 1)
+            push(2, (int)n2, geom_natural(2, n0, n1, n2, 1), BUF_IN, BUF_OUT);
+        return rc;
+    }
+    if (n0 % P) {
+        *err = "the slab stage needs the rank count to divide n0";
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    }
+    const int64_t Xl = n0 / P;
+    if (stage == 3) {
+        // the second exchange's local side: packed blocks [d][z_local][y][x_local] to
+        // natural slabs (forward, after the exchange) or back (inverse, before it), as
+        // a pass of one-point lines: c = x_local, a = z_local*n1 + y, b = d
+        PassGeom g{};
+        g.C = Xl; g.A = n2 * n1; g.B = P;
+        g.ij = 1; g.ok = 1; g.ic = 1; g.oc = 1;
+        const int64_t pa = Xl, pb = n2 * n1 * Xl, na = n0, nb = Xl;
+        g.ia = fwd ? pa : na; g.ib = fwd ? pb : nb;
+        g.oa = fwd ? na : pa; g.ob = fwd ? nb : pb;
+        push(0, 1, g, BUF_IN, BUF_OUT);
+        return rc;
+    }
+    // y lines, columns xl of block d (a = z_local, b = d): natural n0 x n1 x n2 slabs on
+    // one side, the packed blocks [d][z_local][y][x_local] on the other
+    PassGeom nat{}, pk{};
+    nat.C = pk.C = Xl; nat.A = pk.A = n2; nat.B = pk.B = P;
+    nat.ij = n0; nat.ic = 1; nat.ia = n0 * n1; nat.ib = Xl;
+    pk.ij = Xl; pk.ic = 1; pk.ia = n1 * Xl; pk.ib = n2 * n1 * Xl;
+    PassGeom gy{};
+    gy.C = Xl; gy.A = n2; gy.B = P;
+    if (fwd) {
+        gy.ij = nat.ij; gy.ic = nat.ic; gy.ia = nat.ia; gy.ib = nat.ib;
+        gy.ok = pk.ij; gy.oc = pk.ic; gy.oa = pk.ia; gy.ob = pk.ib;
+        push(0, (int)n0, geom_natural(0, n0, n1, n2, 1), BUF_IN, BUF_WS);
+        push(1, (int)n1, gy, BUF_WS, BUF_OUT);
+    } else {
+        gy.ij = pk.ij; gy.ic = pk.ic; gy.ia = pk.ia; gy.ib = pk.ib;
+        gy.ok = nat.ij; gy.oc = nat.ic; gy.oa = nat.ia; gy.ob = nat.ib;
+        push(1, (int)n1, gy, BUF_IN, BUF_WS);
+        push(0, (int)n0, geom_natural(0, n0, n1, n2, 1), BUF_WS, BUF_OUT);
+    }
+    s->need_ws = true;
+    return rc;
+}
+
 int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int direction,
                    const fft3_options *opts, Schedule *out, std::string *err)
 {
@@ -853,6 +932,34 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
     s.dtype = dtype; s.direction = direction;
     if (opts)
         s.opts = *opts;
+    if (s.opts.dist_ranks < 0 || s.opts.dist_stage < 0 || s.opts.dist_stage > 3 ||
+        (s.opts.dist_ranks > 1) != (s.opts.dist_stage != 0)) {
+        *err = "dist_stage 1, 2 or 3 goes with dist_ranks > 1 (both 0 for a one-GPU plan)";
+        return FFT3_ERR_INVALID_ARG;
+    }
+    if (s.opts.dist_ranks > 1) {
+        if (decomp != FFT3_SLAB_PENCIL && decomp != FFT3_AUTO) {
+            *err = "rank-local stages exist for the slab-pencil decomposition";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        int rc = build_dist_stage(&s, err);
+        if (rc)
+            return rc;
+        if (s.passes.empty()) {
+            PassPlan p;
+            p.kind = PK_COPY;
+            p.src = BUF_IN;
+            p.dst = BUF_OUT;
+            p.g = PassGeom{};
+            p.g.C = (int64_t)n0 * n1 * n2;
+            p.g.A = 1; p.g.B = 1;
+            p.g.ij = 1; p.g.ok = 1;
+            p.threads = 256;
+            s.passes.push_back(p);
+        }
+        *out = std::move(s);
+        return FFT3_OK;
+    }
     if (dtype == FFT3_C128_FP64) {
         // complex128 runs every line transform as one pass of the runtime-radix
         // FP64 kernel: pencil-pencil-pencil in natural order (the slab-pencil
@@ -1221,6 +1328,7 @@ std::string Schedule::json() const
       << decomp_name(decomp) << "\",\"variant\":" << opts.variant << ",\"layout\":\""
       << (opts.layout == FFT3_LAYOUT_ROTATED ? "rotated" : opts.layout == FFT3_LAYOUT_PENCILS ? "pencils" : "natural")
       << "\""
+      << ",\"dist_ranks\":" << opts.dist_ranks << ",\"dist_stage\":" << opts.dist_stage
       << ",\"workspace_bytes\":" << (need_ws ? N * 8 : 0) << ",\"hbm_sweeps\":" << passes.size()
       << ",\"twiddle_entries\":" << tw_total << ",\"passes\":[";
     for (size_t i = 0; i < passes.size(); ++i) {

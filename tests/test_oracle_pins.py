@@ -267,6 +267,36 @@ def test_volumetric_simulation_equals_3d_dft(shape, mesh):
     assert oracle.rel_l2(got, oracle.fft3(x, n0, n1, n2)) < 1e-13
 
 
+@pytest.mark.parametrize("shape,p", [((4, 3, 2), 2), ((6, 2, 4), 2), ((4, 2, 4), 4)])
+def test_slab_pencil_simulation_against_brute_force(shape, p):
+    """Fig. 3dslabpencil on a 1D grid: the pencils rank r ends with are the x
+    range of rank r of the N^3 direct sum; with the second exchange, the z range
+    of rank r; the inverse brings either back to N times the slabs."""
+    n0, n1, n2 = shape
+    rng = np.random.default_rng(p + n0)
+    x = rng.standard_normal((n2, n1, n0)) + 1j * rng.standard_normal((n2, n1, n0))
+    slabs = [x[r * (n2 // p):(r + 1) * (n2 // p)] for r in range(p)]
+    ref = oracle.bruteforce3(x, n0, n1, n2).reshape(n2, n1, n0)
+    pen = oracle.slab_pencil_sim(slabs, n0, n1, n2, p)
+    nat = oracle.slab_pencil_sim(slabs, n0, n1, n2, p, natural=True)
+    for r in range(p):
+        assert np.allclose(pen[r], ref[:, :, r * (n0 // p):(r + 1) * (n0 // p)], atol=1e-12)
+        assert np.allclose(nat[r], ref[r * (n2 // p):(r + 1) * (n2 // p)], atol=1e-12)
+    N = n0 * n1 * n2
+    for got in (oracle.slab_pencil_sim(pen, n0, n1, n2, p, oracle.INVERSE),
+                oracle.slab_pencil_sim(nat, n0, n1, n2, p, oracle.INVERSE, natural=True)):
+        for r in range(p):
+            assert np.allclose(got[r] / N, slabs[r], atol=1e-12)
+
+
+def test_slab_pencil_simulation_one_rank_is_the_3d_dft():
+    x = synth.uniform_c64((1, 6, 5, 8), 3).reshape(6, 5, 8)
+    got = oracle.slab_pencil_sim([x], 8, 5, 6, 1)[0]
+    assert oracle.rel_l2(got, oracle.fft3(x, 8, 5, 6)) < 1e-14
+    with pytest.raises(AssertionError):
+        oracle.slab_pencil_sim([x], 8, 5, 6, 4)       # 4 does not divide n2 = 6
+
+
 def test_cyclic_and_blocked_owners():
     own, loc = oracle.cyclic_owner(8, 2)
     assert own.tolist() == [0, 1, 0, 1, 0, 1, 0, 1] and loc.tolist() == [0, 0, 1, 1, 2, 2, 3, 3]
