@@ -212,6 +212,12 @@ int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int d
  *              all z lines of every problem, one compile-time line kernel per
  *              line length: 8, 16, 24, 32, 40, 48, 64, 80, 96, 128), the
  *              pencil-pencil-pencil definition of Section 2.3 per problem.
+ *              The x lines of most lengths run in the registers of a few lanes
+ *              of a warp (warp shuffles between the lanes, 16-byte loads and
+ *              stores where a problem starts 16-byte aligned); in this mode the
+ *              radix_order field picks the x-line kernel of each length: 0 = the
+ *              length's default, r + 1 = candidate r (the shared-memory kernel,
+ *              then the warp-shuffle kernels), modulo their number.
  * The segmented mode runs when every tuning code has decomposition field 3, or
  * with FFT3_AUTO, tuning == NULL and at least 4 Mi values in the batch, provided
  * every line length has a compiled plan; otherwise the executor runs.

@@ -29,6 +29,8 @@ __global__ void k_roots(int n, int sign, const int64_t *m, int64_t count, double
 // One launch of the segmented mode: lines of length n along dimension dim.
 struct SegLaunch {
     int dim, n, kernel, lpt, threads, smem;
+    const void *func;  // the line kernel (k_seg, or k_segw for warp-shuffle x lines)
+    int warp, R, L;    // k_segw: N = R * L, L / 2 lanes per line
     int64_t ntiles;
     int64_t list_off, tstart_off, tcube_off; // offsets into the concatenated device tables
     int64_t tw_off, tw_len;
@@ -154,6 +156,31 @@ constexpr int kBatchBufTarget = 3072;
 // values on (every line length compiled in seg_plans.h).
 constexpr int64_t kSegMinElems = 1ll << 22;
 
+// The compiled kernels for lines of length n in the segmented mode (x lines:
+// contiguous; y and z lines: strided), in the
+// order the radix_order field of a tuning code selects them (field value
+// r + 1 -> entry r mod count): the shared-memory Stockham kernel, then the
+// warp-shuffle kernels in table order.  Field value 0 takes the length's
+// default: its warp-shuffle kernel marked default, else the shared-memory one.
+static std::vector<const SegKernel *> seg_line_candidates(int n, bool contiguous, const SegKernel **dflt)
+{
+    std::vector<const SegKernel *> c;
+    int cnt = 0;
+    const SegKernel *k = seg_kernels(contiguous, &cnt);
+    for (int i = 0; i < cnt; ++i)
+        if (k[i].n == n)
+            c.push_back(&k[i]);
+    *dflt = c.empty() ? nullptr : c[0];
+    k = segw_kernels(&cnt, contiguous);
+    for (int i = 0; i < cnt; ++i)
+        if (k[i].n == n) {
+            c.push_back(&k[i]);
+            if (k[i].dflt)
+                *dflt = &k[i];
+        }
+    return c;
+}
+
 // Decodes a tuning code (0 = defaults): items of roughly 2-4 thousand
 // elements, buffers of at most kBatchBufTarget elements unless a slab needs more.
 static void decode_tuning(int code, int n0, int n1, int n2, int *decomp, int *order, int *lpt, int *lpty,
@@ -221,7 +248,12 @@ int batch_describe(const BatchState *b, std::string *json)
                                                               : (int64_t)b->h_seg_list.size()) - L.list_off;
         o << (k ? "," : "") << "{\"dim\":" << L.dim << ",\"n\":" << L.n << ",\"lines_per_tile\":" << L.lpt
           << ",\"tiles\":" << L.ntiles << ",\"problems\":" << nprob << ",\"threads\":" << L.threads
-          << ",\"smem\":" << L.smem << "}";
+          << ",\"smem\":" << L.smem;
+        if (L.warp)
+            o << ",\"kernel\":\"warp_shuffle\",\"R\":" << L.R << ",\"L\":" << L.L;
+        else
+            o << ",\"kernel\":\"shared_memory\"";
+        o << "}";
     }
     o << "],\"classes\":[";
     bool first = true;
@@ -297,8 +329,6 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
             e = cudaLaunchKernelExC(&cfg, (const void *)&k_seg_all, params);
         }
     } else if (b->seg) {
-        int ccnt = 0, scnt = 0;
-        const SegKernel *skc = seg_kernels(true, &ccnt), *sks = seg_kernels(false, &scnt);
         for (const SegLaunch &L : b->seg_launches) {
             SegArgs s{};
             s.src = L.dim == 0 ? (const float2 *)in : (const float2 *)out;
@@ -313,8 +343,7 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
             s.tw_len = (int)L.tw_len;
             s.conj = b->conj;
             void *params[1] = {&s};
-            const void *f = (L.dim == 0 ? skc : sks)[L.kernel].func;
-            e = cudaLaunchKernel(f, L.grid, dim3(L.threads), params, L.smem, b->cap_stream);
+            e = cudaLaunchKernel(L.func, L.grid, dim3(L.threads), params, L.smem, b->cap_stream);
             if (e != cudaSuccess)
                 break;
         }
@@ -474,7 +503,7 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
         }
         if (b->seg)
             for (int i = 0; i < count; ++i)
-                b->tuning[i] = 3 | (b->seg1 ? items << 8 : 0);
+                b->tuning[i] = 3 | (tuning ? tuning[i] & (7 << 2) : 0) | (b->seg1 ? items << 8 : 0);
     }
     b->buf_elems = (bufmax + 31) / 32 * 32;
     // a third buffer stages the next item's first tile when it still fits
@@ -512,12 +541,23 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
             for (int i = 0; i < count; ++i)
                 byn[dims[3 * i + d]].push_back(i);
             for (auto &kv : byn) {
-                const int kidx = seg_find(d == 0, kv.first);
-                const SegKernel &K = (d == 0 ? skc : sks)[kidx];
+                // the radix_order field of the first problem's code picks among the
+                // shared-memory kernel and the warp-shuffle kernels of this length
+                // and direction (0 = the length's default, seg_line_candidates)
+                const int ord = tuning ? (tuning[kv.second[0]] >> 2) & 7 : 0;
+                int kidx = seg_find(d == 0, kv.first);
+                const SegKernel *dk = nullptr;
+                std::vector<const SegKernel *> cand = seg_line_candidates(kv.first, d == 0, &dk);
+                const SegKernel &K = ord ? *cand[(size_t)(ord - 1) % cand.size()] : *dk;
+                kidx = K.warp ? -1 : kidx;
                 SegLaunch L{};
                 L.dim = d;
                 L.n = kv.first;
                 L.kernel = kidx;
+                L.func = K.func;
+                L.warp = K.warp;
+                L.R = K.warp ? K.rad[0] : 0;
+                L.L = K.warp ? K.rad[1] : 0;
                 L.lpt = K.lpt;
                 L.threads = K.T * L.lpt;
                 L.list_off = (int64_t)seg_list.size();
@@ -544,7 +584,13 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
                 for (int r = 0; r < K.nrad; ++r)
                     lc.rad[r] = K.rad[r];
                 std::vector<int64_t> e;
-                line_twiddle_exponents(lc, &e);
+                if (K.warp) {
+                    // the warp-shuffle kernels read w_n^m, m < n, and keep their lanes' twiddles in registers
+                    for (int m = 0; m < K.n; ++m)
+                        e.push_back(m);
+                } else {
+                    line_twiddle_exponents(lc, &e);
+                }
                 if (e.empty())
                     e.push_back(0);
                 L.tw_off = tw_total;
@@ -553,7 +599,8 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
                 tw_total += L.tw_len;
                 exps.push_back(std::move(e));
                 exp_n.push_back(K.n);
-                L.smem = (int)(L.tw_len + (d == 0 ? L.lpt * pitch_b(K.n) : L.lpt * K.n)) * (int)sizeof(float2);
+                L.smem = K.warp ? 0
+                                : (int)(L.tw_len + (d == 0 ? L.lpt * pitch_b(K.n) : L.lpt * K.n)) * (int)sizeof(float2);
                 b->seg_launches.push_back(L);
             }
         }
@@ -777,7 +824,7 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
                        cudaMemcpyHostToDevice))
             return bail(fail(FFT3_ERR_CUDA, "uploading the segmented pass tables failed"));
         for (SegLaunch &L : b->seg_launches) {
-            const void *f = (L.dim == 0 ? skc : sks)[L.kernel].func;
+            const void *f = L.func;
             rc = prepare_func(f, L.smem);
             if (!rc)
                 rc = occupancy_grid(f, L.threads, L.smem, L.ntiles, dev, &L.grid);

@@ -320,6 +320,109 @@ struct Bfly<5> {
     }
 };
 
+// cos and sin of 2 pi m / 12 (multiples of 30 degrees) and of 2 pi m / 10
+// (multiples of 36 degrees): the twiddles of the composite butterflies below.
+constexpr double kS3 = 0.866025403784438646763723170752936183;  // cos(pi/6)
+constexpr double kC36 = 0.809016994374947424102293417182819059; // cos(pi/5)
+constexpr double kS36 = 0.587785252292473129168705954639072769; // sin(pi/5)
+constexpr double kC72 = 0.309016994374947424102293417182819059; // cos(2 pi/5)
+constexpr double kS72 = 0.951056516295153572116439333379382143; // sin(2 pi/5)
+
+__host__ __device__ constexpr double cos12(int m)
+{
+    m = ((m % 12) + 12) % 12;
+    return m == 0 ? 1.0 : m == 1 ? kS3 : m == 2 ? 0.5 : m == 3 ? 0.0 : m == 4 ? -0.5 : m == 5 ? -kS3
+         : m == 6 ? -1.0 : m == 7 ? -kS3 : m == 8 ? -0.5 : m == 9 ? 0.0 : m == 10 ? 0.5 : kS3;
+}
+__host__ __device__ constexpr double sin12(int m) { return cos12(m - 3); }
+__host__ __device__ constexpr double cos10(int m)
+{
+    m = ((m % 10) + 10) % 10;
+    return m == 0 ? 1.0 : m == 1 ? kC36 : m == 2 ? kC72 : m == 3 ? -kC72 : m == 4 ? -kC36 : m == 5 ? -1.0
+         : m == 6 ? -kC36 : m == 7 ? -kC72 : m == 8 ? kC72 : kC36;
+}
+__host__ __device__ constexpr double sin10(int m)
+{
+    m = ((m % 10) + 10) % 10;
+    return m == 0 || m == 5 ? 0.0 : m == 1 || m == 4 ? kS36 : m == 2 || m == 3 ? kS72 : m == 6 || m == 9 ? -kS36
+                                                                                        : -kS72;
+}
+
+// a * w_N^M for N in {6, 10, 12} (and the powers of two of mul_w), M known at
+// compile time.
+template <int N, int M, class C>
+__device__ __forceinline__ C mul_wn(C a)
+{
+    if constexpr (16 % N == 0) {
+        return mul_w<N, M>(a);
+    } else {
+        static_assert(N == 6 || N == 10 || N == 12, "composite twiddles exist for 6, 10 and 12 points");
+        using X = Cx<C>;
+        using S = typename X::S;
+        constexpr int m = ((M % N) + N) % N;
+        if constexpr (m == 0) {
+            return a;
+        } else if constexpr (N != 10 && (m * (12 / N)) % 3 == 0) {
+            return mul_w<4, (m * (12 / N)) / 3>(a); // multiples of 90 degrees
+        } else {
+            constexpr S c = (S)(N == 10 ? cos10(m) : cos12(m * (12 / N)));
+            constexpr S s = (S)(N == 10 ? sin10(m) : sin12(m * (12 / N)));
+            return X::make(X::fma_(a.x, c, a.y * s), X::fma_(a.y, c, -a.x * s));
+        }
+    }
+}
+
+// DFT_{A B} in registers by Eq. ct with n0 = A, n1 = B: DFT_B on x[i0 + A i1]
+// for each i0, twiddle w_{AB}^{i0 k1}, DFT_A across i0, output y[k1 + B k0].
+template <int A, int B, int I>
+struct CtTwiddle {
+    template <class C>
+    __device__ __forceinline__ static void run(C (*t)[B])
+    {
+        if constexpr (I < A * B) {
+            constexpr int i0 = I / B, k1 = I % B;
+            if constexpr (i0 > 0 && k1 > 0)
+                t[i0][k1] = mul_wn<A * B, i0 * k1>(t[i0][k1]);
+            CtTwiddle<A, B, I + 1>::run(t);
+        }
+    }
+};
+
+template <int A, int B>
+struct BflyCt {
+    template <class C>
+    __device__ __forceinline__ static void run(C *v)
+    {
+        C t[A][B];
+#pragma unroll
+        for (int i0 = 0; i0 < A; ++i0) {
+#pragma unroll
+            for (int i1 = 0; i1 < B; ++i1)
+                t[i0][i1] = v[i0 + A * i1];
+            Bfly<B>::run(t[i0]);
+        }
+        CtTwiddle<A, B, 0>::run(t);
+#pragma unroll
+        for (int k1 = 0; k1 < B; ++k1) {
+            C c[A];
+#pragma unroll
+            for (int i0 = 0; i0 < A; ++i0)
+                c[i0] = t[i0][k1];
+            Bfly<A>::run(c);
+#pragma unroll
+            for (int k0 = 0; k0 < A; ++k0)
+                v[k1 + B * k0] = c[k0];
+        }
+    }
+};
+
+template <>
+struct Bfly<6> : BflyCt<2, 3> {};
+template <>
+struct Bfly<10> : BflyCt<2, 5> {};
+template <>
+struct Bfly<12> : BflyCt<4, 3> {};
+
 // ------------------------------------------------------ stage indexing -- //
 // Shared-memory position of intra-line index `pos` for the line-major layout:
 // one padding slot per 16 keeps the first stages' strided writes free of

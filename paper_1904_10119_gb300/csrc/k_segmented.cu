@@ -20,6 +20,7 @@
 #include "batched.h"
 #include "pass_kernels.cuh"
 #include "seg_plans.h"
+#include "warp_fft.cuh"
 
 namespace fft3 {
 
@@ -72,6 +73,79 @@ __global__ void __launch_bounds__(T *LPT) k_seg(SegArgs a)
 
 static const SegKernel g_seg_contig[] = {FFT3_SEG_PLANS_CONTIG(FFT3_SEG_ROW_C)};
 static const SegKernel g_seg_strided[] = {FFT3_SEG_PLANS_STRIDED(FFT3_SEG_ROW_S)};
+
+// x lines by the warp-shuffle line transform: L / 2 lanes per line, 512 / L
+// lines per 256-thread tile, every line in registers (no shared memory, no
+// block barrier); the lanes' twiddles are read once from the table w_N^m.
+template <int N, int R, int L>
+__global__ void __launch_bounds__(256) k_segw(SegArgs a)
+{
+    using WL = WarpLine<N, R, L>;
+    constexpr int LPT = 256 / WL::W;
+    const int u = (int)threadIdx.x % WL::W, l = (int)threadIdx.x / WL::W;
+    typename WL::Tw tw;
+    WL::load_tw(tw, a.tw, u);
+    const bool conj = a.conj != 0;
+    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const int slot = a.tcube[tile];
+        const BatchCube &cb = a.cubes[a.list[slot]];
+        const int64_t c = (tile - a.tstart[slot]) * LPT + l;
+        const bool valid = c < (int64_t)cb.n1 * cb.n2;
+        const float2 *ip = a.src + cb.off + (valid ? c * N : 0);
+        float2 *op = a.out + cb.off + (valid ? c * N : 0);
+        float2 v[2][R];
+        WL::load(v, ip, u, valid, conj);
+        WL::run(v, tw, u);
+        WL::store(v, op, u, valid, conj);
+    }
+}
+
+// y and z lines (columns) by the same transform: lane group l of a tile is
+// column c0 + l, the L / 2 lanes of a column on different rows of it.
+template <int N, int R, int L>
+__global__ void __launch_bounds__(256) k_segw_s(SegArgs a)
+{
+    using WL = WarpLine<N, R, L>;
+    constexpr int LPT = 256 / WL::W;
+    const int u = (int)threadIdx.x % WL::W, l = (int)threadIdx.x / WL::W;
+    typename WL::Tw tw;
+    WL::load_tw(tw, a.tw, u);
+    const bool conj = a.conj != 0;
+    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const int slot = a.tcube[tile];
+        const BatchCube &cb = a.cubes[a.list[slot]];
+        const int64_t n0 = cb.n0, n1 = cb.n1, n2 = cb.n2;
+        const int64_t c = (tile - a.tstart[slot]) * LPT + l;
+        int64_t lines, first, es;
+        if (a.dim == 1) {
+            lines = n0 * n2; first = (c / n0) * n0 * n1 + c % n0; es = n0;
+        } else {
+            lines = n0 * n1; first = c; es = n0 * n1;
+        }
+        const bool valid = c < lines;
+        const float2 *ip = a.src + cb.off + (valid ? first : 0);
+        float2 *op = a.out + cb.off + (valid ? first : 0);
+        float2 v[2][R];
+        WL::load_strided(v, ip, es, u, valid, conj);
+        WL::run(v, tw, u);
+        WL::store_strided(v, op, es, u, valid, conj);
+    }
+}
+
+#define FFT3_SEGW_ROW(N, R, L, D) {N, L / 2, 512 / L, 2, {R, L}, (const void *)&k_segw<N, R, L>, 1, D},
+#define FFT3_SEGW_ROW_S(N, R, L, D) {N, L / 2, 512 / L, 2, {R, L}, (const void *)&k_segw_s<N, R, L>, 1, D},
+static const SegKernel g_segw[] = {FFT3_SEGW_PLANS(FFT3_SEGW_ROW)};
+static const SegKernel g_segw_s[] = {FFT3_SEGW_PLANS_STRIDED(FFT3_SEGW_ROW_S)};
+
+const SegKernel *segw_kernels(int *count, bool contiguous)
+{
+    if (!contiguous) {
+        *count = (int)(sizeof(g_segw_s) / sizeof(g_segw_s[0]));
+        return g_segw_s;
+    }
+    *count = (int)(sizeof(g_segw) / sizeof(g_segw[0]));
+    return g_segw;
+}
 
 // ---------------------------------------------------------------------------
 // The whole batch in one persistent cooperative launch (k_seg_all): the same

@@ -37,14 +37,71 @@ namespace fft3 {
     X(96, 8, 32, 4, 8, 3)         \
     X(128, 8, 32, 16, 8)
 
+// Contiguous (x) lines by the warp-shuffle line transform (warp_fft.cuh):
+// X(N, R, L, D) with N = R * L, L / 2 lanes per line, 256-thread blocks of
+// 512 / L lines and no shared memory.  D = 1 marks the default kernel of a
+// length (the faster of its rows and the shared-memory kernel, timed on the
+// 4096-cube workload's x lengths: 0.45-0.48 ms against 0.49-0.58 ms per
+// 48 Mi-value batch); lengths without one keep the shared-memory kernel (64
+// and 128 points, where it measured 1% faster).  Each length's first row is
+// its faster warp-shuffle kernel.
+#define FFT3_SEGW_PLANS(X) \
+    X(8, 4, 2, 1)           \
+    X(16, 4, 4, 1)          \
+    X(16, 8, 2, 0)          \
+    X(24, 3, 8, 1)          \
+    X(24, 6, 4, 0)          \
+    X(32, 4, 8, 1)          \
+    X(32, 8, 4, 0)          \
+    X(40, 10, 4, 1)         \
+    X(40, 5, 8, 0)          \
+    X(48, 6, 8, 1)          \
+    X(48, 12, 4, 0)         \
+    X(64, 8, 8, 0)          \
+    X(64, 16, 4, 0)         \
+    X(80, 10, 8, 1)         \
+    X(80, 5, 16, 0)         \
+    X(96, 6, 16, 1)         \
+    X(96, 12, 8, 0)         \
+    X(128, 8, 16, 0)        \
+    X(128, 16, 8, 0)
+
+// y and z lines (columns) by the warp-shuffle transform, the same rows.  None
+// is a default: on the 4096-cube workload they measured slower than the
+// shared-memory column kernels at 24-128 points (by 0-45%; within 3-9% faster
+// at 16 and 40 points), so they run only when a tuning code asks for them.
+#define FFT3_SEGW_PLANS_STRIDED(X) \
+    X(8, 4, 2, 0)                   \
+    X(16, 4, 4, 0)                  \
+    X(16, 8, 2, 0)                  \
+    X(24, 3, 8, 0)                  \
+    X(24, 6, 4, 0)                  \
+    X(32, 4, 8, 0)                  \
+    X(32, 8, 4, 0)                  \
+    X(40, 10, 4, 0)                 \
+    X(40, 5, 8, 0)                  \
+    X(48, 6, 8, 0)                  \
+    X(48, 12, 4, 0)                 \
+    X(64, 8, 8, 0)                  \
+    X(64, 16, 4, 0)                 \
+    X(80, 10, 8, 0)                 \
+    X(80, 5, 16, 0)                 \
+    X(96, 6, 16, 0)                 \
+    X(96, 12, 8, 0)                 \
+    X(128, 8, 16, 0)                \
+    X(128, 16, 8, 0)
+
 struct SegKernel {
     int n, T, lpt, nrad;
     int rad[4];
     const void *func;
+    int warp; // 1: warp-shuffle kernel, T = lanes per line, rad = {R, L}, twiddles w_n^m (m < n)
+    int dflt; // warp-shuffle kernel that is the default for its length
 };
 
 // The compiled lists (device translation unit) and their sizes.
 const SegKernel *seg_kernels(bool contiguous, int *count);
+const SegKernel *segw_kernels(int *count, bool contiguous = true);
 
 // The one-launch executor (k_seg_all): its line kernel kidx is the index in
 // the contiguous list, or the count of that list plus the index in the

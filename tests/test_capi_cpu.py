@@ -399,6 +399,18 @@ def test_schedule_many_modes_and_segmented_tables():
         assert L["tiles"] == int(sum((int(v) + lpt - 1) // lpt for v in lines))
     assert [L["dim"] for L in launches] == sorted(L["dim"] for L in launches)  # x, then y, then z
     assert all(c["tuning"] == 3 for c in d["classes"])
+    # x lines: the warp-shuffle kernels (L / 2 lanes per line, 512 / L lines per tile, no shared
+    # memory) except at 64 and 128 points; y and z lines: the shared-memory column kernels
+    for L in launches:
+        if L["dim"] == 0 and L["n"] not in (64, 128):
+            assert L["kernel"] == "warp_shuffle" and L["R"] * L["L"] == L["n"]
+            assert L["lines_per_tile"] == 512 // L["L"] and L["smem"] == 0 and L["threads"] == 256
+        else:
+            assert L["kernel"] == "shared_memory"
+    # the radix_order field walks the candidates: shared memory first, then the warp-shuffle rows
+    for r, kinds in ((0, {"shared_memory"}), (1, {"warp_shuffle"})):
+        dd = fft3.fft3_plan_schedule_many(dims, offs, tuning=[fft3.tune_code(3, r)] * len(dims))
+        assert {L["kernel"] for L in dd["segmented_launches"]} == kinds
     small = synth.batched_dims(6, 7)
     assert fft3.fft3_plan_schedule_many(small, _batch_layout(small))["mode"] == "executor"
     for kw in ({"decomposition": fft3.FFT3_PENCIL3}, {"tuning": [0] * len(dims)}):

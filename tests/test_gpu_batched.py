@@ -132,6 +132,34 @@ def test_segmented_passes_every_problem(direction):
     assert desc["mode"] == "segmented"
     classes = sum(len(set(int(v) for v in dims[:, d])) for d in range(3))
     assert desc["kernel_launches"] == classes
+    # default x kernels: warp shuffles except at 64 and 128 points
+    for L in desc["segmented_launches"]:
+        want = "shared_memory" if L["dim"] > 0 or L["n"] in (64, 128) else "warp_shuffle"
+        assert L["kernel"] == want, L
+    for off, d in zip(offs, dims):
+        _check_problem(x, got, int(off), d, direction)
+
+
+@pytest.mark.parametrize("cand", [1, 2])
+@pytest.mark.parametrize("gap", [0, 5])
+@pytest.mark.parametrize("direction", [fft3.FFT3_FORWARD, fft3.FFT3_INVERSE])
+def test_segmented_warp_shuffle_lines(cand, gap, direction):
+    """Every line of the segmented passes by the warp-shuffle kernels (the
+    radix_order field of the codes picks candidate `cand` of each length after
+    the shared-memory kernel, for x lines and for y and z columns): every
+    length, problems at 16-byte aligned offsets (128-bit loads and stores) and
+    at odd offsets (8-byte fallback), every problem against the oracle."""
+    xs = [8, 16, 24, 32, 40, 48, 64, 80, 96, 128]
+    dims = np.array([[n, xs[(3 * i) % 4], 8 if i % 2 else 16] for i, n in enumerate(xs)] +
+                    [[n, 16, 24] for n in xs[1:8]] + [[40, 8, 96], [96, 24, 8]])
+    offs, total = _layout(dims, gap=gap)
+    code = fft3.tune_code(3, cand)
+    x, got, desc = _run(dims, offs, total, direction=direction, tuning=[code] * len(dims), seed=3 + cand)
+    xl = [L for L in desc["segmented_launches"] if L["dim"] == 0]
+    # 8-point lines have one warp-shuffle kernel, so candidate 2 wraps to the shared-memory one
+    assert len(xl) == len(xs)
+    assert all(L["kernel"] == "warp_shuffle" for L in desc["segmented_launches"] if cand == 1 or L["n"] != 8)
+    assert all(L["R"] * L["L"] == L["n"] for L in desc["segmented_launches"] if L["kernel"] == "warp_shuffle")
     for off, d in zip(offs, dims):
         _check_problem(x, got, int(off), d, direction)
 
