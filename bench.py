@@ -547,13 +547,13 @@ def size_table(fft3, synth, torch, sizes, decomp_map):
 
 
 def dist_table(fft3, torch, n, hbm, ranks=(2, 4, 8), reps=10):
-    """Local work of one rank of the slab-pencil decomposition on a 1D grid of
-    P processes (n^3 forward): the slab stage on n/P slabs (x pass, y pass
-    storing the blocks packed for the all-to-all) and the pencil stage on the
-    n/P-wide x range (z pass), each timed with CUDA events over `reps`
-    back-to-back executions on this GPU.  The all-to-all between them (one
-    exchange of (P-1)/P of the rank's data) runs over the interconnect and is
-    not part of these numbers."""
+    """Local work of one rank of the distributed decompositions (n^3 forward),
+    each stage timed with CUDA events over `reps` back-to-back executions on
+    this GPU.  Slab-pencil on a 1D grid of P processes: the slab stage on n/P
+    slabs (x pass, y pass storing the blocks packed for the all-to-all) and the
+    pencil stage on the n/P-wide x range (z pass).  Pencil-pencil-pencil on a
+    Py x Pz grid: its x, y and z stages.  The all-to-alls between stages run
+    over the interconnect and are not part of these numbers."""
     table = {}
     st = torch.cuda.current_stream()
     for P in ranks:
@@ -583,6 +583,35 @@ def dist_table(fft3, torch, n, hbm, ranks=(2, 4, 8), reps=10):
         row["local_hbm_frac_of_measured"] = 3 * 2 * 8 * loc / (ms * 1e-3) / 1e9 / hbm
         row["exchange_bytes_per_rank"] = 8 * loc * (P - 1) // P
         table[f"P{P}"] = row
+        del a, b
+    # pencil-pencil-pencil on a Py x Pz grid: the three stages of one rank
+    for Py, Pz in ((2, 2), (4, 2)):
+        loc = n * n * n // (Py * Pz)
+        a = torch.empty(loc, dtype=torch.complex64, device="cuda")
+        a.real.uniform_(-1, 1)
+        a.imag.uniform_(-1, 1)
+        b = torch.empty_like(a)
+        row = {}
+        dims = {1: (n, n // Py, n // Pz), 2: (n // Py, n, n // Pz), 3: (n // Py, n // Pz, n)}
+        for stage, d in dims.items():
+            p = fft3.Plan(*d, 1, fft3.FFT3_PENCIL3, fft3.FFT3_FORWARD, dist_ranks=Py, dist_ranks2=Pz,
+                          dist_stage=stage)
+            for _ in range(3):
+                p.execute(a, b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                p.execute(a, b)
+            e1.record(st)
+            torch.cuda.synchronize()
+            assert p.check() == 0, fft3.last_error()
+            row[f"stage{stage}_ms"] = e0.elapsed_time(e1) / reps
+            row[f"stage{stage}_kind"] = p.describe()["passes"][0]["kind"]
+            p.close()
+        ms = row["stage1_ms"] + row["stage2_ms"] + row["stage3_ms"]
+        row["local_ms"] = ms
+        row["local_hbm_frac_of_measured"] = 3 * 2 * 8 * loc / (ms * 1e-3) / 1e9 / hbm
+        table[f"pencil3_{Py}x{Pz}"] = row
         del a, b
     return table
 

@@ -179,6 +179,25 @@ typedef struct fft3_options {
                          FFT3_AUTO, the split-BF16 dtype, batch > 1, a permuted layout, and for
                          stages 1 and 3 a rank count that does not divide n0 */
     int dist_stage;   /* see dist_ranks */
+    int dist_ranks2;  /* FFT3_PENCIL3 with dist_stage 1..3: a rank-local plan of the pencil-pencil-pencil
+                         decomposition on a Py x Pz grid of processes (Section 2.4), Py = dist_ranks >= 1,
+                         Pz = dist_ranks2 >= 1 (0 = 1), Py Pz > 1.  Rank (p, q) holds at first the x lines
+                         of y in [p n1/Py, (p+1) n1/Py) and z in [q n2/Pz, (q+1) n2/Pz); after the first
+                         all-to-all (among the Py ranks of its row q) the y lines of x in
+                         [p n0/Py, (p+1) n0/Py), z as before; after the second (among the Pz ranks of its
+                         column p) the z lines of that x range and of y in [q n1/Pz, (q+1) n1/Pz), its brick
+                         of the spectrum (the last redistribution left out).  Forward stages:
+                         1 = x lines: create with (n0, n1/Py, n2/Pz); `in` natural [z][y][x]; `out` packed
+                             for the row exchange as [dest][x_local][z][y] (the rotated store of the pass);
+                         2 = y lines: create with (n0/Py, n1, n2/Pz); `in` the row exchange's receive
+                             buffer [src][x][z][y_local] (each line read in its Py runs); `out` packed for
+                             the column exchange as [dest][y_local][z][x];
+                         3 = z lines: create with (n0/Py, n1/Pz, n2); `in` the column exchange's receive
+                             buffer [src][y][z_local][x]; `out` the brick in natural order [z][y][x].
+                         The inverse takes the same plans in the order 3, 2, 1 (each storing what the
+                         previous forward stage read).  Needs Py | n0, Py | n1, Pz | n1, Pz | n2
+                         (FFT3_ERR_UNSUPPORTED_SIZE otherwise); these stages run the runtime-radix kernels
+                         where a line is split over exchange blocks */
     int reserved[8];  /* test hooks of the failure-detection tests, 0 in normal use:
                          [0] = s + 1 makes the x tiles of slab s never signal their
                          completion, so the waits of its y tiles expire;

@@ -25,6 +25,10 @@ Multi-Dimensional DFTs"):
   (Fig. 3dslabpencil): 2D DFTs of each rank's slabs, an all-to-all, the 1D
   DFTs of each rank's z pencils, and the optional second exchange back to
   slabs, simulated with p explicit local arrays: ``slab_pencil_sim``.
+* Section 2.4 -- the pencil-pencil-pencil algorithm on a py x pz grid
+  (Fig. 3dpencilpencil): x DFTs, an all-to-all within each row of the grid,
+  y DFTs, an all-to-all within each column, z DFTs, the spectrum left in
+  bricks (the last redistribution dropped): ``pencil3_sim``.
 * Section 2.4 -- the data rotations xyz -> yzx -> zxy of the
   pencil-pencil-pencil algorithm: ``rotation_dst_index``; the shuffled
   spectrum left when the last redistribution is dropped, and the blocked
@@ -363,6 +367,45 @@ def slab_pencil_sim(local_in, n0: int, n1: int, n2: int, p: int, sign: int = FOR
     else:
         data = [_c128(a).reshape(n2, n1, xl) for a in local_in]
     return slab_dft(to_slabs(pencil_dft(data)))
+
+
+def pencil3_sim(local_in, n0: int, n1: int, n2: int, py: int, pz: int, sign: int = FORWARD):
+    """Pencil-pencil-pencil 3D DFT on a py x pz grid of processes (Section 2.4,
+    Fig. 3dpencilpencil), rank r = q py + p holding an explicit array (n0
+    fastest):
+
+    * pencils: rank (p, q) holds y in [p n1/py, (p+1) n1/py) and z in
+      [q n2/pz, (q+1) n2/pz), all x, as a (n2/pz, n1/py, n0) array;
+    * bricks: rank (p, q) holds x in [p n0/py, (p+1) n0/py), y in
+      [q n1/pz, (q+1) n1/pz), all z, as a (n2, n1/pz, n0/py) array.
+
+    Forward (sign -1): pencils in; x DFTs; an all-to-all among the ranks of
+    each row q gives rank (p, q) the x range p of its row's y ranges; y DFTs;
+    an all-to-all among the ranks of each column p gives it the y range q of
+    its column's z ranges; z DFTs; bricks out.  Inverse (sign +1): the same
+    steps in reverse order, bricks in, pencils out.  Returns the list of
+    outputs in rank order."""
+    assert n0 % py == 0 and n1 % py == 0 and n1 % pz == 0 and n2 % pz == 0
+    xl, yl, y2, zl = n0 // py, n1 // py, n1 // pz, n2 // pz
+    ranks = [(r % py, r // py) for r in range(py * pz)]
+    idx = {pq: r for r, pq in enumerate(ranks)}
+
+    def dft(a, axis):               # 1D DFTs along numpy axis `axis` of a 3D array
+        a = np.ascontiguousarray(a)
+        d2, d1, d0 = a.shape
+        return fft3_dims(a, d0, d1, d2, 1, sign, (2 - axis,)).reshape(a.shape)
+
+    if sign == FORWARD:
+        a = [dft(_c128(t).reshape(zl, yl, n0), 2) for t in local_in]
+        b = [dft(np.concatenate([a[idx[(s, q)]][:, :, p * xl:(p + 1) * xl] for s in range(py)], axis=1), 1)
+             for p, q in ranks]
+        return [dft(np.concatenate([b[idx[(p, s)]][:, q * y2:(q + 1) * y2, :] for s in range(pz)], axis=0), 0)
+                for p, q in ranks]
+    c = [dft(_c128(t).reshape(n2, y2, xl), 0) for t in local_in]
+    b = [dft(np.concatenate([c[idx[(p, s)]][q * zl:(q + 1) * zl] for s in range(pz)], axis=1), 1)
+         for p, q in ranks]
+    return [dft(np.concatenate([b[idx[(s, q)]][:, p * yl:(p + 1) * yl, :] for s in range(py)], axis=2), 2)
+            for p, q in ranks]
 
 
 # --------------------------------------------------------------------------- #

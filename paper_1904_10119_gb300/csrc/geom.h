@@ -14,7 +14,24 @@ struct PassGeom {
     // 0: output element k of a line at k*ok; > 0: at (k/16)*oblk + (k%16)*ok
     // (a line stored in blocks of 16, as the 16-column blocked layouts need)
     int64_t oblk;
+    // Lines split into runs over blocks (the blocks an all-to-all exchanges):
+    // ijb > 0: input element j at (j/ijb)*iblk + (j%ijb)*ij; okb > 0: output
+    // element k at (k/okb)*oblk + (k%okb)*ok.  Only the runtime-radix kernels
+    // (k_pass_g, k_pass_g64) and the layout probe take them.
+    int64_t ijb, iblk, okb;
 };
+
+// Offset of element j of a line under the input (output) index of g.
+__host__ __device__ __forceinline__ int64_t geom_in_elem(const PassGeom &g, int64_t j)
+{
+    return g.ijb > 0 ? (j / g.ijb) * g.iblk + (j % g.ijb) * g.ij : j * g.ij;
+}
+__host__ __device__ __forceinline__ int64_t geom_out_elem(const PassGeom &g, int64_t k)
+{
+    return g.okb > 0 ? (k / g.okb) * g.oblk + (k % g.okb) * g.ok
+         : g.oblk   ? (k >> 4) * g.oblk + (k & 15) * g.ok
+                    : k * g.ok;
+}
 
 // Error flag bits written by device code (read back by fft3_plan_check).
 enum : unsigned {

@@ -40,7 +40,7 @@ __device__ __forceinline__ void pass_g_body(const PassArgs &a, const C *in, C *o
             else { l = e % lpt; j = e / lpt; }
             C v = Cx<C>::make(0, 0);
             if (l < nval)
-                v = ib[l * a.g.ic + (int64_t)j * a.g.ij];
+                v = ib[l * a.g.ic + geom_in_elem(a.g, j)];
             b0[l * P + padpos(j)] = conj ? cconj(v) : v;
         }
         __syncthreads();
@@ -52,7 +52,7 @@ __device__ __forceinline__ void pass_g_body(const PassArgs &a, const C *in, C *o
             else { l = e % lpt; k = e / lpt; }
             if (l < nval) {
                 C v = res[l * P + padpos(k)];
-                ob[l * a.g.oc + (int64_t)k * a.g.ok] = conj ? cconj(v) : v;
+                ob[l * a.g.oc + geom_out_elem(a.g, k)] = conj ? cconj(v) : v;
             }
         }
     }
@@ -117,8 +117,8 @@ __global__ void k_probe_pass(PassArgs a)
         const int64_t c = r % a.g.C;
         r /= a.g.C;
         const int64_t aa = r % a.g.A, b = r / a.g.A;
-        const int64_t jo = a.g.oblk ? (j >> 4) * a.g.oblk + (j & 15) * a.g.ok : j * a.g.ok;
-        a.out[jo + c * a.g.oc + aa * a.g.oa + b * a.g.ob] = a.in[j * a.g.ij + c * a.g.ic + aa * a.g.ia + b * a.g.ib];
+        a.out[geom_out_elem(a.g, j) + c * a.g.oc + aa * a.g.oa + b * a.g.ob] =
+            a.in[geom_in_elem(a.g, j) + c * a.g.ic + aa * a.g.ia + b * a.g.ib];
     }
 }
 

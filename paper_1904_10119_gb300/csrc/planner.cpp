@@ -367,6 +367,24 @@ static int make_line_pass(Schedule *s, int d, int n, const PassGeom &g, bool rot
         return rc;
     const bool contig_in = g.ij == 1;
     const bool strided_in = g.ic == 1 && g.oc == 1;
+    if (g.ijb > 0 || g.okb > 0) {
+        // lines in runs over exchange blocks: the runtime-radix kernels
+        rc = choose_line(n, order, false, &p.line, err);
+        if (rc)
+            return rc;
+        const bool c128 = s->dtype == FFT3_C128_FP64;
+        p.kind = c128 ? PK_G64 : PK_G;
+        p.tw_seg[0] = line_seg(s, p.line);
+        generic_launch_shape_elem(n, p.line.T, !contig_in, (int)s->tw[p.tw_seg[0]].m.size(), c128 ? 16 : 8,
+                                  &p.lpt, &p.threads, &p.smem_bytes);
+        if (p.smem_bytes > kSmemLimit) {
+            *err = "pass needs more shared memory than a block has";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        set_tiles(&p);
+        *out = p;
+        return FFT3_OK;
+    }
     // tc_stages 0: the tcgen05 radix-32 kernels for 1024-point lines, the first
     // shared-memory radix-16 stage (mma.sync) elsewhere; 1, 2: the mma.sync
     // radix-16 modes; 3: the first shared-memory radix-16 stage everywhere
@@ -895,6 +913,89 @@ static int build_dist_stage(Schedule *s, std::string *err)
     return rc;
 }
 
+// Rank-local stages of the pencil-pencil-pencil decomposition on a Py x Pz
+// grid (Section 2.4): each stage is one pass of one dimension's lines whose
+// store packs the blocks of the next all-to-all (the x pass by its rotated
+// store xyz -> yzx, the y pass by storing y slowest), while the line the next
+// stage reads arrives in Py (or Pz) runs, one per sending rank: the
+// two-level line index of the pass geometry (ijb, iblk) reads it in place.
+// Sizes: Xl = n0/Py, Yl = n1/Py, Yl2 = n1/Pz, Zl = n2/Pz; the plan's own
+// dims are the rank's local array (stage 1: n0 x Yl x Zl, stage 2:
+// Xl x n1 x Zl, stage 3: Xl x Yl2 x n2).  The inverse stores what the
+// forward stage reads and reads what it stores.
+static int build_dist_ppp(Schedule *s, std::string *err)
+{
+    const int Py = s->opts.dist_ranks, Pz = std::max(1, s->opts.dist_ranks2), stage = s->opts.dist_stage;
+    const int64_t n0 = s->n0, n1 = s->n1, n2 = s->n2;
+    if (s->dtype != FFT3_C64_FP32 && s->dtype != FFT3_C128_FP64) {
+        *err = "the distributed pencil-pencil-pencil stages run in complex64 or complex128";
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    }
+    if (s->batch != 1 || s->opts.layout != FFT3_LAYOUT_NATURAL) {
+        *err = "the distributed pencil-pencil-pencil stages need batch 1 and the natural layout";
+        return FFT3_ERR_UNSUPPORTED_SIZE;
+    }
+    s->decomp = FFT3_PENCIL3;
+    const bool fwd = s->direction == FFT3_FORWARD;
+    PassPlan p;
+    int rc = FFT3_OK;
+    auto push = [&](int d, int n, const PassGeom &g, bool rot) {
+        if (!rc)
+            rc = make_line_pass(s, d, n, g, rot, BUF_IN, BUF_OUT, &p, err);
+        if (!rc)
+            s->passes.push_back(p);
+    };
+    PassGeom g{};
+    if (stage == 1) { // local n0 x Yl x Zl
+        if (n0 % Py) {
+            *err = "the x stage needs Py to divide n0";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        const int64_t Yl = n1, Zl = n2;
+        if (fwd) {
+            push(0, (int)n0, geom_rotate(0, n0, Yl, Zl, 1), true); // [x][z][y]: x blocks contiguous
+        } else {
+            g.C = Yl; g.A = Zl; g.B = 1;
+            g.ij = Zl * Yl; g.ic = 1; g.ia = Yl;
+            g.ok = 1; g.oc = n0; g.oa = n0 * Yl;
+            push(0, (int)n0, g, false);
+        }
+    } else if (stage == 2) { // local Xl x n1 x Zl
+        if (n1 % Py || n1 % Pz) {
+            *err = "the y stage needs Py and Pz to divide n1";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        const int64_t Xl = n0, Zl = n2, Yl = n1 / Py;
+        g.C = Xl; g.A = Zl; g.B = 1;
+        if (fwd) {
+            // in: [src][x][z][y_local], y = src Yl + y_local; out: [y][z][x]
+            g.ij = 1; g.ijb = Yl; g.iblk = Xl * Zl * Yl; g.ic = Zl * Yl; g.ia = Yl;
+            g.ok = Zl * Xl; g.oc = 1; g.oa = Xl;
+        } else {
+            g.ij = Zl * Xl; g.ic = 1; g.ia = Xl;
+            g.ok = 1; g.okb = Yl; g.oblk = Xl * Zl * Yl; g.oc = Zl * Yl; g.oa = Yl;
+        }
+        push(1, (int)n1, g, false);
+    } else { // stage 3, local Xl x Yl2 x n2
+        if (n2 % Pz) {
+            *err = "the z stage needs Pz to divide n2";
+            return FFT3_ERR_UNSUPPORTED_SIZE;
+        }
+        const int64_t Xl = n0, Yl2 = n1, Zl = n2 / Pz;
+        g.C = Xl; g.A = Yl2; g.B = 1;
+        if (fwd) {
+            // in: [src][y][z_local][x], z = src Zl + z_local; out: natural [z][y][x]
+            g.ij = Xl; g.ijb = Zl; g.iblk = Yl2 * Zl * Xl; g.ic = 1; g.ia = Zl * Xl;
+            g.ok = Xl * Yl2; g.oc = 1; g.oa = Xl;
+        } else {
+            g.ij = Xl * Yl2; g.ic = 1; g.ia = Xl;
+            g.ok = Xl; g.okb = Zl; g.oblk = Yl2 * Zl * Xl; g.oc = 1; g.oa = Zl * Xl;
+        }
+        push(2, (int)n2, g, false);
+    }
+    return rc;
+}
+
 int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int direction,
                    const fft3_options *opts, Schedule *out, std::string *err)
 {
@@ -932,17 +1033,24 @@ int build_schedule(int n0, int n1, int n2, int batch, int dtype, int decomp, int
     s.dtype = dtype; s.direction = direction;
     if (opts)
         s.opts = *opts;
-    if (s.opts.dist_ranks < 0 || s.opts.dist_stage < 0 || s.opts.dist_stage > 3 ||
-        (s.opts.dist_ranks > 1) != (s.opts.dist_stage != 0)) {
-        *err = "dist_stage 1, 2 or 3 goes with dist_ranks > 1 (both 0 for a one-GPU plan)";
-        return FFT3_ERR_INVALID_ARG;
+    {
+        const int dr = s.opts.dist_ranks, dr2 = s.opts.dist_ranks2, st = s.opts.dist_stage;
+        const bool ppp = decomp == FFT3_PENCIL3;
+        const bool bad = dr < 0 || dr2 < 0 || st < 0 || st > 3 ||
+                         (st == 0 ? (dr > 1 || dr2 > 1)
+                                  : ppp ? (dr < 1 || (int64_t)dr * std::max(1, dr2) < 2) : (dr < 2 || dr2 > 1));
+        if (bad) {
+            *err = "dist_stage 1, 2 or 3 goes with dist_ranks > 1 (slab-pencil) or a grid dist_ranks x "
+                   "dist_ranks2 of more than one rank (pencil-pencil-pencil); all 0 for a one-GPU plan";
+            return FFT3_ERR_INVALID_ARG;
+        }
     }
-    if (s.opts.dist_ranks > 1) {
-        if (decomp != FFT3_SLAB_PENCIL && decomp != FFT3_AUTO) {
-            *err = "rank-local stages exist for the slab-pencil decomposition";
+    if (s.opts.dist_stage != 0) {
+        if (decomp != FFT3_SLAB_PENCIL && decomp != FFT3_AUTO && decomp != FFT3_PENCIL3) {
+            *err = "rank-local stages exist for the slab-pencil and pencil-pencil-pencil decompositions";
             return FFT3_ERR_UNSUPPORTED_SIZE;
         }
-        int rc = build_dist_stage(&s, err);
+        int rc = decomp == FFT3_PENCIL3 ? build_dist_ppp(&s, err) : build_dist_stage(&s, err);
         if (rc)
             return rc;
         if (s.passes.empty()) {
@@ -1328,7 +1436,8 @@ std::string Schedule::json() const
       << decomp_name(decomp) << "\",\"variant\":" << opts.variant << ",\"layout\":\""
       << (opts.layout == FFT3_LAYOUT_ROTATED ? "rotated" : opts.layout == FFT3_LAYOUT_PENCILS ? "pencils" : "natural")
       << "\""
-      << ",\"dist_ranks\":" << opts.dist_ranks << ",\"dist_stage\":" << opts.dist_stage
+      << ",\"dist_ranks\":" << opts.dist_ranks << ",\"dist_ranks2\":" << opts.dist_ranks2
+      << ",\"dist_stage\":" << opts.dist_stage
       << ",\"workspace_bytes\":" << (need_ws ? N * 8 : 0) << ",\"hbm_sweeps\":" << passes.size()
       << ",\"twiddle_entries\":" << tw_total << ",\"passes\":[";
     for (size_t i = 0; i < passes.size(); ++i) {
@@ -1370,6 +1479,10 @@ std::string Schedule::json() const
           << ",\"oc\":" << g.oc << ",\"oa\":" << g.oa << ",\"ob\":" << g.ob;
         if (g.oblk)
             o << ",\"oblk\":" << g.oblk;
+        if (g.ijb)
+            o << ",\"ijb\":" << g.ijb << ",\"iblk\":" << g.iblk;
+        if (g.okb)
+            o << ",\"okb\":" << g.okb;
         o << "}}";
     }
     o << "]}";

@@ -1,8 +1,15 @@
-"""Slab-pencil 3D DFT distributed over a 1D grid of P processes (Section 2.4,
-Fig. 3dslabpencil): one process per GPU, each running the rank-local plans of
-``libfft3`` (``fft3_options.dist_ranks`` / ``dist_stage``) on its own device,
-with the exchanges between them done by ``torch.distributed.all_to_all_single``
-(NCCL between GPUs, gloo on the host).
+"""3D DFTs distributed over several processes (Section 2.4): one process per
+GPU, each running the rank-local plans of ``libfft3``
+(``fft3_options.dist_ranks`` / ``dist_ranks2`` / ``dist_stage``) on its own
+device, with the exchanges between them done by
+``torch.distributed.all_to_all_single`` (NCCL between GPUs, gloo on the host).
+
+``SlabPencil``: the slab-pencil decomposition on a 1D grid of P processes
+(Fig. 3dslabpencil).  ``Pencil3``: the pencil-pencil-pencil decomposition on
+a Py x Pz grid (Fig. 3dpencilpencil), one exchange within each row of the
+grid and one within each column.
+
+SlabPencil:
 
 Data distribution (n0 fastest, every local array contiguous):
 
@@ -102,4 +109,96 @@ class SlabPencil:
             else:
                 st[2].execute(x, send)
             self._exchange(send, recv)
+            st[1].execute(recv, out)
+
+
+class Pencil3:
+    """Pencil-pencil-pencil 3D DFT on a Py x Pz grid: rank r = q Py + p.
+
+    Data distribution (n0 fastest, every local array contiguous):
+
+    * pencils (forward input, inverse output): rank (p, q) holds y in
+      [p n1/Py, (p+1) n1/Py) and z in [q n2/Pz, (q+1) n2/Pz), all x, as a
+      (n2/Pz, n1/Py, n0) array;
+    * bricks (forward output, inverse input): rank (p, q) holds x in
+      [p n0/Py, (p+1) n0/Py) and y in [q n1/Pz, (q+1) n1/Pz), all z, as a
+      (n2, n1/Pz, n0/Py) array (the last redistribution left out).
+
+    Forward: stage 1 (x lines, stored packed by destination), an all-to-all
+    among the Py ranks of the row, stage 2 (y lines, read in place from the Py
+    received blocks, stored packed), an all-to-all among the Pz ranks of the
+    column, stage 3 (z lines, read in place, stored as the brick).  Inverse:
+    stages 3, 2, 1 with the exchanges between them in reverse order.  Needs
+    Py | n0, Py | n1, Pz | n1, Pz | n2.  ``stages`` replaces the GPU plans by
+    objects with ``execute(x, out)``, keyed 1, 2, 3."""
+
+    def __init__(self, n0: int, n1: int, n2: int, grid, direction: int = fft3.FFT3_FORWARD,
+                 dtype: int = fft3.FFT3_C64_FP32, stages=None):
+        import torch
+        import torch.distributed as dist
+        self.dist = dist
+        Py, Pz = (int(v) for v in grid)
+        world = dist.get_world_size() if dist.is_initialized() else 1
+        if Py * Pz != world:
+            raise ValueError(f"grid {Py} x {Pz} needs {Py * Pz} ranks, the job has {world}")
+        if n0 % Py or n1 % Py or n1 % Pz or n2 % Pz:
+            raise ValueError(f"grid {Py} x {Pz} must divide n0, n1 (by both) and n2 = {n0}, {n1}, {n2}")
+        self.grid = (Py, Pz)
+        self.rank = dist.get_rank() if dist.is_initialized() else 0
+        self.p, self.q = self.rank % Py, self.rank // Py
+        self.shape = (n0, n1, n2)
+        self.direction = direction
+        self.local_elems = n0 * n1 * n2 // (Py * Pz)
+        self.cdtype = torch.complex128 if dtype == fft3.FFT3_C128_FP64 else torch.complex64
+        # every rank creates every group, in the same order
+        self.row_group = self.col_group = None
+        if world > 1:
+            for q in range(Pz):
+                g = dist.new_group([q * Py + p for p in range(Py)])
+                if q == self.q:
+                    self.row_group = g
+            for p in range(Py):
+                g = dist.new_group([q * Py + p for q in range(Pz)])
+                if p == self.p:
+                    self.col_group = g
+        if stages is None:
+            mk = lambda dims, st: fft3.Plan(*dims, 1, fft3.FFT3_PENCIL3, direction, dtype, dist_ranks=Py,
+                                            dist_ranks2=Pz, dist_stage=st)
+            stages = {1: mk((n0, n1 // Py, n2 // Pz), 1), 2: mk((n0 // Py, n1, n2 // Pz), 2),
+                      3: mk((n0 // Py, n1 // Pz, n2), 3)}
+        self.stages = stages
+        self._bufs = None
+
+    def local_shape(self, spectrum: bool):
+        n0, n1, n2 = self.shape
+        Py, Pz = self.grid
+        return (n2, n1 // Pz, n0 // Py) if spectrum else (n2 // Pz, n1 // Py, n0)
+
+    def _exchange(self, send, recv, group, size):
+        import torch
+        if size == 1:
+            recv.copy_(send)
+            return
+        self.dist.all_to_all_single(torch.view_as_real(recv), torch.view_as_real(send), group=group)
+
+    def execute(self, x, out) -> None:
+        import torch
+        assert x.is_contiguous() and out.is_contiguous() and x.dtype == self.cdtype == out.dtype
+        assert x.numel() == out.numel() == self.local_elems
+        if self._bufs is None or self._bufs[0].device != x.device:
+            self._bufs = tuple(torch.empty(self.local_elems, dtype=self.cdtype, device=x.device) for _ in range(2))
+        send, recv = self._bufs
+        st = self.stages
+        Py, Pz = self.grid
+        if self.direction == fft3.FFT3_FORWARD:
+            st[1].execute(x, send)
+            self._exchange(send, recv, self.row_group, Py)
+            st[2].execute(recv, send)
+            self._exchange(send, recv, self.col_group, Pz)
+            st[3].execute(recv, out)
+        else:
+            st[3].execute(x, send)
+            self._exchange(send, recv, self.col_group, Pz)
+            st[2].execute(recv, send)
+            self._exchange(send, recv, self.row_group, Py)
             st[1].execute(recv, out)

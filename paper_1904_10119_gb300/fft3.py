@@ -44,7 +44,8 @@ class fft3_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("radix_order", ctypes.c_int), ("tile_lines", ctypes.c_int),
                 ("mesh", ctypes.c_int * 3), ("slab_mode", ctypes.c_int), ("tc_stages", ctypes.c_int),
                 ("slab_chunk", ctypes.c_int), ("slab_lines", ctypes.c_int), ("layout", ctypes.c_int),
-                ("dist_ranks", ctypes.c_int), ("dist_stage", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("dist_ranks", ctypes.c_int), ("dist_stage", ctypes.c_int), ("dist_ranks2", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
 
 
 _lib = None
@@ -127,7 +128,7 @@ def _check(rc: int) -> int:
 
 
 def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mode=0, tc_stages=0,
-                 slab_chunk=0, slab_lines=0, layout=0, dist_ranks=0, dist_stage=0) -> fft3_options:
+                 slab_chunk=0, slab_lines=0, layout=0, dist_ranks=0, dist_stage=0, dist_ranks2=0) -> fft3_options:
     o = fft3_options()
     o.variant = int(variant)
     o.radix_order = int(radix_order)
@@ -141,6 +142,7 @@ def make_options(variant=0, radix_order=0, tile_lines=0, mesh=(0, 0, 0), slab_mo
     o.layout = int(layout)
     o.dist_ranks = int(dist_ranks)
     o.dist_stage = int(dist_stage)
+    o.dist_ranks2 = int(dist_ranks2)
     return o
 
 

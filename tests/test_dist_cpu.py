@@ -1,9 +1,10 @@
-"""The distributed slab-pencil decomposition (Section 2.4, Fig. 3dslabpencil)
-on the host: the rank-local stage schedules the planner lowers
-(fft3_options.dist_ranks / dist_stage), replayed numerically with an FP64 line
-DFT through their pass geometries, and the driver that joins them with
-torch.distributed all-to-alls, run as 2 and 4 gloo ranks (one process per
-rank, rendezvous on 127.0.0.1) against the oracle's slab-pencil simulation."""
+"""The distributed decompositions of Section 2.4 on the host: slab-pencil on
+a 1D grid (Fig. 3dslabpencil) and pencil-pencil-pencil on a 2D grid (Fig.
+3dpencilpencil).  The rank-local stage schedules the planner lowers
+(fft3_options.dist_ranks / dist_ranks2 / dist_stage) are replayed numerically
+with an FP64 line DFT through their pass geometries, and the drivers that join
+them with torch.distributed all-to-alls run as gloo ranks (one process per
+rank, rendezvous on 127.0.0.1), both against the oracle's simulations."""
 import os
 import socket
 
@@ -17,6 +18,7 @@ import oracle
 from paper_1904_10119_gb300 import fft3
 
 S = fft3.FFT3_SLAB_PENCIL
+P3 = fft3.FFT3_PENCIL3
 FWD, INV = fft3.FFT3_FORWARD, fft3.FFT3_INVERSE
 
 
@@ -47,8 +49,11 @@ class ReplayStage:
             c = np.arange(g["C"])[None, :, None, None]
             a = np.arange(g["A"])[None, None, :, None]
             b = np.arange(g["B"])[None, None, None, :]
-            src = (j * g["ij"] + c * g["ic"] + a * g["ia"] + b * g["ib"]).reshape(n, -1)
-            dst = (j * g["ok"] + c * g["oc"] + a * g["oa"] + b * g["ob"]).reshape(n, -1)
+            # a line in runs over exchange blocks: element j at (j / jb) * blk + (j % jb) * stride
+            jin = (j // g["ijb"]) * g["iblk"] + (j % g["ijb"]) * g["ij"] if g.get("ijb") else j * g["ij"]
+            jout = (j // g["okb"]) * g["oblk"] + (j % g["okb"]) * g["ok"] if g.get("okb") else j * g["ok"]
+            src = (jin + c * g["ic"] + a * g["ia"] + b * g["ib"]).reshape(n, -1)
+            dst = (jout + c * g["oc"] + a * g["oa"] + b * g["ob"]).reshape(n, -1)
             lines = oracle.dft_matrix(n, self.sign) @ bufs[p["src"]][src]
             bufs[p["dst"]][dst] = lines
         out.copy_(torch.from_numpy(bufs["out"]).to(out.dtype).reshape(out.shape))
@@ -91,9 +96,9 @@ def test_stage_options_rejected(opts, code):
     assert e.value.code == code
 
 
-@pytest.mark.parametrize("decomp,dtype,batch", [(fft3.FFT3_PENCIL3, fft3.FFT3_C64_FP32, 1),
-                                                (fft3.FFT3_VOLUMETRIC, fft3.FFT3_C64_FP32, 1),
-                                                (S, fft3.FFT3_C64_SPLITBF16_TC, 1), (S, fft3.FFT3_C64_FP32, 2)])
+@pytest.mark.parametrize("decomp,dtype,batch", [(fft3.FFT3_VOLUMETRIC, fft3.FFT3_C64_FP32, 1),
+                                                (S, fft3.FFT3_C64_SPLITBF16_TC, 1), (S, fft3.FFT3_C64_FP32, 2),
+                                                (P3, fft3.FFT3_C64_SPLITBF16_TC, 1), (P3, fft3.FFT3_C64_FP32, 2)])
 def test_stage_needs_one_slab_pencil_problem(decomp, dtype, batch):
     with pytest.raises(fft3.Fft3Error) as e:
         fft3.fft3_plan_schedule(64, 32, 8, batch, dtype, decomp, FWD, fft3.make_options(dist_ranks=2, dist_stage=1))
@@ -200,5 +205,157 @@ def test_driver_over_gloo(world, cases):
         n0, n1, n2 = dims
         _, local = _local_inputs(dims, world, direction == INV, natural, seed=sum(dims))
         want = oracle.slab_pencil_sim(local, n0, n1, n2, world, direction, natural)[rank]
+        assert out.shape == want.shape
+        assert np.abs(out - want).max() <= 1e-12 * np.abs(want).max()
+
+
+# ------------------------------------------------------------------------- #
+# pencil-pencil-pencil on a Py x Pz grid                                    #
+# ------------------------------------------------------------------------- #
+def ppp_schedule(dims, stage, grid, direction=FWD):
+    return fft3.fft3_plan_schedule(*dims, 1, 0, P3, direction,
+                                   fft3.make_options(dist_ranks=grid[0], dist_ranks2=grid[1], dist_stage=stage))
+
+
+def ppp_stages(n, grid, direction):
+    n0, n1, n2 = n
+    Py, Pz = grid
+    dims = {1: (n0, n1 // Py, n2 // Pz), 2: (n0 // Py, n1, n2 // Pz), 3: (n0 // Py, n1 // Pz, n2)}
+    return {k: ReplayStage(ppp_schedule(d, k, grid, direction), direction) for k, d in dims.items()}
+
+
+def test_ppp_stage_schedules():
+    """One pass per stage: the x pass with the rotated store (x blocks
+    contiguous), the y and z passes reading their lines in Py / Pz runs
+    (two-level line index, the runtime-radix kernel); the inverse stores in
+    runs what the forward reads in runs."""
+    s1 = ppp_schedule((8, 3, 2), 1, (2, 2))
+    assert [p["kind"] for p in s1["passes"]] == ["line_contig_rotate"] and s1["decomposition"] == "pencil_pencil_pencil"
+    g1 = s1["passes"][0]["geom"]
+    assert (g1["ok"], g1["oc"], g1["oa"]) == (6, 1, 3)                      # out [x][z][y]
+    g2 = ppp_schedule((4, 6, 2), 2, (2, 2))["passes"][0]["geom"]
+    assert (g2["ijb"], g2["iblk"], g2["ij"], g2["ok"]) == (3, 24, 1, 8)     # y runs of n1/Py, out [y][z][x]
+    g3 = ppp_schedule((4, 3, 4), 3, (2, 2))["passes"][0]["geom"]
+    assert (g3["ijb"], g3["iblk"], g3["ij"], g3["ok"]) == (2, 24, 4, 12)    # z runs of n2/Pz, out [z][y][x]
+    g3i = ppp_schedule((4, 3, 4), 3, (2, 2), INV)["passes"][0]["geom"]
+    assert (g3i["okb"], g3i["oblk"], g3i["ok"], g3i["ij"]) == (2, 24, 4, 12)
+    assert all(ppp_schedule(d, k, (2, 2))["workspace_bytes"] == 0
+               for k, d in ((1, (8, 3, 2)), (2, (4, 6, 2)), (3, (4, 3, 4))))
+
+
+@pytest.mark.parametrize("opts,dims,code", [
+    ({"dist_ranks": 1, "dist_stage": 1}, (8, 4, 4), INVALID),                      # a 1 x 1 grid
+    ({"dist_ranks": 0, "dist_ranks2": 2, "dist_stage": 2}, (8, 4, 4), INVALID),
+    ({"dist_ranks2": 2}, (8, 4, 4), INVALID),                                       # grid without a stage
+    ({"dist_ranks": 3, "dist_ranks2": 1, "dist_stage": 1}, (8, 4, 4), UNSUPPORTED),  # 3 does not divide n0
+    ({"dist_ranks": 2, "dist_ranks2": 3, "dist_stage": 2}, (4, 8, 4), UNSUPPORTED),  # 3 does not divide n1
+    ({"dist_ranks": 2, "dist_ranks2": 3, "dist_stage": 3}, (4, 4, 8), UNSUPPORTED)])  # 3 does not divide n2
+def test_ppp_stage_options_rejected(opts, dims, code):
+    with pytest.raises(fft3.Fft3Error) as e:
+        fft3.fft3_plan_schedule(*dims, 1, 0, P3, FWD, fft3.make_options(**opts))
+    assert e.value.code == code
+    with pytest.raises(fft3.Fft3Error) as e:   # the slab-pencil grid is one-dimensional
+        fft3.fft3_plan_schedule(8, 4, 4, 1, 0, S, FWD, fft3.make_options(dist_ranks=2, dist_ranks2=2, dist_stage=1))
+    assert e.value.code == INVALID
+
+
+def _ppp_inputs(n, grid, spectrum, seed):
+    n0, n1, n2 = n
+    Py, Pz = grid
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, (n2, n1, n0)) + 1j * rng.uniform(-1, 1, (n2, n1, n0))
+    out = []
+    for r in range(Py * Pz):
+        p, q = r % Py, r // Py
+        if spectrum:
+            out.append(np.ascontiguousarray(x[:, q * (n1 // Pz):(q + 1) * (n1 // Pz), p * (n0 // Py):(p + 1) * (n0 // Py)]))
+        else:
+            out.append(np.ascontiguousarray(x[q * (n2 // Pz):(q + 1) * (n2 // Pz), p * (n1 // Py):(p + 1) * (n1 // Py)]))
+    return x, out
+
+
+@pytest.mark.parametrize("n,grid", [((8, 6, 4), (2, 2)), ((6, 6, 6), (3, 2)), ((4, 8, 6), (1, 2)), ((6, 3, 5), (3, 1)),
+                                    ((12, 12, 8), (2, 4))])
+@pytest.mark.parametrize("direction", [FWD, INV])
+def test_ppp_replayed_stages_match_the_simulation(n, grid, direction):
+    """Each rank's three stages replayed on the host, the row and column
+    all-to-alls done by slicing: every rank's output equals the oracle's
+    simulation, and the forward bricks reassembled equal the whole 3D DFT."""
+    n0, n1, n2 = n
+    Py, Pz = grid
+    x, local = _ppp_inputs(n, grid, direction == INV, seed=sum(n) + Py)
+    st = ppp_stages(n, grid, direction)
+    R = Py * Pz
+
+    def run(k, arrays):
+        outs = []
+        for a in arrays:
+            o = torch.empty(a.size, dtype=torch.complex128)
+            st[k].execute(torch.from_numpy(a.ravel().copy()), o)
+            outs.append(o.numpy())
+        return outs
+
+    def exchange(sends, row):   # within each row (same q) or column (same p), blocks in member order
+        outs = [None] * R
+        for r in range(R):
+            p, q = r % Py, r // Py
+            members = [q * Py + i for i in range(Py)] if row else [j * Py + p for j in range(Pz)]
+            me = members.index(r)
+            blk = sends[r].size // len(members)
+            outs[r] = np.concatenate([sends[m][me * blk:(me + 1) * blk] for m in members])
+        return outs
+
+    if direction == FWD:
+        data = run(3, exchange(run(2, exchange(run(1, local), True)), False))
+    else:
+        data = run(1, exchange(run(2, exchange(run(3, local), False)), True))
+    ref = oracle.pencil3_sim(local, n0, n1, n2, Py, Pz, direction)
+    scale = max(np.abs(r).max() for r in ref)
+    for got, want in zip(data, ref):
+        assert np.abs(got - want.ravel()).max() <= 1e-12 * scale
+    if direction == FWD:
+        whole = oracle.fft3(x, n0, n1, n2)
+        for r, got in enumerate(data):
+            p, q = r % Py, r // Py
+            brick = whole[:, q * (n1 // Pz):(q + 1) * (n1 // Pz), p * (n0 // Py):(p + 1) * (n0 // Py)]
+            assert np.abs(got.reshape(brick.shape) - brick).max() <= 1e-12 * np.abs(whole).max()
+
+
+def _ppp_rank_main(rank, world, port, grid, cases, q):
+    from paper_1904_10119_gb300.distributed import Pencil3
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+    try:
+        for n, direction in cases:
+            pp = Pencil3(*n, grid, direction, dtype=fft3.FFT3_C128_FP64, stages=ppp_stages(n, grid, direction))
+            _, local = _ppp_inputs(n, grid, direction == INV, seed=sum(n))
+            out = torch.empty(pp.local_shape(spectrum=direction == FWD), dtype=torch.complex128)
+            pp.execute(torch.from_numpy(local[rank]), out)
+            q.put((rank, n, direction, out.numpy()))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("grid,cases", [((2, 2), [((8, 6, 4), FWD), ((8, 6, 4), INV)]),
+                                        ((2, 1), [((4, 6, 3), FWD)]), ((1, 2), [((3, 4, 6), INV)])])
+def test_ppp_driver_over_gloo(grid, cases):
+    """The pencil-pencil-pencil driver's row and column all-to-alls over gloo
+    (subgroups of the 2 x 2, 2 x 1 and 1 x 2 grids): each rank's output equals
+    the oracle's simulation for that rank."""
+    world = grid[0] * grid[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_ppp_rank_main, args=(r, world, port, grid, cases, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=300) for _ in range(world * len(cases))]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for rank, n, direction, out in got:
+        _, local = _ppp_inputs(n, grid, direction == INV, seed=sum(n))
+        want = oracle.pencil3_sim(local, *n, grid[0], grid[1], direction)[rank]
         assert out.shape == want.shape
         assert np.abs(out - want).max() <= 1e-12 * np.abs(want).max()

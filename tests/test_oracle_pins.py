@@ -289,6 +289,29 @@ def test_slab_pencil_simulation_against_brute_force(shape, p):
             assert np.allclose(got[r] / N, slabs[r], atol=1e-12)
 
 
+@pytest.mark.parametrize("shape,grid", [((4, 6, 2), (2, 2)), ((6, 6, 2), (3, 1)), ((2, 4, 4), (1, 4)),
+                                        ((4, 6, 6), (2, 3))])
+def test_pencil3_simulation_against_brute_force(shape, grid):
+    """Fig. 3dpencilpencil on a py x pz grid: the brick rank (p, q) ends with is
+    its x range p and y range q of the N^3 direct sum; the inverse returns N
+    times the pencils."""
+    n0, n1, n2 = shape
+    py, pz = grid
+    rng = np.random.default_rng(py * 10 + pz)
+    x = rng.standard_normal((n2, n1, n0)) + 1j * rng.standard_normal((n2, n1, n0))
+    pencils = [x[(r // py) * (n2 // pz):(r // py + 1) * (n2 // pz), (r % py) * (n1 // py):(r % py + 1) * (n1 // py)]
+               for r in range(py * pz)]
+    ref = oracle.bruteforce3(x, n0, n1, n2).reshape(n2, n1, n0)
+    bricks = oracle.pencil3_sim(pencils, n0, n1, n2, py, pz)
+    for r in range(py * pz):
+        p, q = r % py, r // py
+        want = ref[:, q * (n1 // pz):(q + 1) * (n1 // pz), p * (n0 // py):(p + 1) * (n0 // py)]
+        assert bricks[r].shape == want.shape and np.allclose(bricks[r], want, atol=1e-12)
+    back = oracle.pencil3_sim(bricks, n0, n1, n2, py, pz, oracle.INVERSE)
+    for r in range(py * pz):
+        assert np.allclose(back[r] / (n0 * n1 * n2), pencils[r], atol=1e-12)
+
+
 def test_slab_pencil_simulation_one_rank_is_the_3d_dft():
     x = synth.uniform_c64((1, 6, 5, 8), 3).reshape(6, 5, 8)
     got = oracle.slab_pencil_sim([x], 8, 5, 6, 1)[0]
