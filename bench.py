@@ -400,11 +400,15 @@ def main():
         fft3.fft3_plan_execute_host_pipelined(eplan, [h_in.data_ptr()] * 4, [h_out.data_ptr()] * 4, sp)
         barrier()
         pipelined_ms = (time.perf_counter() - t0) * 1e3 / 4
+        direct = bool(fft3.fft3_plan_describe(eplan).get("host_direct"))
         fft3.fft3_plan_destroy(eplan)
         del h_out
         e2e = {"value": job_ms_per_transform(max_over_ranks(e2e_ms, "cuda"), world), "unit": "ms",
                "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * N, "steps": e2e_steps, "api": "fft3_plan_execute_host",
+               "path": ("direct: the first pass reads the pinned host input and the last pass writes the pinned "
+                        "host output over the host link" if direct else
+                        "staged: copies between pinned host memory and device arrays around the transform"),
                "pipelined_ms_per_transform": pipelined_ms}
 
     extras = {}

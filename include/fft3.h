@@ -281,13 +281,23 @@ int fft3_plan_schedule_many(int count, const int *dims, const int64_t *offsets, 
 int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream);
 
 /* The transform of fft3_plan_execute (Section 2.1 definition, Section 2.3
- * layout) from and to HOST memory: copies `h_in` (batch*n0*n1*n2 values,
- * caller-owned host memory) to plan-owned device buffers, transforms, copies
- * the result to `h_out`, then synchronises `stream`.  Pinned host memory
- * gives full copy bandwidth.  The device staging buffers are allocated on
- * the first call and kept by the plan (FFT3_ERR_OOM if that fails).  The
- * paper's arrays live in the nodes' memory; this entry point is the
- * end-to-end form for callers whose data live on the host. */
+ * layout) from and to HOST memory (batch*n0*n1*n2 values each, caller-owned),
+ * then synchronises `stream`.  Two ways, picked per call:
+ *   direct: when both h_in and h_out are host memory the device can address
+ *           (pinned or registered with CUDA, distinct) and the plan's first
+ *           pass reads its input with plain loads and its last pass writes
+ *           its output with plain stores (the default complex64 and
+ *           complex128 schedules; not batched plans, not the tensor-core x
+ *           pass, which loads by TMA), the first pass reads h_in and the last
+ *           pass writes h_out in place over the host link (on a Grace host,
+ *           the coherent chip-to-chip link), with one plan-owned device array
+ *           for the intermediate passes: no staging copies;
+ *   staged: otherwise h_in is copied to a plan-owned device array, the plan
+ *           runs device to device, and the result is copied to h_out.
+ * The device arrays are allocated on the first call that needs them and kept
+ * by the plan (FFT3_ERR_OOM if that fails).  The paper's arrays live in the
+ * nodes' memory; this entry point is the end-to-end form for callers whose
+ * data live on the host. */
 int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *stream);
 
 /* `count` transforms from and to HOST memory, pipelined: transform i reads

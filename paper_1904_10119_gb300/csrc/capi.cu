@@ -785,15 +785,84 @@ int fft3_plan_execute_pass(fft3_plan p, int k, const void *in, void *out, void *
     return launch_one(p, L, L.func, a, st);
 }
 
+// The address kernels use for host memory the device can reach (pinned or
+// registered with CUDA), or null for other memory.
+static void *host_device_ptr(const void *h)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Whether the schedule can read its input from host memory in its first pass
+// and write its output to host memory in its last: the input is read only by
+// the first pass, with plain loads (not by TMA), and the last pass writes the
+// output with plain stores; no two-stream pair.
+static bool host_direct_ok(const fft3_plan_s *p)
+{
+    const size_t n = p->launches.size();
+    if (p->batch || n == 0)
+        return false;
+    for (size_t k = 0; k < n; ++k) {
+        const Launch &L = p->launches[k];
+        if (pair_head(p, k) || L.dst == BUF_IN || (L.src == BUF_IN && k != 0))
+            return false;
+        if (L.src == BUF_IN && (L.stream_q > 0 || L.tc32 || L.slab_map || L.tma))
+            return false;
+        if (k + 1 == n && (L.dst != BUF_OUT || L.tma || L.slab_map))
+            return false;
+    }
+    return true;
+}
+
+// The schedule with its first pass reading the host input and its last pass
+// writing the host output; the intermediate output lives in the plan's
+// device staging array.
+static int execute_host_direct(fft3_plan_s *p, const void *hin, void *hout, cudaStream_t st)
+{
+    float2 *mid = p->d_stage_out;
+    const size_t n = p->launches.size();
+    for (size_t k = 0; k < n; ++k) {
+        const Launch &L = p->launches[k];
+        PassArgs a = L.args;
+        a.in = L.src == BUF_IN ? (const float2 *)hin : L.src == BUF_OUT ? mid : p->d_ws;
+        a.out = k + 1 == n ? (float2 *)hout : L.dst == BUF_OUT ? mid : p->d_ws;
+        if (L.kind == PK_COPY) {
+            k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems * (p->esize / 8));
+            CUDA_TRY(cudaGetLastError());
+            continue;
+        }
+        int rc = launch_one(p, L, L.func, a, st);
+        if (rc)
+            return rc;
+    }
+    return FFT3_OK;
+}
+
 int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *stream)
 {
     if (!p || !h_in || !h_out)
         return fail(FFT3_ERR_INVALID_ARG, "null plan or buffer");
     size_t bytes = (size_t)p->elems * p->esize;
-    if (!p->d_stage_in) {
-        CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
-        CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
+    void *hin = host_device_ptr(h_in), *hout = host_device_ptr(h_out);
+    if (hin && hout && hin != hout && host_direct_ok(p)) {
+        if (!p->d_stage_out)
+            CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
+        cudaStream_t st = (cudaStream_t)stream;
+        p->last_stream = st;
+        int rc = execute_host_direct(p, hin, hout, st);
+        if (rc)
+            return rc;
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return FFT3_OK;
     }
+    if (!p->d_stage_in)
+        CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
+    if (!p->d_stage_out)
+        CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(cudaMemcpyAsync(p->d_stage_in, h_in, bytes, cudaMemcpyHostToDevice, st));
     int rc = fft3_plan_execute(p, p->d_stage_in, p->d_stage_out, stream);
@@ -815,10 +884,10 @@ int fft3_plan_execute_host_pipelined(fft3_plan p, const void *const *h_in, void 
     if (count == 0)
         return FFT3_OK;
     const size_t bytes = (size_t)p->elems * p->esize;
-    if (!p->d_stage_in) {
+    if (!p->d_stage_in)
         CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
+    if (!p->d_stage_out)
         CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
-    }
     if (!p->d_stage_in2) {
         CUDA_TRY(cudaMalloc(&p->d_stage_in2, bytes));
         CUDA_TRY(cudaMalloc(&p->d_stage_out2, bytes));
@@ -935,7 +1004,7 @@ int fft3_plan_describe(fft3_plan p, char *buf, size_t len)
              ",\"block\":" + std::to_string(L.block.x) + ",\"smem\":" + std::to_string(L.smem) +
              ",\"cluster\":" + std::to_string(L.cluster) + "}";
     }
-    l += "]}";
+    l += std::string("],\"host_direct\":") + (host_direct_ok(p) ? "true" : "false") + "}";
     j = j.substr(0, j.size() - 1) + l;
     if (buf && len > 0) {
         size_t c = std::min(len - 1, j.size());

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from paper_1904_10119_gb300 import fft3, synth
-from tests.gpu_util import assert_parity, run_plan
+from tests.gpu_util import MAXABS_TOL, REL_L2_TOL, assert_parity, run_plan
 
 pytestmark = pytest.mark.gpu
 
@@ -234,6 +234,43 @@ def test_execute_host_buffers():
         out = torch.empty_like(xin).pin_memory()
         fft3.fft3_plan_execute_host(h, xin.data_ptr(), out.data_ptr(), 0)
         assert_parity(x, out.numpy(), shape, 2)
+    finally:
+        fft3.fft3_plan_destroy(h)
+
+
+@pytest.mark.parametrize("decomp,opts,dtype", [
+    (S, {}, fft3.FFT3_C64_FP32), (P, {}, fft3.FFT3_C64_FP32), (P, {"variant": fft3.FFT3_PPP_ROTATE}, fft3.FFT3_C64_FP32),
+    (V, {}, fft3.FFT3_C64_FP32), (P, {}, fft3.FFT3_C64_SPLITBF16_TC), (P, {}, fft3.FFT3_C128_FP64)])
+@pytest.mark.parametrize("direction", [FWD, INV])
+def test_execute_host_direct_and_staged(decomp, opts, dtype, direction):
+    """Host buffers, both ways: pinned buffers (the first pass reads the host
+    input and the last pass writes the host output directly, where the
+    schedule allows) and pageable numpy buffers (staged copies) give the
+    oracle's transform; the input is left unchanged."""
+    shape, batch = (1024, 24, 40), 1
+    n0, n1, n2 = shape
+    c128 = dtype == fft3.FFT3_C128_FP64
+    if c128:
+        rng = np.random.default_rng(4)
+        x = (rng.uniform(-1, 1, (n2, n1, n0)) + 1j * rng.uniform(-1, 1, (n2, n1, n0))).astype(np.complex128)
+    else:
+        x = synth.uniform_c64((batch, n2, n1, n0), 21)
+    h = fft3.fft3_plan_create_ex(*shape, batch, dtype, decomp, direction, fft3.make_options(**opts))
+    try:
+        ref = oracle.fft3(x.ravel(), n0, n1, n2, batch, sign=direction)
+        pinned_in = torch.from_numpy(x.copy()).pin_memory()
+        pinned_out = torch.full_like(pinned_in, complex(float("nan"), float("nan"))).pin_memory()
+        page_in = np.ascontiguousarray(x.copy())
+        page_out = np.full_like(page_in, np.nan)
+        for src, dst, keep in ((pinned_in.data_ptr(), pinned_out, pinned_in.numpy()),
+                               (page_in.ctypes.data, page_out, page_in)):
+            fft3.fft3_plan_execute_host(h, src, dst.data_ptr() if hasattr(dst, "data_ptr") else dst.ctypes.data, 0)
+            got = dst.numpy() if hasattr(dst, "numpy") else dst
+            assert np.array_equal(keep, x), "input modified"
+            rel, mx = oracle.rel_l2(got, ref), oracle.max_abs_ratio(got, ref)
+            tol = (1e-12, 1e-11) if c128 else (REL_L2_TOL, MAXABS_TOL)
+            assert rel <= tol[0] and mx <= tol[1], (rel, mx)
+        assert fft3.fft3_plan_check(h) == 0
     finally:
         fft3.fft3_plan_destroy(h)
 
