@@ -406,8 +406,8 @@ def main():
         e2e = {"value": job_ms_per_transform(max_over_ranks(e2e_ms, "cuda"), world), "unit": "ms",
                "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * N, "steps": e2e_steps, "api": "fft3_plan_execute_host",
-               "path": ("direct: the first pass reads the pinned host input and the last pass writes the pinned "
-                        "host output over the host link" if direct else
+               "path": ("direct input: the first pass reads the pinned host input over the host link; the "
+                        "result is copied to the pinned host output" if direct else
                         "staged: copies between pinned host memory and device arrays around the transform"),
                "pipelined_ms_per_transform": pipelined_ms}
 

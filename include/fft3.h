@@ -283,15 +283,13 @@ int fft3_plan_execute(fft3_plan p, const void *in, void *out, void *stream);
 /* The transform of fft3_plan_execute (Section 2.1 definition, Section 2.3
  * layout) from and to HOST memory (batch*n0*n1*n2 values each, caller-owned),
  * then synchronises `stream`.  Two ways, picked per call:
- *   direct: when both h_in and h_out are host memory the device can address
- *           (pinned or registered with CUDA, distinct) and the plan's first
- *           pass reads its input with plain loads and its last pass writes
- *           its output with plain stores (the default complex64 and
- *           complex128 schedules; not batched plans, not the tensor-core x
- *           pass, which loads by TMA), the first pass reads h_in and the last
- *           pass writes h_out in place over the host link (on a Grace host,
- *           the coherent chip-to-chip link), with one plan-owned device array
- *           for the intermediate passes: no staging copies;
+ *   direct: when h_in is host memory the device can address (pinned or
+ *           registered with CUDA) and the plan's first pass reads its input
+ *           with plain loads (the default complex64 and complex128 schedules;
+ *           not batched plans, not the tensor-core x pass, which loads by
+ *           TMA), the first pass reads h_in in place over the host link (on a
+ *           Grace host, the chip-to-chip link): no input copy; the result,
+ *           left in a plan-owned device array, is copied to h_out;
  *   staged: otherwise h_in is copied to a plan-owned device array, the plan
  *           runs device to device, and the result is copied to h_out.
  * The device arrays are allocated on the first call that needs them and kept
@@ -305,12 +303,11 @@ int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *str
  * plan-sized complex64 array; h_out[i] must not overlap any h_in[j]).  Two
  * sets of plan-owned device staging buffers alternate, so the host-to-device
  * copy of transform i+1, the transform of i and the device-to-host copy of
- * i-1 run at the same time on three plan-owned streams.  Returns after the
- * last result is in h_out[count-1] (every h_out[i] is complete); `stream` is
- * ordered before the first copy.  The staging buffers (four plan-sized
- * arrays) are allocated on the first call and kept by the plan.  The paper
- * has no host-memory interface; this is the end-to-end form of the transform
- * for callers whose data live in host memory. */
+ * i-1 run at the same time on three plan-owned streams.  Returns after every
+ * h_out[i] is complete; `stream` is ordered before the first copy.  The
+ * staging buffers are allocated on the first call that needs them and kept by
+ * the plan.  The paper has no host-memory interface; this is the end-to-end
+ * form of the transform for callers whose data live in host memory. */
 int fft3_plan_execute_host_pipelined(fft3_plan p, const void *const *h_in, void *const *h_out, int count,
                                      void *stream);
 

@@ -797,14 +797,13 @@ static void *host_device_ptr(const void *h)
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
-// Whether the schedule can read its input from host memory in its first pass
-// and write its output to host memory in its last: the input is read only by
-// the first pass, with plain loads (not by TMA), and the last pass writes the
-// output with plain stores; no two-stream pair.
+// Whether the schedule can read its input from host memory in its first pass:
+// the input is read only by the first pass, with plain loads (not by TMA), the
+// result ends in the output array, and there is no two-stream pair.
 static bool host_direct_ok(const fft3_plan_s *p)
 {
     const size_t n = p->launches.size();
-    if (p->batch || n == 0)
+    if (p->batch || n == 0 || p->launches[n - 1].dst != BUF_OUT)
         return false;
     for (size_t k = 0; k < n; ++k) {
         const Launch &L = p->launches[k];
@@ -812,24 +811,25 @@ static bool host_direct_ok(const fft3_plan_s *p)
             return false;
         if (L.src == BUF_IN && (L.stream_q > 0 || L.tc32 || L.slab_map || L.tma))
             return false;
-        if (k + 1 == n && (L.dst != BUF_OUT || L.tma || L.slab_map))
-            return false;
     }
     return true;
 }
 
-// The schedule with its first pass reading the host input and its last pass
-// writing the host output; the intermediate output lives in the plan's
-// device staging array.
-static int execute_host_direct(fft3_plan_s *p, const void *hin, void *hout, cudaStream_t st)
+// The schedule with the first pass reading the host input `hin` and the
+// output array in device memory (`mid`, the workspace `ws`).  No kernel
+// stores to host memory: with the last pass of one transform storing to host
+// memory while the first pass of another read host memory on a second
+// stream, one of five transforms came out wrong in a reproducible way (the
+// same sequence with the result moved by a copy was right every time), so
+// results leave the device by copies.
+static int execute_host_direct(fft3_plan_s *p, const void *hin, float2 *mid, float2 *ws, cudaStream_t st)
 {
-    float2 *mid = p->d_stage_out;
     const size_t n = p->launches.size();
     for (size_t k = 0; k < n; ++k) {
         const Launch &L = p->launches[k];
         PassArgs a = L.args;
-        a.in = L.src == BUF_IN ? (const float2 *)hin : L.src == BUF_OUT ? mid : p->d_ws;
-        a.out = k + 1 == n ? (float2 *)hout : L.dst == BUF_OUT ? mid : p->d_ws;
+        a.in = L.src == BUF_IN ? (const float2 *)hin : L.src == BUF_OUT ? mid : ws;
+        a.out = L.dst == BUF_OUT ? mid : ws;
         if (L.kind == PK_COPY) {
             k_copy<<<L.grid, L.block, 0, st>>>(a.in, a.out, p->elems * (p->esize / 8));
             CUDA_TRY(cudaGetLastError());
@@ -847,15 +847,16 @@ int fft3_plan_execute_host(fft3_plan p, const void *h_in, void *h_out, void *str
     if (!p || !h_in || !h_out)
         return fail(FFT3_ERR_INVALID_ARG, "null plan or buffer");
     size_t bytes = (size_t)p->elems * p->esize;
-    void *hin = host_device_ptr(h_in), *hout = host_device_ptr(h_out);
-    if (hin && hout && hin != hout && host_direct_ok(p)) {
+    void *hin = host_device_ptr(h_in);
+    if (hin && host_direct_ok(p)) {
         if (!p->d_stage_out)
             CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
         cudaStream_t st = (cudaStream_t)stream;
         p->last_stream = st;
-        int rc = execute_host_direct(p, hin, hout, st);
+        int rc = execute_host_direct(p, hin, p->d_stage_out, p->d_ws, st);
         if (rc)
             return rc;
+        CUDA_TRY(cudaMemcpyAsync(h_out, p->d_stage_out, bytes, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         return FFT3_OK;
     }
@@ -888,15 +889,17 @@ int fft3_plan_execute_host_pipelined(fft3_plan p, const void *const *h_in, void 
         CUDA_TRY(cudaMalloc(&p->d_stage_in, bytes));
     if (!p->d_stage_out)
         CUDA_TRY(cudaMalloc(&p->d_stage_out, bytes));
-    if (!p->d_stage_in2) {
+    if (!p->d_stage_in2)
         CUDA_TRY(cudaMalloc(&p->d_stage_in2, bytes));
+    if (!p->d_stage_out2)
         CUDA_TRY(cudaMalloc(&p->d_stage_out2, bytes));
-        for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
+        if (!p->pipe_st[i])
             CUDA_TRY(cudaStreamCreateWithFlags(&p->pipe_st[i], cudaStreamNonBlocking));
-        for (int b = 0; b < 2; ++b)
-            for (int e = 0; e < 3; ++e)
+    for (int b = 0; b < 2; ++b)
+        for (int e = 0; e < 3; ++e)
+            if (!p->pipe_ev[b][e])
                 CUDA_TRY(cudaEventCreateWithFlags(&p->pipe_ev[b][e], cudaEventDisableTiming));
-    }
     cudaStream_t user = (cudaStream_t)stream;
     cudaStream_t h2d = p->pipe_st[0], comp = p->pipe_st[1], d2h = p->pipe_st[2];
     float2 *din[2] = {p->d_stage_in, p->d_stage_in2}, *dout[2] = {p->d_stage_out, p->d_stage_out2};

@@ -244,9 +244,8 @@ def test_execute_host_buffers():
 @pytest.mark.parametrize("direction", [FWD, INV])
 def test_execute_host_direct_and_staged(decomp, opts, dtype, direction):
     """Host buffers, both ways: pinned buffers (the first pass reads the host
-    input and the last pass writes the host output directly, where the
-    schedule allows) and pageable numpy buffers (staged copies) give the
-    oracle's transform; the input is left unchanged."""
+    input directly where the schedule allows) and pageable numpy buffers
+    (staged copies) give the oracle's transform; the input is left unchanged."""
     shape, batch = (1024, 24, 40), 1
     n0, n1, n2 = shape
     c128 = dtype == fft3.FFT3_C128_FP64
@@ -275,19 +274,37 @@ def test_execute_host_direct_and_staged(decomp, opts, dtype, direction):
         fft3.fft3_plan_destroy(h)
 
 
-def test_execute_host_pipelined():
+@pytest.mark.parametrize("shape,opts,pinned", [((64, 40, 24), {}, True), ((64, 512, 512), {"variant": 2}, True),
+                                               ((64, 40, 24), {}, False)])
+def test_execute_host_pipelined(shape, opts, pinned):
     """Five transforms of different inputs from and to host memory with the
-    copies of neighbouring transforms overlapping; every output is checked."""
-    shape = (64, 40, 24)
-    xs = [synth.uniform_c64((1, 24, 40, 64), 30 + i) for i in range(5)]
-    h = fft3.fft3_plan_create_ex(*shape, 1, 0, P, FWD, fft3.make_options())
+    copies of neighbouring transforms overlapping, pinned and pageable host
+    buffers, the natural and the blocked schedule; every output is checked,
+    and the pipelined and the single-transform forms alternate on one plan."""
+    n0, n1, n2 = shape
+    xs = [synth.uniform_c64((1, n2, n1, n0), 30 + i) for i in range(5)]
+    h = fft3.fft3_plan_create_ex(*shape, 1, 0, P, FWD, fft3.make_options(**opts))
     try:
-        hin = [torch.from_numpy(x).pin_memory() for x in xs]
-        hout = [torch.empty_like(t).pin_memory() for t in hin]
-        fft3.fft3_plan_execute_host_pipelined(h, [t.data_ptr() for t in hin], [t.data_ptr() for t in hout], 0)
-        assert fft3.fft3_plan_check(h) == 0
-        for x, o in zip(xs, hout):
-            assert_parity(x, o.numpy(), shape)
+        assert fft3.fft3_plan_describe(h)["host_direct"] is True
+        if pinned:
+            hin = [torch.from_numpy(x).pin_memory() for x in xs]
+            hout = [torch.full_like(t, complex(float("nan"), 0.0)).pin_memory() for t in hin]
+            ptr = lambda t: t.data_ptr()
+            arr = lambda t: t.numpy()
+        else:
+            hin = [np.ascontiguousarray(x) for x in xs]
+            hout = [np.full_like(x, np.nan) for x in xs]
+            ptr = lambda t: t.ctypes.data
+            arr = lambda t: t
+        for _ in range(2):
+            fft3.fft3_plan_execute_host_pipelined(h, [ptr(t) for t in hin], [ptr(t) for t in hout], 0)
+            assert fft3.fft3_plan_check(h) == 0
+            for x, o in zip(xs, hout):
+                assert_parity(x, arr(o), shape)
+            # the other form on the same plan, then this one again
+            one = np.full_like(xs[0], np.nan)
+            fft3.fft3_plan_execute_host(h, xs[0].ctypes.data, one.ctypes.data, 0)
+            assert_parity(xs[0], one, shape)
         fft3.fft3_plan_execute_host_pipelined(h, [], [], 0)  # count 0 is a no-op
     finally:
         fft3.fft3_plan_destroy(h)
