@@ -261,8 +261,13 @@ def test_execute_host_direct_and_staged(decomp, opts, dtype, direction):
         pinned_out = torch.full_like(pinned_in, complex(float("nan"), float("nan"))).pin_memory()
         page_in = np.ascontiguousarray(x.copy())
         page_out = np.full_like(page_in, np.nan)
+        page_out2 = np.full_like(page_in, np.nan)
+        pinned_out2 = torch.full_like(pinned_in, complex(float("nan"), float("nan"))).pin_memory()
+        # pinned, pageable, and the two mixes (the direct input path depends on the input only)
         for src, dst, keep in ((pinned_in.data_ptr(), pinned_out, pinned_in.numpy()),
-                               (page_in.ctypes.data, page_out, page_in)):
+                               (page_in.ctypes.data, page_out, page_in),
+                               (pinned_in.data_ptr(), page_out2, pinned_in.numpy()),
+                               (page_in.ctypes.data, pinned_out2, page_in)):
             fft3.fft3_plan_execute_host(h, src, dst.data_ptr() if hasattr(dst, "data_ptr") else dst.ctypes.data, 0)
             got = dst.numpy() if hasattr(dst, "numpy") else dst
             assert np.array_equal(keep, x), "input modified"
