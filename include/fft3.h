@@ -249,7 +249,14 @@ int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int d
 /* decomp: 1 = slab-pencil, 2 = pencil-pencil-pencil, 3 = the segmented passes
  * (whole batch: every code must ask for it); tile_code: columns per
  * tile of the strided phases, 1 -> 4, 2 -> 8, 3 -> 16, 4 -> 32; items_code:
- * slabs (slab-pencil) or rows (pencil) per first-phase work item, k -> 2^(k-1). */
+ * slabs (slab-pencil) or rows (pencil) per first-phase work item, k -> 2^(k-1).
+ * FFT3_TUNE_SLABZ or'ed into every code: the slab-by-slab executor, one
+ * persistent launch in which a work item is one n0 x n1 slab of a problem
+ * (x and y lines in shared memory, one read and one write) or a tile of its z
+ * lines (read through L2 once the problem's slabs are done), with the
+ * compile-time line kernels of the segmented passes (lengths 8 .. 128 of
+ * their list; FFT3_ERR_UNSUPPORTED_SIZE otherwise). */
+#define FFT3_TUNE_SLABZ (1 << 11)
 int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets,
                           int dtype, int decomposition, int direction, const int *tuning);
 

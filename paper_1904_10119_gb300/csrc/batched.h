@@ -22,6 +22,7 @@ struct BatchCube {
     int lpt;        // columns per tile of the z phase
     int lpty;       // columns per tile of the y phase (pencil-pencil-pencil)
     int spi;        // slabs (BD_SLAB) or rows (BD_PPP) per phase-0 item
+    int zpi;        // the slab executor: z tiles per z item
 };
 
 struct BatchItem {
@@ -93,5 +94,19 @@ struct SegAllArgs {
 };
 
 constexpr int kSegAllThreads = 256;
+
+// The slab-by-slab executor (k_slabz.cu): the item executor's tables, and
+// the twiddle tables of the segmented line kernels (all of them, copied to
+// shared memory), tw_c[k] / tw_s[k] the offset of the k-th contiguous /
+// strided kernel's table, tw_w[k] of the k-th length's table w_N^m.
+struct SlabZArgs {
+    BatchArgs b;
+    const float2 *tw;
+    int tw_len;
+    int tw_c[16], tw_s[16];
+    int tw_w[16]; // w_N^m (m < N) for the warp-shuffle row kernels, lengths 8 .. 128 in order
+};
+__global__ void k_slabz(SlabZArgs z);
+int slabz_smem_bytes(int tw_len, int buf_elems);
 
 } // namespace fft3

@@ -43,6 +43,11 @@ struct BatchState {
     // the segmented passes as one cooperative launch (k_seg_all): waves of
     // problems, steps of segments, and their tables
     int seg1 = 0;
+    // the slab-by-slab executor (k_slabz): tuning codes with FFT3_TUNE_SLABZ
+    int slabz = 0;
+    int sz_tw_c[16] = {}, sz_tw_s[16] = {}, sz_tw_w[16] = {};
+    int sz_smem = 0;
+    dim3 sz_grid;
     int waves = 1;
     std::vector<SegAllSeg> sa_segs;
     std::vector<int> sa_seg0, sa_list, sa_tcube;
@@ -152,6 +157,10 @@ static int line_index(BatchState *b, std::map<std::pair<int, int>, int> &idx, in
 // Elements per shared buffer that keep four blocks of 256 threads on an SM.
 constexpr int kBatchBufTarget = 3072;
 
+// Shared-memory values the slab executor gives a work item's stacked slabs:
+// one 96 x 96 slab with its padding.
+constexpr int kSlabzRoom = 96 * 101;
+
 // FFT3_AUTO without tuning codes runs the segmented passes from this many
 // values on (every line length compiled in seg_plans.h).
 constexpr int64_t kSegMinElems = 1ll << 22;
@@ -233,11 +242,14 @@ int batch_describe(const BatchState *b, std::string *json)
         e.second = b->tuning[i];
     }
     o << "{\"batched\":true,\"mode\":\""
-      << (b->seg1 ? "segmented_one_launch" : b->seg ? "segmented" : "executor") << "\",\"kernel_launches\":"
+      << (b->seg1 ? "segmented_one_launch" : b->seg ? "segmented" : b->slabz ? "slab_executor" : "executor")
+      << "\",\"kernel_launches\":"
       << batch_kernel_launches(b) << ",\"problems\":" << b->cubes.size() << ",\"items\":" << b->items.size()
       << ",\"groups\":" << b->groups << ",\"line_plans\":" << b->lines.size() << ",\"grid\":" << b->grid.x
       << ",\"block\":" << b->threads << ",\"smem\":" << b->smem << ",\"prefetch\":" << b->prefetch << ",\"twiddle_entries\":" << b->tw_total
       << ",\"extent\":" << b->extent;
+    if (b->slabz)
+        o << ",\"slab_executor_grid\":" << b->sz_grid.x << ",\"slab_executor_smem\":" << b->sz_smem;
     if (b->seg1)
         o << ",\"waves\":" << b->waves << ",\"steps\":" << b->sa_ntiles.size() << ",\"segments\":" << b->sa_segs.size()
           << ",\"one_launch_grid\":" << b->sa_grid.x << ",\"one_launch_smem\":" << b->sa_smem;
@@ -347,6 +359,21 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
             if (e != cudaSuccess)
                 break;
         }
+    } else if (b->slabz) {
+        SlabZArgs z{};
+        z.b = a;
+        z.tw = b->d_tw + b->sa_tw_off;
+        z.tw_len = b->sa_tw_len;
+        for (int k = 0; k < 16; ++k) {
+            z.tw_c[k] = b->sz_tw_c[k];
+            z.tw_s[k] = b->sz_tw_s[k];
+            z.tw_w[k] = b->sz_tw_w[k];
+        }
+        e = cudaMemsetAsync(b->d_counters, 0, b->counters_bytes, b->cap_stream);
+        if (e == cudaSuccess) {
+            void *params[1] = {&z};
+            e = cudaLaunchKernel((const void *)&k_slabz, b->sz_grid, dim3(256), params, b->sz_smem, b->cap_stream);
+        }
     } else {
         e = cudaMemsetAsync(b->d_counters, 0, b->counters_bytes, b->cap_stream);
         if (e == cudaSuccess) {
@@ -414,6 +441,11 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
     b->tuning.resize(count);
     int64_t extent = 0;
     int bufmax = 1;
+    // FFT3_TUNE_SLABZ on every code: the slab-by-slab executor
+    int slabz = tuning ? 1 : 0;
+    for (int i = 0; slabz && i < count; ++i)
+        slabz = (tuning[i] & FFT3_TUNE_SLABZ) ? 1 : 0;
+    b->slabz = slabz;
     for (int i = 0; i < count; ++i) {
         const int n0 = dims[3 * i], n1 = dims[3 * i + 1], n2 = dims[3 * i + 2];
         if (n0 < 1 || n1 < 1 || n2 < 1 || n0 > kBatchMaxLine || n1 > kBatchMaxLine || n2 > kBatchMaxLine ||
@@ -423,6 +455,8 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
                                                        std::to_string(kBatchMaxLine) + ", offsets non-negative");
         }
         int code = tuning ? tuning[i] : 0;
+        if (slabz)
+            code = (code & ~3) | 1;
         if (decomposition == FFT3_SLAB_PENCIL && (code & 3) == 0)
             code |= 1;
         if (decomposition == FFT3_PENCIL3 && (code & 3) == 0)
@@ -441,7 +475,34 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, err);
         }
         c.lx = lx; c.ly = ly; c.lz = lz;
-        if (decomp == BD_SLAB) {
+        if (slabz) {
+            // one slab per item; z tiles as wide as the strided line kernel of n2
+            int scnt = 0;
+            const SegKernel *sk = seg_kernels(false, &scnt);
+            int zl = 0;
+            for (int k = 0; k < scnt; ++k)
+                zl = sk[k].n == n2 ? sk[k].lpt : zl;
+            if (!zl)
+                return fail(FFT3_ERR_UNSUPPORTED_SIZE, "the slab executor has no compiled line kernel for length " +
+                                                           std::to_string(n2));
+            // items of about 8 Ki values: several small slabs stacked in the
+            // buffer (at most the room of one 96 x 96 slab), several z tiles
+            // (as many at a time as 256 threads hold groups of the line kernel)
+            int zt = 0;
+            for (int k = 0; k < scnt; ++k)
+                zt = sk[k].n == n2 ? sk[k].T * sk[k].lpt : zt;
+            const int zg = std::max(1, 256 / zt);
+            decomp = BD_SLAB;
+            c.decomp = BD_SLAB;
+            c.lpt = lpt = zl;
+            c.spi = std::max(1, std::min({n2, 8192 / (n0 * n1), kSlabzRoom / (n1 * pitch_b(n0))}));
+            c.zpi = std::max(zg, 8192 / (zl * n2) / zg * zg);
+            c.nph = 2;
+            c.items[0] = (n2 + c.spi - 1) / c.spi;
+            c.items[1] = ((n0 * n1 + zl - 1) / zl + c.zpi - 1) / c.zpi;
+            c.items[2] = 0;
+            bufmax = std::max(bufmax, std::max(c.spi * n1 * pitch_b(n0), zg * zl * n2));
+        } else if (decomp == BD_SLAB) {
             c.spi = std::max(1, std::min(spi, n2));
             c.nph = 2;
             c.items[0] = (n2 + c.spi - 1) / c.spi;
@@ -461,6 +522,20 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
         extent = std::max(extent, offsets[i] + (int64_t)n0 * n1 * n2);
     }
     b->extent = extent;
+    if (slabz) {
+        int cc = 0, sc = 0;
+        const SegKernel *kc = seg_kernels(true, &cc), *ks = seg_kernels(false, &sc);
+        for (int i = 0; i < count; ++i) {
+            bool x = false, y = false;
+            for (int k = 0; k < cc; ++k)
+                x = x || kc[k].n == dims[3 * i];
+            for (int k = 0; k < sc; ++k)
+                y = y || ks[k].n == dims[3 * i + 1];
+            if (!x || !y)
+                return fail(FFT3_ERR_UNSUPPORTED_SIZE, "the slab executor has no compiled line kernel for a length "
+                                                       "of problem " + std::to_string(i));
+        }
+    }
     // segmented mode: every line length compiled, and every tuning code asks
     // for it (decomposition field 3), or FFT3_AUTO without tuning codes (a
     // null array; an array of zeros keeps the executor) on a large enough batch
@@ -605,10 +680,10 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
             }
         }
     }
-    if (b->seg1) {
+    std::vector<int> kt(ccnt + scnt);
+    if (b->seg1 || b->slabz) {
         // every line kernel's twiddle table, one after the other (copied to
-        // shared memory by every block of the one-launch executor)
-        std::vector<int> kt(ccnt + scnt);
+        // shared memory by every block of the one-launch executors)
         b->sa_tw_off = tw_total;
         int64_t local = 0;
         for (int k = 0; k < ccnt + scnt; ++k) {
@@ -630,8 +705,29 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
             exps.push_back(std::move(e));
             exp_n.push_back(K.n);
         }
+        if (b->slabz) {
+            // w_N^m, m < N, for the warp-shuffle row kernels of the slab executor
+            const int wl[10] = {8, 16, 24, 32, 40, 48, 64, 80, 96, 128};
+            for (int k = 0; k < 10; ++k) {
+                std::vector<int64_t> e(wl[k]);
+                for (int m = 0; m < wl[k]; ++m)
+                    e[m] = m;
+                b->sz_tw_w[k] = (int)local;
+                segs.push_back({tw_total + local, (int64_t)e.size()});
+                local += ((int64_t)e.size() + 15) / 16 * 16;
+                exps.push_back(std::move(e));
+                exp_n.push_back(wl[k]);
+            }
+        }
         b->sa_tw_len = (int)local;
         tw_total += local;
+        for (int k = 0; k < ccnt && k < 16; ++k)
+            b->sz_tw_c[k] = kt[k];
+        for (int k = 0; k < scnt && k < 16; ++k)
+            b->sz_tw_s[k] = kt[ccnt + k];
+        b->sz_smem = slabz_smem_bytes(b->sa_tw_len, (bufmax + 31) / 32 * 32);
+    }
+    if (b->seg1) {
         // waves: consecutive problems of about equal volume
         std::vector<int> wave_of(count);
         {
@@ -846,6 +942,15 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         rc = prepare_func((const void *)&k_seg_all, b->sa_smem);
         if (!rc)
             rc = occupancy_grid((const void *)&k_seg_all, kSegAllThreads, b->sa_smem, 0, dev, &b->sa_grid);
+        if (rc)
+            return bail(rc);
+    }
+    if (b->slabz) {
+        if (b->sz_smem > 227 * 1024)
+            return bail(fail(FFT3_ERR_UNSUPPORTED_SIZE, "a slab of this batch needs more shared memory than a block has"));
+        rc = prepare_func((const void *)&k_slabz, b->sz_smem);
+        if (!rc)
+            rc = occupancy_grid((const void *)&k_slabz, 256, b->sz_smem, 0, dev, &b->sz_grid);
         if (rc)
             return bail(rc);
     }

@@ -1,0 +1,284 @@
+// k_slabz.cu -- batched uneven 3D DFTs in one persistent launch, slab by slab
+// (the slab-pencil decomposition of Section 2.3 applied to every problem):
+//   slab items: one n0 x n1 slab of a problem is read from global memory into
+//               shared memory, its x lines (rows) and then its y lines
+//               (columns) are transformed there, and it is written back: one
+//               read and one write per value for the 2D stage;
+//   z items:    a tile of adjacent columns of a problem's n0*n1 plane, its z
+//               lines read through L2 (the slabs were written earlier in the
+//               launch), transformed and written back in place.
+// The line transforms are the compile-time Stockham engines of the segmented
+// passes (seg_plans.h: one radix list and thread count per line length), so
+// the per-value instruction count is theirs, not that of a runtime-radix loop.
+// Work items come from a ticket counter in the order the host gives them
+// (problems in groups, the z items of a group after the slab items of the
+// next group, so a problem's slabs are still in L2 when its z items read
+// them); a z item first waits until every slab item of its problem has
+// finished.  Those slab items hold smaller tickets, so they were claimed by
+// blocks that are already running and never wait: every wait ends.  Each wait
+// is still bounded (about two seconds of clock cycles); on expiry the kernel
+// records kErrWaitTimeout and carries on.
+#include "batched.h"
+#include "pass_kernels.cuh"
+#include "seg_plans.h"
+#include "warp_fft.cuh"
+
+namespace fft3 {
+
+namespace {
+
+constexpr int kSzThreads = 256;
+
+// Shared-memory accessors with a validity flag: an invalid line reads zeros
+// and stores nothing, so every thread of the block can run every barrier of
+// an engine whatever the number of lines.
+struct SzRow { // row of the padded slab buffer: element j at p[padpos(j)]
+    float2 *p;
+    bool valid;
+    __device__ __forceinline__ float2 operator()(int j) const { return valid ? p[padpos(j)] : make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void operator()(int k, float2 v) const
+    {
+        if (valid)
+            p[padpos(k)] = v;
+    }
+};
+struct SzCol { // column of the padded slab buffer: element j at p[j * pitch]
+    float2 *p;
+    int pitch;
+    bool valid;
+    __device__ __forceinline__ float2 operator()(int j) const { return valid ? p[j * pitch] : make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void operator()(int k, float2 v) const
+    {
+        if (valid)
+            p[k * pitch] = v;
+    }
+};
+// Column l of the z tile buffer: element j at p[j * LPT].
+template <int LPT>
+struct SzTile {
+    float2 *p;
+    bool valid;
+    __device__ __forceinline__ float2 operator()(int j) const { return valid ? p[j * LPT] : make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void operator()(int k, float2 v) const
+    {
+        if (valid)
+            p[k * LPT] = v;
+    }
+};
+// Strided global line read through L2 (written earlier in this launch by
+// other blocks) / written back.
+struct SzGLoad {
+    const float2 *p;
+    int64_t s;
+    bool valid, conj;
+    __device__ __forceinline__ float2 operator()(int j) const
+    {
+        const float2 v = valid ? __ldcg(p + (int64_t)j * s) : make_float2(0.f, 0.f);
+        return conj ? cconj(v) : v;
+    }
+};
+
+// Rows of the stacked slabs (x lines) straight from global memory into the
+// padded shared buffer: a row in the registers of L/2 lanes (warp_fft.cuh),
+// 512 / L rows per round, no barrier; `w` is the table w_N^m (m < N).
+template <int N, int R, int L>
+__device__ __noinline__ void sz_rows_warp(const float2 *src, float2 *A, int pitch, int rows, const float2 *w,
+                                          bool conj)
+{
+    using WL = WarpLine<N, R, L>;
+    constexpr int RPR = kSzThreads / WL::W; // rows per round
+    const int u = threadIdx.x % WL::W, l = threadIdx.x / WL::W;
+    typename WL::Tw tw;
+    WL::load_tw(tw, w, u);
+    for (int r0 = 0; r0 < rows; r0 += RPR) {
+        const int row = r0 + l;
+        const bool valid = row < rows;
+        float2 v[2][R];
+        WL::load(v, src + (int64_t)(valid ? row : 0) * N, u, valid, conj);
+        WL::run(v, tw, u);
+        if (valid) {
+            float2 *ar = A + row * pitch;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int k0 = R * WL::rev(2 * u + e);
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    ar[padpos(k0 + k)] = v[e][k];
+            }
+        }
+    }
+}
+
+// Columns of the stacked slabs (y lines): column cc is column cc mod w of
+// slab cc / w (slabs slab_stride values apart in shared memory, w N apart in
+// global memory); 256 / T columns per round, adjacent threads on adjacent
+// columns (conflict-free through the padding).  The last stage stores to the
+// output slabs in global memory (element k of column (cs, c) at
+// dst[(cs N + k) w + c]: adjacent threads, adjacent addresses).
+template <int N, int T, class Rad>
+__device__ __noinline__ void sz_cols(float2 *A, int pitch, int cols, int w, int slab_stride, float2 *dst,
+                                     const float2 *tw, bool conj)
+{
+    constexpr int L = kSzThreads / T;
+    const int tid = threadIdx.x;
+    const int l = tid % L, t = tid / L;
+    for (int c0 = 0; c0 < cols; c0 += L) { // rounds touch disjoint columns: no barrier between them
+        const int c = c0 + l;
+        const bool valid = t < T && c < cols;
+        const int cs = valid ? c / w : 0, cc = valid ? c - cs * w : 0;
+        SzCol acc{A + cs * slab_stride + padpos(cc), pitch, valid};
+        GStore out{dst + (int64_t)cs * N * w + cc, w, valid, conj};
+        EngineFixed<N, T, 1, Rad>::template run<false, false>(t < T ? t : 0, acc, acc, out, tw);
+    }
+}
+
+// Tiles [t0, t1) of LPT adjacent columns of the n0*n1 plane (z lines, element
+// stride es), in place through the shared tile buffers: 256 / (T LPT) tiles
+// at a time, one per thread group.
+template <int N, int T, class Rad, int LPT>
+__device__ __noinline__ void sz_ztiles(float2 *base, int64_t t0, int64_t t1, int64_t ncols, int64_t es, float2 *buf,
+                                       const float2 *tw, bool conj)
+{
+    constexpr int GT = T * LPT, G = kSzThreads / GT;
+    const int tid = threadIdx.x, g = tid / GT, gl = tid % GT;
+    const int l = gl % LPT, t = gl / LPT;
+    for (int64_t tile0 = t0; tile0 < t1; tile0 += G) {
+        if (tile0 > t0)
+            __syncthreads(); // the tile buffers are free
+        const int64_t tile = tile0 + g, c = tile * LPT + l;
+        const bool valid = g < G && tile < t1 && c < ncols;
+        float2 *p = base + (valid ? c : 0);
+        SzGLoad src{p, es, valid, conj};
+        GStore dst{p, es, valid, conj};
+        SzTile<LPT> sm{buf + (g < G ? g : 0) * (LPT * N) + l, valid};
+        EngineFixed<N, T, 1, Rad>::template run<true, false>(t, src, sm, dst, tw);
+    }
+}
+
+// x-row kernels of the slab items: the warp-shuffle transform of each length.
+#define FFT3_SZ_WARP_ROWS(X) \
+    X(8, 4, 2)               \
+    X(16, 4, 4)              \
+    X(24, 3, 8)              \
+    X(32, 4, 8)              \
+    X(40, 10, 4)             \
+    X(48, 6, 8)              \
+    X(64, 8, 8)              \
+    X(80, 10, 8)             \
+    X(96, 6, 16)             \
+    X(128, 8, 16)
+
+__device__ __forceinline__ void sz_run_rows_warp(int n0, const float2 *src, float2 *A, int pitch, int rows,
+                                                 const float2 *tw, const int *off, bool conj)
+{
+    int k = 0;
+#define FFT3_SZ_WROW(N, R, L)                                                        \
+    if (n0 == N) {                                                                   \
+        sz_rows_warp<N, R, L>(src, A, pitch, rows, tw + off[k], conj);              \
+        return;                                                                      \
+    }                                                                                \
+    ++k;
+    FFT3_SZ_WARP_ROWS(FFT3_SZ_WROW)
+#undef FFT3_SZ_WROW
+}
+
+__device__ __forceinline__ void sz_run_cols(int n1, float2 *A, int pitch, int cols, int w, int slab_stride,
+                                            float2 *dst, const float2 *tw, const int *off, bool conj)
+{
+    int k = 0;
+#define FFT3_SZ_COLS(N, T, L, ...)                                                              \
+    if (n1 == N) {                                                                              \
+        sz_cols<N, T, Radices<__VA_ARGS__>>(A, pitch, cols, w, slab_stride, dst, tw + off[k], conj); \
+        return;                                                                                 \
+    }                                                                                           \
+    ++k;
+    FFT3_SEG_PLANS_STRIDED(FFT3_SZ_COLS)
+#undef FFT3_SZ_COLS
+}
+
+__device__ __forceinline__ void sz_run_ztiles(int n2, float2 *base, int64_t t0, int64_t t1, int64_t ncols,
+                                              int64_t es, float2 *buf, const float2 *tw, const int *off, bool conj)
+{
+    int k = 0;
+#define FFT3_SZ_Z(N, T, L, ...)                                                                      \
+    if (n2 == N) {                                                                                   \
+        sz_ztiles<N, T, Radices<__VA_ARGS__>, L>(base, t0, t1, ncols, es, buf, tw + off[k], conj);   \
+        return;                                                                                      \
+    }                                                                                                \
+    ++k;
+    FFT3_SEG_PLANS_STRIDED(FFT3_SZ_Z)
+#undef FFT3_SZ_Z
+}
+
+__device__ __forceinline__ int ld_acquire_sz(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+} // namespace
+
+__global__ void __launch_bounds__(kSzThreads, 2) k_slabz(SlabZArgs z)
+{
+    extern __shared__ __align__(16) float2 smem[];
+    const BatchArgs &a = z.b;
+    float2 *tw = smem;
+    float2 *A = smem + tw_slots(z.tw_len);
+    for (int i = threadIdx.x; i < z.tw_len; i += blockDim.x)
+        tw[i] = z.tw[i];
+    __shared__ int s_q, s_next;
+    const bool conj = a.conj != 0;
+    if (threadIdx.x == 0)
+        s_next = atomicAdd(a.counters, 1);
+    for (;;) {
+        __syncthreads(); // the previous item's buffer (and, first, the twiddles); s_next written
+        const int q = s_next;
+        if (q >= a.nitems)
+            break;
+        __syncthreads(); // every thread has read s_next
+        if (threadIdx.x == 0)
+            s_next = atomicAdd(a.counters, 1); // the next item, claimed while this one runs
+        const BatchItem it = a.items[q];
+        const BatchCube &cb = a.cubes[it.cube];
+        const int n0 = cb.n0, n1 = cb.n1, n2 = cb.n2;
+        if (it.phase == 0) {
+            // slabs [index * spi, ...) stacked in shared memory: all their rows,
+            // then all their columns
+            const int s0 = it.index * cb.spi, ns = min(n2, s0 + cb.spi) - s0;
+            const int P = line_pitch(n0);
+            const float2 *src = a.in + cb.off + (int64_t)s0 * n0 * n1;
+            float2 *dst = a.out + cb.off + (int64_t)s0 * n0 * n1;
+            sz_run_rows_warp(n0, src, A, P, n1 * ns, tw, z.tw_w, conj);
+            __syncthreads();
+            sz_run_cols(n1, A, P, n0 * ns, n0, n1 * P, dst, tw, z.tw_s, conj);
+        } else {
+            if (threadIdx.x == 0) {
+                const int *done = a.counters + 1 + 3 * it.cube;
+                const long long t0 = clock64();
+                while (ld_acquire_sz(done) < cb.items[0]) {
+                    if (clock64() - t0 > a.wait_budget) {
+                        atomicOr(a.err, kErrWaitTimeout);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __syncthreads();
+            const int64_t plane = (int64_t)n0 * n1, ntiles = (plane + cb.lpt - 1) / cb.lpt;
+            const int64_t t0 = (int64_t)it.index * cb.zpi, t1 = min(ntiles, t0 + cb.zpi);
+            sz_run_ztiles(n2, a.out + cb.off, t0, t1, plane, plane, A, tw, z.tw_s, conj);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.counters + 1 + 3 * it.cube + it.phase, 1);
+        }
+    }
+}
+
+// Shared memory of one block: the twiddle tables and the larger of a padded
+// n0 x n1 slab and a z tile.
+int slabz_smem_bytes(int tw_len, int buf_elems) { return (tw_slots(tw_len) + buf_elems) * (int)sizeof(float2); }
+
+} // namespace fft3

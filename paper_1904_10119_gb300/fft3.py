@@ -320,6 +320,9 @@ def fft3_autotune_many(dims, direction=FFT3_FORWARD, reps: int = 3, max_per_clas
     return [int(t[i]) for i in range(count)]
 
 
+FFT3_TUNE_SLABZ = 1 << 11  # or'ed into every tuning code: the slab-by-slab executor
+
+
 def tune_code(decomp: int, radix_order: int = 0, tile_code: int = 0, items_code: int = 0) -> int:
     """FFT3_TUNE of include/fft3.h."""
     return decomp | ((radix_order + 1) << 2) | (tile_code << 5) | (items_code << 8)

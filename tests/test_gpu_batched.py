@@ -121,6 +121,45 @@ def test_4096_uneven_cubes_sampled_and_parseval():
         assert abs(sg - N * sx) <= 1e-5 * N * sx
 
 
+@pytest.mark.parametrize("gap", [0, 5])
+@pytest.mark.parametrize("direction", [fft3.FFT3_FORWARD, fft3.FFT3_INVERSE])
+def test_slab_executor_every_problem(gap, direction):
+    """FFT3_TUNE_SLABZ: one persistent launch of slab items (x and y lines of
+    one slab in shared memory) and z-tile items (read through L2 once the
+    problem's slabs are done); every line length, every problem against the
+    oracle, problems at aligned and odd offsets."""
+    dims = np.vstack([synth.batched_dims(40, 13), [[8, 128, 16], [128, 8, 96], [24, 40, 8], [16, 16, 128],
+                                                   [96, 96, 8]]])
+    offs, total = _layout(dims, gap=gap)
+    code = fft3.tune_code(1) | fft3.FFT3_TUNE_SLABZ
+    x, got, desc = _run(dims, offs, total, direction=direction, tuning=[code] * len(dims), seed=4 + gap)
+    assert desc["mode"] == "slab_executor" and desc["kernel_launches"] == 1
+    assert desc["items"] < sum(int(d[2]) + -(-int(d[0] * d[1]) // 32) for d in dims)  # slabs / tiles grouped
+    for off, d in zip(offs, dims):
+        _check_problem(x, got, int(off), d, direction)
+
+
+def test_slab_executor_4096_cubes_sampled_and_parseval():
+    dims = synth.batched_dims(4096, 7)
+    offs, total = _layout(dims)
+    x, got, desc = _run(dims, offs, total, seed=7, tuning=[fft3.tune_code(1) | fft3.FFT3_TUNE_SLABZ] * len(dims))
+    assert desc["mode"] == "slab_executor"
+    rng = np.random.default_rng(2)
+    seen, sample = set(), []
+    for i, d in enumerate(map(tuple, dims)):
+        if d not in seen:
+            seen.add(d)
+            sample.append(i)
+    sample += list(rng.choice(len(dims), size=32, replace=False))
+    for i in sample[:128]:
+        _check_problem(x, got, int(offs[i]), dims[i], fft3.FFT3_FORWARD)
+    x2 = np.abs(x.astype(np.complex128)) ** 2
+    g2 = np.abs(got.astype(np.complex128)) ** 2
+    for off, d in zip(offs, dims):
+        N = int(np.prod(d))
+        assert abs(g2[off:off + N].sum() - N * x2[off:off + N].sum()) <= 1e-5 * N * x2[off:off + N].sum()
+
+
 @pytest.mark.parametrize("direction", [fft3.FFT3_FORWARD, fft3.FFT3_INVERSE])
 def test_segmented_passes_every_problem(direction):
     """Tuning code decomposition field 3: the batch runs as three segmented
