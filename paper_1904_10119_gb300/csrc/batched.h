@@ -96,9 +96,9 @@ struct SegAllArgs {
 constexpr int kSegAllThreads = 256;
 
 // The slab-by-slab executor (k_slabz.cu): the item executor's tables, and
-// the twiddle tables of the segmented line kernels (all of them, copied to
-// shared memory), tw_c[k] / tw_s[k] the offset of the k-th contiguous /
-// strided kernel's table, tw_w[k] of the k-th length's table w_N^m.
+// the twiddle tables of the segmented line kernels (all of them, read
+// through L1), tw_c[k] / tw_s[k] the offset of the k-th contiguous / strided
+// kernel's table, tw_w[k] of the k-th length's table w_N^m.
 struct SlabZArgs {
     BatchArgs b;
     const float2 *tw;
@@ -107,6 +107,6 @@ struct SlabZArgs {
     int tw_w[16]; // w_N^m (m < N) for the warp-shuffle row kernels, lengths 8 .. 128 in order
 };
 __global__ void k_slabz(SlabZArgs z);
-int slabz_smem_bytes(int tw_len, int buf_elems);
+int slabz_smem_bytes(int buf_elems);
 
 } // namespace fft3

@@ -158,8 +158,8 @@ static int line_index(BatchState *b, std::map<std::pair<int, int>, int> &idx, in
 constexpr int kBatchBufTarget = 3072;
 
 // Shared-memory values the slab executor gives a work item's stacked slabs:
-// one 96 x 96 slab with its padding.
-constexpr int kSlabzRoom = 96 * 101;
+// one 96 x 96 slab with its rows 97 values apart.
+constexpr int kSlabzRoom = 96 * 97;
 
 // FFT3_AUTO without tuning codes runs the segmented passes from this many
 // values on (every line length compiled in seg_plans.h).
@@ -495,13 +495,13 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
             decomp = BD_SLAB;
             c.decomp = BD_SLAB;
             c.lpt = lpt = zl;
-            c.spi = std::max(1, std::min({n2, 8192 / (n0 * n1), kSlabzRoom / (n1 * pitch_b(n0))}));
+            c.spi = std::max(1, std::min({n2, 8192 / (n0 * n1), kSlabzRoom / (n1 * (n0 | 1))}));
             c.zpi = std::max(zg, 8192 / (zl * n2) / zg * zg);
             c.nph = 2;
             c.items[0] = (n2 + c.spi - 1) / c.spi;
             c.items[1] = ((n0 * n1 + zl - 1) / zl + c.zpi - 1) / c.zpi;
             c.items[2] = 0;
-            bufmax = std::max(bufmax, std::max(c.spi * n1 * pitch_b(n0), zg * zl * n2));
+            bufmax = std::max(bufmax, std::max(c.spi * n1 * (n0 | 1), zg * zl * n2));
         } else if (decomp == BD_SLAB) {
             c.spi = std::max(1, std::min(spi, n2));
             c.nph = 2;
@@ -725,7 +725,7 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
             b->sz_tw_c[k] = kt[k];
         for (int k = 0; k < scnt && k < 16; ++k)
             b->sz_tw_s[k] = kt[ccnt + k];
-        b->sz_smem = slabz_smem_bytes(b->sa_tw_len, (bufmax + 31) / 32 * 32);
+        b->sz_smem = slabz_smem_bytes((bufmax + 31) / 32 * 32);
     }
     if (b->seg1) {
         // waves: consecutive problems of about equal volume

@@ -79,8 +79,9 @@ struct SzGLoad {
 };
 
 // Rows of the stacked slabs (x lines) straight from global memory into the
-// padded shared buffer: a row in the registers of L/2 lanes (warp_fft.cuh),
-// 512 / L rows per round, no barrier; `w` is the table w_N^m (m < N).
+// shared buffer (rows `pitch` values apart, pitch odd): a row in the
+// registers of L/2 lanes (warp_fft.cuh), 512 / L rows per round, no barrier;
+// `w` is the table w_N^m (m < N).
 template <int N, int R, int L>
 __device__ __noinline__ void sz_rows_warp(const float2 *src, float2 *A, int pitch, int rows, const float2 *w,
                                           bool conj)
@@ -103,7 +104,7 @@ __device__ __noinline__ void sz_rows_warp(const float2 *src, float2 *A, int pitc
                 const int k0 = R * WL::rev(2 * u + e);
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    ar[padpos(k0 + k)] = v[e][k];
+                    ar[k0 + k] = v[e][k];
             }
         }
     }
@@ -112,7 +113,7 @@ __device__ __noinline__ void sz_rows_warp(const float2 *src, float2 *A, int pitc
 // Columns of the stacked slabs (y lines): column cc is column cc mod w of
 // slab cc / w (slabs slab_stride values apart in shared memory, w N apart in
 // global memory); 256 / T columns per round, adjacent threads on adjacent
-// columns (conflict-free through the padding).  The last stage stores to the
+// columns (conflict-free).  The last stage stores to the
 // output slabs in global memory (element k of column (cs, c) at
 // dst[(cs N + k) w + c]: adjacent threads, adjacent addresses).
 template <int N, int T, class Rad>
@@ -126,7 +127,7 @@ __device__ __noinline__ void sz_cols(float2 *A, int pitch, int cols, int w, int 
         const int c = c0 + l;
         const bool valid = t < T && c < cols;
         const int cs = valid ? c / w : 0, cc = valid ? c - cs * w : 0;
-        SzCol acc{A + cs * slab_stride + padpos(cc), pitch, valid};
+        SzCol acc{A + cs * slab_stride + cc, pitch, valid};
         GStore out{dst + (int64_t)cs * N * w + cc, w, valid, conj};
         EngineFixed<N, T, 1, Rad>::template run<false, false>(t < T ? t : 0, acc, acc, out, tw);
     }
@@ -156,17 +157,18 @@ __device__ __noinline__ void sz_ztiles(float2 *base, int64_t t0, int64_t t1, int
 }
 
 // x-row kernels of the slab items: the warp-shuffle transform of each length.
+// The variants of at most 80 registers (three blocks per SM).
 #define FFT3_SZ_WARP_ROWS(X) \
     X(8, 4, 2)               \
     X(16, 4, 4)              \
     X(24, 3, 8)              \
     X(32, 4, 8)              \
-    X(40, 10, 4)             \
+    X(40, 5, 8)              \
     X(48, 6, 8)              \
-    X(64, 8, 8)              \
-    X(80, 10, 8)             \
+    X(64, 4, 16)             \
+    X(80, 5, 16)             \
     X(96, 6, 16)             \
-    X(128, 8, 16)
+    X(128, 4, 32)
 
 __device__ __forceinline__ void sz_run_rows_warp(int n0, const float2 *src, float2 *A, int pitch, int rows,
                                                  const float2 *tw, const int *off, bool conj)
@@ -219,20 +221,18 @@ __device__ __forceinline__ int ld_acquire_sz(const int *p)
 
 } // namespace
 
-__global__ void __launch_bounds__(kSzThreads, 2) k_slabz(SlabZArgs z)
+__global__ void __launch_bounds__(kSzThreads, 3) k_slabz(SlabZArgs z)
 {
     extern __shared__ __align__(16) float2 smem[];
     const BatchArgs &a = z.b;
-    float2 *tw = smem;
-    float2 *A = smem + tw_slots(z.tw_len);
-    for (int i = threadIdx.x; i < z.tw_len; i += blockDim.x)
-        tw[i] = z.tw[i];
+    const float2 *tw = z.tw; // read through L1: the shared memory holds the slabs
+    float2 *A = smem;
     __shared__ int s_q, s_next;
     const bool conj = a.conj != 0;
     if (threadIdx.x == 0)
         s_next = atomicAdd(a.counters, 1);
     for (;;) {
-        __syncthreads(); // the previous item's buffer (and, first, the twiddles); s_next written
+        __syncthreads(); // the previous item's buffer; s_next written
         const int q = s_next;
         if (q >= a.nitems)
             break;
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kSzThreads, 2) k_slabz(SlabZArgs z)
             // slabs [index * spi, ...) stacked in shared memory: all their rows,
             // then all their columns
             const int s0 = it.index * cb.spi, ns = min(n2, s0 + cb.spi) - s0;
-            const int P = line_pitch(n0);
+            const int P = n0 | 1;
             const float2 *src = a.in + cb.off + (int64_t)s0 * n0 * n1;
             float2 *dst = a.out + cb.off + (int64_t)s0 * n0 * n1;
             sz_run_rows_warp(n0, src, A, P, n1 * ns, tw, z.tw_w, conj);
@@ -277,8 +277,8 @@ __global__ void __launch_bounds__(kSzThreads, 2) k_slabz(SlabZArgs z)
     }
 }
 
-// Shared memory of one block: the twiddle tables and the larger of a padded
-// n0 x n1 slab and a z tile.
-int slabz_smem_bytes(int tw_len, int buf_elems) { return (tw_slots(tw_len) + buf_elems) * (int)sizeof(float2); }
+// Shared memory of one block: the larger of the stacked slabs of an item and
+// its z tiles.
+int slabz_smem_bytes(int buf_elems) { return buf_elems * (int)sizeof(float2); }
 
 } // namespace fft3

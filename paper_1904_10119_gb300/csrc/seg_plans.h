@@ -64,7 +64,9 @@ namespace fft3 {
     X(96, 6, 16, 1)         \
     X(96, 12, 8, 0)         \
     X(128, 8, 16, 0)        \
-    X(128, 16, 8, 0)
+    X(128, 16, 8, 0)        \
+    X(64, 4, 16, 0)         \
+    X(128, 4, 32, 0)
 
 // y and z lines (columns) by the warp-shuffle transform, the same rows.  None
 // is a default: on the 4096-cube workload they measured slower than the

@@ -90,20 +90,22 @@ struct WarpLine {
     }
 
     // v[e][i] = x[2u + e + L i] (conjugated for the inverse); zeros when !valid.
+    // Streaming loads (evict first from L1): each value is read once, and L1
+    // keeps what is read again (twiddle tables).
     __device__ __forceinline__ static void load(float2 (&v)[2][R], const float2 *p, int u, bool valid, bool conj)
     {
         if (valid && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-                const float4 q = *reinterpret_cast<const float4 *>(p + 2 * u + L * i);
+                const float4 q = __ldcs(reinterpret_cast<const float4 *>(p + 2 * u + L * i));
                 v[0][i] = make_float2(q.x, q.y);
                 v[1][i] = make_float2(q.z, q.w);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-                v[0][i] = valid ? p[2 * u + L * i] : make_float2(0.f, 0.f);
-                v[1][i] = valid ? p[2 * u + 1 + L * i] : make_float2(0.f, 0.f);
+                v[0][i] = valid ? __ldcs(p + 2 * u + L * i) : make_float2(0.f, 0.f);
+                v[1][i] = valid ? __ldcs(p + 2 * u + 1 + L * i) : make_float2(0.f, 0.f);
             }
         }
         if (conj) {
