@@ -227,18 +227,17 @@ __global__ void __launch_bounds__(kSzThreads, 3) k_slabz(SlabZArgs z)
     const BatchArgs &a = z.b;
     const float2 *tw = z.tw; // read through L1: the shared memory holds the slabs
     float2 *A = smem;
-    __shared__ int s_q, s_next;
+    __shared__ int s_next[2]; // tickets of the current and the next item, alternating slots
     const bool conj = a.conj != 0;
     if (threadIdx.x == 0)
-        s_next = atomicAdd(a.counters, 1);
-    for (;;) {
-        __syncthreads(); // the previous item's buffer; s_next written
-        const int q = s_next;
+        s_next[0] = atomicAdd(a.counters, 1);
+    for (int slot = 0;; slot ^= 1) {
+        __syncthreads(); // the previous item is done (buffer free, counter published); s_next[slot] written
+        const int q = s_next[slot];
         if (q >= a.nitems)
             break;
-        __syncthreads(); // every thread has read s_next
-        if (threadIdx.x == 0)
-            s_next = atomicAdd(a.counters, 1); // the next item, claimed while this one runs
+        if (threadIdx.x == 0) // the next item, claimed while this one runs; the other slot was
+            s_next[slot ^ 1] = atomicAdd(a.counters, 1); // read before the barrier above
         const BatchItem it = a.items[q];
         const BatchCube &cb = a.cubes[it.cube];
         const int n0 = cb.n0, n1 = cb.n1, n2 = cb.n2;
