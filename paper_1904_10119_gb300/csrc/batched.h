@@ -96,15 +96,15 @@ struct SegAllArgs {
 constexpr int kSegAllThreads = 256;
 
 // The slab-by-slab executor (k_slabz.cu): the item executor's tables, and
-// the twiddle tables of the segmented line kernels (all of them, read
-// through L1), tw_c[k] / tw_s[k] the offset of the k-th contiguous / strided
-// kernel's table, tw_w[k] of the k-th length's table w_N^m.
+// twiddle tables read through L1: tw_s[k] the offset of the k-th strided
+// segmented kernel's table (z tiles), tw_w[k] that of the table w_N^m of the
+// k-th length of FFT3_SLABZ_WARP_PLANS (rows and columns).
 struct SlabZArgs {
     BatchArgs b;
     const float2 *tw;
     int tw_len;
-    int tw_c[16], tw_s[16];
-    int tw_w[16]; // w_N^m (m < N) for the warp-shuffle row kernels, lengths 8 .. 128 in order
+    int tw_s[16];
+    int tw_w[16];
 };
 __global__ void k_slabz(SlabZArgs z);
 int slabz_smem_bytes(int buf_elems);

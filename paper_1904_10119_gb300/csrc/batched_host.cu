@@ -45,7 +45,7 @@ struct BatchState {
     int seg1 = 0;
     // the slab-by-slab executor (k_slabz): tuning codes with FFT3_TUNE_SLABZ
     int slabz = 0;
-    int sz_tw_c[16] = {}, sz_tw_s[16] = {}, sz_tw_w[16] = {};
+    int sz_tw_s[16] = {}, sz_tw_w[16] = {};
     int sz_smem = 0;
     dim3 sz_grid;
     int waves = 1;
@@ -365,7 +365,6 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
         z.tw = b->d_tw + b->sa_tw_off;
         z.tw_len = b->sa_tw_len;
         for (int k = 0; k < 16; ++k) {
-            z.tw_c[k] = b->sz_tw_c[k];
             z.tw_s[k] = b->sz_tw_s[k];
             z.tw_w[k] = b->sz_tw_w[k];
         }
@@ -523,14 +522,17 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
     }
     b->extent = extent;
     if (slabz) {
-        int cc = 0, sc = 0;
-        const SegKernel *kc = seg_kernels(true, &cc), *ks = seg_kernels(false, &sc);
+        // rows and columns by the warp-shuffle variants (the z length was
+        // checked against the strided line kernels above)
+#define FFT3_SZ_LEN(N, R, L) N,
+        const int wl[] = {FFT3_SLABZ_WARP_PLANS(FFT3_SZ_LEN)};
+#undef FFT3_SZ_LEN
         for (int i = 0; i < count; ++i) {
             bool x = false, y = false;
-            for (int k = 0; k < cc; ++k)
-                x = x || kc[k].n == dims[3 * i];
-            for (int k = 0; k < sc; ++k)
-                y = y || ks[k].n == dims[3 * i + 1];
+            for (int n : wl) {
+                x = x || n == dims[3 * i];
+                y = y || n == dims[3 * i + 1];
+            }
             if (!x || !y)
                 return fail(FFT3_ERR_UNSUPPORTED_SIZE, "the slab executor has no compiled line kernel for a length "
                                                        "of problem " + std::to_string(i));
@@ -706,9 +708,11 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
             exp_n.push_back(K.n);
         }
         if (b->slabz) {
-            // w_N^m, m < N, for the warp-shuffle row kernels of the slab executor
-            const int wl[10] = {8, 16, 24, 32, 40, 48, 64, 80, 96, 128};
-            for (int k = 0; k < 10; ++k) {
+            // w_N^m, m < N, for the warp-shuffle rows and columns of the slab executor
+#define FFT3_SZ_LEN(N, R, L) N,
+            const int wl[] = {FFT3_SLABZ_WARP_PLANS(FFT3_SZ_LEN)};
+#undef FFT3_SZ_LEN
+            for (int k = 0; k < (int)(sizeof(wl) / sizeof(wl[0])); ++k) {
                 std::vector<int64_t> e(wl[k]);
                 for (int m = 0; m < wl[k]; ++m)
                     e[m] = m;
@@ -721,8 +725,6 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
         }
         b->sa_tw_len = (int)local;
         tw_total += local;
-        for (int k = 0; k < ccnt && k < 16; ++k)
-            b->sz_tw_c[k] = kt[k];
         for (int k = 0; k < scnt && k < 16; ++k)
             b->sz_tw_s[k] = kt[ccnt + k];
         b->sz_smem = slabz_smem_bytes((bufmax + 31) / 32 * 32);

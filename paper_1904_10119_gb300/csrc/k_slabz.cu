@@ -1,15 +1,16 @@
 // k_slabz.cu -- batched uneven 3D DFTs in one persistent launch, slab by slab
 // (the slab-pencil decomposition of Section 2.3 applied to every problem):
-//   slab items: one n0 x n1 slab of a problem is read from global memory into
-//               shared memory, its x lines (rows) and then its y lines
-//               (columns) are transformed there, and it is written back: one
+//   slab items: a few n0 x n1 slabs of a problem, stacked in shared memory:
+//               their x lines (rows) are read from global memory, transformed
+//               and written into the buffer, then their y lines (columns) are
+//               transformed from the buffer and written to global memory: one
 //               read and one write per value for the 2D stage;
-//   z items:    a tile of adjacent columns of a problem's n0*n1 plane, its z
+//   z items:    tiles of adjacent columns of a problem's n0*n1 plane, their z
 //               lines read through L2 (the slabs were written earlier in the
 //               launch), transformed and written back in place.
-// The line transforms are the compile-time Stockham engines of the segmented
-// passes (seg_plans.h: one radix list and thread count per line length), so
-// the per-value instruction count is theirs, not that of a runtime-radix loop.
+// Rows and columns are warp-shuffle line transforms (warp_fft.cuh; a line in
+// the registers of a few lanes, no barrier), the z tiles the compile-time
+// Stockham engines of the segmented column passes (seg_plans.h).
 // Work items come from a ticket counter in the order the host gives them
 // (problems in groups, the z items of a group after the slab items of the
 // next group, so a problem's slabs are still in L2 when its z items read
@@ -29,31 +30,9 @@ namespace {
 
 constexpr int kSzThreads = 256;
 
-// Shared-memory accessors with a validity flag: an invalid line reads zeros
-// and stores nothing, so every thread of the block can run every barrier of
-// an engine whatever the number of lines.
-struct SzRow { // row of the padded slab buffer: element j at p[padpos(j)]
-    float2 *p;
-    bool valid;
-    __device__ __forceinline__ float2 operator()(int j) const { return valid ? p[padpos(j)] : make_float2(0.f, 0.f); }
-    __device__ __forceinline__ void operator()(int k, float2 v) const
-    {
-        if (valid)
-            p[padpos(k)] = v;
-    }
-};
-struct SzCol { // column of the padded slab buffer: element j at p[j * pitch]
-    float2 *p;
-    int pitch;
-    bool valid;
-    __device__ __forceinline__ float2 operator()(int j) const { return valid ? p[j * pitch] : make_float2(0.f, 0.f); }
-    __device__ __forceinline__ void operator()(int k, float2 v) const
-    {
-        if (valid)
-            p[k * pitch] = v;
-    }
-};
-// Column l of the z tile buffer: element j at p[j * LPT].
+// Column l of the z tile buffer (element j at p[j * LPT]), with a validity
+// flag: an invalid line reads zeros and stores nothing, so every thread of the
+// block can run every barrier of the engine whatever the number of lines.
 template <int LPT>
 struct SzTile {
     float2 *p;
@@ -110,26 +89,29 @@ __device__ __noinline__ void sz_rows_warp(const float2 *src, float2 *A, int pitc
     }
 }
 
-// Columns of the stacked slabs (y lines): column cc is column cc mod w of
-// slab cc / w (slabs slab_stride values apart in shared memory, w N apart in
-// global memory); 256 / T columns per round, adjacent threads on adjacent
-// columns (conflict-free).  The last stage stores to the
-// output slabs in global memory (element k of column (cs, c) at
-// dst[(cs N + k) w + c]: adjacent threads, adjacent addresses).
-template <int N, int T, class Rad>
-__device__ __noinline__ void sz_cols(float2 *A, int pitch, int cols, int w, int slab_stride, float2 *dst,
-                                     const float2 *tw, bool conj)
+// Columns of the stacked slabs (y lines) in the registers of L/2 lanes
+// (warp_fft.cuh): the lanes of a column read different rows of the buffer
+// (pitch odd: conflict free), adjacent lane groups take adjacent columns, and
+// each group stores its column's outputs straight to the output slabs in
+// global memory (element k of column (cs, c) at dst[(cs N + k) w + c]).  A
+// group owns its column: no barrier.
+template <int N, int R, int L>
+__device__ __noinline__ void sz_cols_warp(const float2 *A, int pitch, int cols, int w, int slab_stride, float2 *dst,
+                                          const float2 *tw_w, bool conj)
 {
-    constexpr int L = kSzThreads / T;
-    const int tid = threadIdx.x;
-    const int l = tid % L, t = tid / L;
-    for (int c0 = 0; c0 < cols; c0 += L) { // rounds touch disjoint columns: no barrier between them
+    using WL = WarpLine<N, R, L>;
+    constexpr int CPR = kSzThreads / WL::W; // columns per round
+    const int u = threadIdx.x % WL::W, l = threadIdx.x / WL::W;
+    typename WL::Tw tw;
+    WL::load_tw(tw, tw_w, u);
+    for (int c0 = 0; c0 < cols; c0 += CPR) {
         const int c = c0 + l;
-        const bool valid = t < T && c < cols;
+        const bool valid = c < cols;
         const int cs = valid ? c / w : 0, cc = valid ? c - cs * w : 0;
-        SzCol acc{A + cs * slab_stride + cc, pitch, valid};
-        GStore out{dst + (int64_t)cs * N * w + cc, w, valid, conj};
-        EngineFixed<N, T, 1, Rad>::template run<false, false>(t < T ? t : 0, acc, acc, out, tw);
+        float2 v[2][R];
+        WL::load_strided(v, A + cs * slab_stride + cc, pitch, u, valid, false);
+        WL::run(v, tw, u);
+        WL::store_strided(v, dst + (int64_t)cs * N * w + cc, w, u, valid, conj);
     }
 }
 
@@ -156,20 +138,6 @@ __device__ __noinline__ void sz_ztiles(float2 *base, int64_t t0, int64_t t1, int
     }
 }
 
-// x-row kernels of the slab items: the warp-shuffle transform of each length.
-// The variants of at most 80 registers (three blocks per SM).
-#define FFT3_SZ_WARP_ROWS(X) \
-    X(8, 4, 2)               \
-    X(16, 4, 4)              \
-    X(24, 3, 8)              \
-    X(32, 4, 8)              \
-    X(40, 5, 8)              \
-    X(48, 6, 8)              \
-    X(64, 4, 16)             \
-    X(80, 5, 16)             \
-    X(96, 6, 16)             \
-    X(128, 4, 32)
-
 __device__ __forceinline__ void sz_run_rows_warp(int n0, const float2 *src, float2 *A, int pitch, int rows,
                                                  const float2 *tw, const int *off, bool conj)
 {
@@ -180,22 +148,23 @@ __device__ __forceinline__ void sz_run_rows_warp(int n0, const float2 *src, floa
         return;                                                                      \
     }                                                                                \
     ++k;
-    FFT3_SZ_WARP_ROWS(FFT3_SZ_WROW)
+    FFT3_SLABZ_WARP_PLANS(FFT3_SZ_WROW)
 #undef FFT3_SZ_WROW
 }
 
-__device__ __forceinline__ void sz_run_cols(int n1, float2 *A, int pitch, int cols, int w, int slab_stride,
-                                            float2 *dst, const float2 *tw, const int *off, bool conj)
+__device__ __forceinline__ void sz_run_cols_warp(int n1, const float2 *A, int pitch, int cols, int w,
+                                                 int slab_stride, float2 *dst, const float2 *tw, const int *off,
+                                                 bool conj)
 {
     int k = 0;
-#define FFT3_SZ_COLS(N, T, L, ...)                                                              \
-    if (n1 == N) {                                                                              \
-        sz_cols<N, T, Radices<__VA_ARGS__>>(A, pitch, cols, w, slab_stride, dst, tw + off[k], conj); \
-        return;                                                                                 \
-    }                                                                                           \
+#define FFT3_SZ_WCOL(N, R, L)                                                                 \
+    if (n1 == N) {                                                                            \
+        sz_cols_warp<N, R, L>(A, pitch, cols, w, slab_stride, dst, tw + off[k], conj);        \
+        return;                                                                               \
+    }                                                                                         \
     ++k;
-    FFT3_SEG_PLANS_STRIDED(FFT3_SZ_COLS)
-#undef FFT3_SZ_COLS
+    FFT3_SLABZ_WARP_PLANS(FFT3_SZ_WCOL)
+#undef FFT3_SZ_WCOL
 }
 
 __device__ __forceinline__ void sz_run_ztiles(int n2, float2 *base, int64_t t0, int64_t t1, int64_t ncols,
@@ -250,7 +219,7 @@ __global__ void __launch_bounds__(kSzThreads, 3) k_slabz(SlabZArgs z)
             float2 *dst = a.out + cb.off + (int64_t)s0 * n0 * n1;
             sz_run_rows_warp(n0, src, A, P, n1 * ns, tw, z.tw_w, conj);
             __syncthreads();
-            sz_run_cols(n1, A, P, n0 * ns, n0, n1 * P, dst, tw, z.tw_s, conj);
+            sz_run_cols_warp(n1, A, P, n0 * ns, n0, n1 * P, dst, tw, z.tw_w, conj);
         } else {
             if (threadIdx.x == 0) {
                 const int *done = a.counters + 1 + 3 * it.cube;

@@ -68,6 +68,22 @@ namespace fft3 {
     X(64, 4, 16, 0)         \
     X(128, 4, 32, 0)
 
+// Rows and columns of the slab executor (k_slabz.cu) by the warp-shuffle
+// transform: X(N, R, L), one variant per length, each within the 80 registers
+// of three 256-thread blocks per multiprocessor.  The host derives the
+// executor's line lengths and twiddle tables from the same list.
+#define FFT3_SLABZ_WARP_PLANS(X) \
+    X(8, 4, 2)                   \
+    X(16, 4, 4)                  \
+    X(24, 3, 8)                  \
+    X(32, 4, 8)                  \
+    X(40, 5, 8)                  \
+    X(48, 6, 8)                  \
+    X(64, 4, 16)                 \
+    X(80, 5, 16)                 \
+    X(96, 6, 16)                 \
+    X(128, 4, 32)
+
 // y and z lines (columns) by the warp-shuffle transform, the same rows.  None
 // is a default: on the 4096-cube workload they measured slower than the
 // shared-memory column kernels at 24-128 points (by 0-45%; within 3-9% faster
