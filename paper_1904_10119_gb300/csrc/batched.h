@@ -96,14 +96,14 @@ struct SegAllArgs {
 constexpr int kSegAllThreads = 256;
 
 // The slab-by-slab executor (k_slabz.cu): the item executor's tables, and
-// twiddle tables read through L1: tw_s[k] the offset of the k-th strided
-// segmented kernel's table (z tiles), tw_w[k] that of the table w_N^m of the
-// k-th length of FFT3_SLABZ_WARP_PLANS (rows and columns).
+// twiddle tables read through L1: tw_z[k] the offset of the table of the
+// k-th plan of FFT3_SLABZ_Z_PLANS (z tiles), tw_w[k] that of the table w_N^m
+// of the k-th length of FFT3_SLABZ_WARP_PLANS (rows and columns).
 struct SlabZArgs {
     BatchArgs b;
     const float2 *tw;
     int tw_len;
-    int tw_s[16];
+    int tw_z[16];
     int tw_w[16];
 };
 __global__ void k_slabz(SlabZArgs z);

@@ -45,7 +45,7 @@ struct BatchState {
     int seg1 = 0;
     // the slab-by-slab executor (k_slabz): tuning codes with FFT3_TUNE_SLABZ
     int slabz = 0;
-    int sz_tw_s[16] = {}, sz_tw_w[16] = {};
+    int sz_tw_z[16] = {}, sz_tw_w[16] = {};
     int sz_smem = 0;
     dim3 sz_grid;
     int waves = 1;
@@ -160,6 +160,20 @@ constexpr int kBatchBufTarget = 3072;
 // Shared-memory values the slab executor gives a work item's stacked slabs:
 // one 96 x 96 slab with its rows 97 values apart.
 constexpr int kSlabzRoom = 96 * 97;
+
+// The z-tile plans of the slab executor (FFT3_SLABZ_Z_PLANS): length,
+// threads per line, columns per tile and radix list.
+struct SlabZPlan {
+    int n, T, lpt, nrad, rad[4];
+};
+template <int... R>
+constexpr SlabZPlan slabz_plan(int n, int T, int lpt)
+{
+    return {n, T, lpt, (int)sizeof...(R), {R...}};
+}
+#define FFT3_SZ_ZPLAN(N, T, LPT, ...) slabz_plan<__VA_ARGS__>(N, T, LPT),
+constexpr SlabZPlan kSlabZPlans[] = {FFT3_SLABZ_Z_PLANS(FFT3_SZ_ZPLAN)};
+#undef FFT3_SZ_ZPLAN
 
 // FFT3_AUTO without tuning codes runs the segmented passes from this many
 // values on (every line length compiled in seg_plans.h).
@@ -365,7 +379,7 @@ static int capture(fft3_plan_s *P, const void *in, void *out)
         z.tw = b->d_tw + b->sa_tw_off;
         z.tw_len = b->sa_tw_len;
         for (int k = 0; k < 16; ++k) {
-            z.tw_s[k] = b->sz_tw_s[k];
+            z.tw_z[k] = b->sz_tw_z[k];
             z.tw_w[k] = b->sz_tw_w[k];
         }
         e = cudaMemsetAsync(b->d_counters, 0, b->counters_bytes, b->cap_stream);
@@ -475,22 +489,17 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
         }
         c.lx = lx; c.ly = ly; c.lz = lz;
         if (slabz) {
-            // one slab per item; z tiles as wide as the strided line kernel of n2
-            int scnt = 0;
-            const SegKernel *sk = seg_kernels(false, &scnt);
-            int zl = 0;
-            for (int k = 0; k < scnt; ++k)
-                zl = sk[k].n == n2 ? sk[k].lpt : zl;
-            if (!zl)
+            // z tiles of the FFT3_SLABZ_Z_PLANS plan of n2
+            const SlabZPlan *zp = nullptr;
+            for (const SlabZPlan &q : kSlabZPlans)
+                zp = q.n == n2 ? &q : zp;
+            if (!zp)
                 return fail(FFT3_ERR_UNSUPPORTED_SIZE, "the slab executor has no compiled line kernel for length " +
                                                            std::to_string(n2));
             // items of about 8 Ki values: several small slabs stacked in the
             // buffer (at most the room of one 96 x 96 slab), several z tiles
-            // (as many at a time as 256 threads hold groups of the line kernel)
-            int zt = 0;
-            for (int k = 0; k < scnt; ++k)
-                zt = sk[k].n == n2 ? sk[k].T * sk[k].lpt : zt;
-            const int zg = std::max(1, 256 / zt);
+            // (as many at a time as 256 threads hold groups of the line plan)
+            const int zl = zp->lpt, zg = std::max(1, 256 / (zp->T * zp->lpt));
             decomp = BD_SLAB;
             c.decomp = BD_SLAB;
             c.lpt = lpt = zl;
@@ -523,7 +532,7 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
     b->extent = extent;
     if (slabz) {
         // rows and columns by the warp-shuffle variants (the z length was
-        // checked against the strided line kernels above)
+        // checked against the z-tile plans above)
 #define FFT3_SZ_LEN(N, R, L) N,
         const int wl[] = {FFT3_SLABZ_WARP_PLANS(FFT3_SZ_LEN)};
 #undef FFT3_SZ_LEN
@@ -684,11 +693,12 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
     }
     std::vector<int> kt(ccnt + scnt);
     if (b->seg1 || b->slabz) {
-        // every line kernel's twiddle table, one after the other (copied to
-        // shared memory by every block of the one-launch executors)
+        // the line kernels' twiddle tables, one after the other (the
+        // segmented kernels' copied to shared memory by every block of the
+        // one-launch segmented executor; the slab executor's read through L1)
         b->sa_tw_off = tw_total;
         int64_t local = 0;
-        for (int k = 0; k < ccnt + scnt; ++k) {
+        for (int k = 0; k < (b->seg1 ? ccnt + scnt : 0); ++k) {
             const SegKernel &K = k < ccnt ? skc[k] : sks[k - ccnt];
             LineChoice lc{};
             lc.n = K.n;
@@ -708,7 +718,27 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
             exp_n.push_back(K.n);
         }
         if (b->slabz) {
-            // w_N^m, m < N, for the warp-shuffle rows and columns of the slab executor
+            // the z-tile plans' stage twiddles
+            for (int k = 0; k < (int)(sizeof(kSlabZPlans) / sizeof(kSlabZPlans[0])) && k < 16; ++k) {
+                const SlabZPlan &q = kSlabZPlans[k];
+                LineChoice lc{};
+                lc.n = q.n;
+                lc.fixed = -1;
+                lc.T = q.T;
+                lc.nst = q.nrad;
+                for (int r = 0; r < q.nrad; ++r)
+                    lc.rad[r] = q.rad[r];
+                std::vector<int64_t> e;
+                line_twiddle_exponents(lc, &e);
+                if (e.empty())
+                    e.push_back(0);
+                b->sz_tw_z[k] = (int)local;
+                segs.push_back({tw_total + local, (int64_t)e.size()});
+                local += ((int64_t)e.size() + 15) / 16 * 16;
+                exps.push_back(std::move(e));
+                exp_n.push_back(q.n);
+            }
+            // w_N^m, m < N, for the warp-shuffle rows and columns
 #define FFT3_SZ_LEN(N, R, L) N,
             const int wl[] = {FFT3_SLABZ_WARP_PLANS(FFT3_SZ_LEN)};
 #undef FFT3_SZ_LEN
@@ -725,8 +755,6 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
         }
         b->sa_tw_len = (int)local;
         tw_total += local;
-        for (int k = 0; k < scnt && k < 16; ++k)
-            b->sz_tw_s[k] = kt[ccnt + k];
         b->sz_smem = slabz_smem_bytes((bufmax + 31) / 32 * 32);
     }
     if (b->seg1) {

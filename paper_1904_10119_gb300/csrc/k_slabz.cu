@@ -10,7 +10,7 @@
 //               launch), transformed and written back in place.
 // Rows and columns are warp-shuffle line transforms (warp_fft.cuh; a line in
 // the registers of a few lanes, no barrier), the z tiles the compile-time
-// Stockham engines of the segmented column passes (seg_plans.h).
+// Stockham engines of FFT3_SLABZ_Z_PLANS (seg_plans.h).
 // Work items come from a ticket counter in the order the host gives them
 // (problems in groups, the z items of a group after the slab items of the
 // next group, so a problem's slabs are still in L2 when its z items read
@@ -177,7 +177,7 @@ __device__ __forceinline__ void sz_run_ztiles(int n2, float2 *base, int64_t t0, 
         return;                                                                                      \
     }                                                                                                \
     ++k;
-    FFT3_SEG_PLANS_STRIDED(FFT3_SZ_Z)
+    FFT3_SLABZ_Z_PLANS(FFT3_SZ_Z)
 #undef FFT3_SZ_Z
 }
 
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kSzThreads, 3) k_slabz(SlabZArgs z)
             __syncthreads();
             const int64_t plane = (int64_t)n0 * n1, ntiles = (plane + cb.lpt - 1) / cb.lpt;
             const int64_t t0 = (int64_t)it.index * cb.zpi, t1 = min(ntiles, t0 + cb.zpi);
-            sz_run_ztiles(n2, a.out + cb.off, t0, t1, plane, plane, A, tw, z.tw_s, conj);
+            sz_run_ztiles(n2, a.out + cb.off, t0, t1, plane, plane, A, tw, z.tw_z, conj);
         }
         __syncthreads();
         if (threadIdx.x == 0) {

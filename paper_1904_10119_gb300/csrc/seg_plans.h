@@ -84,6 +84,23 @@ namespace fft3 {
     X(96, 6, 16)                 \
     X(128, 4, 32)
 
+// z tiles of the slab executor (k_slabz.cu): X(N, T, columns per tile,
+// radices...), shared-memory column tiles like FFT3_SEG_PLANS_STRIDED, with T
+// times the tile width chosen so that whole tiles fill 240-256 of the block's
+// 256 threads, and two stages where the length allows (80 = 8 x 10 and
+// 96 = 8 x 12, composite butterflies in registers).
+#define FFT3_SLABZ_Z_PLANS(X) \
+    X(8, 1, 64, 8)            \
+    X(16, 4, 32, 4, 4)        \
+    X(24, 4, 32, 8, 3)        \
+    X(32, 4, 32, 8, 4)        \
+    X(40, 5, 16, 8, 5)        \
+    X(48, 4, 32, 16, 3)       \
+    X(64, 8, 32, 8, 8)        \
+    X(80, 10, 24, 8, 10)      \
+    X(96, 12, 20, 8, 12)      \
+    X(128, 8, 32, 16, 8)
+
 // y and z lines (columns) by the warp-shuffle transform, the same rows.  None
 // is a default: on the 4096-cube workload they measured slower than the
 // shared-memory column kernels at 24-128 points (by 0-45%; within 3-9% faster
