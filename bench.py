@@ -248,8 +248,8 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=1,
                     help="whole oracle transforms timed for cpu_baseline (0 skips the CPU oracle baseline)")
     ap.add_argument("--batched", type=int, default=0, metavar="COUNT",
-                    help="only time COUNT uneven cubes (seed 7): the default batched plan, the persistent and slab executors "
-                         "and the one-launch segmented form")
+                    help="only time COUNT uneven cubes (seed 7): the default batched plan (the slab executor), the "
+                         "segmented passes, the persistent executor and the one-launch segmented form")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -654,11 +654,11 @@ def c128_table(fft3, synth, torch, sizes=(256, 512, 1024), reps=5):
 
 def bench_batched(fft3, synth, torch, hbm, count=4096):
     """`count` independent 3D DFTs with dims drawn from {16..96} (seed 7), one
-    graph-captured execution of the default plan (FFT3_AUTO: the segmented x, y
-    and z passes for a batch this size): ms per batch, GB/s, roofline fractions;
-    the persistent executor (tuning codes 0), the segmented passes as one
-    cooperative launch and the slab-by-slab executor (one persistent launch of
-    slab and z-tile items, FFT3_TUNE_SLABZ) timed beside it."""
+    graph-captured execution of the default plan (FFT3_AUTO: the slab executor,
+    one persistent launch of slab and z-tile items, for a batch this size): ms
+    per batch, GB/s, roofline fractions; the segmented x, y and z passes (24
+    launches, tuning codes 3), the persistent executor (tuning codes 0) and the
+    segmented passes as one cooperative launch timed beside it."""
     import numpy as np
     dims = synth.batched_dims(count, 7)
     vols = dims.prod(axis=1)
@@ -689,9 +689,8 @@ def bench_batched(fft3, synth, torch, hbm, count=4096):
         return e0.elapsed_time(e1) / reps, desc
 
     ms, desc = run(None)
+    ms_seg, dseg = run([3] * count)
     ms_exec, _ = run([0] * count)
-    ms_slabz, dz = run([fft3.tune_code(1) | fft3.FFT3_TUNE_SLABZ] * count)
-    assert dz["mode"] == "slab_executor" and dz["kernel_launches"] == 1, dz
     # the segmented passes in one cooperative launch, 2^(k-1) waves of problems
     one_launch = {}
     for k in (1, 3, 5, 7):
@@ -700,7 +699,8 @@ def bench_batched(fft3, synth, torch, hbm, count=4096):
     one_sweep = 2 * 8 * total
     return {"ms": ms, "mode": desc["mode"], "kernel_launches": desc["kernel_launches"],
             "one_launch_ms": one_launch,
-            "executor_ms": ms_exec, "slab_executor_ms": ms_slabz, "elements": total, "problems": count, "items": desc["items"],
+            "segmented_ms": ms_seg, "segmented_launches": dseg["kernel_launches"],
+            "executor_ms": ms_exec, "elements": total, "problems": count, "items": desc["items"],
             "GBps_one_sweep": one_sweep / (ms * 1e-3) / 1e9,
             "frac_of_1_sweep": one_sweep / (ms * 1e-3) / 1e9 / hbm,
             "frac_of_3_sweeps": 3 * one_sweep / (ms * 1e-3) / 1e9 / hbm,

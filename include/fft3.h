@@ -222,24 +222,38 @@ int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int d
 /* Batched uneven transforms: `count` independent 3D DFTs (Section 2.3 for
  * each), problem i of size dims[3i] x dims[3i+1] x dims[3i+2] (first fastest)
  * starting at complex offset offsets[i] of both the input and the output
- * buffer (the problems' extents must not overlap).  Two execution modes, both
- * captured once in a CUDA graph (re-captured when the buffers change):
- *   executor:  one persistent launch with its counter reset; work items of
- *              every problem's phases in waves that keep a problem's
- *              intermediate in L2;
+ * buffer (the problems' extents must not overlap).  Three execution modes,
+ * each captured once in a CUDA graph (re-captured when the buffers change):
+ *   slab executor: one persistent launch of work items from a ticket counter,
+ *              the slab-pencil definition of Section 2.3 per problem: an item
+ *              is a few n0 x n1 slabs of a problem (x lines read from global
+ *              memory into a shared-memory stack, y lines from the stack
+ *              written to global memory: one read and one write for the 2D
+ *              stage) or a group of z-line tiles of a problem (read through L2
+ *              once every slab of the problem is done; bounded waits).  The x
+ *              and y lines run in the registers of a few lanes of a warp (warp
+ *              shuffles, no block barrier), the z tiles through shared memory;
+ *              line lengths 8, 16, 24, 32, 40, 48, 64, 80, 96, 128;
  *   segmented: three passes over the whole batch (all x lines, all y lines,
  *              all z lines of every problem, one compile-time line kernel per
- *              line length: 8, 16, 24, 32, 40, 48, 64, 80, 96, 128), the
- *              pencil-pencil-pencil definition of Section 2.3 per problem.
- *              The x lines of most lengths run in the registers of a few lanes
- *              of a warp (warp shuffles between the lanes, 16-byte loads and
- *              stores where a problem starts 16-byte aligned); in this mode the
- *              radix_order field picks the x-line kernel of each length: 0 = the
- *              length's default, r + 1 = candidate r (the shared-memory kernel,
- *              then the warp-shuffle kernels), modulo their number.
- * The segmented mode runs when every tuning code has decomposition field 3, or
- * with FFT3_AUTO, tuning == NULL and at least 4 Mi values in the batch, provided
- * every line length has a compiled plan; otherwise the executor runs.
+ *              line length, the same lengths), the pencil-pencil-pencil
+ *              definition of Section 2.3 per problem.  The x lines of most
+ *              lengths run in the registers of a few lanes of a warp (16-byte
+ *              loads and stores where a problem starts 16-byte aligned); in
+ *              this mode the radix_order field picks the x-line kernel of each
+ *              length: 0 = the length's default, r + 1 = candidate r (the
+ *              shared-memory kernel, then the warp-shuffle kernels), modulo
+ *              their number;
+ *   executor:  one persistent launch with its counter reset; work items of
+ *              every problem's phases (runtime radix lists) in waves that keep
+ *              a problem's intermediate in L2.
+ * FFT3_AUTO with tuning == NULL on a batch of at least 4 Mi values takes the
+ * slab executor when every length is one of its lengths and every slab fits
+ * one item (n1 * (n0 | 1) <= 96 * 97), else the segmented passes when every
+ * line length has a compiled plan; other batches take the executor.  With
+ * tuning codes: FFT3_TUNE_SLABZ on every code asks for the slab executor,
+ * decomposition field 3 on every code for the segmented passes, anything
+ * else for the executor.
  * Dimensions: 2*3*5-smooth, <= 128.
  * decomposition: FFT3_SLAB_PENCIL, FFT3_PENCIL3 or FFT3_AUTO (per problem).
  * dtype: FFT3_C64_FP32.  `tuning` may be NULL or point to `count` tuning
@@ -248,15 +262,14 @@ int fft3_plan_create_ex(fft3_plan *out, int n0, int n1, int n2, int batch, int d
     ((decomp) | (((radix_order) + 1) << 2) | ((tile_code) << 5) | ((items_code) << 8))
 /* decomp: 1 = slab-pencil, 2 = pencil-pencil-pencil, 3 = the segmented passes
  * (whole batch: every code must ask for it); tile_code: columns per
- * tile of the strided phases, 1 -> 4, 2 -> 8, 3 -> 16, 4 -> 32; items_code:
- * slabs (slab-pencil) or rows (pencil) per first-phase work item, k -> 2^(k-1).
- * FFT3_TUNE_SLABZ or'ed into every code: the slab-by-slab executor, one
- * persistent launch in which a work item is one n0 x n1 slab of a problem
- * (x and y lines in shared memory, one read and one write) or a tile of its z
- * lines (read through L2 once the problem's slabs are done), with the
- * compile-time line kernels of the segmented passes (lengths 8 .. 128 of
- * their list; FFT3_ERR_UNSUPPORTED_SIZE otherwise). */
-#define FFT3_TUNE_SLABZ (1 << 11)
+ * tile of the strided phases, 1 -> 4, 2 -> 8, 3 -> 16, 4 -> 32; items_code
+ * (4 bits, 0..15): slabs (slab-pencil) or rows (pencil) per first-phase work
+ * item, k -> 2^(k-1), or with decomp 3 the segmented passes in one
+ * cooperative launch in 2^(k-1) waves (k <= 11).
+ * FFT3_TUNE_SLABZ or'ed into every code: the slab executor whatever the
+ * batch size (FFT3_ERR_UNSUPPORTED_SIZE when a length is not one of its
+ * lengths); the other fields are ignored. */
+#define FFT3_TUNE_SLABZ (1 << 12)
 int fft3_plan_create_many(fft3_plan *out, int count, const int *dims, const int64_t *offsets,
                           int dtype, int decomposition, int direction, const int *tuning);
 
@@ -460,8 +473,9 @@ int fft3_autotune(int n0, int n1, int n2, int batch, int dtype, int direction, i
  * to every problem whose shared-buffer need stays within the default
  * buffers; then, for three size classes (thirds of the batch by problem
  * volume) in turn, the code that makes the whole batch fastest (kept when it
- * gains at least 1%); finally the segmented passes (code 3 for every problem),
- * taken when faster.  Writes the assignment to tuning_out.  The batch is
+ * gains at least 1%); finally the segmented passes (code 3 for every problem)
+ * and the slab executor (FFT3_TUNE_SLABZ on every code), each taken when
+ * faster.  Writes the assignment to tuning_out.  The batch is
  * timed as a whole because the executor's buffers, blocks per SM and item
  * order depend on all its problems (per-shape timings in isolation chose
  * codes that made the mixed batch slower).  `offsets` and `max_per_class`

@@ -274,8 +274,17 @@ int fft3_autotune_many(int count, const int *dims, const int64_t *offsets, int d
     float ts = 0.f;
     if ((rc = time_assignment(seg, &ts)))
         return rc;
-    if (ts < bt)
+    if (ts < bt) {
+        bt = ts;
         best = seg;
+    }
+    // 4) the slab-by-slab executor (FFT3_TUNE_SLABZ on every problem;
+    // infeasible when a line length has no compiled variant)
+    std::vector<int> slabz(count, FFT3_TUNE(1, 0, 0, 0) | FFT3_TUNE_SLABZ);
+    if ((rc = time_assignment(slabz, &ts)))
+        return rc;
+    if (ts < bt)
+        best = slabz;
     for (int i = 0; i < count; ++i)
         tuning_out[i] = best[i];
     return FFT3_OK;

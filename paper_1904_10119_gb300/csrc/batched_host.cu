@@ -458,6 +458,32 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
     int slabz = tuning ? 1 : 0;
     for (int i = 0; slabz && i < count; ++i)
         slabz = (tuning[i] & FFT3_TUNE_SLABZ) ? 1 : 0;
+    // FFT3_AUTO without tuning codes takes it from kSegMinElems values on
+    // when every length has its line variants and every slab fits the room of
+    // an item (three blocks per SM); otherwise the segmented rule below
+    if (!tuning && decomposition == FFT3_AUTO) {
+#define FFT3_SZ_LEN(N, R, L) N,
+        const int wl[] = {FFT3_SLABZ_WARP_PLANS(FFT3_SZ_LEN)};
+#undef FFT3_SZ_LEN
+        auto has = [&](int n, bool z) {
+            bool f = false;
+            if (z)
+                for (const SlabZPlan &q : kSlabZPlans)
+                    f = f || q.n == n;
+            else
+                for (int m : wl)
+                    f = f || m == n;
+            return f;
+        };
+        bool fit = true;
+        int64_t values = 0;
+        for (int i = 0; fit && i < count; ++i) {
+            const int n0 = dims[3 * i], n1 = dims[3 * i + 1], n2 = dims[3 * i + 2];
+            fit = has(n0, false) && has(n1, false) && has(n2, true) && n1 * (n0 | 1) <= kSlabzRoom;
+            values += (int64_t)n0 * n1 * n2;
+        }
+        slabz = fit && values >= kSegMinElems ? 1 : 0;
+    }
     b->slabz = slabz;
     for (int i = 0; i < count; ++i) {
         const int n0 = dims[3 * i], n1 = dims[3 * i + 1], n2 = dims[3 * i + 2];
@@ -575,12 +601,12 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
             return fail(FFT3_ERR_UNSUPPORTED_SIZE, "the segmented passes have no compiled plan for a line length "
                                                    "of this batch");
         }
-        b->seg = ok && (all3 || (decomposition == FFT3_AUTO && !tuning && values >= kSegMinElems)) ? 1 : 0;
+        b->seg = ok && !slabz && (all3 || (decomposition == FFT3_AUTO && !tuning && values >= kSegMinElems)) ? 1 : 0;
         // decomposition field 3 with the items field k >= 1 on every code: the
         // segmented passes in one cooperative launch, in 2^(k-1) waves
-        int items = all3 ? (tuning[0] >> 8) : 0;
+        int items = all3 ? (tuning[0] >> 8) & 15 : 0;
         for (int i = 0; all3 && i < count; ++i)
-            items = (tuning[i] >> 8) == items ? items : -1;
+            items = ((tuning[i] >> 8) & 15) == items ? items : -1;
         if (b->seg && items > 0) {
             if (items > 11)
                 return fail(FFT3_ERR_INVALID_ARG, "at most 1024 waves");

@@ -320,7 +320,7 @@ def fft3_autotune_many(dims, direction=FFT3_FORWARD, reps: int = 3, max_per_clas
     return [int(t[i]) for i in range(count)]
 
 
-FFT3_TUNE_SLABZ = 1 << 11  # or'ed into every tuning code: the slab-by-slab executor
+FFT3_TUNE_SLABZ = 1 << 12  # or'ed into every tuning code: the slab-by-slab executor
 
 
 def tune_code(decomp: int, radix_order: int = 0, tile_code: int = 0, items_code: int = 0) -> int:

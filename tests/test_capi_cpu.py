@@ -379,14 +379,20 @@ def _batch_layout(dims):
 
 def test_schedule_many_modes_and_segmented_tables():
     """Host-only batched planning: FFT3_AUTO without tuning codes takes the
-    segmented passes for a large batch of compiled lengths (one launch per
-    dimension and line length, tiles = sum over its problems of ceil(lines /
-    lines per tile)) and the executor for a small one, for explicit
-    decompositions or for zero codes; codes of 3 ask for the segmented passes."""
+    slab executor (one launch) for a large batch whose lengths have its line
+    variants and whose slabs fit an item's room, the segmented passes when a
+    slab does not fit, and the executor for a small batch, for explicit
+    decompositions or for zero codes; codes of 3 ask for the segmented passes
+    (one launch per dimension and line length, tiles = sum over its problems
+    of ceil(lines / lines per tile))."""
     from paper_1904_10119_gb300 import synth
     dims = synth.batched_dims(512, 7)
     offs = _batch_layout(dims)
     d = fft3.fft3_plan_schedule_many(dims, offs)
+    assert d["mode"] == "slab_executor" and d["kernel_launches"] == 1 and d["problems"] == 512
+    big = np.vstack([dims, [[128, 128, 8]]])
+    assert fft3.fft3_plan_schedule_many(big, _batch_layout(big))["mode"] == "segmented"
+    d = fft3.fft3_plan_schedule_many(dims, offs, tuning=[3] * len(dims))
     assert d["mode"] == "segmented" and d["problems"] == 512
     launches = d["segmented_launches"]
     assert d["kernel_launches"] == len(launches) == sum(len(set(dims[:, k])) for k in range(3))

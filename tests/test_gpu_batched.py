@@ -203,10 +203,12 @@ def test_segmented_warp_shuffle_lines(cand, gap, direction):
         _check_problem(x, got, int(off), d, direction)
 
 
-def test_segmented_auto_choice_replay_and_refusal():
-    """FFT3_AUTO picks the segmented passes for a large batch of compiled
-    lengths (and the executor for a small one); replay on new buffers; a
-    line length without a compiled plan is refused when the codes ask for it."""
+def test_auto_choice_replay_and_refusal():
+    """FFT3_AUTO picks the slab executor for a large batch whose lengths all
+    have its line variants and whose slabs fit an item's room, the segmented
+    passes when a slab does not fit (128 x 128), and the executor for a small
+    batch; replay on new buffers gives the same bits; a line length without a
+    compiled plan is refused when the codes ask for the segmented passes."""
     dims = synth.batched_dims(200, 4)
     offs, total = _layout(dims)
     x = synth.uniform_c64(total, 8)
@@ -214,7 +216,8 @@ def test_segmented_auto_choice_replay_and_refusal():
     o1, o2 = torch.empty_like(xd), torch.empty_like(xd)
     h = fft3.fft3_plan_create_many(dims, offs)
     try:
-        assert fft3.fft3_plan_describe(h)["mode"] == "segmented"
+        desc = fft3.fft3_plan_describe(h)
+        assert desc["mode"] == "slab_executor" and desc["kernel_launches"] == 1
         fft3.fft3_plan_execute(h, xd.data_ptr(), o1.data_ptr(), 0)
         fft3.fft3_plan_execute(h, xd.data_ptr(), o2.data_ptr(), 0)
         torch.cuda.synchronize()
@@ -225,6 +228,22 @@ def test_segmented_auto_choice_replay_and_refusal():
     g = o1.cpu().numpy()
     for off, d in list(zip(offs, dims))[::7]:
         _check_problem(x, g, int(off), d, fft3.FFT3_FORWARD)
+    big = np.vstack([dims, [[128, 128, 8]]])
+    bo, btotal = _layout(big)
+    xb = synth.uniform_c64(btotal, 9)
+    xbd = torch.from_numpy(xb).cuda()
+    ob = torch.empty_like(xbd)
+    h = fft3.fft3_plan_create_many(big, bo)
+    try:
+        assert fft3.fft3_plan_describe(h)["mode"] == "segmented"
+        fft3.fft3_plan_execute(h, xbd.data_ptr(), ob.data_ptr(), 0)
+        torch.cuda.synchronize()
+        assert fft3.fft3_plan_check(h) == 0
+    finally:
+        fft3.fft3_plan_destroy(h)
+    gb = ob.cpu().numpy()
+    for off, d in list(zip(bo, big))[::29] + [(bo[-1], big[-1])]:
+        _check_problem(xb, gb, int(off), d, fft3.FFT3_FORWARD)
     small = synth.batched_dims(6, 4)
     so, _ = _layout(small)
     h = fft3.fft3_plan_create_many(small, so)
@@ -275,3 +294,22 @@ def test_one_launch_segmented_4096_cubes_sampled_and_parseval():
         N = int(np.prod(d))
         sx, sg = x2[off:off + N].sum(), g2[off:off + N].sum()
         assert abs(sg - N * sx) <= 1e-5 * N * sx
+
+
+def test_autotune_many_assignment_is_exact():
+    """fft3_autotune_many times the whole batch under the default codes, every
+    candidate code, per-size-class codes, the segmented passes and the slab
+    executor, and returns one code per problem; the plan built from that
+    assignment computes every problem to the oracle's tolerance, both
+    directions."""
+    dims = synth.batched_dims(12, 5, choices=(16, 24, 32))
+    codes = fft3.fft3_autotune_many(dims, reps=1)
+    assert len(codes) == len(dims)
+    slabz = [c & fft3.FFT3_TUNE_SLABZ for c in codes]
+    seg = [(c & 3) == 3 for c in codes]
+    assert len(set(slabz)) == 1 and (not any(seg) or all(seg))  # whole-batch modes are all or nothing
+    offs, total = _layout(dims, gap=1)
+    for direction in (fft3.FFT3_FORWARD, fft3.FFT3_INVERSE):
+        x, got, desc = _run(dims, offs, total, direction=direction, tuning=codes, seed=4)
+        for off, d in zip(offs, dims):
+            _check_problem(x, got, int(off), d, direction)
