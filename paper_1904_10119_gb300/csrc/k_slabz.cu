@@ -205,8 +205,25 @@ __global__ void __launch_bounds__(kSzThreads, 3) k_slabz(SlabZArgs z)
         const int q = s_next[slot];
         if (q >= a.nitems)
             break;
-        if (threadIdx.x == 0) // the next item, claimed while this one runs; the other slot was
-            s_next[slot ^ 1] = atomicAdd(a.counters, 1); // read before the barrier above
+        if (threadIdx.x == 0) { // the next item, claimed while this one runs; the other slot was
+            const int qn = atomicAdd(a.counters, 1); // read before the barrier above
+            s_next[slot ^ 1] = qn;
+            if (qn < a.nitems && a.items[qn].phase == 0) {
+                // a slab item: its input (contiguous slabs) is fetched into L2
+                // now, so its row loads find it there; only the 16-byte-aligned
+                // interior of the range, in pieces of at most 32 KB
+                const BatchItem nt = a.items[qn];
+                const BatchCube &nc = a.cubes[nt.cube];
+                const int s0 = nt.index * nc.spi, ns = min(nc.n2, s0 + nc.spi) - s0;
+                const float2 *p = a.in + nc.off + (int64_t)s0 * nc.n0 * nc.n1;
+                uintptr_t b = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+                const uintptr_t e = (uintptr_t)(p + (int64_t)ns * nc.n0 * nc.n1) & ~(uintptr_t)15;
+                for (; b < e; b += 32768) {
+                    const unsigned len = (unsigned)min((uintptr_t)32768, e - b);
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"(len) : "memory");
+                }
+            }
+        }
         const BatchItem it = a.items[q];
         const BatchCube &cb = a.cubes[it.cube];
         const int n0 = cb.n0, n1 = cb.n1, n2 = cb.n2;
