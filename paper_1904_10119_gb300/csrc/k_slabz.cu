@@ -3,8 +3,9 @@
 //   slab items: a few n0 x n1 slabs of a problem, stacked in shared memory:
 //               their x lines (rows) are read from global memory, transformed
 //               and written into the buffer, then their y lines (columns) are
-//               transformed from the buffer and written to global memory: one
-//               read and one write per value for the 2D stage;
+//               transformed in place in the buffer, and the stack is copied to
+//               global memory with contiguous stores: one read and one write
+//               per value for the 2D stage;
 //   z items:    tiles of adjacent columns of a problem's n0*n1 plane, their z
 //               lines read through L2 (the slabs were written earlier in the
 //               launch), transformed and written back in place.
@@ -92,12 +93,10 @@ __device__ __noinline__ void sz_rows_warp(const float2 *src, float2 *A, int pitc
 // Columns of the stacked slabs (y lines) in the registers of L/2 lanes
 // (warp_fft.cuh): the lanes of a column read different rows of the buffer
 // (pitch odd: conflict free), adjacent lane groups take adjacent columns, and
-// each group stores its column's outputs straight to the output slabs in
-// global memory (element k of column (cs, c) at dst[(cs N + k) w + c]).  A
-// group owns its column: no barrier.
+// each group writes its column's outputs back in place (a group owns its
+// column: no barrier).
 template <int N, int R, int L>
-__device__ __noinline__ void sz_cols_warp(const float2 *A, int pitch, int cols, int w, int slab_stride, float2 *dst,
-                                          const float2 *tw_w, bool conj)
+__device__ __noinline__ void sz_cols_warp(float2 *A, int pitch, int cols, int w, int slab_stride, const float2 *tw_w)
 {
     using WL = WarpLine<N, R, L>;
     constexpr int CPR = kSzThreads / WL::W; // columns per round
@@ -108,10 +107,37 @@ __device__ __noinline__ void sz_cols_warp(const float2 *A, int pitch, int cols, 
         const int c = c0 + l;
         const bool valid = c < cols;
         const int cs = valid ? c / w : 0, cc = valid ? c - cs * w : 0;
+        float2 *p = A + cs * slab_stride + cc;
         float2 v[2][R];
-        WL::load_strided(v, A + cs * slab_stride + cc, pitch, u, valid, false);
+        WL::load_strided(v, p, pitch, u, valid, false);
         WL::run(v, tw, u);
-        WL::store_strided(v, dst + (int64_t)cs * N * w + cc, w, u, valid, conj);
+        WL::store_strided(v, p, pitch, u, valid, false);
+    }
+}
+
+// The stacked slabs (rows of n0 values, n0 even, `pitch` apart) to dst, where
+// they are contiguous: each thread moves pairs of values of a row, 16-byte
+// stores when dst is 16-byte aligned; conjugated for the inverse.
+__device__ __noinline__ void sz_copy_out(const float2 *A, int pitch, int n0, int rows, float2 *dst, bool conj)
+{
+    const int half = n0 >> 1, rpp = kSzThreads / half; // rows per pass
+    const int rr = threadIdx.x / half, x = 2 * (threadIdx.x - rr * half);
+    if (rr >= rpp)
+        return;
+    const bool v4 = (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+    for (int r = rr; r < rows; r += rpp) {
+        float2 a = A[r * pitch + x], b = A[r * pitch + x + 1];
+        if (conj) {
+            a = cconj(a);
+            b = cconj(b);
+        }
+        float2 *q = dst + (int64_t)r * n0 + x;
+        if (v4) {
+            *reinterpret_cast<float4 *>(q) = make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            q[0] = a;
+            q[1] = b;
+        }
     }
 }
 
@@ -152,16 +178,15 @@ __device__ __forceinline__ void sz_run_rows_warp(int n0, const float2 *src, floa
 #undef FFT3_SZ_WROW
 }
 
-__device__ __forceinline__ void sz_run_cols_warp(int n1, const float2 *A, int pitch, int cols, int w,
-                                                 int slab_stride, float2 *dst, const float2 *tw, const int *off,
-                                                 bool conj)
+__device__ __forceinline__ void sz_run_cols_warp(int n1, float2 *A, int pitch, int cols, int w, int slab_stride,
+                                                 const float2 *tw, const int *off)
 {
     int k = 0;
-#define FFT3_SZ_WCOL(N, R, L)                                                                 \
-    if (n1 == N) {                                                                            \
-        sz_cols_warp<N, R, L>(A, pitch, cols, w, slab_stride, dst, tw + off[k], conj);        \
-        return;                                                                               \
-    }                                                                                         \
+#define FFT3_SZ_WCOL(N, R, L)                                                        \
+    if (n1 == N) {                                                                   \
+        sz_cols_warp<N, R, L>(A, pitch, cols, w, slab_stride, tw + off[k]);          \
+        return;                                                                      \
+    }                                                                                \
     ++k;
     FFT3_SLABZ_WARP_PLANS(FFT3_SZ_WCOL)
 #undef FFT3_SZ_WCOL
@@ -236,7 +261,9 @@ __global__ void __launch_bounds__(kSzThreads, 3) k_slabz(SlabZArgs z)
             float2 *dst = a.out + cb.off + (int64_t)s0 * n0 * n1;
             sz_run_rows_warp(n0, src, A, P, n1 * ns, tw, z.tw_w, conj);
             __syncthreads();
-            sz_run_cols_warp(n1, A, P, n0 * ns, n0, n1 * P, dst, tw, z.tw_w, conj);
+            sz_run_cols_warp(n1, A, P, n0 * ns, n0, n1 * P, tw, z.tw_w);
+            __syncthreads();
+            sz_copy_out(A, P, n0, n1 * ns, dst, conj);
         } else {
             if (threadIdx.x == 0) {
                 const int *done = a.counters + 1 + 3 * it.cube;
