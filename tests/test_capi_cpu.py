@@ -544,6 +544,54 @@ def test_tcgen05_radix32_schedule():
     assert s["passes"][1]["kind"] == "line_strided_r32_tc" and s["passes"][1]["tiles"] == 2 * 3
 
 
+def _slabz_plan_list(name):
+    """Rows X(...) of a macro list in seg_plans.h, as tuples of ints."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(fft3.LIB_PATH), "csrc", "seg_plans.h")
+    txt = open(path).read()
+    body = txt[txt.index(f"#define {name}(X)"):]
+    body = body[:body.index("\n\n")]
+    return [tuple(int(v) for v in m.split(",")) for m in re.findall(r"X\(([^)]*)\)", body)]
+
+
+def test_schedule_many_slab_executor_items_and_refusals():
+    """Host-only planning of the slab executor: items = sum over problems of
+    the slab stacks (as many n0 x n1 slabs as fit about 8 Ki values and the
+    room of one 96 x 97 slab) plus the z-tile groups (tiles of the z plan's
+    width; about 8 Ki values, whole rounds of tiles per group); one 74.5 KB
+    stack per block; explicit FFT3_TUNE_SLABZ codes take it for any batch
+    size, and refuse a length outside its lists; codes without the flag on
+    every problem do not take it."""
+    from paper_1904_10119_gb300 import synth
+    zplans = {n: (T, lpt) for n, T, lpt, *_ in _slabz_plan_list("FFT3_SLABZ_Z_PLANS")}
+    rows = {n for n, _, _ in _slabz_plan_list("FFT3_SLABZ_WARP_PLANS")}
+    assert set(zplans) == rows == {8, 16, 24, 32, 40, 48, 64, 80, 96, 128}
+    dims = synth.batched_dims(4096, 7)
+    offs = _batch_layout(dims)
+    d = fft3.fft3_plan_schedule_many(dims, offs)
+    assert d["mode"] == "slab_executor" and d["kernel_launches"] == 1
+    items = 0
+    for n0, n1, n2 in (tuple(int(v) for v in r) for r in dims):
+        spi = max(1, min(n2, 8192 // (n0 * n1), 96 * 97 // (n1 * (n0 | 1))))
+        T, lpt = zplans[n2]
+        zg = max(1, 256 // (T * lpt))
+        zpi = max(zg, 8192 // (lpt * n2) // zg * zg)
+        items += -(-n2 // spi) + -(-(-(-(n0 * n1) // lpt)) // zpi)
+    assert d["items"] == items
+    assert d["slab_executor_smem"] == 96 * 97 * 8  # three blocks per SM
+    small = np.array([[16, 24, 32], [48, 16, 40], [96, 8, 64]])
+    so = _batch_layout(small)
+    flag = fft3.FFT3_TUNE_SLABZ
+    assert fft3.fft3_plan_schedule_many(small, so, tuning=[flag] * 3)["mode"] == "slab_executor"
+    assert fft3.fft3_plan_schedule_many(small, so, tuning=[flag, flag, 0])["mode"] != "slab_executor"
+    assert fft3.fft3_plan_schedule_many(small, so)["mode"] == "executor"  # below 4 Mi values
+    for bad in ([[30, 16, 16]], [[16, 30, 16]], [[16, 16, 30]]):
+        with pytest.raises(fft3.Fft3Error) as e:
+            fft3.fft3_plan_schedule_many(bad, [0], tuning=[flag])
+        assert e.value.code == -2
+
+
 def test_schedule_many_one_launch_segmented_steps():
     """Tuning codes 3 | (k << 8): the segmented passes in one cooperative launch
     in 2^(k-1) waves of problems.  One wave: three steps (x, y, z lines); W
