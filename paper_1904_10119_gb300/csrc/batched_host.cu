@@ -618,11 +618,16 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
                 b->tuning[i] = 3 | (tuning ? tuning[i] & (7 << 2) : 0) | (b->seg1 ? items << 8 : 0);
     }
     b->buf_elems = (bufmax + 31) / 32 * 32;
-    // a third buffer stages the next item's first tile when it still fits
-    b->prefetch = 3 * b->buf_elems * (int)sizeof(float2) <= 200 * 1024 ? 1 : 0;
-    b->smem = (2 + b->prefetch) * b->buf_elems * (int)sizeof(float2);
-    if (b->smem > 227 * 1024) {
-        return fail(FFT3_ERR_UNSUPPORTED_SIZE, "a work item of this batch needs more shared memory than a block has");
+    if (!slabz) {
+        // the item executor's two buffers, and a third that stages the next
+        // item's first tile when it still fits (the slab executor has one
+        // stack, sized below)
+        b->prefetch = 3 * b->buf_elems * (int)sizeof(float2) <= 200 * 1024 ? 1 : 0;
+        b->smem = (2 + b->prefetch) * b->buf_elems * (int)sizeof(float2);
+        if (b->smem > 227 * 1024) {
+            return fail(FFT3_ERR_UNSUPPORTED_SIZE,
+                        "a work item of this batch needs more shared memory than a block has");
+        }
     }
     // line plans and their twiddle tables
     std::vector<int64_t> m;
@@ -782,6 +787,8 @@ static int batch_plan_host(BatchState *b, int count, const int *dims, const int6
         b->sa_tw_len = (int)local;
         tw_total += local;
         b->sz_smem = slabz_smem_bytes((bufmax + 31) / 32 * 32);
+        if (b->sz_smem > 227 * 1024)
+            return fail(FFT3_ERR_UNSUPPORTED_SIZE, "a slab of this batch needs more shared memory than a block has");
     }
     if (b->seg1) {
         // waves: consecutive problems of about equal volume
@@ -960,11 +967,13 @@ extern "C" int fft3_plan_create_many(fft3_plan *out, int count, const int *dims,
         if (e != cudaSuccess)
             return bail(fail(FFT3_ERR_CUDA, std::string("twiddle generation: ") + cudaGetErrorString(e)));
     }
-    rc = prepare_func((const void *)&k_batched, b->smem);
-    if (!rc)
-        rc = occupancy_grid((const void *)&k_batched, b->threads, b->smem, 0, dev, &b->grid);
-    if (rc)
-        return bail(rc);
+    if (!b->slabz) {
+        rc = prepare_func((const void *)&k_batched, b->smem);
+        if (!rc)
+            rc = occupancy_grid((const void *)&k_batched, b->threads, b->smem, 0, dev, &b->grid);
+        if (rc)
+            return bail(rc);
+    }
     if (b->seg) {
         if (cudaMalloc(&b->d_seg_list, std::max<size_t>(1, seg_list.size()) * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&b->d_seg_tcube, std::max<size_t>(1, seg_tcube.size()) * sizeof(int)) != cudaSuccess ||

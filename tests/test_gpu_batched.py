@@ -313,3 +313,17 @@ def test_autotune_many_assignment_is_exact():
         x, got, desc = _run(dims, offs, total, direction=direction, tuning=codes, seed=4)
         for off, d in zip(offs, dims):
             _check_problem(x, got, int(off), d, direction)
+
+
+@pytest.mark.parametrize("direction", [fft3.FFT3_FORWARD, fft3.FFT3_INVERSE])
+def test_slab_executor_slab_larger_than_the_room(direction):
+    """Explicit FFT3_TUNE_SLABZ codes on a batch with a 128 x 128 slab (more
+    than the 96 x 97 values FFT3_AUTO allows): one slab per item, a larger
+    stack per block (fewer blocks per SM), every problem against the oracle."""
+    dims = np.array([[128, 128, 8], [128, 96, 16], [96, 128, 24], [16, 16, 16], [40, 24, 128]])
+    offs, total = _layout(dims, gap=3)
+    code = fft3.tune_code(1) | fft3.FFT3_TUNE_SLABZ
+    x, got, desc = _run(dims, offs, total, direction=direction, tuning=[code] * len(dims), seed=6)
+    assert desc["mode"] == "slab_executor" and desc["slab_executor_smem"] == 128 * 129 * 8
+    for off, d in zip(offs, dims):
+        _check_problem(x, got, int(off), d, direction)
