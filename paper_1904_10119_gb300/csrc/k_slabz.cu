@@ -10,8 +10,8 @@
 //               lines read through L2 (the slabs were written earlier in the
 //               launch), transformed and written back in place.
 // Rows and columns are warp-shuffle line transforms (warp_fft.cuh; a line in
-// the registers of a few lanes, no barrier), the z tiles the compile-time
-// Stockham engines of FFT3_SLABZ_Z_PLANS (seg_plans.h).
+// the registers of a few lanes, no barrier within a transform), the z tiles
+// the compile-time Stockham engines of FFT3_SLABZ_Z_PLANS (seg_plans.h).
 // Work items come from a ticket counter in the order the host gives them
 // (problems in groups, the z items of a group after the slab items of the
 // next group, so a problem's slabs are still in L2 when its z items read
@@ -19,7 +19,9 @@
 // finished.  Those slab items hold smaller tickets, so they were claimed by
 // blocks that are already running and never wait: every wait ends.  Each wait
 // is still bounded (about two seconds of clock cycles); on expiry the kernel
-// records kErrWaitTimeout and carries on.
+// records kErrWaitTimeout and carries on.  A block claims its next ticket
+// while it runs the current item and, for a slab item, prefetches that item's
+// input into L2.
 #include "batched.h"
 #include "pass_kernels.cuh"
 #include "seg_plans.h"
